@@ -1,0 +1,340 @@
+/*
+ * Plain FP64 reference for the ray-based line formal solution of Magritte
+ * (arXiv 2411.03040).  TEST INFRASTRUCTURE ONLY: nothing in the product path
+ * links, loads or calls this file; only the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark do.
+ *
+ * Deliberately slow and literal: every (origin, ray pair, frequency bin, line)
+ * rebuilds its full ray, evaluates the opacity at every point in the paper's
+ * own frequency variables, and solves the second-order (Feautrier) system with
+ * the textbook Rybicki-Hummer elimination.  OpenMP runs over origin points only.
+ * Built with -ffp-contract=off so that no multiply-add is fused: the ray-walk
+ * predicates must round exactly as written.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_C     299792458.0
+#define OR_KB    1.380649e-23
+#define OR_H     6.62607015e-34
+#define OR_SQRTPI 1.7724538509055160273
+
+/* ------------------------------------------------------------------------ */
+/* Ray walk through the neighbour graph.                                     */
+/*                                                                           */
+/* The paper defers the tracer to its earlier Magritte papers (Sec. 2, 3.4). */
+/* Rule used here: from the current point c (initially the origin o), the    */
+/* candidates are the neighbours m of c whose projection                     */
+/*   Z_m = (x_m - x_o) . n                                                   */
+/* exceeds Z_c; among them take the one with the smallest squared distance   */
+/* to the ray line, |(x_m - x_o) - Z_m n|^2, ties to the smaller index.  The */
+/* walk ends on a boundary point (kept as the last ray point) or when no     */
+/* candidate exists (a stall, except for a boundary origin with no           */
+/* candidate, whose half-ray is simply empty).                               */
+/* ------------------------------------------------------------------------ */
+static int64_t walk(int64_t o, const double *n, const double *pos, const int64_t *off,
+                    const int32_t *nb, const uint8_t *bnd, int64_t N,
+                    int32_t *out, int *stalled)
+{
+    int64_t c = o, len = 0;
+    double Zc = 0.0;
+    const double xo = pos[3 * o], yo = pos[3 * o + 1], zo = pos[3 * o + 2];
+    *stalled = 0;
+    for (;;) {
+        int64_t best = -1;
+        double bestd = 0.0, bestZ = 0.0;
+        for (int64_t k = off[c]; k < off[c + 1]; ++k) {
+            int64_t m = nb[k];
+            double dx = pos[3 * m] - xo;
+            double dy = pos[3 * m + 1] - yo;
+            double dz = pos[3 * m + 2] - zo;
+            double Z = dx * n[0] + dy * n[1] + dz * n[2];
+            if (!(Z > Zc)) continue;
+            double px = dx - Z * n[0];
+            double py = dy - Z * n[1];
+            double pz = dz - Z * n[2];
+            double d2 = px * px + py * py + pz * pz;
+            if (best < 0 || d2 < bestd || (d2 == bestd && m < best)) {
+                best = m;
+                bestd = d2;
+                bestZ = Z;
+            }
+        }
+        if (best < 0) {
+            if (!(c == o && bnd[o])) *stalled = 1;
+            return len;
+        }
+        if (out) out[len] = (int32_t)best;
+        ++len;
+        c = best;
+        Zc = bestZ;
+        if (bnd[best] || len > N) return len;
+    }
+}
+
+/* Half-ray lengths for every (direction r, origin o): len[r*N + o]. */
+void oracle_trace_lengths(int64_t N, const double *pos, const int64_t *off, const int32_t *nb,
+                          const uint8_t *bnd, int32_t R, const double *dirs,
+                          int64_t *len, uint8_t *stall)
+{
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < (int64_t)R * N; ++t) {
+        int64_t r = t / N, o = t % N;
+        int st;
+        len[t] = walk(o, dirs + 3 * r, pos, off, nb, bnd, N, NULL, &st);
+        stall[t] = (uint8_t)st;
+    }
+}
+
+/* Fill the point lists; ray_off has R*N+1 entries (exclusive prefix of lengths). */
+void oracle_trace_fill(int64_t N, const double *pos, const int64_t *off, const int32_t *nb,
+                       const uint8_t *bnd, int32_t R, const double *dirs,
+                       const int64_t *ray_off, int32_t *idx)
+{
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < (int64_t)R * N; ++t) {
+        int64_t r = t / N, o = t % N;
+        int st;
+        walk(o, dirs + 3 * r, pos, off, nb, bnd, N, idx + ray_off[t], &st);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Planck function B_nu(T) in W m^-2 Hz^-1 sr^-1.                            */
+/* ------------------------------------------------------------------------ */
+double oracle_planck(double nu, double T)
+{
+    if (T <= 0.0) return 0.0;
+    return 2.0 * OR_H * nu * nu * nu / (OR_C * OR_C) / expm1(OR_H * nu / (OR_KB * T));
+}
+
+/* Gaussian line profile (Sec. 4.3, eq. gaussian) at offset (nu - nu_ij). */
+static double profile(double offset, double dnu)
+{
+    double t = offset / dnu;
+    return exp(-t * t) / (dnu * OR_SQRTPI);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Optical depth of one segment between points 0 and 1 (Sec. 4.3).           */
+/*   dx      : Euclidean length of the segment                                */
+/*   chi0/1  : chi^{ij} at the endpoints (frequency-integrated line opacity)  */
+/*   dnu0/1  : line widths at the endpoints (eq. line width)                  */
+/*   dnubar  : width from the segment-averaged temperature and turbulence     */
+/*   off0/1  : comoving-frame offset from line centre, nu_cmf - nu_ij, of the */
+/*             frequency bin at each endpoint                                 */
+/*   thr     : switch threshold on |Doppler shift| / dnubar (0.35 in Magritte)*/
+/* Below the threshold: trapezoidal rule (eq. trapezoidal rule) of the full   */
+/* integrand chi^{ij} phi(nu) evaluated at the endpoints.  At or above it: the */
+/* semi-analytic form (eq. semi-analytic): the average of chi^{ij} times the   */
+/* exact integral of the Gaussian, (erf(t1) - erf(t0)) / (2 Delta nu), with    */
+/* t = offset / dnubar; same-sign tails use erfc to avoid cancellation.       */
+/* ------------------------------------------------------------------------ */
+double oracle_segment_dtau(double dx, double chi0, double chi1, double dnu0, double dnu1,
+                           double dnubar, double off0, double off1, double thr)
+{
+    double shift = off1 - off0;
+    if (fabs(shift) < thr * dnubar) {
+        return dx * 0.5 * (chi0 * profile(off0, dnu0) + chi1 * profile(off1, dnu1));
+    }
+    double t0 = off0 / dnubar, t1 = off1 / dnubar, E;
+    if (t0 > 0.0 && t1 > 0.0)
+        E = erfc(t0) - erfc(t1);
+    else if (t0 < 0.0 && t1 < 0.0)
+        E = erfc(-t1) - erfc(-t0);
+    else
+        E = erf(t1) - erf(t0);
+    return dx * 0.5 * (chi0 + chi1) * E / (2.0 * shift);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Second-order (Feautrier) two-point system on one ray, solved at point io. */
+/*                                                                           */
+/* Points d = 0..D-1, dtau[d] = optical depth of segment (d, d+1).  Interior */
+/* rows: -A_d u_{d-1} + B_d u_d - C_d u_{d+1} = S_d with                     */
+/*   A_d = 2/(a(a+b)), C_d = 2/(b(a+b)), B_d = 1 + A_d + C_d,                */
+/* a = dtau[d-1], b = dtau[d].  End rows (Auer 1967 second-order boundary):  */
+/*   (1 + 2/t + 2/t^2) u_0 - (2/t^2) u_1 = S_0 + (2/t) I_left,               */
+/* mirrored at D-1 with I_right, t the optical depth of the end segment.     */
+/* Elimination: Rybicki & Hummer (1991) F-form from both ends,               */
+/*   F_d = (1 + A_d F_{d-1}/(1+F_{d-1})) / C_d,                              */
+/*   z_d = (S_d + A_d z_{d-1}) / (C_d (1 + F_d)),                            */
+/* and the mirrored G, w from the right.  At io:                             */
+/*   u = (S + A z_{io-1} + C w_{io+1}) / den,  L = 1/den (the diagonal of    */
+/*   the inverse matrix), den = B - A/(1+F) - C/(1+G).                       */
+/* D == 1: no system; u = background, L = 0.                                 */
+/* ------------------------------------------------------------------------ */
+void oracle_feautrier_at(int64_t D, const double *dtau, const double *S,
+                         double I_left, double I_right, int64_t io,
+                         double *u_out, double *L_out)
+{
+    if (D <= 1) {
+        *u_out = 0.5 * (I_left + I_right);
+        *L_out = 0.0;
+        return;
+    }
+    double F = 0.0, z = 0.0, G = 0.0, w = 0.0;
+    /* forward sweep over rows 0 .. io-1 */
+    for (int64_t d = 0; d < io; ++d) {
+        if (d == 0) {
+            double t = dtau[0];
+            double B0 = 1.0 + 2.0 / t + 2.0 / (t * t);
+            F = (1.0 + 2.0 / t) * t * t / 2.0;
+            z = (S[0] + 2.0 * I_left / t) / B0;
+        } else {
+            double a = dtau[d - 1], b = dtau[d];
+            double A = 2.0 / (a * (a + b)), C = 2.0 / (b * (a + b));
+            double Fn = (1.0 + A * F / (1.0 + F)) / C;
+            z = (S[d] + A * z) / (C * (1.0 + Fn));
+            F = Fn;
+        }
+    }
+    /* backward sweep over rows D-1 .. io+1 */
+    for (int64_t d = D - 1; d > io; --d) {
+        if (d == D - 1) {
+            double t = dtau[D - 2];
+            double B1 = 1.0 + 2.0 / t + 2.0 / (t * t);
+            G = (1.0 + 2.0 / t) * t * t / 2.0;
+            w = (S[D - 1] + 2.0 * I_right / t) / B1;
+        } else {
+            double a = dtau[d - 1], b = dtau[d];
+            double A = 2.0 / (a * (a + b)), C = 2.0 / (b * (a + b));
+            double Gn = (1.0 + C * G / (1.0 + G)) / A;
+            w = (S[d] + C * w) / (A * (1.0 + Gn));
+            G = Gn;
+        }
+    }
+    double den, num;
+    if (io == 0) {
+        double t = dtau[0];
+        double C = 2.0 / (t * t);
+        den = 1.0 + 2.0 / t + C * G / (1.0 + G);
+        num = S[0] + 2.0 * I_left / t + C * w;
+    } else if (io == D - 1) {
+        double t = dtau[D - 2];
+        double A = 2.0 / (t * t);
+        den = 1.0 + 2.0 / t + A * F / (1.0 + F);
+        num = S[D - 1] + 2.0 * I_right / t + A * z;
+    } else {
+        double a = dtau[io - 1], b = dtau[io];
+        double A = 2.0 / (a * (a + b)), C = 2.0 / (b * (a + b));
+        den = 1.0 + A * F / (1.0 + F) + C * G / (1.0 + G);
+        num = S[io] + A * z + C * w;
+    }
+    *u_out = num / den;
+    *L_out = 1.0 / den;
+}
+
+/* ------------------------------------------------------------------------ */
+/* J-bar and Lambda* at a list of origin points.                             */
+/*                                                                           */
+/* For origin o, ray pair (r, rb) (n_rb = -n_r), GH bin q and line ij:        */
+/*  - the full ray runs from the far end of the rb half-ray through o to the  */
+/*    far end of the r half-ray (points from the trace);                      */
+/*  - the bin frequency is nu_q = nu_ij + x_q dnu_ij(o), centred on the line  */
+/*    in o's comoving frame;                                                  */
+/*  - a point c on half-ray h sees the photons travelling toward o at the     */
+/*    comoving frequency nu_q (1 + n_h . (v_c - v_o)/c), so its offset from   */
+/*    line centre is x_q dnu_ij(o) + nu_q n_h . (v_c - v_o)/c;                */
+/*  - segment optical depths follow oracle_segment_dtau, floored at tau_min;  */
+/*  - both ends see the background I_bg = B_nu(T_bg) at nu_q;                 */
+/*  - Jbar  += (2/R) w_q u_o,  Lstar += (2/R) w_q L*_oo  (w_q normalised GH). */
+/* width_mode 0: dnubar from the averaged T and vturb^2; 1: mean of widths.   */
+/* chi and S are [M][N] (SI); outputs are [n_orig][M].                        */
+/* ------------------------------------------------------------------------ */
+void oracle_formal_solve(int64_t N, const double *pos, const double *vel, const double *temp,
+                         const double *vturb2, double mol_mass,
+                         int32_t R, const double *dirs, int32_t P, const int32_t *pairs,
+                         const int64_t *ray_off, const int32_t *ray_idx,
+                         int32_t M, const double *nu, const double *chi, const double *S,
+                         int32_t Q, const double *xq, const double *wq, double T_bg,
+                         double tau_min, double thr, int width_mode,
+                         int64_t n_orig, const int64_t *orig, double *Jbar, double *Lstar)
+{
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t io_ = 0; io_ < n_orig; ++io_) {
+        int64_t o = orig[io_];
+        /* longest full ray over the pairs */
+        int64_t Dmax = 1;
+        for (int32_t p = 0; p < P; ++p) {
+            int64_t r = pairs[2 * p], rb = pairs[2 * p + 1];
+            int64_t D = 1 + (ray_off[r * N + o + 1] - ray_off[r * N + o])
+                          + (ray_off[rb * N + o + 1] - ray_off[rb * N + o]);
+            if (D > Dmax) Dmax = D;
+        }
+        int64_t *pt = malloc(sizeof(int64_t) * Dmax);
+        double *beta = malloc(sizeof(double) * Dmax);
+        double *dx = malloc(sizeof(double) * Dmax);
+        double *dnu = malloc(sizeof(double) * Dmax);
+        double *off = malloc(sizeof(double) * Dmax);
+        double *dtau = malloc(sizeof(double) * Dmax);
+        double *Sd = malloc(sizeof(double) * Dmax);
+        for (int32_t m = 0; m < M; ++m) {
+            Jbar[io_ * M + m] = 0.0;
+            Lstar[io_ * M + m] = 0.0;
+        }
+        for (int32_t p = 0; p < P; ++p) {
+            int64_t r = pairs[2 * p], rb = pairs[2 * p + 1];
+            const double *nr = dirs + 3 * r, *nrb = dirs + 3 * rb;
+            int64_t b0 = ray_off[rb * N + o], nrbl = ray_off[rb * N + o + 1] - b0;
+            int64_t f0 = ray_off[r * N + o], nrl = ray_off[r * N + o + 1] - f0;
+            int64_t D = 1 + nrbl + nrl, d_o = nrbl;
+            /* assemble the full ray: far end of rb ... o ... far end of r */
+            for (int64_t k = 0; k < nrbl; ++k) {
+                int64_t c = ray_idx[b0 + (nrbl - 1 - k)];
+                pt[k] = c;
+                beta[k] = (nrb[0] * (vel[3 * c] - vel[3 * o]) + nrb[1] * (vel[3 * c + 1] - vel[3 * o + 1])
+                           + nrb[2] * (vel[3 * c + 2] - vel[3 * o + 2])) / OR_C;
+            }
+            pt[d_o] = o;
+            beta[d_o] = 0.0;
+            for (int64_t k = 0; k < nrl; ++k) {
+                int64_t c = ray_idx[f0 + k];
+                pt[d_o + 1 + k] = c;
+                beta[d_o + 1 + k] = (nr[0] * (vel[3 * c] - vel[3 * o]) + nr[1] * (vel[3 * c + 1] - vel[3 * o + 1])
+                                     + nr[2] * (vel[3 * c + 2] - vel[3 * o + 2])) / OR_C;
+            }
+            for (int64_t d = 0; d + 1 < D; ++d) {
+                int64_t a = pt[d], b = pt[d + 1];
+                double ex = pos[3 * b] - pos[3 * a], ey = pos[3 * b + 1] - pos[3 * a + 1],
+                       ez = pos[3 * b + 2] - pos[3 * a + 2];
+                dx[d] = sqrt(ex * ex + ey * ey + ez * ez);
+            }
+            for (int32_t m = 0; m < M; ++m) {
+                double nij = nu[m];
+                for (int64_t d = 0; d < D; ++d) {
+                    int64_t c = pt[d];
+                    dnu[d] = nij / OR_C * sqrt(2.0 * OR_KB * temp[c] / mol_mass + vturb2[c]);
+                    Sd[d] = S[(int64_t)m * N + c];
+                }
+                for (int32_t q = 0; q < Q; ++q) {
+                    double nuq = nij + xq[q] * dnu[d_o];
+                    double Ibg = oracle_planck(nuq, T_bg);
+                    for (int64_t d = 0; d < D; ++d)
+                        off[d] = xq[q] * dnu[d_o] + nuq * beta[d];
+                    for (int64_t d = 0; d + 1 < D; ++d) {
+                        int64_t a = pt[d], b = pt[d + 1];
+                        double dnb;
+                        if (width_mode == 0) {
+                            double Tb = 0.5 * (temp[a] + temp[b]);
+                            double vb = 0.5 * (vturb2[a] + vturb2[b]);
+                            dnb = nij / OR_C * sqrt(2.0 * OR_KB * Tb / mol_mass + vb);
+                        } else {
+                            dnb = 0.5 * (dnu[d] + dnu[d + 1]);
+                        }
+                        double t = oracle_segment_dtau(dx[d], chi[(int64_t)m * N + a], chi[(int64_t)m * N + b],
+                                                       dnu[d], dnu[d + 1], dnb, off[d], off[d + 1], thr);
+                        dtau[d] = t > tau_min ? t : tau_min;
+                    }
+                    double u, L;
+                    oracle_feautrier_at(D, dtau, Sd, Ibg, Ibg, d_o, &u, &L);
+                    Jbar[io_ * M + m] += (2.0 / R) * wq[q] * u;
+                    Lstar[io_ * M + m] += (2.0 / R) * wq[q] * L;
+                }
+            }
+        }
+        free(pt); free(beta); free(dx); free(dnu); free(off); free(dtau); free(Sd);
+    }
+}
