@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Throughput of the line radiative-transfer hot path on GB300.
+
+Metric: point x ray-pair x frequency-bin formal solutions per second (each
+producing u and Lambda*_oo at the origin for one line; J-bar and Lambda* are
+their reductions), FP32-mixed path, whole job.
+
+One step = one pass of the whole hot path over the model: trace every
+half-ray through the neighbour graph, per-point line data from the current
+populations, the formal solution of every (point, ray pair, bin, line) reduced
+into J-bar and Lambda*, the statistical-equilibrium solve at every point, and
+one adaptive Ng step (one iteration of the ALI driver).
+
+Default workload: 100k-point shell outflow, 41-level rotor (40 lines), 48 rays
+(24 pairs), 50 Gauss-Hermite bins per line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "point·ray·freq formal solutions/s (J̄+Λ*), FP32-mixed vs FP64 at 1e-4 J̄"
+UNIT = "formal solutions/s"
+OPS_PER_LINE_STEP = 10      # FP32 ops of one elimination row for one line (see the formal-solve kernel)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--points", type=int, default=None, help="override the point count (same laws)")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 and CPU-baseline legs")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle origins per CPU sample (0 = auto)")
+    return ap.parse_args()
+
+
+def workload_config(model, idx):
+    return {
+        "workload": model.name, "points": model.n_points, "rays": int(model.dirs.shape[0]),
+        "ray_pairs": int(model.dirs.shape[0]) // 2, "levels": int(model.lines.n_levels),
+        "lines": int(model.lines.n_lines), "bins_per_line": int(model.n_quad),
+        "source": f"synthetic workload {idx} (seeded)",
+        "step": "trace + line data + formal solution (J-bar, Lambda*) + statistical equilibrium + adaptive Ng",
+        "l2": "flushed between timed steps (256 MiB write, untimed)",
+    }
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(world, v):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def fs_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_fs.cu", "mgt_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2411_03040_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(units_per_launch_key):
+    """Per-launch DRAM bytes of the formal-solve kernel from a committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "k_fs_dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_source_sha") != fs_source_hash():
+        return None
+    return d
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(model, n_origins, seed=0):
+    """One bounded sample of the workload through the oracle: trace, line data,
+    formal solution and statistical equilibrium at n_origins origins.
+    Returns (formal solutions, seconds, threads)."""
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    orig = np.sort(rng.choice(model.n_points, n_origins, replace=False))
+    t0 = time.perf_counter()
+    rays = O.trace(model, orig)
+    pops = O.lte_populations(model.temp, model.n_spec, model.lines.energy_J, model.lines.g)
+    chi, S, _ = O.line_chi_S(pops, model.lines)
+    J, L = O.formal_solve(model, rays, chi, S, origins=orig)
+    sub = lambda a: a[orig]
+    O.stat_equilibrium(pops[orig], J, L, sub(model.temp), sub(model.n_coll), sub(model.n_spec), model.lines)
+    dt = time.perf_counter() - t0
+    units = n_origins * (model.dirs.shape[0] // 2) * model.lines.n_lines * model.n_quad
+    return units, dt, os.cpu_count()
+
+
+def run_reference(args, model, cfg):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    n = args.cpu_sample or max(8, min(model.n_points, 48))
+    for w in range(args.warmup):
+        oracle_sample(model, n, seed=100 + w)
+    units, secs = 0, 0.0
+    for k in range(args.steps):
+        u, dt, cores = oracle_sample(model, n, seed=k)
+        units += u
+        secs += dt
+    value = units / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": dict(cfg, parallelism="host cores (OpenMP over origins)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} random origin points per step, all pairs/lines/bins, "
+                                   "trace + line data + formal solution + SE"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- GPU arm
+def desc_bytes(model):
+    ln = model.lines
+    arrs = [model.pos, model.vel, model.temp, model.vturb2, model.n_coll, model.n_spec, model.nbr_offsets,
+            model.nbrs, model.boundary, model.dirs, ln.energy_J, ln.g, ln.up, ln.lo, ln.A, ln.freq_Hz, ln.cup,
+            ln.clo, ln.K_ul]
+    return int(sum(np.asarray(a).nbytes for a in arrs))
+
+
+def pinned_copy(model):
+    """The model's host arrays in pinned (page-locked) memory."""
+    import copy
+
+    import torch
+
+    def pin(a):
+        a = np.ascontiguousarray(a)
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    m = copy.copy(model)
+    for f in ("pos", "vel", "temp", "vturb2", "n_coll", "n_spec", "nbr_offsets", "nbrs", "boundary", "dirs"):
+        setattr(m, f, pin(getattr(model, f)))
+    return m
+
+
+def run_mine(args, model, cfg):
+    import torch
+
+    from paper_2411_03040_gb300 import build as B
+    from paper_2411_03040_gb300 import mgt
+
+    world, rank, local = dist_setup(args.gpus)
+    B.build()
+    mgt.load()
+    stream = torch.cuda.Stream()
+    units = model.n_points * (model.dirs.shape[0] // 2) * model.lines.n_lines * model.n_quad
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    with torch.cuda.stream(stream):
+        h = mgt.mgt_model_create(model, stream=stream)
+        tst = mgt.mgt_trace_rays(h, stream=stream)
+
+        fs_ev = []
+
+        def step(record):
+            mgt.mgt_trace_rays(h, stream=stream)
+            if record:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED, want=False, stream=stream)
+            if record:
+                b.record(stream)
+                fs_ev.append((a, b))
+            mgt.mgt_stat_equilibrium(h, want=False, stream=stream)
+            mgt.mgt_ng_accelerate(h, mgt.MGT_NG_ADAPTIVE, n_max=8, stream=stream)
+
+        for _ in range(max(3, args.warmup)):
+            step(False)
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        barrier(world)
+        torch.cuda.synchronize()
+        n0 = mgt.mgt_launch_count()
+        ev = []
+        for k in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(True)
+            b.record(stream)
+            ev.append((a, b))
+            flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        barrier(world)
+        launches = mgt.mgt_launch_count() - n0
+        clk = clocks.stop()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        fs_ms = sum(a.elapsed_time(b) for a, b in fs_ev) / args.steps
+        ms = allreduce_max(world, ms)
+        value = world * units / (ms * 1e-3)
+
+        extras = {}
+        if not args.no_extras and rank == 0:
+            # FP64 path: one timed solve, and the FP32 vs FP64 difference of J-bar
+            J32, L32 = mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED, stream=stream)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mgt.mgt_formal_solve(h, mgt.MGT_FP64, want=False, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fs64_ms = a.elapsed_time(b)
+            J64, L64 = mgt.mgt_formal_solve(h, mgt.MGT_FP64, stream=stream)
+            extras["fp64_formal_solve"] = {
+                "value": units / (fs64_ms * 1e-3), "unit": UNIT, "ms": fs64_ms,
+                "fp32_mixed_speedup": fs64_ms / fs_ms,
+                "max_rel_diff_Jbar_fp32_vs_fp64": float(np.max(np.abs(J32 - J64) / np.abs(J64))),
+                "max_rel_diff_Lstar_fp32_vs_fp64": float(np.max(np.abs(L32 - L64) / np.abs(L64)))}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": dict(cfg, parallelism="single GPU" if world == 1 else f"{world} independent replicas")}
+
+    # roofline of the dominant kernel (formal solution)
+    pk, src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    line_steps = tst["total_steps"] * model.lines.n_lines * model.n_quad
+    achieved = OPS_PER_LINE_STEP * line_steps / (fs_ms * 1e-3) / 1e12
+    peak = 152 * 4 * 32 * sm_max * 1e6 / 1e12
+    tr = traffic_record("line_steps")
+    out["roofline"] = {
+        "bound": "alu", "kernel": "k_fs<float,8> (formal solution + J-bar/Lambda* reduction)",
+        "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak,
+        "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+        "peak_source": f"{src}: 152 SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz (one FP32/MUFU op per lane "
+                       "per cycle)",
+        "ops_per_launch": OPS_PER_LINE_STEP * line_steps, "line_steps_per_launch": line_steps,
+        "launch_ms": fs_ms, "step_ms": ms, "share_of_step": fs_ms / ms}
+    out["gpu_launches"] = launches
+    out["clocks"] = clk
+    out["trace"] = tst
+    out.update(extras)
+
+    if not args.no_extras and rank == 0:
+        # end to end through the C-ABI with host buffers (pinned), copies inside
+        pm = pinned_copy(model)
+        pops_host = torch.empty((model.n_points, model.lines.n_levels), dtype=torch.float64,
+                                pin_memory=True).numpy()
+        h2d = desc_bytes(model)
+        d2h = pops_host.nbytes
+        times = []
+        for k in range(max(1, args.warmup) + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                he = mgt.mgt_model_create(pm, stream=stream)
+                mgt.mgt_trace_rays(he, stream=stream)
+                mgt.mgt_formal_solve(he, mgt.MGT_FP32_MIXED, want=False, stream=stream)
+                res = mgt.mgt_stat_equilibrium(he, want=True, stream=stream)
+                pops_host[...] = res
+                mgt.mgt_ng_accelerate(he, mgt.MGT_NG_ADAPTIVE, n_max=8, stream=stream)
+                he.close()
+            torch.cuda.synchronize()
+            if k >= max(1, args.warmup):
+                times.append(time.perf_counter() - t0)
+        e2e_s = float(np.mean(times))
+        out["e2e"] = {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "ms_per_step": 1e3 * e2e_s,
+                      "path": "mgt_model_create from pinned host arrays -> trace -> formal solve -> SE (populations "
+                              "to host) -> Ng -> destroy"}
+        # the oracle on the host cores, bounded sample
+        import oracle as O
+        O.build()
+        n = args.cpu_sample or max(8, min(model.n_points, 640))
+        u, dt, cores = oracle_sample(model, n, seed=0)
+        out["cpu_baseline"] = {"value": u / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{n} random origin points, all {model.dirs.shape[0] // 2} pairs x "
+                                         f"{model.lines.n_lines} lines x {model.n_quad} bins; trace + line data + "
+                                         f"formal solution + SE; {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    from paper_2411_03040_gb300 import synth
+    model = synth.config_model(args.workload, n_points=args.points)
+    cfg = workload_config(model, args.workload)
+    if args.impl == "reference":
+        run_reference(args, model, cfg)
+    else:
+        run_mine(args, model, cfg)
+
+
+if __name__ == "__main__":
+    main()

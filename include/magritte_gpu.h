@@ -1,0 +1,251 @@
+/*
+ * magritte_gpu.h -- C-ABI of the GB300 (sm_103a) line radiative-transfer hot
+ * path of Magritte (arXiv 2411.03040).
+ *
+ * The calls follow the paper's statement of the problem: a model built from
+ * positions, velocities, neighbours, boundary points, temperature, turbulence,
+ * species densities, uniform rays, line data and a quadrature order (Sec. 3.2,
+ * Listing 2), and the solver steps of Listing 3 (compute the radiation field,
+ * compute level populations with Ng-acceleration).
+ *
+ * Conventions shared by every entry point
+ *  - All arrays are plain C pointers.  Host arrays passed to mgt_model_create
+ *    are borrowed for the duration of the call and copied; the library owns all
+ *    device memory of a model until mgt_model_destroy.
+ *  - Output pointers are caller-owned.  Where an `on_device` flag is taken,
+ *    nonzero means the pointer is a device address on the model's device,
+ *    zero means host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is stream-ordered.  Calls that return data to host memory
+ *    synchronise the stream before returning.
+ *  - Every call returns an mgt_status.  MGT_ERR_ARG means the arguments were
+ *    rejected before any work or allocation.  Device-side problems (a kernel's
+ *    bounded loop running out, an index out of range) are recorded in a device
+ *    error word and reported as MGT_ERR_BOUNDS / MGT_ERR_TIMEOUT by the next
+ *    synchronising call or by mgt_sync.  mgt_last_error() returns a
+ *    thread-local message describing the last non-OK status.
+ *  - SI units throughout (m, s, K, kg, J, Hz, W m^-2 Hz^-1 sr^-1).
+ */
+#ifndef MAGRITTE_GPU_H
+#define MAGRITTE_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mgt_model mgt_model;
+
+typedef enum {
+    MGT_OK = 0,
+    MGT_ERR_ARG = 1,           /* invalid argument; nothing was done */
+    MGT_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    MGT_ERR_OOM = 3,           /* device allocation failed */
+    MGT_ERR_NOT_CONVERGED = 4, /* ALI ended with non-finite populations */
+    MGT_ERR_SINGULAR = 5,      /* a linear system could not be solved */
+    MGT_ERR_TIMEOUT = 6,       /* a bounded device loop ran out */
+    MGT_ERR_BOUNDS = 7,        /* a device index check failed */
+    MGT_ERR_STATE = 8          /* call out of order (e.g. solve before trace) */
+} mgt_status;
+
+typedef enum {
+    MGT_FP64 = 0,        /* every step of the formal solution in FP64 */
+    MGT_FP32_MIXED = 1   /* opacity, optical depth and elimination in FP32, FP32
+                            compensated accumulation of J-bar / Lambda*; the
+                            trapezoid/erf switch is re-decided in FP64 next to
+                            the threshold; SE and Ng stay FP64 */
+} mgt_precision;
+
+/*
+ * Model inputs (Sec. 3.2, Listing 2: geometry.points.{position, velocity,
+ * neighbors, n_neighbors}, geometry.boundary.boundary2point,
+ * thermodynamics.{temperature.gas, turbulence.vturb2},
+ * chemistry.species.abundance, uniform rays, LAMDA-style line data,
+ * quadrature order).  All pointers are host pointers.
+ */
+typedef struct {
+    int64_t n_points;            /* N >= 1 */
+    const double *pos;           /* [N][3] m */
+    const double *vel;           /* [N][3] m/s */
+    const double *temp;          /* [N] K, > 0 */
+    const double *vturb2;        /* [N] m^2/s^2, >= 0 (microturbulence squared) */
+    const double *n_coll;        /* [N] m^-3 collision-partner density, >= 0 */
+    const double *n_spec;        /* [N] m^-3 line-species density, > 0 */
+    const int64_t *nbr_offsets;  /* [N+1] CSR offsets into nbrs, nbr_offsets[0] = 0 */
+    const int32_t *nbrs;         /* [nbr_offsets[N]] neighbour indices in [0, N) */
+    int32_t n_boundary;          /* number of boundary points */
+    const int32_t *boundary;     /* [n_boundary] boundary point indices */
+    int32_t n_rays;              /* R, even; every direction has its antipode */
+    const double *dirs;          /* [R][3] unit vectors */
+    int32_t n_quad;              /* Q Gauss-Hermite bins per line, 1..64 */
+    double mol_mass_kg;          /* molecular mass of the line species, > 0 */
+    double T_bg;                 /* background (CMB) temperature in K, >= 0 */
+    int32_t n_levels;            /* L, 2..64 */
+    const double *energy_J;      /* [L] level energies */
+    const double *g;             /* [L] statistical weights */
+    int32_t n_lines;             /* M radiative lines, 1..L*(L-1)/2 */
+    const int32_t *up;           /* [M] upper level */
+    const int32_t *lo;           /* [M] lower level */
+    const double *A;             /* [M] Einstein A_ul, s^-1 */
+    const double *freq_Hz;       /* [M] line centre frequencies */
+    int32_t n_coll_trans;        /* K collisional transitions */
+    const int32_t *cup;          /* [K] upper level */
+    const int32_t *clo;          /* [K] lower level */
+    const double *K_ul;          /* [K] downward rate coefficients, m^3/s */
+} mgt_model_desc;
+
+/* Numerical options of the formal solution (Sec. 4.3). */
+typedef struct {
+    double switch_threshold;  /* trapezoid below |Doppler shift|/dnu_bar, erf form at or
+                                 above it; default 0.35 (Sec. 4.3) */
+    int32_t width_mode;       /* dnu_bar of a segment: 0 = from the averaged temperature
+                                 and turbulence (default), 1 = mean of the endpoint widths */
+    int32_t lines_per_thread; /* FP32 kernel schedule: 0 = auto, else 4 or 8 */
+} mgt_solve_opts;
+
+typedef struct {
+    int64_t total_steps;      /* sum of half-ray lengths over all points and directions */
+    int64_t n_stalls;         /* walks that ended without reaching a boundary point */
+    int32_t max_half_ray;     /* longest half-ray (points) */
+    double mean_half_ray;     /* total_steps / (N * R) */
+} mgt_trace_stats;
+
+typedef enum { MGT_NG_NONE = 0, MGT_NG_CLASSICAL = 1, MGT_NG_ADAPTIVE = 2 } mgt_ng_mode;
+
+typedef struct {
+    int32_t mode;       /* mgt_ng_mode */
+    int32_t n_steps;    /* classical: regular iterations between predictions (>= 2) */
+    int32_t n_max;      /* adaptive: maximum iterates kept (3..16) */
+} mgt_ng_opts;
+
+typedef struct {
+    int32_t n_iter;             /* regular ALI iterations */
+    mgt_precision precision;    /* formal-solution precision */
+    mgt_ng_opts ng;
+} mgt_ali_opts;
+
+typedef struct {
+    int32_t iterations;         /* regular iterations done */
+    int32_t ng_accepted;        /* Ng predictions used */
+    double last_maxrel;         /* max relative population change of the last iteration */
+} mgt_ali_stats;
+
+/*
+ * Create a model from host inputs (Sec. 3.2, Listing 2).  Validates every
+ * input (finite values, unit directions with antipodes, indices in range,
+ * N >= 1, sizes within the limits above); on MGT_ERR_ARG nothing is
+ * allocated and *out is left NULL.  Level populations start at LTE
+ * (compute_LTE_level_populations, Listing 3).  The Gauss-Hermite nodes
+ * (set_quadrature) and the per-point line widths (Sec. 4.3, eq. line width)
+ * are computed here.  `stream` orders the uploads.
+ */
+mgt_status mgt_model_create(mgt_model **out, const mgt_model_desc *desc, void *stream);
+
+/* Free all device and host memory of a model (NULL is a no-op). */
+mgt_status mgt_model_destroy(mgt_model *m);
+
+/* Set the numerical options of mgt_formal_solve; NULL restores the defaults. */
+mgt_status mgt_set_solve_opts(mgt_model *m, const mgt_solve_opts *opts);
+
+/*
+ * Trace every half-ray: for each point o and direction n, the chain of points
+ * o -> c1 -> c2 ... through the neighbour graph (the tracer of the paper's
+ * earlier Magritte papers, Sec. 2 / Sec. 4.1 cost ~ points per ray).  Rule:
+ * from the current point c, candidates are neighbours m with
+ * Z_m = (x_m - x_o).n > Z_c; the candidate with the smallest squared distance
+ * to the ray line wins (ties to the smaller index); the walk ends on a
+ * boundary point (included) or stalls when no candidate exists.  All
+ * predicates are evaluated in FP64 without fused multiply-adds, so the point
+ * lists are bit-exact with any implementation of the same expressions.
+ * Stores the ray geometry on the device.  `stats` (host, may be NULL) is
+ * filled after a stream synchronisation.
+ */
+mgt_status mgt_trace_rays(mgt_model *m, mgt_trace_stats *stats, void *stream);
+
+/* Copy the traced rays to host memory: ray_off [R*N+1] (exclusive prefix of
+ * half-ray lengths, direction-major: entry r*N+o) and idx [total_steps] point
+ * indices in outward order.  Either pointer may be NULL. */
+mgt_status mgt_get_rays(mgt_model *m, int64_t *ray_off, int32_t *idx, void *stream);
+
+/* Set level populations [N][L] (m^-3; host pointer), or LTE when pops is NULL.
+ * Resets the Ng history. */
+mgt_status mgt_set_populations(mgt_model *m, const double *pops, void *stream);
+
+/* Copy the current level populations [N][L] to `pops` (host or device). */
+mgt_status mgt_get_populations(mgt_model *m, double *pops, int on_device, void *stream);
+
+/*
+ * Radiation field from the current populations: per point and line the line
+ * opacity and source function, per (point, ray pair, Gauss-Hermite bin, line)
+ * the Doppler-shifted Gaussian opacity along the ray, segment optical depths
+ * (Sec. 4.3: trapezoidal rule, or the semi-analytic erf form when the Doppler
+ * shift across the segment reaches switch_threshold line widths), the
+ * second-order two-point (Feautrier) system with background B_nu(T_bg) at both
+ * ends, and its solution u and Lambda*_oo at the origin, reduced into
+ *   Jbar[m][o]  = sum_pairs (2/R) sum_q w_q u,
+ *   Lstar[m][o] = sum_pairs (2/R) sum_q w_q Lambda*_oo.
+ * Jbar in W m^-2 Hz^-1 sr^-1, Lstar dimensionless; both [M][N] f64, line-major.
+ * Either output may be NULL (the result stays on the device for
+ * mgt_stat_equilibrium).  Requires mgt_trace_rays.
+ */
+mgt_status mgt_formal_solve(mgt_model *m, mgt_precision p, double *Jbar, double *Lstar,
+                            int on_device, void *stream);
+
+/*
+ * Statistical equilibrium (Listing 3, compute_level_populations; the paper's
+ * Sec. 5 "solution of the statistical equilibrium equations"): per point the
+ * steady state of the rate equations with radiative rates preconditioned by
+ * Lambda* (down: A(1 - Lambda*) + B_ul J_eff, up: B_lu J_eff,
+ * J_eff = Jbar - Lambda* S_old, floored at zero) and collisional rates in
+ * detailed balance, normalised to n_spec; solved in FP64 by state reduction.
+ * Uses the Jbar/Lambda* of the last mgt_formal_solve.  The result becomes the
+ * current populations (the previous ones are kept for mgt_ng_accelerate) and
+ * is copied to pops_out [N][L] (host) when not NULL.
+ */
+mgt_status mgt_stat_equilibrium(mgt_model *m, double *pops_out, void *stream);
+
+/*
+ * Ng-acceleration step after mgt_stat_equilibrium (Sec. 4.2, Appendix A).
+ * Pushes the new populations (as fractions n_i/n_spec) into the history and
+ * writes the maximum relative change against the previous populations to
+ * *maxrel (host, may be NULL).  Classical mode: after n_steps regular
+ * iterations the prediction sum_k c_k x_{k+1},
+ * c = (R R^T)^-1 1 / (1^T (R R^T)^-1 1), replaces the populations.  Adaptive
+ * mode: with m >= 3 iterates since the last prediction, the running prediction
+ * is used when its maximum relative change is below that of the regular
+ * iterates, or when m reaches n_max.  A prediction with a negative population
+ * or a non-finite coefficient solve is not used (the history restarts).
+ * *accepted (host, may be NULL) is 1 when a prediction replaced the
+ * populations.  Synchronises the stream.
+ */
+mgt_status mgt_ng_accelerate(mgt_model *m, const mgt_ng_opts *opts, int *accepted, double *maxrel,
+                             void *stream);
+
+/*
+ * Accelerated Lambda iteration (Listing 3, compute_level_populations with
+ * Ng_acc and N_iter_max): from the current populations, opts->n_iter regular
+ * iterations of {formal solution, statistical equilibrium, Ng step}.
+ * Requires mgt_trace_rays.  Returns MGT_ERR_NOT_CONVERGED if the populations
+ * become non-finite.  `stats` (host) may be NULL.
+ */
+mgt_status mgt_ali_solve(mgt_model *m, const mgt_ali_opts *opts, mgt_ali_stats *stats, void *stream);
+
+/* Wait for the model's work on `stream` and report any device-side error. */
+mgt_status mgt_sync(mgt_model *m, void *stream);
+
+/* Model sizes: any pointer may be NULL. */
+mgt_status mgt_model_sizes(const mgt_model *m, int64_t *n_points, int32_t *n_rays, int32_t *n_levels,
+                           int32_t *n_lines, int32_t *n_quad);
+
+/* Number of kernels this library has launched in the process so far (all
+ * models, all threads); library kernels such as CUB scans are not counted. */
+mgt_status mgt_launch_count(int64_t *count);
+
+/* Thread-local description of the last non-OK status of this thread. */
+const char *mgt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MAGRITTE_GPU_H */

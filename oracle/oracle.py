@@ -66,8 +66,8 @@ def _load():
             lib = ctypes.CDLL(build())
             P = ctypes.c_void_p
             i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
-            lib.oracle_trace_lengths.argtypes = [i64, P, P, P, P, i32, P, P, P]
-            lib.oracle_trace_fill.argtypes = [i64, P, P, P, P, i32, P, P, P]
+            lib.oracle_trace_lengths.argtypes = [i64, P, P, P, P, i32, P, i64, P, P, P]
+            lib.oracle_trace_fill.argtypes = [i64, P, P, P, P, i32, P, i64, P, P, P]
             lib.oracle_planck.argtypes = [f64, f64]
             lib.oracle_planck.restype = f64
             lib.oracle_segment_dtau.argtypes = [f64] * 9
@@ -189,8 +189,9 @@ class Rays:
         return self.idx[self.off[t]:self.off[t + 1]]
 
 
-def trace(model) -> Rays:
-    """Trace every half-ray of every origin (rule in oracle_c.c)."""
+def trace(model, origins=None) -> Rays:
+    """Trace every half-ray of every origin (rule in oracle_c.c); with
+    ``origins`` only those origins' half-rays (the others stay empty)."""
     lib = _load()
     N, R = model.n_points, model.dirs.shape[0]
     pos = np.ascontiguousarray(model.pos, np.float64)
@@ -201,11 +202,15 @@ def trace(model) -> Rays:
     dirs = np.ascontiguousarray(model.dirs, np.float64)
     lens = np.zeros(R * N, np.int64)
     stall = np.zeros(R * N, np.uint8)
-    lib.oracle_trace_lengths(N, _p(pos), _p(off), _p(nb), _p(bnd), R, _p(dirs), _p(lens), _p(stall))
+    org = None if origins is None else np.ascontiguousarray(origins, np.int64)
+    n_org = 0 if org is None else org.shape[0]
+    lib.oracle_trace_lengths(N, _p(pos), _p(off), _p(nb), _p(bnd), R, _p(dirs), n_org,
+                             None if org is None else _p(org), _p(lens), _p(stall))
     ray_off = np.zeros(R * N + 1, np.int64)
     np.cumsum(lens, out=ray_off[1:])
     idx = np.zeros(int(ray_off[-1]), np.int32)
-    lib.oracle_trace_fill(N, _p(pos), _p(off), _p(nb), _p(bnd), R, _p(dirs), _p(ray_off), _p(idx))
+    lib.oracle_trace_fill(N, _p(pos), _p(off), _p(nb), _p(bnd), R, _p(dirs), n_org,
+                          None if org is None else _p(org), _p(ray_off), _p(idx))
     return Rays(ray_off, idx, int(stall.sum()), N, R, stall)
 
 
@@ -226,7 +231,7 @@ def feautrier_at(dtau, S, I_left, I_right, io):
     return u.value, L.value
 
 
-def formal_solve(model, rays: Rays, chi, S, origins=None, tau_min=1e-30, thr=0.35,
+def formal_solve(model, rays: Rays, chi, S, origins=None, tau_min=1e-150, thr=0.35,
                  width_mode=0):
     """J-bar and Lambda* ([n][M], SI) at ``origins`` (default: all points)."""
     lib = _load()
@@ -441,7 +446,7 @@ class NgAdaptive:
 # --------------------------------------------------------------------------
 # Accelerated Lambda iteration
 # --------------------------------------------------------------------------
-def ali_solve(model, rays=None, n_iter=20, ng=None, pops0=None, tau_min=1e-30, thr=0.35,
+def ali_solve(model, rays=None, n_iter=20, ng=None, pops0=None, tau_min=1e-150, thr=0.35,
               callback=None):
     """LTE start (or pops0), then n_iter regular iterations of
     {chi,S from pops -> formal solution (Jbar, Lstar) -> statistical equilibrium

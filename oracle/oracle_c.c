@@ -74,30 +74,33 @@ static int64_t walk(int64_t o, const double *n, const double *pos, const int64_t
     }
 }
 
-/* Half-ray lengths for every (direction r, origin o): len[r*N + o]. */
+/* Half-ray lengths for every direction r and origin o in orig[0..n_orig)
+ * (all points when orig is NULL): len[r*N + o]; other entries are untouched. */
 void oracle_trace_lengths(int64_t N, const double *pos, const int64_t *off, const int32_t *nb,
                           const uint8_t *bnd, int32_t R, const double *dirs,
-                          int64_t *len, uint8_t *stall)
+                          int64_t n_orig, const int64_t *orig, int64_t *len, uint8_t *stall)
 {
+    int64_t n = orig ? n_orig : N;
     #pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t t = 0; t < (int64_t)R * N; ++t) {
-        int64_t r = t / N, o = t % N;
+    for (int64_t t = 0; t < (int64_t)R * n; ++t) {
+        int64_t r = t / n, o = orig ? orig[t % n] : t % n;
         int st;
-        len[t] = walk(o, dirs + 3 * r, pos, off, nb, bnd, N, NULL, &st);
-        stall[t] = (uint8_t)st;
+        len[r * N + o] = walk(o, dirs + 3 * r, pos, off, nb, bnd, N, NULL, &st);
+        stall[r * N + o] = (uint8_t)st;
     }
 }
 
 /* Fill the point lists; ray_off has R*N+1 entries (exclusive prefix of lengths). */
 void oracle_trace_fill(int64_t N, const double *pos, const int64_t *off, const int32_t *nb,
                        const uint8_t *bnd, int32_t R, const double *dirs,
-                       const int64_t *ray_off, int32_t *idx)
+                       int64_t n_orig, const int64_t *orig, const int64_t *ray_off, int32_t *idx)
 {
+    int64_t n = orig ? n_orig : N;
     #pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t t = 0; t < (int64_t)R * N; ++t) {
-        int64_t r = t / N, o = t % N;
+    for (int64_t t = 0; t < (int64_t)R * n; ++t) {
+        int64_t r = t / n, o = orig ? orig[t % n] : t % n;
         int st;
-        walk(o, dirs + 3 * r, pos, off, nb, bnd, N, idx + ray_off[t], &st);
+        walk(o, dirs + 3 * r, pos, off, nb, bnd, N, idx + ray_off[r * N + o], &st);
     }
 }
 

@@ -1,0 +1,170 @@
+// Statistical equilibrium: one warp per point, FP64, state reduction.
+//
+// Rates i -> j per point (s^-1):
+//   radiative, preconditioned by the diagonal approximate Lambda operator
+//   (Rybicki & Hummer 1991), J_eff = Jbar - Lambda* S_old:
+//       u -> l : max(A_ul (1 - Lambda*) + B_ul J_eff, 0)
+//       l -> u : max(B_lu J_eff, 0)
+//   collisional: C_ul = n_coll K_ul, C_lu = C_ul (g_u/g_l) exp(-(E_u - E_l)/kT).
+// The steady state sum_j n_j R_ji = n_i sum_j R_ij, normalised to n_spec, is
+// found by state reduction (Grassmann, Taksar & Heyman 1985): eliminate the
+// highest level first, folding the paths through it into the remaining rates,
+// R_ij += R_in R_nj / S_n with S_n = sum_{j<n} R_nj; then n_0 = 1,
+// n_k = sum_{i<k} n_i R_ik / S_k and normalise.  Only non-negative numbers are
+// added, so populations many decades below the ground level keep full
+// relative accuracy.  All warp reductions run in a fixed lane order, so the
+// result is bitwise reproducible.
+#include <algorithm>
+
+#include "mgt_common.cuh"
+
+namespace mgt {
+
+namespace {
+
+struct SEArgs {
+    int64_t N;
+    int L, M, Mpad, K;
+    const double *pops_old;   // [N][L]
+    const double *J, *Lst;    // [N][M]
+    const double *T, *ncoll, *nspec;
+    const double *line_tab;   // [8][Mpad]: nu, A, Bul, Blu, ...
+    const int32_t *line_ul;   // [2][Mpad]
+    const double *level_tab;  // [2][L]: E, g
+    const double *Kul;        // [K]
+    const int32_t *coll_ul;   // [2][K]
+    const int16_t *entry;     // [3][L*L]
+    double *pops_out;         // [N][L]
+    int wpb;                  // warps (points) per block
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+constexpr int kMaxWarpsPerBlock = 4;
+
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) k_se(SEArgs a)
+{
+    extern __shared__ __align__(16) double sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int L = a.L, LL = L * L;
+    const int per_warp = LL + 2 * L + 2 * a.Mpad;
+    double *R = sm + warp * per_warp;     // R[i*L + j]: rate i -> j
+    double *Sn = R + LL;                  // [L] pivots
+    double *xx = Sn + L;                  // [L] unnormalised populations
+    double *rdown = xx + L;               // [Mpad] radiative u -> l rate per line
+    double *rup = rdown + a.Mpad;         // [Mpad] radiative l -> u rate per line
+    const int64_t p = (int64_t)blockIdx.x * a.wpb + warp;
+    if (p >= a.N) return;                 // whole warp leaves together
+
+    const double *po = a.pops_old + p * L;
+    const double Tp = a.T[p], nc = a.ncoll[p];
+    // per-line preconditioned radiative rates
+    for (int k = lane; k < a.M; k += 32) {
+        const int u = a.line_ul[k], l = a.line_ul[a.Mpad + k];
+        const double A = a.line_tab[a.Mpad + k], Bul = a.line_tab[2 * a.Mpad + k], Blu = a.line_tab[3 * a.Mpad + k];
+        const double x_l = po[l] * Blu, x_u = po[u] * Bul;
+        double net = x_l - x_u;
+        const double fl = 1e-30 * (x_l + x_u);
+        if (net < fl) net = fl;
+        const double S_old = net > 0.0 ? po[u] * A / net : 0.0;
+        const double Js = a.J[p * a.M + k], Ls = a.Lst[p * a.M + k];
+        const double Jeff = Js - Ls * S_old;
+        rdown[k] = fmax(A * (1.0 - Ls) + Bul * Jeff, 0.0);
+        rup[k] = fmax(Blu * Jeff, 0.0);
+    }
+    __syncwarp();
+    const double *E = a.level_tab, *g = a.level_tab + L;
+    const double ikT = 1.0 / (kKB * Tp);
+    for (int e = lane; e < LL; e += 32) {
+        const int i = e / L, j = e - i * L;
+        double v = 0.0;
+        if (i != j) {
+            const int kd = a.entry[e], ku = a.entry[LL + e], kc = a.entry[2 * LL + e];
+            if (kd >= 0) v += rdown[kd];
+            if (ku >= 0) v += rup[ku];
+            if (kc >= 0) {
+                const int cu = a.coll_ul[kc], cl = a.coll_ul[a.K + kc];
+                const double Cul = nc * a.Kul[kc];
+                if (i == cu)
+                    v += Cul;
+                else
+                    v += Cul * g[cu] / g[cl] * exp(-(E[cu] - E[cl]) * ikT);
+            }
+        }
+        R[e] = v;
+    }
+    __syncwarp();
+    // state reduction, highest level first
+    for (int n = L - 1; n >= 1; --n) {
+        double part = 0.0;
+        for (int j = lane; j < n; j += 32) part += R[n * L + j];
+        double s = warp_sum(part);
+        s = s > 0.0 ? s : 1e-300;
+        if (lane == 0) Sn[n] = s;
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) R[n * L + j] = R[n * L + j] / s;
+        __syncwarp();
+        const int nn = n * n;
+        for (int e = lane; e < nn; e += 32) {
+            const int i = e / n, j = e - i * n;
+            R[i * L + j] += R[i * L + n] * R[n * L + j];
+        }
+        __syncwarp();
+    }
+    if (lane == 0) xx[0] = 1.0;
+    __syncwarp();
+    for (int n = 1; n < L; ++n) {
+        double part = 0.0;
+        for (int i = lane; i < n; i += 32) part += xx[i] * R[i * L + n];
+        const double v = warp_sum(part);
+        if (lane == 0) xx[n] = v / Sn[n];
+        __syncwarp();
+    }
+    double part = 0.0;
+    for (int i = lane; i < L; i += 32) part += xx[i];
+    const double tot = warp_sum(part);
+    const double f = a.nspec[p] / tot;
+    for (int i = lane; i < L; i += 32) a.pops_out[p * L + i] = xx[i] * f;
+}
+
+}  // namespace
+
+mgt_status launch_stat_eq(mgt_model *m, cudaStream_t s)
+{
+    SEArgs a{};
+    a.N = m->N;
+    a.L = m->L;
+    a.M = m->M;
+    a.Mpad = m->Mpad;
+    a.K = m->K;
+    a.pops_old = m->d_pops_prev;
+    a.J = m->d_J;
+    a.Lst = m->d_Lst;
+    a.T = m->d_temp;
+    a.ncoll = m->d_ncoll;
+    a.nspec = m->d_nspec;
+    a.line_tab = m->d_line_tab;
+    a.line_ul = m->d_line_ul;
+    a.level_tab = m->d_level_tab;
+    a.Kul = m->d_coll_tab;
+    a.coll_ul = m->d_coll_ul;
+    a.entry = m->d_entry;
+    a.pops_out = m->d_pops;
+    const size_t per_warp = sizeof(double) * ((size_t)m->L * m->L + 2 * m->L + 2 * m->Mpad);
+    const size_t max_smem = 227 * 1024;
+    int wpb = (int)std::min<size_t>(kMaxWarpsPerBlock, max_smem / per_warp);
+    if (wpb < 1) return set_error(MGT_ERR_ARG, "statistical equilibrium: too many levels/lines for shared memory");
+    a.wpb = wpb;
+    const size_t smem = per_warp * wpb;
+    MGT_CUDA(cudaFuncSetAttribute(k_se, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_se<<<ceil_div(m->N, wpb), 32 * wpb, smem, s>>>(a);
+    MGT_LAUNCH_CHECK("k_se");
+    return MGT_OK;
+}
+
+}  // namespace mgt

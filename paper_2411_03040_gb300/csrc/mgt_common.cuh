@@ -1,0 +1,150 @@
+// Internal declarations of the GB300 line-transfer library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/magritte_gpu.h"
+
+namespace mgt {
+
+// Physical constants (CODATA 2018, exact SI definitions).
+constexpr double kH = 6.62607015e-34;
+constexpr double kC = 299792458.0;
+constexpr double kKB = 1.380649e-23;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kSqrtPi = 1.77245385090551602730;
+
+// Device error word codes (first error wins).
+enum DevErr : int { kDevOk = 0, kDevBounds = 1, kDevTimeout = 2 };
+
+constexpr int kMaxQuad = 64;
+constexpr int kMaxLevels = 64;
+constexpr int kMaxNgHist = 16;
+
+// One traced step in the single-precision layout, 16 bytes:
+//   x: point index c_k
+//   y: |x_{c_k} - x_{c_{k-1}}| in model length units (f32 bits)
+//   z: beta_k = n.(v_{c_k} - v_o)/c (f32 bits)
+//   w: (beta_k - beta_{k-1}) / wbar_k (f32 bits), wbar the segment's averaged
+//      relative line width (dimensionless, delta nu / nu)
+// c_0 = o, beta_0 = 0.
+using Step32 = int4;
+
+// Double-precision geometry of the same step: {dx, beta, dbeta/wbar, unused}.
+struct alignas(32) Step64 {
+    double dx, beta, dbw, pad;
+};
+
+struct NgState {
+    mgt_ng_opts opts{MGT_NG_NONE, 4, 8};
+    int n_slots = 0;
+    std::vector<int> hist;              // slot ids, oldest first
+    std::vector<double> G;              // Gram of residuals, kMaxNgHist^2 (row-major)
+    int pred_slot = -1, prev_pred_slot = -1;
+    bool have_prev_pred = false;
+    double *d_slots = nullptr;          // [n_slots][N*L]
+    double *d_partials = nullptr;       // block partials of the reductions
+    double *d_red = nullptr;            // reduced values (dots, maxrel, negatives)
+    double *h_red = nullptr;            // pinned host copy
+    size_t partial_cap = 0;
+};
+
+}  // namespace mgt
+
+struct mgt_model {
+    int device = 0;
+    int64_t N = 0;
+    int32_t R = 0, P = 0, Q = 0, L = 0, M = 0, Mpad = 0, K = 0, n_boundary = 0;
+    int64_t nnz = 0;
+    double mol_mass = 0, T_bg = 0, L_unit = 1.0;
+    mgt_solve_opts opts{0.35, 0, 0};
+
+    // host copies of the small tables
+    std::vector<double> energy, g, A, freq, Kul;
+    std::vector<int32_t> up, lo, cup, clo;
+    std::vector<int32_t> pairs;                // [P][2] (r, rb)
+    std::vector<double> xq, wq;                // Gauss-Hermite nodes / normalised weights
+    std::vector<double> nbg_line, hnu_kTbg, U_line;  // per padded line
+
+    // device: per point
+    double *d_pos = nullptr, *d_vel = nullptr, *d_temp = nullptr, *d_vturb2 = nullptr;
+    double *d_ncoll = nullptr, *d_nspec = nullptr, *d_w64 = nullptr;
+    float2 *d_w32 = nullptr;                   // {w, 1/w}
+    int32_t *d_nbr_off = nullptr, *d_nbrs = nullptr;
+    uint8_t *d_bnd = nullptr;
+    double *d_dirs = nullptr;
+    int2 *d_pairs = nullptr;
+    // device: per line / level tables
+    double *d_xq = nullptr, *d_wq = nullptr;
+    double *d_line_tab = nullptr;              // [8][Mpad]: nu, A, Bul, Blu, nbgmax, hnu_kTbg, U, unused
+    int32_t *d_line_ul = nullptr;              // [2][Mpad]: up, lo (-1 for padding)
+    double *d_level_tab = nullptr;             // [2][L]: energy, g
+    double *d_coll_tab = nullptr;              // [K]: K_ul
+    int32_t *d_coll_ul = nullptr;              // [2][K]
+    int16_t *d_entry = nullptr;                // [3][L*L]: radiative-down line, radiative-up line, collision
+    // device: state
+    double *d_pops = nullptr, *d_pops_prev = nullptr;   // [N][L]
+    float2 *d_line32 = nullptr;                // [N][Mpad] {chi~, S'}
+    double2 *d_line64 = nullptr;               // [N][Mpad]
+    double *d_J = nullptr, *d_Lst = nullptr;   // [N][M]
+    int *d_err = nullptr;                      // [4]
+    unsigned long long *d_count = nullptr;     // [4] counters (opacity floors, stalls)
+    // rays
+    int64_t *d_ray_off = nullptr;              // [R*N+1]
+    mgt::Step32 *d_steps32 = nullptr;
+    mgt::Step64 *d_steps64 = nullptr;
+    int64_t total_steps = 0;
+    int32_t max_half = 0;
+    int64_t n_stalls = 0;
+    bool traced = false, have_J = false, line_dirty = true;
+    int steps_width_mode = 0, steps64_width_mode = -1;
+
+    mgt::NgState ng;
+};
+
+namespace mgt {
+
+// error helpers (api.cu)
+void note_launch();
+mgt_status set_error(mgt_status s, const std::string &msg);
+mgt_status cuda_status(cudaError_t e, const char *what);
+mgt_status check_device_error(mgt_model *m, cudaStream_t s);
+
+// geometry / line-data kernels (k_geom.cu)
+mgt_status launch_widths(mgt_model *m, cudaStream_t s);
+mgt_status launch_lte(mgt_model *m, cudaStream_t s);
+mgt_status launch_line_data(mgt_model *m, cudaStream_t s);
+mgt_status trace_all(mgt_model *m, cudaStream_t s);
+mgt_status build_steps64(mgt_model *m, cudaStream_t s);
+
+// formal solution (k_fs.cu)
+mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s);
+
+// statistical equilibrium (k_se.cu)
+mgt_status launch_stat_eq(mgt_model *m, cudaStream_t s);
+
+// Ng (k_ng.cu)
+mgt_status ng_reset(mgt_model *m, cudaStream_t s);
+mgt_status ng_step(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *maxrel, cudaStream_t s);
+void ng_free(mgt_model *m);
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace mgt
+
+#define MGT_CUDA(call)                                                      \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return ::mgt::cuda_status(e_, #call);        \
+    } while (0)
+
+#define MGT_LAUNCH_CHECK(what)                                              \
+    do {                                                                    \
+        cudaError_t e_ = cudaGetLastError();                                \
+        if (e_ != cudaSuccess) return ::mgt::cuda_status(e_, what);         \
+        ::mgt::note_launch();                                               \
+    } while (0)

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libmgt.so (the C-ABI in include/magritte_gpu.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions carry the C names.  Arrays are numpy (host) or anything with
+``data_ptr()`` (a torch CUDA tensor, used with ``on_device=1``); ``stream`` is
+a ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or None (the legacy
+default stream).
+
+Loading fails loudly when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmgt.so")
+
+MGT_OK, MGT_ERR_ARG, MGT_ERR_CUDA, MGT_ERR_OOM, MGT_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
+MGT_ERR_SINGULAR, MGT_ERR_TIMEOUT, MGT_ERR_BOUNDS, MGT_ERR_STATE = 5, 6, 7, 8
+MGT_FP64, MGT_FP32_MIXED = 0, 1
+MGT_NG_NONE, MGT_NG_CLASSICAL, MGT_NG_ADAPTIVE = 0, 1, 2
+
+_P = ctypes.c_void_p
+_i64, _i32, _f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+
+
+class mgt_model_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_points", _i64), ("pos", _P), ("vel", _P), ("temp", _P), ("vturb2", _P), ("n_coll", _P),
+        ("n_spec", _P), ("nbr_offsets", _P), ("nbrs", _P), ("n_boundary", _i32), ("boundary", _P),
+        ("n_rays", _i32), ("dirs", _P), ("n_quad", _i32), ("mol_mass_kg", _f64), ("T_bg", _f64),
+        ("n_levels", _i32), ("energy_J", _P), ("g", _P), ("n_lines", _i32), ("up", _P), ("lo", _P),
+        ("A", _P), ("freq_Hz", _P), ("n_coll_trans", _i32), ("cup", _P), ("clo", _P), ("K_ul", _P),
+    ]
+
+
+class mgt_solve_opts(ctypes.Structure):
+    _fields_ = [("switch_threshold", _f64), ("width_mode", _i32), ("lines_per_thread", _i32)]
+
+
+class mgt_trace_stats(ctypes.Structure):
+    _fields_ = [("total_steps", _i64), ("n_stalls", _i64), ("max_half_ray", _i32), ("mean_half_ray", _f64)]
+
+
+class mgt_ng_opts(ctypes.Structure):
+    _fields_ = [("mode", _i32), ("n_steps", _i32), ("n_max", _i32)]
+
+
+class mgt_ali_opts(ctypes.Structure):
+    _fields_ = [("n_iter", _i32), ("precision", _i32), ("ng", mgt_ng_opts)]
+
+
+class mgt_ali_stats(ctypes.Structure):
+    _fields_ = [("iterations", _i32), ("ng_accepted", _i32), ("last_maxrel", _f64)]
+
+
+# name -> argtypes (every function returns an int status, except mgt_last_error)
+SIGNATURES = {
+    "mgt_model_create": [ctypes.POINTER(_P), ctypes.POINTER(mgt_model_desc), _P],
+    "mgt_model_destroy": [_P],
+    "mgt_set_solve_opts": [_P, ctypes.POINTER(mgt_solve_opts)],
+    "mgt_trace_rays": [_P, ctypes.POINTER(mgt_trace_stats), _P],
+    "mgt_get_rays": [_P, _P, _P, _P],
+    "mgt_set_populations": [_P, _P, _P],
+    "mgt_get_populations": [_P, _P, ctypes.c_int, _P],
+    "mgt_formal_solve": [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P],
+    "mgt_stat_equilibrium": [_P, _P, _P],
+    "mgt_ng_accelerate": [_P, ctypes.POINTER(mgt_ng_opts), ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(_f64), _P],
+    "mgt_ali_solve": [_P, ctypes.POINTER(mgt_ali_opts), ctypes.POINTER(mgt_ali_stats), _P],
+    "mgt_sync": [_P, _P],
+    "mgt_model_sizes": [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                        ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
+    "mgt_launch_count": [ctypes.POINTER(_i64)],
+    "mgt_last_error": [],
+}
+
+_lib = None
+
+
+class MgtError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where} failed with status {status}: {msg}")
+        self.status = status
+
+
+def load(path: str | None = None):
+    """Load libmgt.so (built by paper_2411_03040_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with paper_2411_03040_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(p)
+    for name, args in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "mgt_last_error" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status, where):
+    if status != MGT_OK:
+        raise MgtError(status, where, load().mgt_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Model:
+    """Owns one mgt_model handle and keeps its host inputs alive while in use."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().mgt_model_destroy(self.handle)
+        except Exception:
+            pass
+        self.handle = None
+
+    def close(self):
+        if self.handle:
+            _check(load().mgt_model_destroy(self.handle), "mgt_model_destroy")
+            self.handle = None
+
+
+def mgt_model_create(model, stream=None) -> Model:
+    """``model`` has the fields of paper_2411_03040_gb300.synth.Model."""
+    lib = load()
+    ln = model.lines
+    arr = lambda a, t: np.ascontiguousarray(a, dtype=t)
+    keep = dict(
+        pos=arr(model.pos, np.float64), vel=arr(model.vel, np.float64), temp=arr(model.temp, np.float64),
+        vturb2=arr(model.vturb2, np.float64), n_coll=arr(model.n_coll, np.float64),
+        n_spec=arr(model.n_spec, np.float64), off=arr(model.nbr_offsets, np.int64),
+        nbrs=arr(model.nbrs, np.int32), bnd=arr(model.boundary, np.int32), dirs=arr(model.dirs, np.float64),
+        E=arr(ln.energy_J, np.float64), g=arr(ln.g, np.float64), up=arr(ln.up, np.int32),
+        lo=arr(ln.lo, np.int32), A=arr(ln.A, np.float64), nu=arr(ln.freq_Hz, np.float64),
+        cup=arr(ln.cup, np.int32), clo=arr(ln.clo, np.int32), K=arr(ln.K_ul, np.float64))
+    k = keep
+    d = mgt_model_desc(
+        n_points=model.n_points, pos=_ptr(k["pos"]), vel=_ptr(k["vel"]), temp=_ptr(k["temp"]),
+        vturb2=_ptr(k["vturb2"]), n_coll=_ptr(k["n_coll"]), n_spec=_ptr(k["n_spec"]),
+        nbr_offsets=_ptr(k["off"]), nbrs=_ptr(k["nbrs"]), n_boundary=k["bnd"].shape[0], boundary=_ptr(k["bnd"]),
+        n_rays=k["dirs"].shape[0], dirs=_ptr(k["dirs"]), n_quad=int(model.n_quad),
+        mol_mass_kg=float(ln.mol_mass_kg), T_bg=float(model.T_bg), n_levels=int(ln.n_levels),
+        energy_J=_ptr(k["E"]), g=_ptr(k["g"]), n_lines=int(ln.n_lines), up=_ptr(k["up"]), lo=_ptr(k["lo"]),
+        A=_ptr(k["A"]), freq_Hz=_ptr(k["nu"]), n_coll_trans=int(k["cup"].shape[0]), cup=_ptr(k["cup"]),
+        clo=_ptr(k["clo"]), K_ul=_ptr(k["K"]))
+    h = ctypes.c_void_p()
+    _check(lib.mgt_model_create(ctypes.byref(h), ctypes.byref(d), _stream(stream)), "mgt_model_create")
+    return Model(h, keep)
+
+
+def mgt_model_sizes(m: Model):
+    n, r, l, mm, q = _i64(), _i32(), _i32(), _i32(), _i32()
+    _check(load().mgt_model_sizes(m.handle, ctypes.byref(n), ctypes.byref(r), ctypes.byref(l), ctypes.byref(mm),
+                                  ctypes.byref(q)), "mgt_model_sizes")
+    return dict(n_points=n.value, n_rays=r.value, n_levels=l.value, n_lines=mm.value, n_quad=q.value)
+
+
+def mgt_set_solve_opts(m: Model, switch_threshold=0.35, width_mode=0, lines_per_thread=0):
+    o = mgt_solve_opts(switch_threshold, width_mode, lines_per_thread)
+    _check(load().mgt_set_solve_opts(m.handle, ctypes.byref(o)), "mgt_set_solve_opts")
+
+
+def mgt_trace_rays(m: Model, stream=None) -> dict:
+    st = mgt_trace_stats()
+    _check(load().mgt_trace_rays(m.handle, ctypes.byref(st), _stream(stream)), "mgt_trace_rays")
+    return dict(total_steps=st.total_steps, n_stalls=st.n_stalls, max_half_ray=st.max_half_ray,
+                mean_half_ray=st.mean_half_ray)
+
+
+def mgt_get_rays(m: Model, stream=None):
+    s = mgt_model_sizes(m)
+    off = np.zeros(s["n_rays"] * s["n_points"] + 1, np.int64)
+    _check(load().mgt_get_rays(m.handle, _ptr(off), None, _stream(stream)), "mgt_get_rays")
+    idx = np.zeros(int(off[-1]), np.int32)
+    _check(load().mgt_get_rays(m.handle, None, _ptr(idx) if idx.size else None, _stream(stream)), "mgt_get_rays")
+    return off, idx
+
+
+def mgt_set_populations(m: Model, pops=None, stream=None):
+    p = None if pops is None else np.ascontiguousarray(pops, np.float64)
+    _check(load().mgt_set_populations(m.handle, _ptr(p), _stream(stream)), "mgt_set_populations")
+
+
+def mgt_get_populations(m: Model, out=None, stream=None):
+    s = mgt_model_sizes(m)
+    if out is None:
+        out = np.zeros((s["n_points"], s["n_levels"]), np.float64)
+    on_dev = 1 if hasattr(out, "data_ptr") else 0
+    _check(load().mgt_get_populations(m.handle, _ptr(out), on_dev, _stream(stream)), "mgt_get_populations")
+    return out
+
+
+def mgt_formal_solve(m: Model, precision=MGT_FP32_MIXED, Jbar=None, Lstar=None, want=True, stream=None):
+    """Returns (Jbar, Lstar) [M][N].  With ``want`` False nothing is copied out.
+    Given torch CUDA tensors the results are written on the device."""
+    if not want:
+        _check(load().mgt_formal_solve(m.handle, precision, None, None, 0, _stream(stream)), "mgt_formal_solve")
+        return None, None
+    s = mgt_model_sizes(m)
+    if Jbar is None:
+        Jbar = np.zeros((s["n_lines"], s["n_points"]), np.float64)
+    if Lstar is None:
+        Lstar = np.zeros((s["n_lines"], s["n_points"]), np.float64)
+    on_dev = 1 if hasattr(Jbar, "data_ptr") else 0
+    _check(load().mgt_formal_solve(m.handle, precision, _ptr(Jbar), _ptr(Lstar), on_dev, _stream(stream)),
+           "mgt_formal_solve")
+    return Jbar, Lstar
+
+
+def mgt_stat_equilibrium(m: Model, want=True, stream=None):
+    out = None
+    if want:
+        s = mgt_model_sizes(m)
+        out = np.zeros((s["n_points"], s["n_levels"]), np.float64)
+    _check(load().mgt_stat_equilibrium(m.handle, _ptr(out), _stream(stream)), "mgt_stat_equilibrium")
+    return out
+
+
+def mgt_ng_accelerate(m: Model, mode=MGT_NG_NONE, n_steps=4, n_max=8, stream=None):
+    o = mgt_ng_opts(mode, n_steps, n_max)
+    acc = ctypes.c_int(0)
+    mr = _f64(0.0)
+    _check(load().mgt_ng_accelerate(m.handle, ctypes.byref(o), ctypes.byref(acc), ctypes.byref(mr),
+                                    _stream(stream)), "mgt_ng_accelerate")
+    return bool(acc.value), mr.value
+
+
+def mgt_ali_solve(m: Model, n_iter=20, precision=MGT_FP32_MIXED, ng_mode=MGT_NG_NONE, n_steps=4, n_max=8,
+                  stream=None):
+    o = mgt_ali_opts(n_iter, precision, mgt_ng_opts(ng_mode, n_steps, n_max))
+    st = mgt_ali_stats()
+    _check(load().mgt_ali_solve(m.handle, ctypes.byref(o), ctypes.byref(st), _stream(stream)), "mgt_ali_solve")
+    return dict(iterations=st.iterations, ng_accepted=st.ng_accepted, last_maxrel=st.last_maxrel)
+
+
+def mgt_sync(m: Model, stream=None):
+    _check(load().mgt_sync(m.handle, _stream(stream)), "mgt_sync")
+
+
+def mgt_launch_count() -> int:
+    c = _i64(0)
+    _check(load().mgt_launch_count(ctypes.byref(c)), "mgt_launch_count")
+    return c.value
+
+
+def mgt_last_error() -> str:
+    return load().mgt_last_error().decode()

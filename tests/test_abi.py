@@ -1,0 +1,126 @@
+"""The C-ABI library builds, loads and exports what include/*.h declares.
+
+CPU only: no compute call reaches the GPU.  Invalid inputs are rejected by
+argument validation, which runs before any CUDA call.
+"""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "magritte_gpu.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2411_03040_gb300 import build, mgt
+    build.build()
+    return mgt.load()
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mgt_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    out = subprocess.run(["nm", "-D", "--defined-only", os.path.join(ROOT, "paper_2411_03040_gb300", "libmgt.so")],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(mgt_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+    # the binding declares every entry point
+    from paper_2411_03040_gb300 import mgt
+    assert set(names) <= set(mgt.SIGNATURES)
+
+
+def test_struct_layout_matches_header(tmp_path):
+    from paper_2411_03040_gb300 import mgt
+    structs = {
+        "mgt_model_desc": mgt.mgt_model_desc,
+        "mgt_solve_opts": mgt.mgt_solve_opts,
+        "mgt_trace_stats": mgt.mgt_trace_stats,
+        "mgt_ng_opts": mgt.mgt_ng_opts,
+        "mgt_ali_opts": mgt.mgt_ali_opts,
+        "mgt_ali_stats": mgt.mgt_ali_stats,
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(out[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
+
+
+def _small_model():
+    from paper_2411_03040_gb300 import synth
+    return synth.config_model(1, n_points=60)
+
+
+@pytest.mark.parametrize("breaker,fragment", [
+    (lambda m: setattr(m, "temp", np.where(np.arange(m.n_points) == 3, -1.0, m.temp)), "temperature"),
+    (lambda m: setattr(m, "pos", np.where(np.arange(3 * m.n_points).reshape(-1, 3) == 7, np.nan, m.pos)), "finite"),
+    (lambda m: setattr(m, "dirs", m.dirs[:-1]), "even"),
+    (lambda m: setattr(m, "dirs", m.dirs * 1.01), "unit"),
+    (lambda m: setattr(m, "nbrs", np.where(np.arange(m.nbrs.shape[0]) == 5, m.n_points, m.nbrs)), "neighbour"),
+    (lambda m: setattr(m, "n_quad", 65), "n_quad"),
+    (lambda m: setattr(m, "boundary", np.append(m.boundary, -2)), "boundary"),
+    (lambda m: setattr(m.lines, "A", -m.lines.A), "line A"),
+    (lambda m: setattr(m, "n_spec", np.zeros_like(m.n_spec)), "n_spec"),
+])
+def test_invalid_inputs_rejected_before_any_device_work(lib, breaker, fragment):
+    from paper_2411_03040_gb300 import mgt
+    m = _small_model()
+    breaker(m)
+    with pytest.raises(mgt.MgtError) as e:
+        mgt.mgt_model_create(m)
+    assert e.value.status == mgt.MGT_ERR_ARG
+    assert fragment in str(e.value)
+
+
+def test_unpaired_direction_rejected(lib):
+    from paper_2411_03040_gb300 import mgt
+    m = _small_model()
+    d = m.dirs.copy()
+    d[0] = d[0] + np.array([0.0, 1e-6, 0.0])
+    d[0] /= np.linalg.norm(d[0])
+    m.dirs = d
+    with pytest.raises(mgt.MgtError) as e:
+        mgt.mgt_model_create(m)
+    assert e.value.status == mgt.MGT_ERR_ARG and "antipode" in str(e.value)
+
+
+def test_null_arguments(lib):
+    assert lib.mgt_model_create(None, None, None) == 1
+    assert lib.mgt_trace_rays(None, None, None) == 1
+    assert lib.mgt_formal_solve(None, 0, None, None, 0, None) == 1
+    assert lib.mgt_model_destroy(None) == 0
+    assert b"NULL" in lib.mgt_last_error()
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    code = ("import paper_2411_03040_gb300.mgt as g\n"
+            f"g.LIB_PATH = {str(tmp_path / 'nope.so')!r}\n"
+            "try:\n    g.load()\nexcept RuntimeError as e:\n    print('RAISED', 'no CPU fallback' in str(e))\n")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT).stdout
+    assert "RAISED True" in out

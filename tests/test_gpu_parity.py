@@ -1,0 +1,280 @@
+"""CUDA path vs the CPU oracle, element by element, through the C-ABI.
+
+Tolerances (relative, max over elements): ray point lists bit-exact; J-bar
+and Lambda* 1e-10 on the FP64 path and 1e-4 on the FP32-mixed path;
+statistical-equilibrium populations fed by either path's own J-bar 1e-8
+(FP64); converged ALI populations 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2411_03040_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def mgt():
+    from paper_2411_03040_gb300 import build, mgt as binding
+    build.build()
+    binding.load()
+    return binding
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    assert a.shape == b.shape
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+def oracle_fields(model, rays, origins=None):
+    pops = O.lte_populations(model.temp, model.n_spec, model.lines.energy_J, model.lines.g)
+    chi, S, _ = O.line_chi_S(pops, model.lines)
+    return O.formal_solve(model, rays, chi, S, origins=origins)
+
+
+def gpu_fields(mgt, h, precision):
+    J, L = mgt.mgt_formal_solve(h, precision)
+    return J.T, L.T            # -> [N][M], the oracle's layout
+
+
+# ------------------------------------------------------------------- tracing
+def _models_for_trace():
+    out = [synth.config_model(1), synth.lattice_model(n_side=7),
+           synth.shell_model(4000, 3, 2, 5, seed=7, name="shell-4k"),
+           synth.shell_model(3000, 3, 2, 5, grf_sigma=5e3, seed=8, name="grf-3k")]
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "trace_tiny.json")))
+    for case in g["cases"]:
+        pos = np.asarray(case["pos"], np.float64)
+        off = np.zeros(len(case["nbrs"]) + 1, np.int64)
+        for i, v in enumerate(case["nbrs"]):
+            off[i + 1] = off[i] + len(v)
+        nb = np.concatenate([np.asarray(v, np.int32) for v in case["nbrs"]])
+        n = len(pos)
+        out.append(synth.Model(case["name"], pos, np.zeros_like(pos), np.full(n, 50.0), np.zeros(n),
+                               np.ones(n), np.ones(n), off, nb, np.asarray(case["boundary"], np.int32),
+                               np.asarray(case["dirs"], np.float64), 3,
+                               synth.linear_rotor(2, np.random.default_rng(0))))
+    return out
+
+
+@pytest.mark.parametrize("model", _models_for_trace(), ids=lambda m: m.name)
+def test_trace_bit_exact(mgt, model):
+    h = mgt.mgt_model_create(model)
+    st = mgt.mgt_trace_rays(h)
+    off, idx = mgt.mgt_get_rays(h)
+    ref = O.trace(model)
+    np.testing.assert_array_equal(off, ref.off)
+    np.testing.assert_array_equal(idx, ref.idx)
+    assert st["n_stalls"] == ref.stalls
+    assert st["total_steps"] == ref.off[-1]
+
+
+# --------------------------------------------------------- formal solution
+@pytest.fixture(scope="module")
+def sphere(mgt):
+    m = synth.config_model(1)
+    h = mgt.mgt_model_create(m)
+    mgt.mgt_trace_rays(h)
+    rays = O.trace(m)
+    J, L = oracle_fields(m, rays)
+    return m, h, rays, J, L
+
+
+def test_sphere_fp64_all_points(mgt, sphere):
+    m, h, rays, J, L = sphere
+    Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP64)
+    assert rel_err(Jg, J) < TOL64
+    assert rel_err(Lg, L) < TOL64
+
+
+def test_sphere_fp32_all_points(mgt, sphere):
+    m, h, rays, J, L = sphere
+    Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP32_MIXED)
+    assert rel_err(Jg, J) < TOL32
+    assert rel_err(Lg, L) < TOL32
+
+
+def test_fp32_is_deterministic(mgt, sphere):
+    m, h, *_ = sphere
+    a = gpu_fields(mgt, h, mgt.MGT_FP32_MIXED)
+    b = gpu_fields(mgt, h, mgt.MGT_FP32_MIXED)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_device_outputs_match_host_outputs(mgt, sphere):
+    torch = pytest.importorskip("torch")
+    m, h, *_ = sphere
+    Jh, Lh = mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED)
+    Jd = torch.empty(Jh.shape, dtype=torch.float64, device="cuda")
+    Ld = torch.empty(Lh.shape, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream()
+    mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED, Jd, Ld, stream=s)
+    s.synchronize()
+    np.testing.assert_array_equal(Jd.cpu().numpy(), Jh)
+    np.testing.assert_array_equal(Ld.cpu().numpy(), Lh)
+
+
+@pytest.mark.parametrize("lpt", [4, 8])
+def test_ragged_line_count_both_schedules(mgt, lpt):
+    # 6 levels -> 5 lines: one full group of 4 plus a ragged one, or one
+    # group of 8 with three padding lines
+    m = synth.sphere_model(700, n_levels=6, nside=1, n_quad=9, seed=77, name="ragged")
+    h = mgt.mgt_model_create(m)
+    mgt.mgt_set_solve_opts(h, lines_per_thread=lpt)
+    mgt.mgt_trace_rays(h)
+    rays = O.trace(m)
+    J, L = oracle_fields(m, rays)
+    Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP32_MIXED)
+    assert rel_err(Jg, J) < TOL32 and rel_err(Lg, L) < TOL32
+    Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP64)
+    assert rel_err(Jg, J) < TOL64 and rel_err(Lg, L) < TOL64
+
+
+@pytest.mark.parametrize("grf", [0.0, 5e3], ids=["shell", "shell-grf"])
+def test_shell_41_levels_sampled(mgt, grf):
+    # the 41-level rotor with 50 (or 40) bins on a small shell outflow;
+    # with the random velocity field most segments take the erf branch
+    q = 50 if grf == 0.0 else 40
+    m = synth.shell_model(5000, 41, 2, q, grf_sigma=grf, seed=9 if grf == 0 else 10,
+                          name="shell-5k")
+    h = mgt.mgt_model_create(m)
+    mgt.mgt_trace_rays(h)
+    rays = O.trace(m)
+    rng = np.random.default_rng(1)
+    orig = np.sort(np.concatenate([rng.choice(m.n_points, 30, replace=False), m.boundary[:4]]))
+    J, L = oracle_fields(m, rays, orig)
+    Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP64)
+    assert rel_err(Jg[orig], J) < TOL64
+    assert rel_err(Lg[orig], L) < TOL64
+    Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP32_MIXED)
+    assert rel_err(Jg[orig], J) < TOL32
+    assert rel_err(Lg[orig], L) < TOL32
+
+
+def test_single_point_model_is_background(mgt):
+    # no neighbours: every half-ray is empty, u = I_bg, Lambda* = 0
+    lines = synth.linear_rotor(3, np.random.default_rng(0))
+    m = synth.Model("single", np.zeros((1, 3)), np.zeros((1, 3)), np.array([40.0]), np.array([1e6]),
+                    np.array([1e9]), np.array([1e3]), np.zeros(2, np.int64), np.zeros(0, np.int32),
+                    np.array([0], np.int32), synth.healpix_directions(1), 7, lines)
+    h = mgt.mgt_model_create(m)
+    st = mgt.mgt_trace_rays(h)
+    assert st["total_steps"] == 0
+    x, w = O.gauss_hermite(7)
+    for prec in (mgt.MGT_FP64, mgt.MGT_FP32_MIXED):
+        Jg, Lg = gpu_fields(mgt, h, prec)
+        for k in range(lines.n_lines):
+            dnu = O.line_width(lines.freq_Hz[k], 40.0, 1e6, lines.mol_mass_kg)
+            exact = np.sum(w * O.planck(lines.freq_Hz[k] + x * dnu, m.T_bg))
+            assert abs(Jg[0, k] / exact - 1) < (TOL64 if prec == mgt.MGT_FP64 else TOL32)
+        assert np.all(Lg == 0.0)
+
+
+# ----------------------------------------------------- statistical equilibrium
+def test_stat_equilibrium_parity(mgt, sphere):
+    m, h, rays, J, L = sphere
+    mgt.mgt_set_populations(h, None)
+    mgt.mgt_formal_solve(h, mgt.MGT_FP64, want=False)
+    pg = mgt.mgt_stat_equilibrium(h)
+    p0 = O.lte_populations(m.temp, m.n_spec, m.lines.energy_J, m.lines.g)
+    po = O.stat_equilibrium(p0, J, L, m.temp, m.n_coll, m.n_spec, m.lines)
+    assert rel_err(pg, po) < 1e-8
+    np.testing.assert_allclose(pg.sum(1), m.n_spec, rtol=1e-13)
+
+
+def test_stat_equilibrium_tiny_populations_41_levels(mgt):
+    # cold gas: upper levels ~1e-60 of the ground level keep full relative accuracy
+    m = synth.shell_model(1500, 41, 1, 7, seed=12, name="cold")
+    m.temp = np.full(m.n_points, 25.0)
+    h = mgt.mgt_model_create(m)
+    mgt.mgt_trace_rays(h)
+    mgt.mgt_formal_solve(h, mgt.MGT_FP64, want=False)
+    pg = mgt.mgt_stat_equilibrium(h)
+    rays = O.trace(m)
+    J, L = oracle_fields(m, rays)
+    p0 = O.lte_populations(m.temp, m.n_spec, m.lines.energy_J, m.lines.g)
+    po = O.stat_equilibrium(p0, J, L, m.temp, m.n_coll, m.n_spec, m.lines)
+    assert (po / m.n_spec[:, None]).min() < 1e-50
+    assert rel_err(pg, po) < 1e-8
+
+
+# ------------------------------------------------------------------- ALI + Ng
+@pytest.fixture(scope="module")
+def ali_ref():
+    m = synth.config_model(1, n_points=400)
+    rays = O.trace(m)
+    ref, ch = O.ali_solve(m, rays, n_iter=60)
+    return m, rays, ref
+
+
+@pytest.mark.parametrize("mode,prec", [(0, 0), (1, 0), (2, 0), (1, 1), (2, 1)],
+                         ids=["plain64", "classical64", "adaptive64", "classical32", "adaptive32"])
+def test_ali_converges_to_oracle_fixed_point(mgt, ali_ref, mode, prec):
+    m, rays, ref = ali_ref
+    h = mgt.mgt_model_create(m)
+    mgt.mgt_trace_rays(h)
+    n_iter = 60 if mode == 0 else 24
+    st = mgt.mgt_ali_solve(h, n_iter=n_iter, precision=prec, ng_mode=mode, n_steps=4, n_max=8)
+    assert st["iterations"] == n_iter
+    if mode != 0:
+        assert st["ng_accepted"] >= 1
+    pg = mgt.mgt_get_populations(h)
+    assert rel_err(pg, ref) < 1e-5
+
+
+def test_ng_step_by_step_matches_oracle_controller(mgt, ali_ref):
+    # the same ALI sequence on both sides with classical Ng: the accept
+    # pattern and the populations after every step agree
+    m, rays, _ = ali_ref
+    h = mgt.mgt_model_create(m)
+    mgt.mgt_trace_rays(h)
+    pops = O.lte_populations(m.temp, m.n_spec, m.lines.energy_J, m.lines.g)
+    ng = O.NgClassical(4)
+    ng.reset((pops / m.n_spec[:, None]).ravel())
+    for it in range(9):
+        chi, S, _ = O.line_chi_S(pops, m.lines)
+        J, L = O.formal_solve(m, rays, chi, S)
+        new = O.stat_equilibrium(pops, J, L, m.temp, m.n_coll, m.n_spec, m.lines)
+        mr = O.maxrel(new, pops)
+        x, acc = ng.push((new / m.n_spec[:, None]).ravel())
+        if acc:
+            new = x.reshape(pops.shape) * m.n_spec[:, None]
+        pops = new
+        mgt.mgt_formal_solve(h, mgt.MGT_FP64, want=False)
+        mgt.mgt_stat_equilibrium(h, want=False)
+        acc_g, mr_g = mgt.mgt_ng_accelerate(h, mgt.MGT_NG_CLASSICAL, n_steps=4)
+        assert acc_g == acc, it
+        assert abs(mr_g / mr - 1) < 1e-6
+        assert rel_err(mgt.mgt_get_populations(h), pops) < 1e-8
+
+
+# ------------------------------------------------ full size, sampled outputs
+@pytest.mark.slow
+def test_full_size_shell_100k_sampled(mgt):
+    # the benchmark workload in its launch configuration; the oracle computes
+    # sampled origins one by one
+    m = synth.config_model(2)
+    h = mgt.mgt_model_create(m)
+    mgt.mgt_trace_rays(h)
+    rays = O.trace(m)
+    off, idx = mgt.mgt_get_rays(h)
+    np.testing.assert_array_equal(off, rays.off)
+    np.testing.assert_array_equal(idx, rays.idx)
+    rng = np.random.default_rng(2)
+    orig = np.sort(rng.choice(m.n_points, 24, replace=False))
+    J, L = oracle_fields(m, rays, orig)
+    Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP32_MIXED)
+    assert rel_err(Jg[orig], J) < TOL32
+    assert rel_err(Lg[orig], L) < TOL32
+    assert np.all(np.isfinite(Jg)) and np.all(Lg >= 0) and np.all(Lg < 1)
+    Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP64)
+    assert rel_err(Jg[orig], J) < TOL64
+    assert rel_err(Lg[orig], L) < TOL64
