@@ -102,6 +102,9 @@ typedef struct {
     int32_t width_mode;       /* dnu_bar of a segment: 0 = from the averaged temperature
                                  and turbulence (default), 1 = mean of the endpoint widths */
     int32_t lines_per_thread; /* FP32 kernel schedule: 0 = auto, else 4 or 8 */
+    int32_t schedule;         /* 0 = auto (bulk-copy staging of ray chunks when one origin
+                                 fills a block), 1 = per-thread gathers from global memory */
+    int32_t reserved;         /* must be 0 */
 } mgt_solve_opts;
 
 typedef struct {

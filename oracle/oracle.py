@@ -410,9 +410,12 @@ class NgClassical:
 
 class NgAdaptive:
     """Adaptive Ng (Sec. 4.2): after each regular iteration with m >= 3
-    iterates since the last reset, compute the running prediction P_m from all
-    of them; use it when max-rel-change(P_m, P_{m-1}) < max-rel-change(x_m,
-    x_{m-1}) (P_2 := x_2), or unconditionally once m reaches N_max."""
+    iterates since the last prediction was used, compute the running
+    prediction P_m from all of them; use it when max-rel-change(P_m, P_{m-1})
+    < max-rel-change(x_m, x_{m-1}) (P_2 := x_2), or unconditionally once m
+    reaches N_max.  A prediction chosen for use but holding a negative
+    population is not used and the history restarts from x_m; an exactly
+    singular Gram matrix restarts it too."""
 
     def __init__(self, n_max=8):
         self.n_max = n_max
@@ -432,11 +435,14 @@ class NgAdaptive:
         if m < 3:
             return x, False
         pred = ng_predict(self.hist)
-        if pred is None or not np.all(pred >= 0):
+        if pred is None:
             self.reset(x)
             return x, False
-        accept = maxrel(pred, self.prev_pred) < maxrel(self.hist[-1], self.hist[-2]) or m >= self.n_max
-        if accept:
+        use = maxrel(pred, self.prev_pred) < maxrel(self.hist[-1], self.hist[-2]) or m >= self.n_max
+        if use:
+            if not np.all(pred >= 0):
+                self.reset(x)
+                return x, False
             self.reset(pred)
             return pred, True
         self.prev_pred = pred

@@ -211,7 +211,7 @@ static mgt_status validate(const mgt_model_desc *d)
 
 static void free_model(mgt_model *m)
 {
-    void *ptrs[] = {m->d_pos, m->d_vel, m->d_temp, m->d_vturb2, m->d_ncoll, m->d_nspec, m->d_w64, m->d_w32,
+    void *ptrs[] = {m->d_nbr_pos, m->d_order, m->d_pos, m->d_vel, m->d_temp, m->d_vturb2, m->d_ncoll, m->d_nspec, m->d_w64, m->d_w32,
                     m->d_nbr_off, m->d_nbrs, m->d_bnd, m->d_dirs, m->d_pairs, m->d_xq, m->d_wq, m->d_line_tab,
                     m->d_line_ul, m->d_level_tab, m->d_coll_tab, m->d_coll_ul, m->d_entry, m->d_pops,
                     m->d_pops_prev, m->d_line32, m->d_line64, m->d_J, m->d_Lst, m->d_err, m->d_count,
@@ -241,6 +241,41 @@ template <typename T> static mgt_status upload(T *dst, const T *src, size_t n, c
         mgt_status st_ = (x);              \
         if (st_ != MGT_OK) return st_;     \
     } while (0)
+
+// Points sorted along a Morton (Z-order) curve of their positions: walks and
+// origins visited in this order keep neighbouring work close in memory.
+static std::vector<int32_t> morton_order(const double *pos, int64_t N)
+{
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = 0; i < N; ++i)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], pos[3 * i + d]);
+            hi[d] = std::max(hi[d], pos[3 * i + d]);
+        }
+    auto spread = [](uint64_t v) {
+        v &= 0x1fffff;
+        v = (v | v << 32) & 0x1f00000000ffffULL;
+        v = (v | v << 16) & 0x1f0000ff0000ffULL;
+        v = (v | v << 8) & 0x100f00f00f00f00fULL;
+        v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+        v = (v | v << 2) & 0x1249249249249249ULL;
+        return v;
+    };
+    std::vector<std::pair<uint64_t, int32_t>> key(N);
+    for (int64_t i = 0; i < N; ++i) {
+        uint64_t k = 0;
+        for (int d = 0; d < 3; ++d) {
+            const double span = hi[d] > lo[d] ? hi[d] - lo[d] : 1.0;
+            const uint64_t q = (uint64_t)std::min(2097151.0, std::max(0.0, (pos[3 * i + d] - lo[d]) / span * 2097151.0));
+            k |= spread(q) << d;
+        }
+        key[i] = {k, (int32_t)i};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<int32_t> out(N);
+    for (int64_t i = 0; i < N; ++i) out[i] = key[i].second;
+    return out;
+}
 
 static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_t s)
 {
@@ -331,6 +366,8 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
     MGT_TRY(dalloc(&m->d_w32, N));
     MGT_TRY(dalloc(&m->d_nbr_off, N + 1));
     MGT_TRY(dalloc(&m->d_nbrs, m->nnz));
+    MGT_TRY(dalloc(&m->d_nbr_pos, 3 * m->nnz));
+    MGT_TRY(dalloc(&m->d_order, N));
     MGT_TRY(dalloc(&m->d_bnd, N));
     MGT_TRY(dalloc(&m->d_dirs, 3 * (size_t)m->R));
     MGT_TRY(dalloc(&m->d_pairs, m->P));
@@ -344,8 +381,8 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
     MGT_TRY(dalloc(&m->d_entry, entry.size()));
     MGT_TRY(dalloc(&m->d_pops, N * L));
     MGT_TRY(dalloc(&m->d_pops_prev, N * L));
-    MGT_TRY(dalloc(&m->d_line32, N * Mp));
-    MGT_TRY(dalloc(&m->d_line64, N * Mp));
+    MGT_TRY(dalloc(&m->d_line32, N * row_stride32(Mp)));
+    MGT_TRY(dalloc(&m->d_line64, N * row_stride64(Mp)));
     MGT_TRY(dalloc(&m->d_J, N * m->M));
     MGT_TRY(dalloc(&m->d_Lst, N * m->M));
     MGT_TRY(dalloc(&m->d_err, 4));
@@ -359,6 +396,16 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
     MGT_TRY(upload(m->d_nspec, d->n_spec, N, s));
     MGT_TRY(upload(m->d_nbr_off, off32.data(), N + 1, s));
     MGT_TRY(upload(m->d_nbrs, d->nbrs, m->nnz, s));
+    {
+        std::vector<double> np(3 * (size_t)m->nnz);
+        for (int64_t k = 0; k < m->nnz; ++k)
+            for (int c = 0; c < 3; ++c) np[3 * k + c] = d->pos[3 * (int64_t)d->nbrs[k] + c];
+        MGT_TRY(upload(m->d_nbr_pos, np.data(), np.size(), s));
+        MGT_CUDA(cudaStreamSynchronize(s));   // np goes out of scope
+        const std::vector<int32_t> ord = morton_order(d->pos, N);
+        MGT_TRY(upload(m->d_order, ord.data(), (size_t)N, s));
+        MGT_CUDA(cudaStreamSynchronize(s));
+    }
     MGT_TRY(upload(m->d_bnd, bnd.data(), N, s));
     MGT_TRY(upload(m->d_dirs, d->dirs, 3 * (size_t)m->R, s));
     std::vector<int2> pr(m->P);
@@ -456,8 +503,10 @@ mgt_status mgt_model_destroy(mgt_model *m)
 mgt_status mgt_set_solve_opts(mgt_model *m, const mgt_solve_opts *o)
 {
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
-    mgt_solve_opts d{0.35, 0, 0};
+    mgt_solve_opts d{0.35, 0, 0, 0, 0};
     if (o) {
+        if (o->schedule != 0 && o->schedule != 1) return set_error(MGT_ERR_ARG, "schedule must be 0 or 1");
+        if (o->reserved != 0) return set_error(MGT_ERR_ARG, "reserved must be 0");
         if (!(o->switch_threshold >= 0.0) || !std::isfinite(o->switch_threshold))
             return set_error(MGT_ERR_ARG, "switch_threshold must be >= 0");
         if (o->width_mode != 0 && o->width_mode != 1) return set_error(MGT_ERR_ARG, "width_mode must be 0 or 1");

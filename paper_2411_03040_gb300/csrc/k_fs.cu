@@ -1,12 +1,20 @@
 // Formal solution of the line transfer equation along every ray pair, frequency
 // bin and line, reduced into J-bar and Lambda* (the hot loop).
 //
-// Mapping: one CTA per origin point (or OPB origins when Q * groups is small);
-// each thread owns one Gauss-Hermite bin q and LPT consecutive lines and loops
-// over all ray pairs.  Every thread of an origin walks the same ray, so trip
-// counts never diverge; the per-step, line-independent work (comoving
-// frequency, Gaussian, the trapezoid/erf switch, erf) is done once per (q,
-// step) and shared by the thread's LPT lines.
+// Mapping: each thread owns one Gauss-Hermite bin q and LPT consecutive lines
+// of one origin and loops over all ray pairs.  All threads of an origin walk
+// the same ray, so trip counts never diverge; the per-step, line-independent
+// work (comoving frequency, Gaussian, the trapezoid/erf switch, erf) is done
+// once per (q, step) and shared by the thread's LPT lines.
+//
+// Two kernels:
+//  * k_fs_staged: one CTA per origin.  Each half-ray is cut into chunks of CH
+//    steps; warp 0 moves the next chunk's step records and point rows (line
+//    data + width) into shared memory with bulk asynchronous copies
+//    (cp.async.bulk, completion on an mbarrier) while the CTA eliminates the
+//    current chunk from shared memory.
+//  * k_fs_gather: several origins per CTA (small bin x line counts); every
+//    thread gathers its rows straight from global memory.
 //
 // Second-order (Feautrier) system along a ray with points d = 0..D-1 and
 // segment optical depths, rows -A u_{d-1} + (1 + A + C) u_d - C u_{d+1} = S_d,
@@ -20,6 +28,8 @@
 // dtau -> 0 is exact and FP32 keeps its relative accuracy.  At the origin,
 // with h = (a_L + a_R)/2 from the two adjacent segments,
 //     u = (S h + Y_L + Y_R) / (h + P_L + P_R),  Lambda*_oo = h / (h + P_L + P_R).
+#include <algorithm>
+
 #include "mgt_common.cuh"
 
 namespace mgt {
@@ -55,67 +65,64 @@ template <> struct Prec<double> {
 
 struct FSArgs {
     int64_t N;
-    int R, P, Q, M, Mpad, Gtot, Gb, OPB;
+    int R, P, Q, M, Mpad, RS, Gtot, Gb, OPB;
     const int2 *pairs;
     const int64_t *ray_off;
     const Step32 *s32;
     const Step64 *s64;
-    const float2 *w32;
-    const double *w64;
-    const void *line;          // float2* or double2*, [N][Mpad] {chi~', S'}
+    const void *line;          // float2* or double2*, [N][RS] rows (see row_stride32/64)
+    const int32_t *order;      // origin visiting order (space-filling curve), [N]
     const double *xq, *wq;
     const double *line_tab;    // [8][Mpad]
-    const double *vel, *dirs;
+    const double *vel, *dirs, *w64;
     double thr;
     int width_mode;
     double *J, *Lst;           // [N][M]
+    int *err;
 };
 
+// Geometry of one traced step in the solver's precision.
 template <typename T> struct StepG {
-    int64_t idx;
     T dx, beta, dbw;
 };
 
-template <typename T> __device__ __forceinline__ StepG<T> get_step(const FSArgs &a, int64_t s);
+template <typename T> __device__ __forceinline__ StepG<T> step_from(const void *p);
 
-template <> __device__ __forceinline__ StepG<float> get_step<float>(const FSArgs &a, int64_t s)
+template <> __device__ __forceinline__ StepG<float> step_from<float>(const void *p)
 {
-    int4 v = __ldg(a.s32 + s);
-    return {(int64_t)v.x, __int_as_float(v.y), __int_as_float(v.z), __int_as_float(v.w)};
+    const int4 v = *reinterpret_cast<const int4 *>(p);
+    return {__int_as_float(v.y), __int_as_float(v.z), __int_as_float(v.w)};
 }
 
-template <> __device__ __forceinline__ StepG<double> get_step<double>(const FSArgs &a, int64_t s)
+template <> __device__ __forceinline__ StepG<double> step_from<double>(const void *p)
 {
-    int idx = __ldg(&a.s32[s].x);
-    const double2 *p = reinterpret_cast<const double2 *>(a.s64 + s);
-    double2 v0 = __ldg(p), v1 = __ldg(p + 1);
-    return {(int64_t)idx, v0.x, v0.y, v1.x};
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    const double2 v0 = q[0], v1 = q[1];
+    return {v0.x, v0.y, v1.x};
 }
 
-template <typename T> struct WG {
-    T w, iw;
-};
+template <typename T> __device__ __forceinline__ StepG<T> step_global(const FSArgs &a, int64_t s);
 
-template <typename T> __device__ __forceinline__ WG<T> get_w(const FSArgs &a, int64_t c);
-
-template <> __device__ __forceinline__ WG<float> get_w<float>(const FSArgs &a, int64_t c)
+template <> __device__ __forceinline__ StepG<float> step_global<float>(const FSArgs &a, int64_t s)
 {
-    float2 v = __ldg(a.w32 + c);
-    return {v.x, v.y};
+    const int4 v = __ldg(a.s32 + s);
+    return {__int_as_float(v.y), __int_as_float(v.z), __int_as_float(v.w)};
 }
 
-template <> __device__ __forceinline__ WG<double> get_w<double>(const FSArgs &a, int64_t c)
+template <> __device__ __forceinline__ StepG<double> step_global<double>(const FSArgs &a, int64_t s)
 {
-    double w = __ldg(a.w64 + c);
-    return {w, 1.0 / w};
+    const double2 *q = reinterpret_cast<const double2 *>(a.s64 + s);
+    const double2 v0 = __ldg(q), v1 = __ldg(q + 1);
+    return {v0.x, v0.y, v1.x};
 }
 
-template <int LPT> __device__ __forceinline__ void load_line(const float2 *p, float (&chi)[LPT], float (&S)[LPT])
+// LPT lines {chi~', S'} of one row (global or shared), 16-byte aligned.
+template <int LPT> __device__ __forceinline__ void load_lines(const float2 *p, float (&chi)[LPT], float (&S)[LPT])
 {
     const float4 *v = reinterpret_cast<const float4 *>(p);
 #pragma unroll
     for (int i = 0; i < LPT / 2; ++i) {
-        float4 x = __ldg(v + i);
+        const float4 x = v[i];
         chi[2 * i] = x.x;
         S[2 * i] = x.y;
         chi[2 * i + 1] = x.z;
@@ -123,11 +130,11 @@ template <int LPT> __device__ __forceinline__ void load_line(const float2 *p, fl
     }
 }
 
-template <int LPT> __device__ __forceinline__ void load_line(const double2 *p, double (&chi)[LPT], double (&S)[LPT])
+template <int LPT> __device__ __forceinline__ void load_lines(const double2 *p, double (&chi)[LPT], double (&S)[LPT])
 {
 #pragma unroll
     for (int i = 0; i < LPT; ++i) {
-        double2 x = __ldg(p + i);
+        const double2 x = p[i];
         chi[i] = x.x;
         S[i] = x.y;
     }
@@ -136,23 +143,127 @@ template <int LPT> __device__ __forceinline__ void load_line(const double2 *p, d
 // The trapezoid / erf decision re-taken in FP64 for a segment whose FP32
 // Doppler-shift ratio lies within rounding of the threshold, so that both
 // precisions (and the FP64 reference) branch alike.
-__device__ __noinline__ bool trapezoid_fp64(const FSArgs &a, int r, int64_t o, int64_t c_far, int64_t c_near,
-                                            double xq64, double wo64)
+__device__ __noinline__ bool trapezoid_fp64(const FSArgs &a, int r, int64_t c_far, int64_t c_near, double xq64,
+                                            double wo64)
 {
     const double *n = a.dirs + 3 * r;
     const double *vf = a.vel + 3 * c_far, *vn = a.vel + 3 * c_near;
-    double dbeta = (n[0] * (vf[0] - vn[0]) + n[1] * (vf[1] - vn[1]) + n[2] * (vf[2] - vn[2])) / kC;
-    double wf = a.w64[c_far], wn = a.w64[c_near];
-    double wbar = a.width_mode == 0 ? sqrt(0.5 * (wf * wf + wn * wn)) : 0.5 * (wf + wn);
-    double du = (1.0 + xq64 * wo64) * dbeta / wbar;
-    (void)o;
+    const double dbeta = (n[0] * (vf[0] - vn[0]) + n[1] * (vf[1] - vn[1]) + n[2] * (vf[2] - vn[2])) / kC;
+    const double wf = a.w64[c_far], wn = a.w64[c_near];
+    const double wbar = a.width_mode == 0 ? sqrt(0.5 * (wf * wf + wn * wn)) : 0.5 * (wf + wn);
+    const double du = (1.0 + xq64 * wo64) * dbeta / wbar;
     return fabs(du) < a.thr;
 }
 
-// Eliminate one half-ray from its far end inward to the origin.
+// Line-independent coefficients of one segment: dtau_line = cf chi_far + cn chi_near.
+//   du    : reduced Doppler shift near minus far, in units of the averaged width
+//   trap  : trapezoid branch (|du| below the threshold)
+template <typename T>
+__device__ __forceinline__ void segment_coefs(bool trap, T dx, T du, T z_f, T g_f, T w_f, T g_n, T w_n, int width_mode,
+                                              T &cf, T &cn)
+{
+    if (trap) {
+        cf = T(0.5) * dx * g_f;
+        cn = T(0.5) * dx * g_n;
+    } else {
+        const T iwbar = width_mode == 0 ? Prec<T>::rsqrt_(T(0.5) * (w_f * w_f + w_n * w_n)) : T(2) / (w_f + w_n);
+        const T ubf = z_f * iwbar, ubn = ubf + du;
+        T E;
+        if (ubf > T(0) && ubn > T(0))
+            E = Prec<T>::erfc_(ubf) - Prec<T>::erfc_(ubn);
+        else if (ubf < T(0) && ubn < T(0))
+            E = Prec<T>::erfc_(-ubn) - Prec<T>::erfc_(-ubf);
+        else
+            E = Prec<T>::erf_(ubn) - Prec<T>::erf_(ubf);
+        const T kk = dx * T(kSqrtPi) * E * iwbar / (T(4) * du);
+        cf = kk * w_f;
+        cn = kk * w_n;
+    }
+}
+
+// One elimination row for the thread's LPT lines.
 template <typename T, int LPT>
-__device__ __forceinline__ void sweep(const FSArgs &a, int64_t o, int r, int line0, T Aq, T Bq, const T *Ibg,
-                                      double xq64, double wo64, T (&P)[LPT], T (&Y)[LPT], T (&aa)[LPT])
+__device__ __forceinline__ void eliminate_row(T cf, T cn, const T (&chi_f)[LPT], const T (&S_f)[LPT],
+                                              const T (&chi_n)[LPT], T (&P)[LPT], T (&Y)[LPT], T (&aa)[LPT])
+{
+#pragma unroll
+    for (int l = 0; l < LPT; ++l) {
+        const T b = cf * chi_f[l] + cn * chi_n[l];
+        const T h = T(0.5) * (aa[l] + b);
+        const T H = h + P[l];
+        const T q = Prec<T>::rcp(T(1) + b * H);
+        P[l] = H * q;
+        Y[l] = (S_f[l] * h + Y[l]) * q;
+        aa[l] = b;
+    }
+}
+
+// Combine both halves at the origin and accumulate w_q u and w_q Lambda*
+// (compensated sums kept in shared memory, one column per thread).
+template <typename T, int LPT>
+__device__ __forceinline__ void combine_accumulate(T wqn, const T (&So)[LPT], const T (&PL)[LPT], const T (&YL)[LPT],
+                                                   const T (&aL)[LPT], const T (&PR)[LPT], const T (&YR)[LPT],
+                                                   const T (&aR)[LPT], T *acc, int bd, int tid)
+{
+#pragma unroll
+    for (int l = 0; l < LPT; ++l) {
+        const T h = T(0.5) * (aL[l] + aR[l]);
+        const T inv = Prec<T>::rcp(h + PL[l] + PR[l]);
+        const T u = (So[l] * h + YL[l] + YR[l]) * inv;
+        const T Ls = h * inv;
+        T *sJ = acc + (0 * LPT + l) * bd + tid, *cJ = acc + (1 * LPT + l) * bd + tid;
+        T *sL = acc + (2 * LPT + l) * bd + tid, *cL = acc + (3 * LPT + l) * bd + tid;
+        T y = wqn * u - *cJ, tt = *sJ + y;
+        *cJ = (tt - *sJ) - y;
+        *sJ = tt;
+        y = wqn * Ls - *cL;
+        tt = *sL + y;
+        *cL = (tt - *sL) - y;
+        *sL = tt;
+    }
+}
+
+// B_nu_q(T_bg) / U_line for the thread's bin and lines (depends on the origin
+// through nu_q = nu (1 + x_q w_o)).
+template <typename T, int LPT>
+__device__ __forceinline__ void background(const FSArgs &a, int line0, double xq64, double wo64, T (&Ibg)[LPT])
+{
+    const T f = T(1) + T(xq64) * T(wo64);
+#pragma unroll
+    for (int l = 0; l < LPT; ++l) {
+        const int k = line0 + l;
+        const double hk = a.line_tab[5 * a.Mpad + k], nbg = a.line_tab[4 * a.Mpad + k];
+        Ibg[l] = (k < a.M && hk > 0.0) ? Prec<T>::bg(f, T(hk)) / T(nbg) : T(0);
+    }
+}
+
+// Final reduction over bins: red[2][OPB][Mb][Q] -> J, Lstar of the block's lines.
+__device__ __forceinline__ void reduce_out(const FSArgs &a, const double *red, int Mb, int mline0, int64_t o_base,
+                                           bool ordered)
+{
+    const double wdir = 2.0 / a.R;
+    for (int e = threadIdx.x; e < a.OPB * Mb; e += blockDim.x) {
+        const int lo2 = e / Mb, lb = e - lo2 * Mb;
+        const int line = mline0 + lb;
+        const int64_t oi = o_base + lo2;
+        if (oi >= a.N || line >= a.M) continue;
+        const int64_t o2 = ordered ? (int64_t)a.order[oi] : oi;
+        double sJ = 0.0, sL = 0.0;
+        for (int qq = 0; qq < a.Q; ++qq) {
+            sJ += red[((0 * a.OPB + lo2) * Mb + lb) * a.Q + qq];
+            sL += red[((1 * a.OPB + lo2) * Mb + lb) * a.Q + qq];
+        }
+        a.J[o2 * a.M + line] = sJ * wdir * a.line_tab[6 * a.Mpad + line];
+        a.Lst[o2 * a.M + line] = sL * wdir;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gather kernel: OPB origins per CTA, rows read from global memory.
+// ---------------------------------------------------------------------------
+template <typename T, int LPT>
+__device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, int line0, T Aq, T Bq, const T *Ibg,
+                                             double xq64, double wo64, T (&P)[LPT], T (&Y)[LPT], T (&aa)[LPT])
 {
     using LD = typename Prec<T>::LD;
     const LD *line = reinterpret_cast<const LD *>(a.line);
@@ -167,61 +278,33 @@ __device__ __forceinline__ void sweep(const FSArgs &a, int64_t o, int r, int lin
     }
     if (n == 0) return;
     const T thr = (T)a.thr;
-    StepG<T> sf = get_step<T>(a, s0 + n - 1);
+    int64_t c_f = a.s32[s0 + n - 1].x;
+    StepG<T> sf = step_global<T>(a, s0 + n - 1);
     T chi_f[LPT], S_f[LPT];
-    load_line<LPT>(line + sf.idx * a.Mpad + line0, chi_f, S_f);
-    WG<T> wf = get_w<T>(a, sf.idx);
+    load_lines<LPT>(line + c_f * a.RS + line0, chi_f, S_f);
+    LD wf = line[c_f * a.RS + a.Mpad];
     T z_f = Aq + Bq * sf.beta;
-    T g_f = Prec<T>::gauss(z_f * wf.iw);
+    T g_f = Prec<T>::gauss(z_f * wf.y);
     for (int k = n; k >= 1; --k) {
-        StepG<T> sn;
+        int64_t c_n = o;
+        StepG<T> sn{T(0), T(0), T(0)};
         if (k > 1) {
-            sn = get_step<T>(a, s0 + k - 2);
-        } else {
-            sn.idx = o;
-            sn.dx = T(0);
-            sn.beta = T(0);
-            sn.dbw = T(0);
+            c_n = a.s32[s0 + k - 2].x;
+            sn = step_global<T>(a, s0 + k - 2);
         }
         T chi_n[LPT], S_n[LPT];
-        load_line<LPT>(line + sn.idx * a.Mpad + line0, chi_n, S_n);
-        WG<T> wn = get_w<T>(a, sn.idx);
+        load_lines<LPT>(line + c_n * a.RS + line0, chi_n, S_n);
+        const LD wn = line[c_n * a.RS + a.Mpad];
         const T z_n = Aq + Bq * sn.beta;
-        const T g_n = Prec<T>::gauss(z_n * wn.iw);
-        // reduced Doppler shift across the segment, near minus far, in units
-        // of the segment-averaged width
+        const T g_n = Prec<T>::gauss(z_n * wn.y);
         const T du = -Bq * sf.dbw;
         bool trap = fabs(du) < thr;
-        if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(2e-5) * thr)
-            trap = trapezoid_fp64(a, r, o, sf.idx, sn.idx, xq64, wo64);
+        if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(2e-5) * thr) trap = trapezoid_fp64(a, r, c_f, c_n, xq64, wo64);
         T cf, cn;
-        if (trap) {
-            cf = T(0.5) * sf.dx * g_f;
-            cn = T(0.5) * sf.dx * g_n;
-        } else {
-            const T iwbar = a.width_mode == 0 ? Prec<T>::rsqrt_(T(0.5) * (wf.w * wf.w + wn.w * wn.w))
-                                              : T(2) / (wf.w + wn.w);
-            const T ubf = z_f * iwbar, ubn = ubf + du;
-            T E;
-            if (ubf > T(0) && ubn > T(0))
-                E = Prec<T>::erfc_(ubf) - Prec<T>::erfc_(ubn);
-            else if (ubf < T(0) && ubn < T(0))
-                E = Prec<T>::erfc_(-ubn) - Prec<T>::erfc_(-ubf);
-            else
-                E = Prec<T>::erf_(ubn) - Prec<T>::erf_(ubf);
-            const T kk = sf.dx * T(kSqrtPi) * E * iwbar / (T(4) * du);
-            cf = kk * wf.w;
-            cn = kk * wn.w;
-        }
+        segment_coefs<T>(trap, sf.dx, du, z_f, g_f, (T)wf.x, g_n, (T)wn.x, a.width_mode, cf, cn);
+        eliminate_row<T, LPT>(cf, cn, chi_f, S_f, chi_n, P, Y, aa);
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
-            const T b = cf * chi_f[l] + cn * chi_n[l];
-            const T h = T(0.5) * (aa[l] + b);
-            const T H = h + P[l];
-            const T q = Prec<T>::rcp(T(1) + b * H);
-            P[l] = H * q;
-            Y[l] = (S_f[l] * h + Y[l]) * q;
-            aa[l] = b;
             chi_f[l] = chi_n[l];
             S_f[l] = S_n[l];
         }
@@ -229,17 +312,18 @@ __device__ __forceinline__ void sweep(const FSArgs &a, int64_t o, int r, int lin
         g_f = g_n;
         wf = wn;
         sf = sn;
+        c_f = c_n;
     }
 }
 
-template <typename T, int LPT> __global__ void __launch_bounds__(256) k_fs(FSArgs a)
+template <typename T, int LPT> __global__ void __launch_bounds__(256) k_fs_gather(FSArgs a)
 {
     using LD = typename Prec<T>::LD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int bd = blockDim.x, tid = threadIdx.x;
     const int QG = a.Q * a.Gb;
-    const int Mb = a.Gb * LPT;                       // lines covered by this block
-    T *acc = reinterpret_cast<T *>(smem_raw);        // [4][LPT][bd]: J, J-comp, L, L-comp
+    const int Mb = a.Gb * LPT;
+    T *acc = reinterpret_cast<T *>(smem_raw);                       // [4][LPT][bd]
     double *red = reinterpret_cast<double *>(acc + 4 * LPT * bd);   // [2][OPB][Mb][Q]
 
     const int lo_ = tid / QG, rem = tid - lo_ * QG, gl = rem / a.Q, q = rem - gl * a.Q;
@@ -247,58 +331,27 @@ template <typename T, int LPT> __global__ void __launch_bounds__(256) k_fs(FSArg
     const int line0 = gg * LPT;
     const int64_t o = (int64_t)blockIdx.x * a.OPB + lo_;
     const bool active = lo_ < a.OPB && o < a.N && gg < a.Gtot;
-    const int mline0 = blockIdx.y * Mb;              // first line of this block
 
-    // background B_nu_q(T_bg) / U_line for this thread's bin and lines; it
-    // depends on the origin through nu_q = nu (1 + x_q w_o)
-    T Ibg[LPT];
-    const double xq64 = active ? a.xq[q] : 0.0;
-    const double wo64 = active ? a.w64[o] : 0.0;
     if (active) {
-        const T f = T(1) + T(xq64) * T(wo64);
+        const double xq64 = a.xq[q], wo64 = a.w64[o];
+        T Ibg[LPT];
+        background<T, LPT>(a, line0, xq64, wo64, Ibg);
 #pragma unroll
-        for (int l = 0; l < LPT; ++l) {
-            const int k = line0 + l;
-            const double hk = a.line_tab[5 * a.Mpad + k], nbg = a.line_tab[4 * a.Mpad + k];
-            Ibg[l] = (k < a.M && hk > 0.0) ? Prec<T>::bg(f, T(hk)) / T(nbg) : T(0);
-        }
-#pragma unroll
-        for (int l = 0; l < LPT; ++l) {
-            acc[(0 * LPT + l) * bd + tid] = T(0);
-            acc[(1 * LPT + l) * bd + tid] = T(0);
-            acc[(2 * LPT + l) * bd + tid] = T(0);
-            acc[(3 * LPT + l) * bd + tid] = T(0);
-        }
-        const T x = T(xq64), wo = T(wo64);
-        const T Aq = x * wo, Bq = T(1) + Aq;
+        for (int l = 0; l < LPT; ++l)
+            for (int c = 0; c < 4; ++c) acc[(c * LPT + l) * bd + tid] = T(0);
+        const T Aq = T(xq64) * T(wo64), Bq = T(1) + Aq;
         const T wqn = T(a.wq[q]);
         const LD *line = reinterpret_cast<const LD *>(a.line);
         T So[LPT], dummy[LPT];
-        load_line<LPT>(line + o * a.Mpad + line0, dummy, So);
+        load_lines<LPT>(line + o * a.RS + line0, dummy, So);
         for (int p = 0; p < a.P; ++p) {
             const int2 pr = a.pairs[p];
             T PL[LPT], YL[LPT], aL[LPT], PR[LPT], YR[LPT], aR[LPT];
-            sweep<T, LPT>(a, o, pr.y, line0, Aq, Bq, Ibg, xq64, wo64, PL, YL, aL);
-            sweep<T, LPT>(a, o, pr.x, line0, Aq, Bq, Ibg, xq64, wo64, PR, YR, aR);
-#pragma unroll
-            for (int l = 0; l < LPT; ++l) {
-                const T h = T(0.5) * (aL[l] + aR[l]);
-                const T inv = Prec<T>::rcp(h + PL[l] + PR[l]);
-                const T u = (So[l] * h + YL[l] + YR[l]) * inv;
-                const T Ls = h * inv;
-                // compensated (Kahan) accumulation of w_q u and w_q Lambda*
-                T *sJ = acc + (0 * LPT + l) * bd + tid, *cJ = acc + (1 * LPT + l) * bd + tid;
-                T *sL = acc + (2 * LPT + l) * bd + tid, *cL = acc + (3 * LPT + l) * bd + tid;
-                T y = wqn * u - *cJ, tt = *sJ + y;
-                *cJ = (tt - *sJ) - y;
-                *sJ = tt;
-                y = wqn * Ls - *cL;
-                tt = *sL + y;
-                *cL = (tt - *sL) - y;
-                *sL = tt;
-            }
+            sweep_gather<T, LPT>(a, o, pr.y, line0, Aq, Bq, Ibg, xq64, wo64, PL, YL, aL);
+            sweep_gather<T, LPT>(a, o, pr.x, line0, Aq, Bq, Ibg, xq64, wo64, PR, YR, aR);
+            combine_accumulate<T, LPT>(wqn, So, PL, YL, aL, PR, YR, aR, acc, bd, tid);
         }
-        const int lb = gl * LPT;                     // line offset within the block
+        const int lb = gl * LPT;
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
             if (line0 + l < a.M) {
@@ -310,23 +363,311 @@ template <typename T, int LPT> __global__ void __launch_bounds__(256) k_fs(FSArg
         }
     }
     __syncthreads();
-    const double wdir = 2.0 / a.R;
-    for (int e = tid; e < a.OPB * Mb; e += bd) {
-        const int lo2 = e / Mb, lb = e - lo2 * Mb;
-        const int line = mline0 + lb;
-        const int64_t o2 = (int64_t)blockIdx.x * a.OPB + lo2;
-        if (o2 >= a.N || line >= a.M) continue;
-        double sJ = 0.0, sL = 0.0;
-        for (int qq = 0; qq < a.Q; ++qq) {
-            sJ += red[((0 * a.OPB + lo2) * Mb + lb) * a.Q + qq];
-            sL += red[((1 * a.OPB + lo2) * Mb + lb) * a.Q + qq];
-        }
-        a.J[o2 * a.M + line] = sJ * wdir * a.line_tab[6 * a.Mpad + line];
-        a.Lst[o2 * a.M + line] = sL * wdir;
+    reduce_out(a, red, Mb, blockIdx.y * Mb, (int64_t)blockIdx.x * a.OPB, false);
+}
+
+// ---------------------------------------------------------------------------
+// Staged kernel: one origin per CTA, ray chunks moved to shared memory by
+// bulk asynchronous copies one chunk ahead of the elimination.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.b32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase with the given parity; gives up after ~2 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > 2000000000ull) return false;
     }
 }
 
-template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_t s)
+struct Chunk {
+    int p, h;          // pair, half (0: the pair's second direction, 1: its first)
+    int64_t s0;        // first step record of the half-ray
+    int n;             // half-ray length
+    int k_lo, k_hi;    // steps covered by the chunk
+};
+
+__device__ __forceinline__ void half_extent(const FSArgs &a, int64_t o, int p, int h, int64_t &s0, int &n)
+{
+    const int2 pr = a.pairs[p];
+    const int r = h == 0 ? pr.y : pr.x;
+    const int64_t t = (int64_t)r * a.N + o;
+    s0 = a.ray_off[t];
+    n = (int)(a.ray_off[t + 1] - s0);
+}
+
+// First chunk at or after half (p, h); false if none.
+__device__ __forceinline__ bool first_chunk_from(const FSArgs &a, int64_t o, int p, int h, int CH, Chunk &c)
+{
+    for (; p < a.P; ++p, h = 0) {
+        for (; h < 2; ++h) {
+            int64_t s0;
+            int n;
+            half_extent(a, o, p, h, s0, n);
+            if (n > 0) {
+                c = {p, h, s0, n, max(1, n - CH + 1), n};
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool next_chunk(const FSArgs &a, int64_t o, const Chunk &cur, int CH, Chunk &nx)
+{
+    if (cur.k_lo > 1) {
+        nx = cur;
+        nx.k_hi = cur.k_lo - 1;
+        nx.k_lo = max(1, nx.k_hi - CH + 1);
+        return true;
+    }
+    return cur.h == 0 ? first_chunk_from(a, o, cur.p, 1, CH, nx) : first_chunk_from(a, o, cur.p + 1, 0, CH, nx);
+}
+
+// Issue the copies of chunk c into one buffer (warp 0).  Point slot j holds
+// c_{k_lo-1+j} (c_0 = o); step slot j holds the record of step k_lo-1+j
+// (slot 0 unused when k_lo = 1).
+template <typename T>
+__device__ __forceinline__ void issue_chunk(const FSArgs &a, int64_t o, const Chunk &c, unsigned char *steps_buf,
+                                            unsigned char *rows_buf, uint64_t *bar, int rowB, int lane)
+{
+    constexpr int SB = sizeof(T) == 4 ? 16 : 32;
+    const int npts = c.k_hi - c.k_lo + 2;
+    const int kf = max(1, c.k_lo - 1);
+    const int nsteps = c.k_hi - kf + 1;
+    const uint32_t bytes = (uint32_t)(npts * rowB + nsteps * SB);
+    const unsigned char *lines = reinterpret_cast<const unsigned char *>(a.line);
+    if (lane == 0) mbar_expect_tx(bar, bytes);
+    __syncwarp();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (lane < npts) {
+        const int k = c.k_lo - 1 + lane;
+        const int64_t pt = k == 0 ? o : (int64_t)__ldg(&a.s32[c.s0 + k - 1].x);
+        bulk_g2s(rows_buf + lane * rowB, lines + pt * (int64_t)rowB, (uint32_t)rowB, bar);
+    }
+    if (lane == 0) {
+        const void *src = sizeof(T) == 4 ? (const void *)(a.s32 + c.s0 + kf - 1) : (const void *)(a.s64 + c.s0 + kf - 1);
+        bulk_g2s(steps_buf + (kf - (c.k_lo - 1)) * SB, src, (uint32_t)(nsteps * SB), bar);
+    }
+}
+
+template <typename T, int LPT, int CH> __global__ void __launch_bounds__(256) k_fs_staged(FSArgs a)
+{
+    using LD = typename Prec<T>::LD;
+    constexpr int SB = sizeof(T) == 4 ? 16 : 32;
+    constexpr int NPT = CH + 1;
+    static_assert(NPT <= 32, "one point row per producer lane");
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rowB = a.RS * (int)sizeof(LD);
+    const int Mb = a.Gb * LPT;
+
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);                   // [2]
+    int *abort_flag = reinterpret_cast<int *>(smem + 16);
+    unsigned char *stage = smem + 128;                                    // steps [2][NPT][SB], rows [2][NPT][rowB]
+    unsigned char *steps_s = stage;
+    unsigned char *rows_s = stage + 2 * NPT * SB;
+    const int stage_bytes = 2 * NPT * (SB + rowB);
+    const int red_bytes = 2 * Mb * a.Q * (int)sizeof(double);
+    unsigned char *after = stage + ((max(stage_bytes, red_bytes) + 127) & ~127);
+    T *ibg = reinterpret_cast<T *>(after);                                // [Mb][Q]
+    T *acc = ibg + ((Mb * a.Q + 3) & ~3);                                 // [4][LPT][bd]
+    double *red = reinterpret_cast<double *>(stage);                      // reuses the staging area at the end
+
+    const int64_t o = a.order[blockIdx.x];
+    const int gl = tid / a.Q, q = tid - gl * a.Q;
+    const int gg = blockIdx.y * a.Gb + gl;
+    const int line0 = gg * LPT;
+    const bool active = tid < a.Q * a.Gb && gg < a.Gtot;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const double xq64 = active ? a.xq[q] : 0.0, wo64 = active ? a.w64[o] : 0.0;
+    if (active) {
+        T Ibg[LPT];
+        background<T, LPT>(a, line0, xq64, wo64, Ibg);
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) {
+            ibg[(gl * LPT + l) * a.Q + q] = Ibg[l];
+            for (int c = 0; c < 4; ++c) acc[(c * LPT + l) * bd + tid] = T(0);
+        }
+    }
+    __syncthreads();
+
+    Chunk cur;
+    const bool any = first_chunk_from(a, o, 0, 0, CH, cur);
+    if (any && warp == 0) issue_chunk<T>(a, o, cur, steps_s, rows_s, &bar[0], rowB, lane);
+
+    const T Aq = T(xq64) * T(wo64), Bq = T(1) + Aq;
+    const T thr = (T)a.thr;
+    const T wqn = active ? T(a.wq[q]) : T(0);
+    int ci = 0;                 // chunks consumed
+    bool ok = true;
+    T PL[LPT], YL[LPT], aL[LPT], P[LPT], Y[LPT], aa[LPT];
+    T chi_f[LPT], S_f[LPT];
+    T z_f = 0, g_f = 0, w_f = 1;
+    for (int p = 0; p < a.P; ++p) {
+        const int2 pr = a.pairs[p];
+        for (int h = 0; h < 2; ++h) {
+            const int r = h == 0 ? pr.y : pr.x;
+            int64_t s0;
+            int n;
+            half_extent(a, o, p, h, s0, n);
+#pragma unroll
+            for (int l = 0; l < LPT; ++l) {
+                P[l] = T(1);
+                Y[l] = active ? ibg[(gl * LPT + l) * a.Q + q] : T(0);
+                aa[l] = T(0);
+            }
+            for (int k_hi = n; k_hi >= 1; k_hi -= CH) {
+                const int k_lo = max(1, k_hi - CH + 1);
+                // everyone is done with the buffer about to be refilled; stop
+                // together if any wait gave up
+                if (__syncthreads_or(!ok)) {
+                    if (tid == 0) *abort_flag = 1;
+                    goto done;
+                }
+                if (warp == 0) {
+                    Chunk nx;
+                    const Chunk c{p, h, s0, n, k_lo, k_hi};
+                    if (next_chunk(a, o, c, CH, nx))
+                        issue_chunk<T>(a, o, nx, steps_s + ((ci + 1) & 1) * NPT * SB,
+                                       rows_s + ((ci + 1) & 1) * NPT * rowB, &bar[(ci + 1) & 1], rowB, lane);
+                }
+                ok = mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1);
+                if (ok && active) {
+                    const unsigned char *Sb = steps_s + (ci & 1) * NPT * SB;
+                    const LD *Rb = reinterpret_cast<const LD *>(rows_s + (ci & 1) * NPT * rowB);
+                    if (k_hi == n) {            // far end of the half-ray
+                        const int jf = k_hi - k_lo + 1;
+                        const LD *row = Rb + jf * a.RS;
+                        load_lines<LPT>(row + line0, chi_f, S_f);
+                        const LD wv = row[a.Mpad];
+                        w_f = (T)wv.x;
+                        z_f = Aq + Bq * step_from<T>(Sb + jf * SB).beta;
+                        g_f = Prec<T>::gauss(z_f * (T)wv.y);
+                    }
+                    for (int k = k_hi; k >= k_lo; --k) {
+                        const int jf = k - k_lo + 1, jn = jf - 1;
+                        const StepG<T> sf = step_from<T>(Sb + jf * SB);
+                        const T beta_n = k > 1 ? step_from<T>(Sb + jn * SB).beta : T(0);
+                        const LD *row = Rb + jn * a.RS;
+                        T chi_n[LPT], S_n[LPT];
+                        load_lines<LPT>(row + line0, chi_n, S_n);
+                        const LD wv = row[a.Mpad];
+                        const T w_n = (T)wv.x;
+                        const T z_n = Aq + Bq * beta_n;
+                        const T g_n = Prec<T>::gauss(z_n * (T)wv.y);
+                        const T du = -Bq * sf.dbw;
+                        bool trap = fabs(du) < thr;
+                        if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(2e-5) * thr) {
+                            const int64_t c_f = __ldg(&a.s32[s0 + k - 1].x);
+                            const int64_t c_n = k > 1 ? (int64_t)__ldg(&a.s32[s0 + k - 2].x) : o;
+                            trap = trapezoid_fp64(a, r, c_f, c_n, xq64, wo64);
+                        }
+                        T cf, cn;
+                        segment_coefs<T>(trap, sf.dx, du, z_f, g_f, w_f, g_n, w_n, a.width_mode, cf, cn);
+                        eliminate_row<T, LPT>(cf, cn, chi_f, S_f, chi_n, P, Y, aa);
+#pragma unroll
+                        for (int l = 0; l < LPT; ++l) {
+                            chi_f[l] = chi_n[l];
+                            S_f[l] = S_n[l];
+                        }
+                        z_f = z_n;
+                        g_f = g_n;
+                        w_f = w_n;
+                    }
+                }
+                ++ci;
+            }
+            if (h == 0) {
+#pragma unroll
+                for (int l = 0; l < LPT; ++l) {
+                    PL[l] = P[l];
+                    YL[l] = Y[l];
+                    aL[l] = aa[l];
+                }
+            } else if (active) {
+                T So[LPT], dummy[LPT];
+                load_lines<LPT>(reinterpret_cast<const LD *>(a.line) + o * a.RS + line0, dummy, So);
+                combine_accumulate<T, LPT>(wqn, So, PL, YL, aL, P, Y, aa, acc, bd, tid);
+            }
+        }
+    }
+done:
+    __syncthreads();
+    if (*abort_flag) {
+        // give in-flight copies a bounded chance to land before the CTA exits
+        if (tid == 0) {
+            atomicCAS(a.err, 0, (int)kDevTimeout);
+            mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1);
+            mbar_wait_bounded(&bar[(ci + 1) & 1], ((ci + 1) >> 1) & 1);
+        }
+        return;
+    }
+    if (active) {
+        const int lb = gl * LPT;
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) {
+            if (line0 + l < a.M) {
+                red[(0 * Mb + lb + l) * a.Q + q] =
+                    (double)acc[(0 * LPT + l) * bd + tid] - (double)acc[(1 * LPT + l) * bd + tid];
+                red[(1 * Mb + lb + l) * a.Q + q] =
+                    (double)acc[(2 * LPT + l) * bd + tid] - (double)acc[(3 * LPT + l) * bd + tid];
+            }
+        }
+    }
+    __syncthreads();
+    reduce_out(a, red, Mb, blockIdx.y * Mb, (int64_t)blockIdx.x, true);
+}
+
+constexpr int kChunk = 31;
+
+template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_t s, int force_gather)
 {
     FSArgs a{};
     a.N = m->N;
@@ -335,6 +676,7 @@ template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_
     a.Q = m->Q;
     a.M = m->M;
     a.Mpad = m->Mpad;
+    a.RS = sizeof(T) == 4 ? row_stride32(m->Mpad) : row_stride64(m->Mpad);
     a.Gtot = (m->M + LPT - 1) / LPT;              // groups covering the real lines
     int gb = a.Gtot;
     while (gb > 1 && a.Q * gb > 256) --gb;
@@ -344,27 +686,47 @@ template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_
     a.ray_off = m->d_ray_off;
     a.s32 = m->d_steps32;
     a.s64 = m->d_steps64;
-    a.w32 = m->d_w32;
-    a.w64 = m->d_w64;
     a.line = sizeof(T) == 4 ? (const void *)m->d_line32 : (const void *)m->d_line64;
+    a.order = m->d_order;
     a.xq = m->d_xq;
     a.wq = m->d_wq;
     a.line_tab = m->d_line_tab;
     a.vel = m->d_vel;
     a.dirs = m->d_dirs;
+    a.w64 = m->d_w64;
     a.thr = m->opts.switch_threshold;
     a.width_mode = m->opts.width_mode;
     a.J = m->d_J;
     a.Lst = m->d_Lst;
-    int threads = a.OPB * a.Q * a.Gb;
-    int bd = ((threads + 31) / 32) * 32;
-    if (bd > 1024) return set_error(MGT_ERR_ARG, "formal solve: too many bins x line groups per block");
+    a.err = m->d_err;
     const int Mb = a.Gb * LPT;
-    size_t smem = sizeof(T) * 4 * LPT * bd + sizeof(double) * 2 * a.OPB * Mb * a.Q;
-    MGT_CUDA(cudaFuncSetAttribute(k_fs<T, LPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // one origin per CTA when bins x groups fill a CTA: the staged kernel
+    const bool staged = !force_gather && a.Q * a.Gb >= 96;
+    if (staged) {
+        a.OPB = 1;
+        const int threads = a.Q * a.Gb;
+        const int bd = ((threads + 31) / 32) * 32;
+        constexpr int SB = sizeof(T) == 4 ? 16 : 32;
+        const int rowB = a.RS * (int)sizeof(typename Prec<T>::LD);
+        const int stage_bytes = 2 * (kChunk + 1) * (SB + rowB);
+        const int red_bytes = 2 * Mb * a.Q * (int)sizeof(double);
+        const size_t smem = 128 + ((std::max(stage_bytes, red_bytes) + 127) & ~127) +
+                            sizeof(T) * (((Mb * a.Q + 3) & ~3) + 4 * LPT * bd);
+        MGT_CUDA(cudaFuncSetAttribute(k_fs_staged<T, LPT, kChunk>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        dim3 grid((unsigned)m->N, (unsigned)ceil_div(a.Gtot, a.Gb));
+        k_fs_staged<T, LPT, kChunk><<<grid, bd, smem, s>>>(a);
+        MGT_LAUNCH_CHECK("k_fs_staged");
+        return MGT_OK;
+    }
+    const int threads = a.OPB * a.Q * a.Gb;
+    const int bd = ((threads + 31) / 32) * 32;
+    if (bd > 256) return set_error(MGT_ERR_ARG, "formal solve: too many bins x line groups per block");
+    const size_t smem = sizeof(T) * 4 * LPT * bd + sizeof(double) * 2 * a.OPB * Mb * a.Q;
+    MGT_CUDA(cudaFuncSetAttribute(k_fs_gather<T, LPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)ceil_div(m->N, a.OPB), (unsigned)ceil_div(a.Gtot, a.Gb));
-    k_fs<T, LPT><<<grid, bd, smem, s>>>(a);
-    MGT_LAUNCH_CHECK("k_fs");
+    k_fs_gather<T, LPT><<<grid, bd, smem, s>>>(a);
+    MGT_LAUNCH_CHECK("k_fs_gather");
     return MGT_OK;
 }
 
@@ -381,8 +743,9 @@ mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s)
 {
     const int lpt = fs_lines_per_thread(m, p);
     if (m->Mpad % lpt != 0) return set_error(MGT_ERR_STATE, "line padding does not match the schedule");
-    if (p == MGT_FP64) return launch_typed<double, 4>(m, s);
-    return lpt == 4 ? launch_typed<float, 4>(m, s) : launch_typed<float, 8>(m, s);
+    const int force_gather = m->opts.schedule == 1;   // 0: automatic, 1: gather kernel
+    if (p == MGT_FP64) return launch_typed<double, 4>(m, s, force_gather);
+    return lpt == 4 ? launch_typed<float, 4>(m, s, force_gather) : launch_typed<float, 8>(m, s, force_gather);
 }
 
 }  // namespace mgt

@@ -62,7 +62,8 @@ mgt_status launch_lte(mgt_model *m, cudaStream_t s)
 //           line centre, so that chi(nu) = chi~ exp(-u^2);
 //   S'    = S^{ij} / U_line, U_line = (2 h nu^3/c^2) max(n_bg(nu), 1e-30)
 //         = n_u B_ul / (net * nbgmax).
-// Padding lines (line >= M) get zero opacity and source.
+// Row layout: entries 0..Mpad-1 are the lines (zero for padding lines),
+// entry Mpad holds {w, 1/w} of the point, the FP32 row ends with a zero pair.
 // ---------------------------------------------------------------------------
 __global__ void k_line_data(int64_t N, int L, int M, int Mpad, const double *__restrict__ pops,
                             const double *__restrict__ w64, const double *__restrict__ line_tab,
@@ -70,11 +71,12 @@ __global__ void k_line_data(int64_t N, int L, int M, int Mpad, const double *__r
                             float2 *__restrict__ out32, double2 *__restrict__ out64,
                             unsigned long long *__restrict__ n_floor)
 {
+    const int RS = row_stride32(Mpad), RS64 = row_stride64(Mpad);
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= N * Mpad) return;
-    int64_t p = t / Mpad;
-    int k = (int)(t - p * Mpad);
-    double chi = 0.0, S = 0.0;
+    if (t >= N * RS) return;
+    int64_t p = t / RS;
+    int k = (int)(t - p * RS);
+    double a0 = 0.0, a1 = 0.0;
     if (k < M) {
         int u = line_ul[k], l = line_ul[Mpad + k];
         double Bul = line_tab[2 * Mpad + k], Blu = line_tab[3 * Mpad + k];
@@ -87,17 +89,20 @@ __global__ void k_line_data(int64_t N, int L, int M, int Mpad, const double *__r
             atomicAdd(n_floor, 1ULL);
         }
         if (net > 0.0) {
-            chi = kH * net * Lunit / (4.0 * kPi * kSqrtPi * w64[p]);
-            S = b / (net * nbgmax);
+            a0 = kH * net * Lunit / (4.0 * kPi * kSqrtPi * w64[p]);
+            a1 = b / (net * nbgmax);
         }
+    } else if (k == Mpad) {
+        a0 = w64[p];
+        a1 = 1.0 / a0;
     }
-    out32[t] = make_float2((float)chi, (float)S);
-    if (out64) out64[t] = make_double2(chi, S);
+    out32[t] = make_float2((float)a0, (float)a1);
+    if (out64 && k < RS64) out64[p * RS64 + k] = make_double2(a0, a1);
 }
 
 mgt_status launch_line_data(mgt_model *m, cudaStream_t s)
 {
-    int64_t n = m->N * m->Mpad;
+    int64_t n = m->N * row_stride32(m->Mpad);
     k_line_data<<<ceil_div(n, 256), 256, 0, s>>>(m->N, m->L, m->M, m->Mpad, m->d_pops, m->d_w64, m->d_line_tab,
                                                 m->d_line_ul, m->L_unit, m->d_line32, m->d_line64,
                                                 m->d_count + 0);
@@ -121,8 +126,10 @@ struct WalkArgs {
     const double *pos;
     const int32_t *off;
     const int32_t *nb;
+    const double *nb_pos;     // [nnz][3] position of each neighbour entry (contiguous per point)
     const uint8_t *bnd;
     const double *dirs;
+    const int32_t *order;     // walks of one direction are visited in this point order
 };
 
 __device__ __forceinline__ double dot3_exact(double ax, double ay, double az, double bx, double by, double bz)
@@ -139,9 +146,9 @@ __device__ __forceinline__ int64_t walk_next(const WalkArgs &a, int64_t c, doubl
     const int32_t k1 = a.off[c + 1];
     for (int32_t k = a.off[c]; k < k1; ++k) {
         int64_t mm = a.nb[k];
-        double dx = __dsub_rn(a.pos[3 * mm], xo);
-        double dy = __dsub_rn(a.pos[3 * mm + 1], yo);
-        double dz = __dsub_rn(a.pos[3 * mm + 2], zo);
+        double dx = __dsub_rn(a.nb_pos[3 * (int64_t)k], xo);
+        double dy = __dsub_rn(a.nb_pos[3 * (int64_t)k + 1], yo);
+        double dz = __dsub_rn(a.nb_pos[3 * (int64_t)k + 2], zo);
         double Z = dot3_exact(dx, dy, dz, n0, n1, n2);
         if (!(Z > Zc)) continue;
         double px = __dsub_rn(dx, __dmul_rn(Z, n0));
@@ -164,7 +171,7 @@ __global__ void k_trace_count(WalkArgs a, int64_t *__restrict__ len, unsigned lo
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)a.R * a.N) return;
     int r = (int)(t / a.N);
-    int64_t o = t - (int64_t)r * a.N;
+    int64_t o = a.order[t - (int64_t)r * a.N];
     double n0 = a.dirs[3 * r], n1 = a.dirs[3 * r + 1], n2 = a.dirs[3 * r + 2];
     double xo = a.pos[3 * o], yo = a.pos[3 * o + 1], zo = a.pos[3 * o + 2];
     int64_t c = o, n = 0;
@@ -181,7 +188,7 @@ __global__ void k_trace_count(WalkArgs a, int64_t *__restrict__ len, unsigned lo
         Zc = Zn;
         if (a.bnd[nx] || n >= a.N) break;   // Z strictly increases: at most N-1 steps
     }
-    len[t] = n;
+    len[(int64_t)r * a.N + o] = n;
 }
 
 // Pass 2: the same walk, writing the point list and its single-precision
@@ -193,11 +200,12 @@ __global__ void k_trace_fill(WalkArgs a, const int64_t *__restrict__ off, const 
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)a.R * a.N) return;
     int r = (int)(t / a.N);
-    int64_t o = t - (int64_t)r * a.N;
+    int64_t o = a.order[t - (int64_t)r * a.N];
+    const int64_t w = (int64_t)r * a.N + o;
     double n0 = a.dirs[3 * r], n1 = a.dirs[3 * r + 1], n2 = a.dirs[3 * r + 2];
     double xo = a.pos[3 * o], yo = a.pos[3 * o + 1], zo = a.pos[3 * o + 2];
     const double vox = vel[3 * o], voy = vel[3 * o + 1], voz = vel[3 * o + 2];
-    const int64_t base = off[t], cap = off[t + 1] - base;
+    const int64_t base = off[w], cap = off[w + 1] - base;
     int64_t c = o, n = 0;
     double Zc = 0.0;
     double px = xo, py = yo, pz = zo;            // previous point (c_{k-1})
@@ -265,7 +273,7 @@ __global__ void k_steps64(int64_t N, int32_t R, const int64_t *__restrict__ off,
 mgt_status trace_all(mgt_model *m, cudaStream_t s)
 {
     const int64_t W = (int64_t)m->R * m->N;
-    WalkArgs a{m->N, m->R, m->d_pos, m->d_nbr_off, m->d_nbrs, m->d_bnd, m->d_dirs};
+    WalkArgs a{m->N, m->R, m->d_pos, m->d_nbr_off, m->d_nbrs, m->d_nbr_pos, m->d_bnd, m->d_dirs, m->d_order};
     if (!m->d_ray_off) MGT_CUDA(cudaMalloc(&m->d_ray_off, sizeof(int64_t) * (W + 1)));
     int64_t *d_len = nullptr;
     MGT_CUDA(cudaMallocAsync(&d_len, sizeof(int64_t) * (W + 1), s));

@@ -298,8 +298,8 @@ mgt_status ng_step(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *ma
     auto predict = [&](const double *prev, double *mr_pred, bool *negative) -> mgt_status {
         const int nres = mcount - 1;
         Coef cf{};
-        if (!ng_coefficients(ng.G, nres, cf.c)) {
-            *negative = true;  // treated as unusable
+        if (!ng_coefficients(ng.G, nres, cf.c)) {   // exactly singular: no prediction
+            *negative = true;
             *mr_pred = INFINITY;
             return MGT_OK;
         }
@@ -364,11 +364,15 @@ mgt_status ng_step(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *ma
     bool neg;
     st = predict(ng.have_prev_pred ? slot_ptr(ng.prev_pred_slot) : nullptr, &mrp, &neg);
     if (st != MGT_OK) return st;
-    if (neg) {
+    if (std::isinf(mrp)) {          // singular Gram matrix
         restart_from_newest();
         return check_device_error(m, s);
     }
     if (mrp < mr_regular || mcount >= opts.n_max) {
+        if (neg) {
+            restart_from_newest();
+            return check_device_error(m, s);
+        }
         st = use_prediction();
         if (st != MGT_OK) return st;
         return check_device_error(m, s);

@@ -61,7 +61,7 @@ struct mgt_model {
     int32_t R = 0, P = 0, Q = 0, L = 0, M = 0, Mpad = 0, K = 0, n_boundary = 0;
     int64_t nnz = 0;
     double mol_mass = 0, T_bg = 0, L_unit = 1.0;
-    mgt_solve_opts opts{0.35, 0, 0};
+    mgt_solve_opts opts{0.35, 0, 0, 0, 0};
 
     // host copies of the small tables
     std::vector<double> energy, g, A, freq, Kul;
@@ -75,6 +75,8 @@ struct mgt_model {
     double *d_ncoll = nullptr, *d_nspec = nullptr, *d_w64 = nullptr;
     float2 *d_w32 = nullptr;                   // {w, 1/w}
     int32_t *d_nbr_off = nullptr, *d_nbrs = nullptr;
+    double *d_nbr_pos = nullptr;               // [nnz][3] position of each neighbour entry
+    int32_t *d_order = nullptr;                // [N] points in Morton (Z-curve) order
     uint8_t *d_bnd = nullptr;
     double *d_dirs = nullptr;
     int2 *d_pairs = nullptr;
@@ -88,8 +90,8 @@ struct mgt_model {
     int16_t *d_entry = nullptr;                // [3][L*L]: radiative-down line, radiative-up line, collision
     // device: state
     double *d_pops = nullptr, *d_pops_prev = nullptr;   // [N][L]
-    float2 *d_line32 = nullptr;                // [N][Mpad] {chi~, S'}
-    double2 *d_line64 = nullptr;               // [N][Mpad]
+    float2 *d_line32 = nullptr;                // [N][Mpad+2] {chi~', S'} ..., {w, 1/w}, {0, 0}
+    double2 *d_line64 = nullptr;               // [N][Mpad+1] {chi~', S'} ..., {w, 1/w}
     double *d_J = nullptr, *d_Lst = nullptr;   // [N][M]
     int *d_err = nullptr;                      // [4]
     unsigned long long *d_count = nullptr;     // [4] counters (opacity floors, stalls)
@@ -133,6 +135,12 @@ mgt_status ng_step(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *ma
 void ng_free(mgt_model *m);
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Per-point line-data rows: Mpad line entries {chi~', S'} followed by the
+// point's {w, 1/w} (and, for FP32, one zero pad entry), so that a row is a
+// multiple of 16 bytes and can be moved by one bulk copy.
+inline int row_stride32(int Mpad) { return Mpad + 2; }   // float2 entries
+inline int row_stride64(int Mpad) { return Mpad + 1; }   // double2 entries
 
 }  // namespace mgt
 

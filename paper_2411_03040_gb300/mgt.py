@@ -38,7 +38,8 @@ class mgt_model_desc(ctypes.Structure):
 
 
 class mgt_solve_opts(ctypes.Structure):
-    _fields_ = [("switch_threshold", _f64), ("width_mode", _i32), ("lines_per_thread", _i32)]
+    _fields_ = [("switch_threshold", _f64), ("width_mode", _i32), ("lines_per_thread", _i32),
+                ("schedule", _i32), ("reserved", _i32)]
 
 
 class mgt_trace_stats(ctypes.Structure):
@@ -182,8 +183,8 @@ def mgt_model_sizes(m: Model):
     return dict(n_points=n.value, n_rays=r.value, n_levels=l.value, n_lines=mm.value, n_quad=q.value)
 
 
-def mgt_set_solve_opts(m: Model, switch_threshold=0.35, width_mode=0, lines_per_thread=0):
-    o = mgt_solve_opts(switch_threshold, width_mode, lines_per_thread)
+def mgt_set_solve_opts(m: Model, switch_threshold=0.35, width_mode=0, lines_per_thread=0, schedule=0):
+    o = mgt_solve_opts(switch_threshold, width_mode, lines_per_thread, schedule, 0)
     _check(load().mgt_set_solve_opts(m.handle, ctypes.byref(o)), "mgt_set_solve_opts")
 
 
