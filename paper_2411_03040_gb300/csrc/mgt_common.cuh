@@ -139,8 +139,8 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // Per-point line-data rows: Mpad line entries {chi~', S'} followed by the
 // point's {w, 1/w} (and, for FP32, one zero pad entry), so that a row is a
 // multiple of 16 bytes and can be moved by one bulk copy.
-inline int row_stride32(int Mpad) { return Mpad + 2; }   // float2 entries
-inline int row_stride64(int Mpad) { return Mpad + 1; }   // double2 entries
+__host__ __device__ inline int row_stride32(int Mpad) { return Mpad + 2; }   // float2 entries
+__host__ __device__ inline int row_stride64(int Mpad) { return Mpad + 1; }   // double2 entries
 
 }  // namespace mgt
 
