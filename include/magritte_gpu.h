@@ -102,8 +102,11 @@ typedef struct {
     int32_t width_mode;       /* dnu_bar of a segment: 0 = from the averaged temperature
                                  and turbulence (default), 1 = mean of the endpoint widths */
     int32_t lines_per_thread; /* FP32 kernel schedule: 0 = auto, else 4 or 8 */
-    int32_t schedule;         /* 0 = auto (bulk-copy staging of ray chunks when one origin
-                                 fills a block), 1 = per-thread gathers from global memory */
+    int32_t schedule;         /* formal-solve kernel: 0 = auto, 1 = per-thread gathers from
+                                 global memory, 2 = bulk-copy staging of ray chunks in shared
+                                 memory (registers capped for two blocks per SM), 3 = staging
+                                 with one block per SM; 2 and 3 need one origin to fill a
+                                 block (bins x line groups >= 96), else 1 is used */
     int32_t reserved;         /* must be 0 */
 } mgt_solve_opts;
 
@@ -112,6 +115,8 @@ typedef struct {
     int64_t n_stalls;         /* walks that ended without reaching a boundary point */
     int32_t max_half_ray;     /* longest half-ray (points) */
     double mean_half_ray;     /* total_steps / (N * R) */
+    int64_t n_fp64_steps;     /* walk steps that FP32 error bounds could not settle and that
+                                 were decided by the FP64 predicates themselves */
 } mgt_trace_stats;
 
 typedef enum { MGT_NG_NONE = 0, MGT_NG_CLASSICAL = 1, MGT_NG_ADAPTIVE = 2 } mgt_ng_mode;
@@ -161,6 +166,8 @@ mgt_status mgt_set_solve_opts(mgt_model *m, const mgt_solve_opts *opts);
  * boundary point (included) or stalls when no candidate exists.  All
  * predicates are evaluated in FP64 without fused multiply-adds, so the point
  * lists are bit-exact with any implementation of the same expressions.
+ * Most steps are settled by FP32 arithmetic with rigorous error bounds that
+ * prove the FP64 predicates agree; the others are evaluated in FP64.
  * Stores the ray geometry on the device.  `stats` (host, may be NULL) is
  * filled after a stream synchronisation.
  */

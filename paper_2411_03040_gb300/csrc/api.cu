@@ -211,7 +211,7 @@ static mgt_status validate(const mgt_model_desc *d)
 
 static void free_model(mgt_model *m)
 {
-    void *ptrs[] = {m->d_nbr_pos, m->d_order, m->d_pos, m->d_vel, m->d_temp, m->d_vturb2, m->d_ncoll, m->d_nspec, m->d_w64, m->d_w32,
+    void *ptrs[] = {m->d_nbr_pos, m->d_nbr_hl, m->d_order, m->d_pos, m->d_vel, m->d_temp, m->d_vturb2, m->d_ncoll, m->d_nspec, m->d_w64, m->d_w32,
                     m->d_nbr_off, m->d_nbrs, m->d_bnd, m->d_dirs, m->d_pairs, m->d_xq, m->d_wq, m->d_line_tab,
                     m->d_line_ul, m->d_level_tab, m->d_coll_tab, m->d_coll_ul, m->d_entry, m->d_pops,
                     m->d_pops_prev, m->d_line32, m->d_line64, m->d_J, m->d_Lst, m->d_err, m->d_count,
@@ -367,6 +367,7 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
     MGT_TRY(dalloc(&m->d_nbr_off, N + 1));
     MGT_TRY(dalloc(&m->d_nbrs, m->nnz));
     MGT_TRY(dalloc(&m->d_nbr_pos, 3 * m->nnz));
+    MGT_TRY(dalloc(&m->d_nbr_hl, 6 * m->nnz));
     MGT_TRY(dalloc(&m->d_order, N));
     MGT_TRY(dalloc(&m->d_bnd, N));
     MGT_TRY(dalloc(&m->d_dirs, 3 * (size_t)m->R));
@@ -398,9 +399,21 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
     MGT_TRY(upload(m->d_nbrs, d->nbrs, m->nnz, s));
     {
         std::vector<double> np(3 * (size_t)m->nnz);
+        std::vector<float> hl(6 * (size_t)m->nnz);
+        double xmax = 0.0;
+        for (int64_t i = 0; i < 3 * N; ++i) xmax = std::max(xmax, std::fabs(d->pos[i]));
         for (int64_t k = 0; k < m->nnz; ++k)
-            for (int c = 0; c < 3; ++c) np[3 * k + c] = d->pos[3 * (int64_t)d->nbrs[k] + c];
+            for (int c = 0; c < 3; ++c) {
+                const double x = d->pos[3 * (int64_t)d->nbrs[k] + c];
+                const float hi = (float)x;
+                np[3 * k + c] = x;
+                hl[6 * k + c] = hi;
+                hl[6 * k + 3 + c] = (float)(x - (double)hi);
+            }
+        // |x - (hi + lo)| <= 2^-24 |lo| <= 2^-48 |x|; four times that, for both endpoints
+        m->pos_slack = (float)(4.0 * std::ldexp(xmax, -48));
         MGT_TRY(upload(m->d_nbr_pos, np.data(), np.size(), s));
+        MGT_TRY(upload(m->d_nbr_hl, hl.data(), hl.size(), s));
         MGT_CUDA(cudaStreamSynchronize(s));   // np goes out of scope
         const std::vector<int32_t> ord = morton_order(d->pos, N);
         MGT_TRY(upload(m->d_order, ord.data(), (size_t)N, s));
@@ -505,7 +518,7 @@ mgt_status mgt_set_solve_opts(mgt_model *m, const mgt_solve_opts *o)
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
     mgt_solve_opts d{0.35, 0, 0, 0, 0};
     if (o) {
-        if (o->schedule != 0 && o->schedule != 1) return set_error(MGT_ERR_ARG, "schedule must be 0 or 1");
+        if (o->schedule < 0 || o->schedule > 3) return set_error(MGT_ERR_ARG, "schedule must be 0..3");
         if (o->reserved != 0) return set_error(MGT_ERR_ARG, "reserved must be 0");
         if (!(o->switch_threshold >= 0.0) || !std::isfinite(o->switch_threshold))
             return set_error(MGT_ERR_ARG, "switch_threshold must be >= 0");
@@ -529,6 +542,7 @@ mgt_status mgt_trace_rays(mgt_model *m, mgt_trace_stats *stats, void *stream)
         stats->n_stalls = m->n_stalls;
         stats->max_half_ray = m->max_half;
         stats->mean_half_ray = (double)m->total_steps / ((double)m->N * m->R);
+        stats->n_fp64_steps = m->n_exact_steps;
     }
     return MGT_OK;
 }

@@ -39,7 +39,7 @@ namespace {
 template <typename T> struct Prec;
 
 template <> struct Prec<float> {
-    using LD = float2;
+    using V2 = float2;
     static __device__ __forceinline__ float rcp(float x)
     {
         float r;
@@ -54,7 +54,7 @@ template <> struct Prec<float> {
 };
 
 template <> struct Prec<double> {
-    using LD = double2;
+    using V2 = double2;
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double gauss(double u) { return exp(-u * u); }
     static __device__ __forceinline__ double erf_(double x) { return erf(x); }
@@ -70,7 +70,7 @@ struct FSArgs {
     const int64_t *ray_off;
     const Step32 *s32;
     const Step64 *s64;
-    const void *line;          // float2* or double2*, [N][RS] rows (see row_stride32/64)
+    const void *line;          // float* or double*, [N][RS] rows (see row_stride32/64)
     const int32_t *order;      // origin visiting order (space-filling curve), [N]
     const double *xq, *wq;
     const double *line_tab;    // [8][Mpad]
@@ -116,27 +116,28 @@ template <> __device__ __forceinline__ StepG<double> step_global<double>(const F
     return {v0.x, v0.y, v1.x};
 }
 
-// LPT lines {chi~', S'} of one row (global or shared), 16-byte aligned.
-template <int LPT> __device__ __forceinline__ void load_lines(const float2 *p, float (&chi)[LPT], float (&S)[LPT])
+// LPT consecutive scalars of a row (global or shared memory), 16-byte aligned.
+template <int LPT> __device__ __forceinline__ void load_vec(const float *p, float (&v)[LPT])
 {
-    const float4 *v = reinterpret_cast<const float4 *>(p);
+    const float4 *q = reinterpret_cast<const float4 *>(p);
 #pragma unroll
-    for (int i = 0; i < LPT / 2; ++i) {
-        const float4 x = v[i];
-        chi[2 * i] = x.x;
-        S[2 * i] = x.y;
-        chi[2 * i + 1] = x.z;
-        S[2 * i + 1] = x.w;
+    for (int i = 0; i < LPT / 4; ++i) {
+        const float4 x = q[i];
+        v[4 * i] = x.x;
+        v[4 * i + 1] = x.y;
+        v[4 * i + 2] = x.z;
+        v[4 * i + 3] = x.w;
     }
 }
 
-template <int LPT> __device__ __forceinline__ void load_lines(const double2 *p, double (&chi)[LPT], double (&S)[LPT])
+template <int LPT> __device__ __forceinline__ void load_vec(const double *p, double (&v)[LPT])
 {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
 #pragma unroll
-    for (int i = 0; i < LPT; ++i) {
-        const double2 x = p[i];
-        chi[i] = x.x;
-        S[i] = x.y;
+    for (int i = 0; i < LPT / 2; ++i) {
+        const double2 x = q[i];
+        v[2 * i] = x.x;
+        v[2 * i + 1] = x.y;
     }
 }
 
@@ -158,6 +159,11 @@ __device__ __noinline__ bool trapezoid_fp64(const FSArgs &a, int r, int64_t c_fa
 // Line-independent coefficients of one segment: dtau_line = cf chi_far + cn chi_near.
 //   du    : reduced Doppler shift near minus far, in units of the averaged width
 //   trap  : trapezoid branch (|du| below the threshold)
+// Semi-analytic branch: with ubar the reduced frequencies at the averaged
+// width, E = erf(ubar_near) - erf(ubar_far).  Reflecting (a, b) -> (-b, -a)
+// when a + b < 0 leaves E unchanged, after which E = erfc(a) - erfc(b) has no
+// cancellation: either both arguments are >= 0 (tails as differences of small
+// erfc values) or they straddle zero and E >= erf(|du|/2) (|du| >= threshold).
 template <typename T>
 __device__ __forceinline__ void segment_coefs(bool trap, T dx, T du, T z_f, T g_f, T w_f, T g_n, T w_n, int width_mode,
                                               T &cf, T &cn)
@@ -166,16 +172,16 @@ __device__ __forceinline__ void segment_coefs(bool trap, T dx, T du, T z_f, T g_
         cf = T(0.5) * dx * g_f;
         cn = T(0.5) * dx * g_n;
     } else {
-        const T iwbar = width_mode == 0 ? Prec<T>::rsqrt_(T(0.5) * (w_f * w_f + w_n * w_n)) : T(2) / (w_f + w_n);
-        const T ubf = z_f * iwbar, ubn = ubf + du;
-        T E;
-        if (ubf > T(0) && ubn > T(0))
-            E = Prec<T>::erfc_(ubf) - Prec<T>::erfc_(ubn);
-        else if (ubf < T(0) && ubn < T(0))
-            E = Prec<T>::erfc_(-ubn) - Prec<T>::erfc_(-ubf);
-        else
-            E = Prec<T>::erf_(ubn) - Prec<T>::erf_(ubf);
-        const T kk = dx * T(kSqrtPi) * E * iwbar / (T(4) * du);
+        const T iwbar = width_mode == 0 ? Prec<T>::rsqrt_(T(0.5) * (w_f * w_f + w_n * w_n))
+                                        : Prec<T>::rcp(T(0.5) * (w_f + w_n));
+        T a = z_f * iwbar, b = a + du;
+        if (a + b < T(0)) {
+            const T t = a;
+            a = -b;
+            b = -t;
+        }
+        const T E = Prec<T>::erfc_(a) - Prec<T>::erfc_(b);
+        const T kk = dx * T(0.25 * kSqrtPi) * E * iwbar * Prec<T>::rcp(du);
         cf = kk * w_f;
         cn = kk * w_n;
     }
@@ -265,8 +271,7 @@ template <typename T, int LPT>
 __device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, int line0, T Aq, T Bq, const T *Ibg,
                                              double xq64, double wo64, T (&P)[LPT], T (&Y)[LPT], T (&aa)[LPT])
 {
-    using LD = typename Prec<T>::LD;
-    const LD *line = reinterpret_cast<const LD *>(a.line);
+    const T *line = reinterpret_cast<const T *>(a.line);
     const int64_t t = (int64_t)r * a.N + o;
     const int64_t s0 = a.ray_off[t];
     const int n = (int)(a.ray_off[t + 1] - s0);
@@ -281,10 +286,11 @@ __device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, 
     int64_t c_f = a.s32[s0 + n - 1].x;
     StepG<T> sf = step_global<T>(a, s0 + n - 1);
     T chi_f[LPT], S_f[LPT];
-    load_lines<LPT>(line + c_f * a.RS + line0, chi_f, S_f);
-    LD wf = line[c_f * a.RS + a.Mpad];
+    load_vec<LPT>(line + c_f * a.RS + line0, chi_f);
+    load_vec<LPT>(line + c_f * a.RS + a.Mpad + line0, S_f);
+    T w_f = line[c_f * a.RS + 2 * a.Mpad];
     T z_f = Aq + Bq * sf.beta;
-    T g_f = Prec<T>::gauss(z_f * wf.y);
+    T g_f = Prec<T>::gauss(z_f * line[c_f * a.RS + 2 * a.Mpad + 1]);
     for (int k = n; k >= 1; --k) {
         int64_t c_n = o;
         StepG<T> sn{T(0), T(0), T(0)};
@@ -292,16 +298,18 @@ __device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, 
             c_n = a.s32[s0 + k - 2].x;
             sn = step_global<T>(a, s0 + k - 2);
         }
+        const T *row = line + c_n * a.RS;
         T chi_n[LPT], S_n[LPT];
-        load_lines<LPT>(line + c_n * a.RS + line0, chi_n, S_n);
-        const LD wn = line[c_n * a.RS + a.Mpad];
+        load_vec<LPT>(row + line0, chi_n);
+        load_vec<LPT>(row + a.Mpad + line0, S_n);
+        const T w_n = row[2 * a.Mpad];
         const T z_n = Aq + Bq * sn.beta;
-        const T g_n = Prec<T>::gauss(z_n * wn.y);
+        const T g_n = Prec<T>::gauss(z_n * row[2 * a.Mpad + 1]);
         const T du = -Bq * sf.dbw;
         bool trap = fabs(du) < thr;
         if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(2e-5) * thr) trap = trapezoid_fp64(a, r, c_f, c_n, xq64, wo64);
         T cf, cn;
-        segment_coefs<T>(trap, sf.dx, du, z_f, g_f, (T)wf.x, g_n, (T)wn.x, a.width_mode, cf, cn);
+        segment_coefs<T>(trap, sf.dx, du, z_f, g_f, w_f, g_n, w_n, a.width_mode, cf, cn);
         eliminate_row<T, LPT>(cf, cn, chi_f, S_f, chi_n, P, Y, aa);
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
@@ -310,7 +318,7 @@ __device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, 
         }
         z_f = z_n;
         g_f = g_n;
-        wf = wn;
+        w_f = w_n;
         sf = sn;
         c_f = c_n;
     }
@@ -318,7 +326,6 @@ __device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, 
 
 template <typename T, int LPT> __global__ void __launch_bounds__(256) k_fs_gather(FSArgs a)
 {
-    using LD = typename Prec<T>::LD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int bd = blockDim.x, tid = threadIdx.x;
     const int QG = a.Q * a.Gb;
@@ -341,9 +348,9 @@ template <typename T, int LPT> __global__ void __launch_bounds__(256) k_fs_gathe
             for (int c = 0; c < 4; ++c) acc[(c * LPT + l) * bd + tid] = T(0);
         const T Aq = T(xq64) * T(wo64), Bq = T(1) + Aq;
         const T wqn = T(a.wq[q]);
-        const LD *line = reinterpret_cast<const LD *>(a.line);
-        T So[LPT], dummy[LPT];
-        load_lines<LPT>(line + o * a.RS + line0, dummy, So);
+        const T *line = reinterpret_cast<const T *>(a.line);
+        T So[LPT];
+        load_vec<LPT>(line + o * a.RS + a.Mpad + line0, So);
         for (int p = 0; p < a.P; ++p) {
             const int2 pr = a.pairs[p];
             T PL[LPT], YL[LPT], aL[LPT], PR[LPT], YR[LPT], aR[LPT];
@@ -491,15 +498,14 @@ __device__ __forceinline__ void issue_chunk(const FSArgs &a, int64_t o, const Ch
     }
 }
 
-template <typename T, int LPT, int CH> __global__ void __launch_bounds__(256) k_fs_staged(FSArgs a)
+template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds__(256, MINB) k_fs_staged(FSArgs a)
 {
-    using LD = typename Prec<T>::LD;
     constexpr int SB = sizeof(T) == 4 ? 16 : 32;
     constexpr int NPT = CH + 1;
     static_assert(NPT <= 32, "one point row per producer lane");
     extern __shared__ __align__(128) unsigned char smem[];
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int rowB = a.RS * (int)sizeof(LD);
+    const int rowB = a.RS * (int)sizeof(T);
     const int Mb = a.Gb * LPT;
 
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);                   // [2]
@@ -512,6 +518,7 @@ template <typename T, int LPT, int CH> __global__ void __launch_bounds__(256) k_
     unsigned char *after = stage + ((max(stage_bytes, red_bytes) + 127) & ~127);
     T *ibg = reinterpret_cast<T *>(after);                                // [Mb][Q]
     T *acc = ibg + ((Mb * a.Q + 3) & ~3);                                 // [4][LPT][bd]
+    T *half0 = acc + 4 * LPT * bd;                                        // [3][LPT][bd] first half's P, Y, a
     double *red = reinterpret_cast<double *>(stage);                      // reuses the staging area at the end
 
     const int64_t o = a.order[blockIdx.x];
@@ -547,8 +554,7 @@ template <typename T, int LPT, int CH> __global__ void __launch_bounds__(256) k_
     const T wqn = active ? T(a.wq[q]) : T(0);
     int ci = 0;                 // chunks consumed
     bool ok = true;
-    T PL[LPT], YL[LPT], aL[LPT], P[LPT], Y[LPT], aa[LPT];
-    T chi_f[LPT], S_f[LPT];
+    T P[LPT], Y[LPT], aa[LPT];
     T z_f = 0, g_f = 0, w_f = 1;
     for (int p = 0; p < a.P; ++p) {
         const int2 pr = a.pairs[p];
@@ -581,27 +587,26 @@ template <typename T, int LPT, int CH> __global__ void __launch_bounds__(256) k_
                 ok = mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1);
                 if (ok && active) {
                     const unsigned char *Sb = steps_s + (ci & 1) * NPT * SB;
-                    const LD *Rb = reinterpret_cast<const LD *>(rows_s + (ci & 1) * NPT * rowB);
+                    const T *Rb = reinterpret_cast<const T *>(rows_s + (ci & 1) * NPT * rowB);
                     if (k_hi == n) {            // far end of the half-ray
                         const int jf = k_hi - k_lo + 1;
-                        const LD *row = Rb + jf * a.RS;
-                        load_lines<LPT>(row + line0, chi_f, S_f);
-                        const LD wv = row[a.Mpad];
-                        w_f = (T)wv.x;
+                        const T *row = Rb + jf * a.RS;
+                        w_f = row[2 * a.Mpad];
                         z_f = Aq + Bq * step_from<T>(Sb + jf * SB).beta;
-                        g_f = Prec<T>::gauss(z_f * (T)wv.y);
+                        g_f = Prec<T>::gauss(z_f * row[2 * a.Mpad + 1]);
                     }
                     for (int k = k_hi; k >= k_lo; --k) {
                         const int jf = k - k_lo + 1, jn = jf - 1;
                         const StepG<T> sf = step_from<T>(Sb + jf * SB);
                         const T beta_n = k > 1 ? step_from<T>(Sb + jn * SB).beta : T(0);
-                        const LD *row = Rb + jn * a.RS;
-                        T chi_n[LPT], S_n[LPT];
-                        load_lines<LPT>(row + line0, chi_n, S_n);
-                        const LD wv = row[a.Mpad];
-                        const T w_n = (T)wv.x;
+                        const T *rowf = Rb + jf * a.RS, *rown = Rb + jn * a.RS;
+                        T chi_f[LPT], S_f[LPT], chi_n[LPT];
+                        load_vec<LPT>(rowf + line0, chi_f);
+                        load_vec<LPT>(rowf + a.Mpad + line0, S_f);
+                        load_vec<LPT>(rown + line0, chi_n);
+                        const T w_n = rown[2 * a.Mpad];
                         const T z_n = Aq + Bq * beta_n;
-                        const T g_n = Prec<T>::gauss(z_n * (T)wv.y);
+                        const T g_n = Prec<T>::gauss(z_n * rown[2 * a.Mpad + 1]);
                         const T du = -Bq * sf.dbw;
                         bool trap = fabs(du) < thr;
                         if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(2e-5) * thr) {
@@ -612,11 +617,6 @@ template <typename T, int LPT, int CH> __global__ void __launch_bounds__(256) k_
                         T cf, cn;
                         segment_coefs<T>(trap, sf.dx, du, z_f, g_f, w_f, g_n, w_n, a.width_mode, cf, cn);
                         eliminate_row<T, LPT>(cf, cn, chi_f, S_f, chi_n, P, Y, aa);
-#pragma unroll
-                        for (int l = 0; l < LPT; ++l) {
-                            chi_f[l] = chi_n[l];
-                            S_f[l] = S_n[l];
-                        }
                         z_f = z_n;
                         g_f = g_n;
                         w_f = w_n;
@@ -625,15 +625,23 @@ template <typename T, int LPT, int CH> __global__ void __launch_bounds__(256) k_
                 ++ci;
             }
             if (h == 0) {
+                if (active) {
 #pragma unroll
-                for (int l = 0; l < LPT; ++l) {
-                    PL[l] = P[l];
-                    YL[l] = Y[l];
-                    aL[l] = aa[l];
+                    for (int l = 0; l < LPT; ++l) {
+                        half0[(0 * LPT + l) * bd + tid] = P[l];
+                        half0[(1 * LPT + l) * bd + tid] = Y[l];
+                        half0[(2 * LPT + l) * bd + tid] = aa[l];
+                    }
                 }
             } else if (active) {
-                T So[LPT], dummy[LPT];
-                load_lines<LPT>(reinterpret_cast<const LD *>(a.line) + o * a.RS + line0, dummy, So);
+                T So[LPT], PL[LPT], YL[LPT], aL[LPT];
+                load_vec<LPT>(reinterpret_cast<const T *>(a.line) + o * a.RS + a.Mpad + line0, So);
+#pragma unroll
+                for (int l = 0; l < LPT; ++l) {
+                    PL[l] = half0[(0 * LPT + l) * bd + tid];
+                    YL[l] = half0[(1 * LPT + l) * bd + tid];
+                    aL[l] = half0[(2 * LPT + l) * bd + tid];
+                }
                 combine_accumulate<T, LPT>(wqn, So, PL, YL, aL, P, Y, aa, acc, bd, tid);
             }
         }
@@ -667,7 +675,7 @@ done:
 
 constexpr int kChunk = 31;
 
-template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_t s, int force_gather)
+template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_t s, int schedule)
 {
     FSArgs a{};
     a.N = m->N;
@@ -701,21 +709,28 @@ template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_
     a.err = m->d_err;
     const int Mb = a.Gb * LPT;
     // one origin per CTA when bins x groups fill a CTA: the staged kernel
-    const bool staged = !force_gather && a.Q * a.Gb >= 96;
+    // (schedule 2: register-capped for two blocks per SM, 3: one block per SM)
+    const bool staged = schedule != 1 && a.Q * a.Gb >= 96;
     if (staged) {
         a.OPB = 1;
         const int threads = a.Q * a.Gb;
         const int bd = ((threads + 31) / 32) * 32;
         constexpr int SB = sizeof(T) == 4 ? 16 : 32;
-        const int rowB = a.RS * (int)sizeof(typename Prec<T>::LD);
+        const int rowB = a.RS * (int)sizeof(T);
         const int stage_bytes = 2 * (kChunk + 1) * (SB + rowB);
         const int red_bytes = 2 * Mb * a.Q * (int)sizeof(double);
         const size_t smem = 128 + ((std::max(stage_bytes, red_bytes) + 127) & ~127) +
-                            sizeof(T) * (((Mb * a.Q + 3) & ~3) + 4 * LPT * bd);
-        MGT_CUDA(cudaFuncSetAttribute(k_fs_staged<T, LPT, kChunk>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+                            sizeof(T) * (((Mb * a.Q + 3) & ~3) + 7 * LPT * bd);
         dim3 grid((unsigned)m->N, (unsigned)ceil_div(a.Gtot, a.Gb));
-        k_fs_staged<T, LPT, kChunk><<<grid, bd, smem, s>>>(a);
+        if (schedule == 3) {
+            MGT_CUDA(cudaFuncSetAttribute(k_fs_staged<T, LPT, kChunk, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            k_fs_staged<T, LPT, kChunk, 1><<<grid, bd, smem, s>>>(a);
+        } else {
+            MGT_CUDA(cudaFuncSetAttribute(k_fs_staged<T, LPT, kChunk, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            k_fs_staged<T, LPT, kChunk, 2><<<grid, bd, smem, s>>>(a);
+        }
         MGT_LAUNCH_CHECK("k_fs_staged");
         return MGT_OK;
     }
@@ -743,9 +758,10 @@ mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s)
 {
     const int lpt = fs_lines_per_thread(m, p);
     if (m->Mpad % lpt != 0) return set_error(MGT_ERR_STATE, "line padding does not match the schedule");
-    const int force_gather = m->opts.schedule == 1;   // 0: automatic, 1: gather kernel
-    if (p == MGT_FP64) return launch_typed<double, 4>(m, s, force_gather);
-    return lpt == 4 ? launch_typed<float, 4>(m, s, force_gather) : launch_typed<float, 8>(m, s, force_gather);
+    // 0: automatic, 1: gather kernel, 2: staged (two blocks per SM), 3: staged (one block per SM)
+    const int sch = m->opts.schedule;
+    if (p == MGT_FP64) return launch_typed<double, 4>(m, s, sch);
+    return lpt == 4 ? launch_typed<float, 4>(m, s, sch) : launch_typed<float, 8>(m, s, sch);
 }
 
 }  // namespace mgt

@@ -76,6 +76,8 @@ struct mgt_model {
     float2 *d_w32 = nullptr;                   // {w, 1/w}
     int32_t *d_nbr_off = nullptr, *d_nbrs = nullptr;
     double *d_nbr_pos = nullptr;               // [nnz][3] position of each neighbour entry
+    float *d_nbr_hl = nullptr;                 // [nnz][6] the same split into float hi + lo parts
+    float pos_slack = 0.0f;                    // bound on |x - (hi + lo)|
     int32_t *d_order = nullptr;                // [N] points in Morton (Z-curve) order
     uint8_t *d_bnd = nullptr;
     double *d_dirs = nullptr;
@@ -90,8 +92,8 @@ struct mgt_model {
     int16_t *d_entry = nullptr;                // [3][L*L]: radiative-down line, radiative-up line, collision
     // device: state
     double *d_pops = nullptr, *d_pops_prev = nullptr;   // [N][L]
-    float2 *d_line32 = nullptr;                // [N][Mpad+2] {chi~', S'} ..., {w, 1/w}, {0, 0}
-    double2 *d_line64 = nullptr;               // [N][Mpad+1] {chi~', S'} ..., {w, 1/w}
+    float *d_line32 = nullptr;                 // [N][row_stride32] chi~', S', w, 1/w, 0, 0
+    double *d_line64 = nullptr;                // [N][row_stride64] chi~', S', w, 1/w
     double *d_J = nullptr, *d_Lst = nullptr;   // [N][M]
     int *d_err = nullptr;                      // [4]
     unsigned long long *d_count = nullptr;     // [4] counters (opacity floors, stalls)
@@ -102,6 +104,7 @@ struct mgt_model {
     int64_t total_steps = 0;
     int32_t max_half = 0;
     int64_t n_stalls = 0;
+    int64_t n_exact_steps = 0;
     bool traced = false, have_J = false, line_dirty = true;
     int steps_width_mode = 0, steps64_width_mode = -1;
 
@@ -136,11 +139,14 @@ void ng_free(mgt_model *m);
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
-// Per-point line-data rows: Mpad line entries {chi~', S'} followed by the
-// point's {w, 1/w} (and, for FP32, one zero pad entry), so that a row is a
-// multiple of 16 bytes and can be moved by one bulk copy.
-__host__ __device__ inline int row_stride32(int Mpad) { return Mpad + 2; }   // float2 entries
-__host__ __device__ inline int row_stride64(int Mpad) { return Mpad + 1; }   // double2 entries
+// Per-point line-data rows, in scalars of the row's precision:
+//   [0, Mpad)        chi~'  per line (zero for padding lines)
+//   [Mpad, 2 Mpad)   S'     per line
+//   2 Mpad, 2 Mpad+1 the point's w and 1/w; FP32 rows end with two zeros
+// Mpad is a multiple of 8, so a row is a multiple of 16 bytes (one bulk copy)
+// and every group of 4 (FP32) or 2 (FP64) lines starts 16-byte aligned.
+__host__ __device__ inline int row_stride32(int Mpad) { return 2 * Mpad + 4; }   // floats
+__host__ __device__ inline int row_stride64(int Mpad) { return 2 * Mpad + 2; }   // doubles
 
 }  // namespace mgt
 

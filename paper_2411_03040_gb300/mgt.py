@@ -43,7 +43,8 @@ class mgt_solve_opts(ctypes.Structure):
 
 
 class mgt_trace_stats(ctypes.Structure):
-    _fields_ = [("total_steps", _i64), ("n_stalls", _i64), ("max_half_ray", _i32), ("mean_half_ray", _f64)]
+    _fields_ = [("total_steps", _i64), ("n_stalls", _i64), ("max_half_ray", _i32), ("mean_half_ray", _f64),
+                ("n_fp64_steps", _i64)]
 
 
 class mgt_ng_opts(ctypes.Structure):
@@ -192,7 +193,7 @@ def mgt_trace_rays(m: Model, stream=None) -> dict:
     st = mgt_trace_stats()
     _check(load().mgt_trace_rays(m.handle, ctypes.byref(st), _stream(stream)), "mgt_trace_rays")
     return dict(total_steps=st.total_steps, n_stalls=st.n_stalls, max_half_ray=st.max_half_ray,
-                mean_half_ray=st.mean_half_ray)
+                mean_half_ray=st.mean_half_ray, n_fp64_steps=st.n_fp64_steps)
 
 
 def mgt_get_rays(m: Model, stream=None):
