@@ -402,16 +402,22 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
         std::vector<float> hl(6 * (size_t)m->nnz);
         double xmax = 0.0;
         for (int64_t i = 0; i < 3 * N; ++i) xmax = std::max(xmax, std::fabs(d->pos[i]));
+        // exact power-of-two scaling that brings coordinates to order one, so
+        // FP32 squared distances cannot overflow
+        int ex = 0;
+        std::frexp(xmax > 0.0 ? xmax : 1.0, &ex);
+        m->pos_scale = std::ldexp(1.0, -ex);
         for (int64_t k = 0; k < m->nnz; ++k)
             for (int c = 0; c < 3; ++c) {
                 const double x = d->pos[3 * (int64_t)d->nbrs[k] + c];
-                const float hi = (float)x;
+                const double xs = x * m->pos_scale;
+                const float hi = (float)xs;
                 np[3 * k + c] = x;
                 hl[6 * k + c] = hi;
-                hl[6 * k + 3 + c] = (float)(x - (double)hi);
+                hl[6 * k + 3 + c] = (float)(xs - (double)hi);
             }
-        // |x - (hi + lo)| <= 2^-24 |lo| <= 2^-48 |x|; four times that, for both endpoints
-        m->pos_slack = (float)(4.0 * std::ldexp(xmax, -48));
+        // |xs - (hi + lo)| <= 2^-24 |lo| <= 2^-48 |xs| <= 2^-48; four times that, for both endpoints
+        m->pos_slack = (float)std::ldexp(1.0, -46);
         MGT_TRY(upload(m->d_nbr_pos, np.data(), np.size(), s));
         MGT_TRY(upload(m->d_nbr_hl, hl.data(), hl.size(), s));
         MGT_CUDA(cudaStreamSynchronize(s));   // np goes out of scope

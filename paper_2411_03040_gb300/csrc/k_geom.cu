@@ -145,7 +145,8 @@ struct WalkArgs {
     const int32_t *off;
     const int32_t *nb;
     const double *nb_pos;     // [nnz][3] position of each neighbour entry (contiguous per point)
-    const float *nb_hl;       // [nnz][6] the same positions split into float hi + lo parts
+    const float *nb_hl;       // [nnz][6] the same positions times pos_scale, split into float hi + lo
+    double pos_scale;         // power of two near 1 / (largest coordinate): exact scaling
     const uint8_t *bnd;
     const double *dirs;
     const int32_t *order;     // walks of one direction are visited in this point order
@@ -187,73 +188,12 @@ __device__ __noinline__ int64_t walk_next_exact(const WalkArgs &a, int64_t c, do
     return best;
 }
 
-// Per-walk constants of the filtered step.
+// Per-walk constants.
 struct WalkFrame {
     double xo, yo, zo, n0, n1, n2;     // FP64 origin and direction
     float ohx, ohy, ohz, olx, oly, olz; // origin split into hi + lo floats
     float f0, f1, f2;                  // direction in FP32
 };
-
-// Next point of the walk, decided with FP32 arithmetic when error bounds
-// prove that the FP64 predicates give the same answer, else by
-// walk_next_exact.  Bounds (generous multiples of the rounding analysis):
-//   offsets   |d32 - d64| <= ed = 2e-6 (|d32|_max + slack)
-//   projection |Z32 - Z64| <= eZ = 2e-6 |d32|_1 + 2 ed, plus 1e-7 |Z_c| for Z_c
-//   perpendicular components  ep = ed + eZ + 2e-7 (|p32|_max + |Z32|)
-//   squared distance |d2_32 - d2_64| <= 4 |p32| ep + 4 ep^2 + 1e-6 d2_32.
-// A neighbour is a candidate only if Z32 - eZ clears Z_c; not one only if
-// Z32 + eZ stays below it; otherwise the step is undecided.  The FP32 winner
-// is accepted only if its upper d2 bound is below every other candidate's
-// lower bound (so ties always go to FP64).
-__device__ __forceinline__ int64_t walk_next(const WalkArgs &a, const WalkFrame &f, int64_t c, double Zc, double *Znext)
-{
-    const float Zcf = (float)Zc;
-    const float eZc = 1e-7f * fabsf(Zcf) + 1e-30f;
-    int32_t kbest = -1;
-    float d2best = 0.0f, Ubest = 0.0f, Lbest = 0.0f, minLother = 3.0e38f;
-    bool undecided = false;
-    const int32_t k0 = a.off[c], k1 = a.off[c + 1];
-    for (int32_t k = k0; k < k1; ++k) {
-        const float *hl = a.nb_hl + 6 * (int64_t)k;
-        const float dx = (hl[0] - f.ohx) + (hl[3] - f.olx);
-        const float dy = (hl[1] - f.ohy) + (hl[4] - f.oly);
-        const float dz = (hl[2] - f.ohz) + (hl[5] - f.olz);
-        const float adx = fabsf(dx), ady = fabsf(dy), adz = fabsf(dz);
-        const float ed = 2e-6f * (fmaxf(adx, fmaxf(ady, adz)) + a.pos_slack);
-        const float Z = fmaf(dz, f.f2, fmaf(dy, f.f1, dx * f.f0));
-        const float eZ = 2e-6f * (adx + ady + adz) + 2.0f * ed + eZc;
-        if (Z - eZ > Zcf) {
-            const float px = fmaf(-Z, f.f0, dx), py = fmaf(-Z, f.f1, dy), pz = fmaf(-Z, f.f2, dz);
-            const float d2 = fmaf(pz, pz, fmaf(py, py, px * px));
-            const float ep = ed + eZ + 2e-7f * (fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz))) + fabsf(Z));
-            const float e2 = 4.0f * sqrtf(d2) * ep + 4.0f * ep * ep + 1e-6f * d2;
-            const float U = d2 + e2, Lo = d2 - e2;
-            if (kbest < 0 || d2 < d2best) {
-                if (kbest >= 0) minLother = fminf(minLother, Lbest);
-                kbest = k;
-                d2best = d2;
-                Ubest = U;
-                Lbest = Lo;
-            } else {
-                minLother = fminf(minLother, Lo);
-            }
-        } else if (!(Z + eZ < Zcf)) {
-            undecided = true;
-            break;
-        }
-    }
-    if (undecided || (kbest >= 0 && !(Ubest < minLother))) {
-        atomicAdd(a.n_exact, 1ULL);
-        return walk_next_exact(a, c, f.xo, f.yo, f.zo, f.n0, f.n1, f.n2, Zc, Znext);
-    }
-    if (kbest < 0) {
-        *Znext = 0.0;
-        return -1;
-    }
-    const double *q = a.nb_pos + 3 * (int64_t)kbest;
-    *Znext = dot3_exact(__dsub_rn(q[0], f.xo), __dsub_rn(q[1], f.yo), __dsub_rn(q[2], f.zo), f.n0, f.n1, f.n2);
-    return a.nb[kbest];
-}
 
 __device__ __forceinline__ WalkFrame make_frame(const WalkArgs &a, int64_t o, int r)
 {
@@ -264,86 +204,211 @@ __device__ __forceinline__ WalkFrame make_frame(const WalkArgs &a, int64_t o, in
     f.xo = a.pos[3 * o];
     f.yo = a.pos[3 * o + 1];
     f.zo = a.pos[3 * o + 2];
-    f.ohx = (float)f.xo;
-    f.ohy = (float)f.yo;
-    f.ohz = (float)f.zo;
-    f.olx = (float)(f.xo - (double)f.ohx);
-    f.oly = (float)(f.yo - (double)f.ohy);
-    f.olz = (float)(f.zo - (double)f.ohz);
+    const double sx = f.xo * a.pos_scale, sy = f.yo * a.pos_scale, sz = f.zo * a.pos_scale;
+    f.ohx = (float)sx;
+    f.ohy = (float)sy;
+    f.ohz = (float)sz;
+    f.olx = (float)(sx - (double)f.ohx);
+    f.oly = (float)(sy - (double)f.ohy);
+    f.olz = (float)(sz - (double)f.ohz);
     f.f0 = (float)f.n0;
     f.f1 = (float)f.n1;
     f.f2 = (float)f.n2;
     return f;
 }
 
-// Pass 1: half-ray length and stall flag of every (direction, origin).
-__global__ void k_trace_count(WalkArgs a, int64_t *__restrict__ len, unsigned long long *__restrict__ n_stall)
+__device__ __forceinline__ float warp_min(float v)
 {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)a.R * a.N) return;
-    int r = (int)(t / a.N);
-    int64_t o = a.order[t - (int64_t)r * a.N];
-    const WalkFrame f = make_frame(a, o, r);
-    int64_t c = o, n = 0;
-    double Zc = 0.0;
-    for (;;) {
-        double Zn;
-        int64_t nx = walk_next(a, f, c, Zc, &Zn);
-        if (nx < 0) {
-            if (!(c == o && a.bnd[o])) atomicAdd(n_stall, 1ULL);
-            break;
-        }
-        ++n;
-        c = nx;
-        Zc = Zn;
-        if (a.bnd[nx] || n >= a.N) break;   // Z strictly increases: at most N-1 steps
-    }
-    len[(int64_t)r * a.N + o] = n;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
-// Pass 2: the same walk, writing the point list and its single-precision
-// geometry (see Step32).  `off` is the exclusive prefix of the lengths.
-__global__ void k_trace_fill(WalkArgs a, const int64_t *__restrict__ off, const double *__restrict__ vel,
-                             const double *__restrict__ w64, double inv_Lunit, int width_mode,
-                             Step32 *__restrict__ steps, int *__restrict__ err)
+// ---------------------------------------------------------------------------
+// One warp per walk.  At each step the lanes evaluate the neighbours of the
+// current point c in parallel with FP32 arithmetic and error bounds that
+// cover both the FP32 and the FP64 rounding (generous multiples of the
+// rounding analysis):
+//   offsets    |d32 - d64| <= ed = 2e-6 (|d32|_max + slack)
+//   projection |Z32 - Z64| <= eZ = 2e-6 |d32|_1 + 2 ed
+//   perpendicular components  ep = ed + eZ + 2e-7 (|p32|_max + |Z32|)
+//   squared distance |d2_32 - d2_64| <= 4 |p32| ep + 4 ep^2 + 1e-6 d2_32.
+// The current point's projection Z_c is carried as the winner's FP32 value
+// with its bound eZ_c.  A neighbour is a candidate when Z32 - eZ clears
+// Z_c + eZ_c, not one when Z32 + eZ stays at or below Z_c - eZ_c; anything in
+// between leaves the step undecided.  The FP32 winner (smallest d2, lowest
+// lane) is accepted only if its upper d2 bound is below every other
+// candidate's lower bound, so near-ties never decide.  Undecided steps run
+// walk_next_exact, the FP64 predicates themselves (exact Z_c recomputed by
+// the same expression).  The point lists are therefore those of the FP64 rule.
+//
+// FILL = false: half-ray length and stall count.  FILL = true: also the step
+// records (see Step32): dx and the widths in FP32 from hi/lo positions, the
+// velocity projections beta and dbeta in FP64.
+// ---------------------------------------------------------------------------
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_trace_warp(WalkArgs a, int64_t *__restrict__ len_or_off,
+                                                    unsigned long long *__restrict__ n_stall,
+                                                    const double *__restrict__ vel, const float2 *__restrict__ w32,
+                                                    float inv_Lunit, int width_mode, Step32 *__restrict__ steps,
+                                                    int *__restrict__ err)
 {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)a.R * a.N) return;
-    int r = (int)(t / a.N);
-    int64_t o = a.order[t - (int64_t)r * a.N];
-    const int64_t w = (int64_t)r * a.N + o;
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (wg >= (int64_t)a.R * a.N) return;                      // whole warp
+    const int r = (int)(wg / a.N);
+    const int64_t o = a.order[wg - (int64_t)r * a.N];
+    const int64_t wi = (int64_t)r * a.N + o;
     const WalkFrame f = make_frame(a, o, r);
-    const double vox = vel[3 * o], voy = vel[3 * o + 1], voz = vel[3 * o + 2];
-    const int64_t base = off[w], cap = off[w + 1] - base;
+    int64_t base = 0, cap = a.N;
+    if (FILL) {
+        base = len_or_off[wi];
+        cap = len_or_off[wi + 1] - base;
+    }
+    // previous point (for the step records, lane 0)
+    float ph[3] = {f.ohx, f.ohy, f.ohz}, pl[3] = {f.olx, f.oly, f.olz};
+    double pvx = 0, pvy = 0, pvz = 0, vox = 0, voy = 0, voz = 0;
+    float pw = 0.0f;
+    if (FILL && lane == 0) {
+        vox = pvx = vel[3 * o];
+        voy = pvy = vel[3 * o + 1];
+        voz = pvz = vel[3 * o + 2];
+        pw = w32[o].x;
+    }
     int64_t c = o, n = 0;
-    double Zc = 0.0;
-    double px = f.xo, py = f.yo, pz = f.zo;      // previous point (c_{k-1})
-    double pvx = vox, pvy = voy, pvz = voz, pw = w64[o];
+    float Zc = 0.0f, eZc = 0.0f;        // Z of o is exactly 0
     for (;;) {
-        double Zn;
-        int64_t nx = walk_next(a, f, c, Zc, &Zn);
-        if (nx < 0) break;
-        if (n >= cap) {                          // cannot happen for a deterministic walk
-            atomicCAS(err, 0, (int)kDevBounds);
-            return;
+        const int32_t k0 = a.off[c], k1 = a.off[c + 1];
+        float bd2 = 3.0e38f, bU = 0.0f, bL = 0.0f, bZ = 0.0f, beZ = 0.0f, minLother = 3.0e38f;
+        int32_t bk = -1;
+        bool undecided = false;
+        for (int32_t kb = k0; kb < k1; kb += 32) {
+            const int32_t k = kb + lane;
+            bool cand = false;
+            float d2 = 3.0e38f, U = 0.0f, Lo = 3.0e38f, Z = 0.0f, eZ = 0.0f;
+            bool und = false;
+            if (k < k1) {
+                const float *hl = a.nb_hl + 6 * (int64_t)k;
+                const float dx = (hl[0] - f.ohx) + (hl[3] - f.olx);
+                const float dy = (hl[1] - f.ohy) + (hl[4] - f.oly);
+                const float dz = (hl[2] - f.ohz) + (hl[5] - f.olz);
+                const float adx = fabsf(dx), ady = fabsf(dy), adz = fabsf(dz);
+                const float ed = 2e-6f * (fmaxf(adx, fmaxf(ady, adz)) + a.pos_slack);
+                Z = fmaf(dz, f.f2, fmaf(dy, f.f1, dx * f.f0));
+                eZ = 2e-6f * (adx + ady + adz) + 2.0f * ed;
+                if (Z - eZ > Zc + eZc) {
+                    cand = true;
+                    const float px = fmaf(-Z, f.f0, dx), py = fmaf(-Z, f.f1, dy), pz = fmaf(-Z, f.f2, dz);
+                    d2 = fmaf(pz, pz, fmaf(py, py, px * px));
+                    const float ep = ed + eZ + 2e-7f * (fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz))) + fabsf(Z));
+                    const float e2 = 4.0f * sqrtf(d2) * ep + 4.0f * ep * ep + 1e-6f * d2;
+                    U = d2 + e2;
+                    Lo = d2 - e2;
+                } else if (!(Z + eZ <= Zc - eZc)) {
+                    und = true;
+                }
+            }
+            if (__any_sync(0xffffffffu, und)) {
+                undecided = true;
+                break;
+            }
+            const float m = warp_min(cand ? d2 : 3.0e38f);
+            const unsigned wins = __ballot_sync(0xffffffffu, cand && d2 == m);
+            if (wins == 0u) continue;                          // no candidate in this chunk
+            const int wl = __ffs(wins) - 1;
+            const float cU = __shfl_sync(0xffffffffu, U, wl), cL = __shfl_sync(0xffffffffu, Lo, wl);
+            const float cZ = __shfl_sync(0xffffffffu, Z, wl), ceZ = __shfl_sync(0xffffffffu, eZ, wl);
+            const float oL = warp_min((cand && lane != wl) ? Lo : 3.0e38f);
+            if (bk < 0 || m < bd2) {
+                if (bk >= 0) minLother = fminf(minLother, bL);
+                minLother = fminf(minLother, oL);
+                bk = kb + wl;
+                bd2 = m;
+                bU = cU;
+                bL = cL;
+                bZ = cZ;
+                beZ = ceZ;
+            } else {
+                minLother = fminf(minLother, fminf(cL, oL));
+            }
         }
-        double qx = a.pos[3 * nx], qy = a.pos[3 * nx + 1], qz = a.pos[3 * nx + 2];
-        double vx = vel[3 * nx], vy = vel[3 * nx + 1], vz = vel[3 * nx + 2], wq = w64[nx];
-        double ex = qx - px, ey = qy - py, ez = qz - pz;
-        double dx = sqrt(ex * ex + ey * ey + ez * ez) * inv_Lunit;
-        double beta = (f.n0 * (vx - vox) + f.n1 * (vy - voy) + f.n2 * (vz - voz)) / kC;
-        double dbeta = (f.n0 * (vx - pvx) + f.n1 * (vy - pvy) + f.n2 * (vz - pvz)) / kC;
-        double wbar = width_mode == 0 ? sqrt(0.5 * (wq * wq + pw * pw)) : 0.5 * (wq + pw);
-        steps[base + n] = make_int4((int)nx, __float_as_int((float)dx), __float_as_int((float)beta),
-                                    __float_as_int((float)(dbeta / wbar)));
+        int64_t nx;
+        if (undecided || (bk >= 0 && !(bU < minLother))) {
+            // FP64 predicates, evaluated by lane 0
+            int64_t v = -1;
+            double Zn = 0.0;
+            if (lane == 0) {
+                atomicAdd(a.n_exact, 1ULL);
+                double Zc64 = 0.0;
+                if (c != o) {
+                    const double *q = a.pos + 3 * c;
+                    Zc64 = dot3_exact(__dsub_rn(q[0], f.xo), __dsub_rn(q[1], f.yo), __dsub_rn(q[2], f.zo), f.n0,
+                                      f.n1, f.n2);
+                }
+                v = walk_next_exact(a, c, f.xo, f.yo, f.zo, f.n0, f.n1, f.n2, Zc64, &Zn);
+            }
+            nx = __shfl_sync(0xffffffffu, v, 0);
+            Zn = __shfl_sync(0xffffffffu, Zn, 0);
+            Zc = (float)Zn;
+            eZc = 1e-7f * fabsf(Zc) + 1e-30f;
+            if (nx >= 0) {
+                bk = -1;                                       // locate the winner's entry for FILL
+                for (int32_t kb = k0; kb < k1; kb += 32) {
+                    const unsigned hit = __ballot_sync(0xffffffffu, kb + lane < k1 && a.nb[kb + lane] == nx);
+                    if (hit) {
+                        bk = kb + __ffs(hit) - 1;
+                        break;
+                    }
+                }
+            }
+        } else if (bk < 0) {
+            nx = -1;
+        } else {
+            nx = a.nb[bk];
+            Zc = bZ;
+            eZc = beZ;
+        }
+        if (nx < 0) {
+            if (!FILL && lane == 0 && !(c == o && a.bnd[o])) atomicAdd(n_stall, 1ULL);
+            break;
+        }
+        if (FILL && lane == 0) {
+            if (n >= cap) {                      // cannot happen for a deterministic walk
+                atomicCAS(err, 0, (int)kDevBounds);
+                break;
+            }
+            const float *hl = a.nb_hl + 6 * (int64_t)bk;
+            const float ex = (hl[0] - ph[0]) + (hl[3] - pl[0]);
+            const float ey = (hl[1] - ph[1]) + (hl[4] - pl[1]);
+            const float ez = (hl[2] - ph[2]) + (hl[5] - pl[2]);
+            const float dxs = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex))) * inv_Lunit;
+            const double vx = vel[3 * nx], vy = vel[3 * nx + 1], vz = vel[3 * nx + 2];
+            const double beta = (f.n0 * (vx - vox) + f.n1 * (vy - voy) + f.n2 * (vz - voz)) / kC;
+            const double dbeta = (f.n0 * (vx - pvx) + f.n1 * (vy - pvy) + f.n2 * (vz - pvz)) / kC;
+            const float wq = w32[nx].x;
+            const float wbar = width_mode == 0 ? sqrtf(0.5f * (wq * wq + pw * pw)) : 0.5f * (wq + pw);
+            steps[base + n] = make_int4((int)nx, __float_as_int(dxs), __float_as_int((float)beta),
+                                        __float_as_int((float)dbeta / wbar));
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                ph[d] = hl[d];
+                pl[d] = hl[3 + d];
+            }
+            pvx = vx;
+            pvy = vy;
+            pvz = vz;
+            pw = wq;
+        }
         ++n;
         c = nx;
-        Zc = Zn;
-        px = qx; py = qy; pz = qz;
-        pvx = vx; pvy = vy; pvz = vz; pw = wq;
         if (a.bnd[nx] || n >= a.N) break;
     }
-    if (n != cap) atomicCAS(err, 0, (int)kDevBounds);
+    if (lane == 0) {
+        if (!FILL)
+            len_or_off[wi] = n;
+        else if (n != cap)
+            atomicCAS(err, 0, (int)kDevBounds);
+    }
 }
 
 // Double-precision step geometry for the FP64 formal solution, from the
@@ -382,14 +447,15 @@ __global__ void k_steps64(int64_t N, int32_t R, const int64_t *__restrict__ off,
 mgt_status trace_all(mgt_model *m, cudaStream_t s)
 {
     const int64_t W = (int64_t)m->R * m->N;
-    WalkArgs a{m->N, m->R, m->d_pos, m->d_nbr_off, m->d_nbrs, m->d_nbr_pos, m->d_nbr_hl, m->d_bnd, m->d_dirs,
-               m->d_order, m->pos_slack, m->d_count + 2};
+    WalkArgs a{m->N,       m->R,          m->d_pos,       m->d_nbr_off, m->d_nbrs,     m->d_nbr_pos,
+               m->d_nbr_hl, m->pos_scale, m->d_bnd, m->d_dirs, m->d_order, m->pos_slack, m->d_count + 2};
     if (!m->d_ray_off) MGT_CUDA(cudaMalloc(&m->d_ray_off, sizeof(int64_t) * (W + 1)));
     int64_t *d_len = nullptr;
     MGT_CUDA(cudaMallocAsync(&d_len, sizeof(int64_t) * (W + 1), s));
     MGT_CUDA(cudaMemsetAsync(m->d_count + 1, 0, 2 * sizeof(unsigned long long), s));
-    k_trace_count<<<ceil_div(W, 128), 128, 0, s>>>(a, d_len, m->d_count + 1);
-    MGT_LAUNCH_CHECK("k_trace_count");
+    k_trace_warp<false><<<ceil_div(W * 32, 256), 256, 0, s>>>(a, d_len, m->d_count + 1, nullptr, nullptr, 0.0f, 0,
+                                                              nullptr, m->d_err);
+    MGT_LAUNCH_CHECK("k_trace_warp<count>");
     MGT_CUDA(cudaMemsetAsync(d_len + W, 0, sizeof(int64_t), s));
     size_t tmp_bytes = 0;
     MGT_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, d_len, m->d_ray_off, W + 1, s));
@@ -433,9 +499,11 @@ mgt_status trace_all(mgt_model *m, cudaStream_t s)
     m->n_stalls = (int64_t)stalls;
     m->n_exact_steps = (int64_t)exact_steps;   // pass 1 only
     if (total > 0) {
-        k_trace_fill<<<ceil_div(W, 128), 128, 0, s>>>(a, m->d_ray_off, m->d_vel, m->d_w64, 1.0 / m->L_unit,
-                                                      m->opts.width_mode, m->d_steps32, m->d_err);
-        MGT_LAUNCH_CHECK("k_trace_fill");
+        k_trace_warp<true><<<ceil_div(W * 32, 256), 256, 0, s>>>(a, m->d_ray_off, nullptr, m->d_vel, m->d_w32,
+                                                                 (float)(1.0 / (m->pos_scale * m->L_unit)),
+                                                                 m->opts.width_mode,
+                                                                 m->d_steps32, m->d_err);
+        MGT_LAUNCH_CHECK("k_trace_warp<fill>");
     }
     m->steps_width_mode = m->opts.width_mode;
     m->traced = true;

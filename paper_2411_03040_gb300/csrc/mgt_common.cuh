@@ -76,8 +76,9 @@ struct mgt_model {
     float2 *d_w32 = nullptr;                   // {w, 1/w}
     int32_t *d_nbr_off = nullptr, *d_nbrs = nullptr;
     double *d_nbr_pos = nullptr;               // [nnz][3] position of each neighbour entry
-    float *d_nbr_hl = nullptr;                 // [nnz][6] the same split into float hi + lo parts
-    float pos_slack = 0.0f;                    // bound on |x - (hi + lo)|
+    float *d_nbr_hl = nullptr;                 // [nnz][6] the same times pos_scale, split into float hi + lo
+    double pos_scale = 1.0;                    // power of two near 1 / (largest coordinate)
+    float pos_slack = 0.0f;                    // bound on |x pos_scale - (hi + lo)|
     int32_t *d_order = nullptr;                // [N] points in Morton (Z-curve) order
     uint8_t *d_bnd = nullptr;
     double *d_dirs = nullptr;
