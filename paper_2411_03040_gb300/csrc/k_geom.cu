@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(256) k_trace_warp(WalkArgs a, int64_t *__restr
             }
             nx = __shfl_sync(0xffffffffu, v, 0);
             Zn = __shfl_sync(0xffffffffu, Zn, 0);
-            Zc = (float)Zn;
+            Zc = (float)(Zn * a.pos_scale);          // the filter works in scaled units (exact factor)
             eZc = 1e-7f * fabsf(Zc) + 1e-30f;
             if (nx >= 0) {
                 bk = -1;                                       // locate the winner's entry for FILL
