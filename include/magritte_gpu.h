@@ -241,6 +241,41 @@ mgt_status mgt_ng_accelerate(mgt_model *m, const mgt_ng_opts *opts, int *accepte
  */
 mgt_status mgt_ali_solve(mgt_model *m, const mgt_ali_opts *opts, mgt_ali_stats *stats, void *stream);
 
+/*
+ * Ng extrapolation without any device allocation.  The paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory -- an application whose own allocator owns the whole GPU (a pool
+ * carved out at start-up that nothing else may grow), or an iteration loop
+ * that must not call cudaMalloc/cudaFree because those calls can synchronise
+ * the device and stall the caller's other streams.
+ *
+ * Computes the prediction of mgt_ng_accelerate from iterates the caller holds:
+ * with r_k = x_{k+1} - x_k (k = 0..n_iterates-2) and G = R R^T,
+ * c = G^-1 1 / (1^T G^-1 1) and prediction = sum_k c_k x_{k+1}.
+ *   n_iterates  2..MGT_NG_NOALLOC_MAX_ITERATES; larger counts are rejected
+ *               with MGT_ERR_ARG (the scratch holds at most 16 residuals)
+ *   iterates    device, [n_iterates][len] f64 row-major, oldest first
+ *   len         elements per iterate, >= 1
+ *   prediction  device, [len] f64 (caller-owned; may not alias iterates)
+ *   coef        host, [n_iterates-1] coefficients c_k, may be NULL
+ *   n_negative  host, number of negative prediction entries, may be NULL
+ * Both device buffers must be on the current device.  MGT_ERR_SINGULAR (the
+ * Gram matrix cannot be solved) leaves `prediction` untouched.  Synchronises
+ * `stream`.
+ *
+ * Working memory is one static device array of MGT_NG_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading this library holds until the process exits; the call
+ * itself allocates nothing on the device.  The first call on a device looks
+ * up that device's address of the array (cudaGetSymbolAddress), so make it
+ * before any stream capture.  All calls share the one array: calls that can
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.
+ */
+#define MGT_NG_NOALLOC_MAX_ITERATES 17
+#define MGT_NG_NOALLOC_SCRATCH_BYTES 157952
+mgt_status mgt_ng_extrapolate_noalloc(int32_t n_iterates, const double *iterates, int64_t len,
+                                      double *prediction, double *coef, int64_t *n_negative, void *stream);
+
 /* Wait for the model's work on `stream` and report any device-side error. */
 mgt_status mgt_sync(mgt_model *m, void *stream);
 

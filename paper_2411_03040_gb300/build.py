@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmgt.so")
-SOURCES = ["api.cu", "k_geom.cu", "k_fs.cu", "k_se.cu", "k_ng.cu"]
+SOURCES = ["api.cu", "k_geom.cu", "k_fs.cu", "k_se.cu", "k_ng.cu", "k_ng_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -73,6 +73,7 @@ SIGNATURES = {
     "mgt_ng_accelerate": [_P, ctypes.POINTER(mgt_ng_opts), ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(_f64), _P],
     "mgt_ali_solve": [_P, ctypes.POINTER(mgt_ali_opts), ctypes.POINTER(mgt_ali_stats), _P],
+    "mgt_ng_extrapolate_noalloc": [_i32, _P, _i64, _P, _P, ctypes.POINTER(_i64), _P],
     "mgt_sync": [_P, _P],
     "mgt_model_sizes": [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                         ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
@@ -260,6 +261,19 @@ def mgt_ali_solve(m: Model, n_iter=20, precision=MGT_FP32_MIXED, ng_mode=MGT_NG_
     st = mgt_ali_stats()
     _check(load().mgt_ali_solve(m.handle, ctypes.byref(o), ctypes.byref(st), _stream(stream)), "mgt_ali_solve")
     return dict(iterations=st.iterations, ng_accepted=st.ng_accepted, last_maxrel=st.last_maxrel)
+
+
+def mgt_ng_extrapolate_noalloc(iterates, prediction, stream=None):
+    """Ng prediction from ``iterates`` (device tensor [n][len] f64, oldest
+    first) into ``prediction`` (device tensor [len] f64) without any device
+    allocation; returns (coefficients, number of negative entries)."""
+    n = int(iterates.shape[0])
+    ln = int(prediction.numel())
+    coef = np.zeros(max(n - 1, 1), np.float64)
+    neg = _i64(0)
+    _check(load().mgt_ng_extrapolate_noalloc(n, _ptr(iterates), ln, _ptr(prediction), _ptr(coef),
+                                             ctypes.byref(neg), _stream(stream)), "mgt_ng_extrapolate_noalloc")
+    return coef[:n - 1], neg.value
 
 
 def mgt_sync(m: Model, stream=None):
