@@ -211,7 +211,7 @@ static mgt_status validate(const mgt_model_desc *d)
 
 static void free_model(mgt_model *m)
 {
-    void *ptrs[] = {m->d_nbr_pos, m->d_nbr_hl, m->d_order, m->d_pos, m->d_vel, m->d_temp, m->d_vturb2, m->d_ncoll, m->d_nspec, m->d_w64, m->d_w32,
+    void *ptrs[] = {m->d_nbr_pos, m->d_nbr_hl, m->d_pos_hl, m->d_vel_hl, m->d_dirs32, m->d_order, m->d_pos, m->d_vel, m->d_temp, m->d_vturb2, m->d_ncoll, m->d_nspec, m->d_w64, m->d_w32,
                     m->d_nbr_off, m->d_nbrs, m->d_bnd, m->d_dirs, m->d_pairs, m->d_xq, m->d_wq, m->d_line_tab,
                     m->d_line_ul, m->d_level_tab, m->d_coll_tab, m->d_coll_ul, m->d_entry, m->d_pops,
                     m->d_pops_prev, m->d_line32, m->d_line64, m->d_J, m->d_Lst, m->d_err, m->d_count,
@@ -368,6 +368,9 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
     MGT_TRY(dalloc(&m->d_nbrs, m->nnz));
     MGT_TRY(dalloc(&m->d_nbr_pos, 3 * m->nnz));
     MGT_TRY(dalloc(&m->d_nbr_hl, 6 * m->nnz));
+    MGT_TRY(dalloc(&m->d_pos_hl, 6 * N));
+    MGT_TRY(dalloc(&m->d_vel_hl, 6 * N));
+    MGT_TRY(dalloc(&m->d_dirs32, (size_t)m->R));
     MGT_TRY(dalloc(&m->d_order, N));
     MGT_TRY(dalloc(&m->d_bnd, N));
     MGT_TRY(dalloc(&m->d_dirs, 3 * (size_t)m->R));
@@ -418,9 +421,28 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
             }
         // |xs - (hi + lo)| <= 2^-24 |lo| <= 2^-48 |xs| <= 2^-48; four times that, for both endpoints
         m->pos_slack = (float)std::ldexp(1.0, -46);
+        // per point: the scaled position and v/c, each split into float hi + lo
+        std::vector<float> phl(6 * (size_t)N), vhl(6 * (size_t)N);
+        for (int64_t i = 0; i < N; ++i)
+            for (int c = 0; c < 3; ++c) {
+                const double xs = d->pos[3 * i + c] * m->pos_scale;
+                const float hi = (float)xs;
+                phl[6 * i + c] = hi;
+                phl[6 * i + 3 + c] = (float)(xs - (double)hi);
+                const double vb = d->vel[3 * i + c] / kC;
+                const float vh = (float)vb;
+                vhl[6 * i + c] = vh;
+                vhl[6 * i + 3 + c] = (float)(vb - (double)vh);
+            }
+        std::vector<float4> d32(m->R);
+        for (int r = 0; r < m->R; ++r)
+            d32[r] = make_float4((float)d->dirs[3 * r], (float)d->dirs[3 * r + 1], (float)d->dirs[3 * r + 2], 0.0f);
         MGT_TRY(upload(m->d_nbr_pos, np.data(), np.size(), s));
         MGT_TRY(upload(m->d_nbr_hl, hl.data(), hl.size(), s));
-        MGT_CUDA(cudaStreamSynchronize(s));   // np goes out of scope
+        MGT_TRY(upload(m->d_pos_hl, phl.data(), phl.size(), s));
+        MGT_TRY(upload(m->d_vel_hl, vhl.data(), vhl.size(), s));
+        MGT_TRY(upload(m->d_dirs32, d32.data(), d32.size(), s));
+        MGT_CUDA(cudaStreamSynchronize(s));   // the host staging vectors go out of scope
         const std::vector<int32_t> ord = morton_order(d->pos, N);
         MGT_TRY(upload(m->d_order, ord.data(), (size_t)N, s));
         MGT_CUDA(cudaStreamSynchronize(s));

@@ -165,7 +165,12 @@ template <int LPT> __device__ __forceinline__ void load_vec(const double *p, dou
 
 // The trapezoid / erf decision re-taken in FP64 for a segment whose FP32
 // Doppler-shift ratio lies within rounding of the threshold, so that both
-// precisions (and the FP64 reference) branch alike.
+// precisions (and the FP64 reference) branch alike.  The FP32 ratio comes from
+// velocity projections formed from hi + lo floats of v/c: its error is about
+// 2e-7 |v_far - v_near|_1 / (c wbar) + 4e-7 |du|, below 7e-5 (2e-4 of the
+// threshold 0.35) for velocity jumps up to ~300 line widths between
+// neighbouring points.
+constexpr float kSwitchBand = 2e-4f;
 __device__ __noinline__ bool trapezoid_fp64(const FSArgs &a, int r, int64_t c_far, int64_t c_near, double xq64,
                                             double wo64)
 {
@@ -329,7 +334,7 @@ __device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, 
         const T g_n = Prec<T>::gauss(z_n * row[2 * a.Mpad + 1]);
         const T du = -Bq * sf.dbw;
         bool trap = fabs(du) < thr;
-        if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(2e-5) * thr) trap = trapezoid_fp64(a, r, c_f, c_n, xq64, wo64);
+        if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(kSwitchBand) * thr) trap = trapezoid_fp64(a, r, c_f, c_n, xq64, wo64);
         T cf, cn;
         segment_coefs<T>(trap, sf.dx, du, z_f, g_f, w_f, g_n, w_n, a.width_mode, cf, cn);
         eliminate_row<T, LPT>(cf, cn, chi_f, S_f, chi_n, P, Y, aa);
@@ -631,7 +636,7 @@ template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds
                         const T g_n = Prec<T>::gauss(z_n * rown[2 * a.Mpad + 1]);
                         const T du = -Bq * sf.dbw;
                         bool trap = fabs(du) < thr;
-                        if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(2e-5) * thr) {
+                        if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(kSwitchBand) * thr) {
                             const int64_t c_f = __ldg(&a.s32[s0 + k - 1].x);
                             const int64_t c_n = k > 1 ? (int64_t)__ldg(&a.s32[s0 + k - 2].x) : o;
                             trap = trapezoid_fp64(a, r, c_f, c_n, xq64, wo64);

@@ -149,6 +149,8 @@ struct WalkArgs {
     double pos_scale;         // power of two near 1 / (largest coordinate): exact scaling
     const uint8_t *bnd;
     const double *dirs;
+    const float *pos_hl;      // [N][6] positions times pos_scale, split into float hi + lo
+    const float4 *dirs32;     // [R] directions in FP32
     const int32_t *order;     // walks of one direction are visited in this point order
     float pos_slack;          // bound on |x - (hi + lo)| over all coordinates
     unsigned long long *n_exact;   // steps decided by the FP64 predicates
@@ -188,32 +190,28 @@ __device__ __noinline__ int64_t walk_next_exact(const WalkArgs &a, int64_t c, do
     return best;
 }
 
-// Per-walk constants.
+// Per-walk constants, all FP32 (GB300's FP64 pipe is far too narrow for
+// per-walk or per-step FP64 work; the FP64 values are loaded only on the rare
+// steps the FP32 filter cannot settle).
 struct WalkFrame {
-    double xo, yo, zo, n0, n1, n2;     // FP64 origin and direction
-    float ohx, ohy, ohz, olx, oly, olz; // origin split into hi + lo floats
+    float ohx, ohy, ohz, olx, oly, olz; // origin (scaled) split into hi + lo floats
     float f0, f1, f2;                  // direction in FP32
 };
 
 __device__ __forceinline__ WalkFrame make_frame(const WalkArgs &a, int64_t o, int r)
 {
     WalkFrame f;
-    f.n0 = a.dirs[3 * r];
-    f.n1 = a.dirs[3 * r + 1];
-    f.n2 = a.dirs[3 * r + 2];
-    f.xo = a.pos[3 * o];
-    f.yo = a.pos[3 * o + 1];
-    f.zo = a.pos[3 * o + 2];
-    const double sx = f.xo * a.pos_scale, sy = f.yo * a.pos_scale, sz = f.zo * a.pos_scale;
-    f.ohx = (float)sx;
-    f.ohy = (float)sy;
-    f.ohz = (float)sz;
-    f.olx = (float)(sx - (double)f.ohx);
-    f.oly = (float)(sy - (double)f.ohy);
-    f.olz = (float)(sz - (double)f.ohz);
-    f.f0 = (float)f.n0;
-    f.f1 = (float)f.n1;
-    f.f2 = (float)f.n2;
+    const float *p = a.pos_hl + 6 * o;
+    f.ohx = p[0];
+    f.ohy = p[1];
+    f.ohz = p[2];
+    f.olx = p[3];
+    f.oly = p[4];
+    f.olz = p[5];
+    const float4 n = a.dirs32[r];
+    f.f0 = n.x;
+    f.f1 = n.y;
+    f.f2 = n.z;
     return f;
 }
 
@@ -243,13 +241,13 @@ __device__ __forceinline__ float warp_min(float v)
 // the same expression).  The point lists are therefore those of the FP64 rule.
 //
 // FILL = false: half-ray length and stall count.  FILL = true: also the step
-// records (see Step32): dx and the widths in FP32 from hi/lo positions, the
-// velocity projections beta and dbeta in FP64.
+// records (see Step32), all in FP32: dx from the hi/lo positions, the
+// velocity projections beta and dbeta from hi/lo values of v/c, the widths.
 // ---------------------------------------------------------------------------
 template <bool FILL>
 __global__ void __launch_bounds__(256) k_trace_warp(WalkArgs a, int64_t *__restrict__ len_or_off,
                                                     unsigned long long *__restrict__ n_stall,
-                                                    const double *__restrict__ vel, const float2 *__restrict__ w32,
+                                                    const float *__restrict__ vel_hl, const float2 *__restrict__ w32,
                                                     float inv_Lunit, int width_mode, Step32 *__restrict__ steps,
                                                     int *__restrict__ err)
 {
@@ -265,14 +263,17 @@ __global__ void __launch_bounds__(256) k_trace_warp(WalkArgs a, int64_t *__restr
         base = len_or_off[wi];
         cap = len_or_off[wi + 1] - base;
     }
-    // previous point (for the step records, lane 0)
+    // previous point (for the step records, lane 0): scaled position and
+    // v/c as float hi + lo, relative width; the origin's v/c
     float ph[3] = {f.ohx, f.ohy, f.ohz}, pl[3] = {f.olx, f.oly, f.olz};
-    double pvx = 0, pvy = 0, pvz = 0, vox = 0, voy = 0, voz = 0;
+    float pvh[3] = {0, 0, 0}, pvl[3] = {0, 0, 0}, voh[3] = {0, 0, 0}, vol[3] = {0, 0, 0};
     float pw = 0.0f;
     if (FILL && lane == 0) {
-        vox = pvx = vel[3 * o];
-        voy = pvy = vel[3 * o + 1];
-        voz = pvz = vel[3 * o + 2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            voh[d] = pvh[d] = vel_hl[6 * o + d];
+            vol[d] = pvl[d] = vel_hl[6 * o + 3 + d];
+        }
         pw = w32[o].x;
     }
     int64_t c = o, n = 0;
@@ -339,13 +340,14 @@ __global__ void __launch_bounds__(256) k_trace_warp(WalkArgs a, int64_t *__restr
             double Zn = 0.0;
             if (lane == 0) {
                 atomicAdd(a.n_exact, 1ULL);
+                const double xo = a.pos[3 * o], yo = a.pos[3 * o + 1], zo = a.pos[3 * o + 2];
+                const double n0 = a.dirs[3 * r], n1 = a.dirs[3 * r + 1], n2 = a.dirs[3 * r + 2];
                 double Zc64 = 0.0;
                 if (c != o) {
                     const double *q = a.pos + 3 * c;
-                    Zc64 = dot3_exact(__dsub_rn(q[0], f.xo), __dsub_rn(q[1], f.yo), __dsub_rn(q[2], f.zo), f.n0,
-                                      f.n1, f.n2);
+                    Zc64 = dot3_exact(__dsub_rn(q[0], xo), __dsub_rn(q[1], yo), __dsub_rn(q[2], zo), n0, n1, n2);
                 }
-                v = walk_next_exact(a, c, f.xo, f.yo, f.zo, f.n0, f.n1, f.n2, Zc64, &Zn);
+                v = walk_next_exact(a, c, xo, yo, zo, n0, n1, n2, Zc64, &Zn);
             }
             nx = __shfl_sync(0xffffffffu, v, 0);
             Zn = __shfl_sync(0xffffffffu, Zn, 0);
@@ -382,21 +384,30 @@ __global__ void __launch_bounds__(256) k_trace_warp(WalkArgs a, int64_t *__restr
             const float ey = (hl[1] - ph[1]) + (hl[4] - pl[1]);
             const float ez = (hl[2] - ph[2]) + (hl[5] - pl[2]);
             const float dxs = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex))) * inv_Lunit;
-            const double vx = vel[3 * nx], vy = vel[3 * nx + 1], vz = vel[3 * nx + 2];
-            const double beta = (f.n0 * (vx - vox) + f.n1 * (vy - voy) + f.n2 * (vz - voz)) / kC;
-            const double dbeta = (f.n0 * (vx - pvx) + f.n1 * (vy - pvy) + f.n2 * (vz - pvz)) / kC;
+            // velocity differences from hi + lo floats: relative error ~1e-7 of
+            // |v_c - v_o| / c, well inside the FP32 path's tolerance
+            const float *vq = vel_hl + 6 * nx;
+            float vh[3], vl[3], db[3], dp[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                vh[d] = vq[d];
+                vl[d] = vq[3 + d];
+                db[d] = (vh[d] - voh[d]) + (vl[d] - vol[d]);
+                dp[d] = (vh[d] - pvh[d]) + (vl[d] - pvl[d]);
+            }
+            const float beta = fmaf(f.f2, db[2], fmaf(f.f1, db[1], f.f0 * db[0]));
+            const float dbeta = fmaf(f.f2, dp[2], fmaf(f.f1, dp[1], f.f0 * dp[0]));
             const float wq = w32[nx].x;
             const float wbar = width_mode == 0 ? sqrtf(0.5f * (wq * wq + pw * pw)) : 0.5f * (wq + pw);
-            steps[base + n] = make_int4((int)nx, __float_as_int(dxs), __float_as_int((float)beta),
-                                        __float_as_int((float)dbeta / wbar));
+            steps[base + n] = make_int4((int)nx, __float_as_int(dxs), __float_as_int(beta),
+                                        __float_as_int(dbeta / wbar));
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 ph[d] = hl[d];
                 pl[d] = hl[3 + d];
+                pvh[d] = vh[d];
+                pvl[d] = vl[d];
             }
-            pvx = vx;
-            pvy = vy;
-            pvz = vz;
             pw = wq;
         }
         ++n;
@@ -447,8 +458,9 @@ __global__ void k_steps64(int64_t N, int32_t R, const int64_t *__restrict__ off,
 mgt_status trace_all(mgt_model *m, cudaStream_t s)
 {
     const int64_t W = (int64_t)m->R * m->N;
-    WalkArgs a{m->N,       m->R,          m->d_pos,       m->d_nbr_off, m->d_nbrs,     m->d_nbr_pos,
-               m->d_nbr_hl, m->pos_scale, m->d_bnd, m->d_dirs, m->d_order, m->pos_slack, m->d_count + 2};
+    WalkArgs a{m->N,        m->R,         m->d_pos,    m->d_nbr_off, m->d_nbrs,  m->d_nbr_pos,
+               m->d_nbr_hl, m->pos_scale, m->d_bnd,    m->d_dirs,    m->d_pos_hl, m->d_dirs32,
+               m->d_order,  m->pos_slack, m->d_count + 2};
     if (!m->d_ray_off) MGT_CUDA(cudaMalloc(&m->d_ray_off, sizeof(int64_t) * (W + 1)));
     int64_t *d_len = nullptr;
     MGT_CUDA(cudaMallocAsync(&d_len, sizeof(int64_t) * (W + 1), s));
@@ -499,7 +511,7 @@ mgt_status trace_all(mgt_model *m, cudaStream_t s)
     m->n_stalls = (int64_t)stalls;
     m->n_exact_steps = (int64_t)exact_steps;   // pass 1 only
     if (total > 0) {
-        k_trace_warp<true><<<ceil_div(W * 32, 256), 256, 0, s>>>(a, m->d_ray_off, nullptr, m->d_vel, m->d_w32,
+        k_trace_warp<true><<<ceil_div(W * 32, 256), 256, 0, s>>>(a, m->d_ray_off, nullptr, m->d_vel_hl, m->d_w32,
                                                                  (float)(1.0 / (m->pos_scale * m->L_unit)),
                                                                  m->opts.width_mode,
                                                                  m->d_steps32, m->d_err);

@@ -77,6 +77,9 @@ struct mgt_model {
     int32_t *d_nbr_off = nullptr, *d_nbrs = nullptr;
     double *d_nbr_pos = nullptr;               // [nnz][3] position of each neighbour entry
     float *d_nbr_hl = nullptr;                 // [nnz][6] the same times pos_scale, split into float hi + lo
+    float *d_pos_hl = nullptr;                 // [N][6] positions times pos_scale, float hi + lo
+    float *d_vel_hl = nullptr;                 // [N][6] velocities / c, float hi + lo
+    float4 *d_dirs32 = nullptr;                // [R] directions in FP32 {n0, n1, n2, 0}
     double pos_scale = 1.0;                    // power of two near 1 / (largest coordinate)
     float pos_slack = 0.0f;                    // bound on |x pos_scale - (hi + lo)|
     int32_t *d_order = nullptr;                // [N] points in Morton (Z-curve) order
