@@ -37,8 +37,10 @@ mgt_status check_device_error(mgt_model *m, cudaStream_t s)
     MGT_CUDA(cudaStreamSynchronize(s));
     if (h[0] == kDevOk) return MGT_OK;
     MGT_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(int) * 4, s));
-    if (h[0] == kDevTimeout) return set_error(MGT_ERR_TIMEOUT, "a bounded device loop ran out");
-    return set_error(MGT_ERR_BOUNDS, "a device index check failed");
+    const std::string where = " (site " + std::to_string(h[1]) + ", item " + std::to_string(h[2]) + ", step " +
+                              std::to_string(h[3]) + ")";
+    if (h[0] == kDevTimeout) return set_error(MGT_ERR_TIMEOUT, "a bounded device loop ran out" + where);
+    return set_error(MGT_ERR_BOUNDS, "a device index check failed" + where);
 }
 
 // ---------------------------------------------------------------------------
@@ -135,7 +137,7 @@ static mgt_status validate(const mgt_model_desc *d)
     if (!d) return set_error(MGT_ERR_ARG, "desc is NULL");
     const int64_t N = d->n_points;
     if (N < 1) return set_error(MGT_ERR_ARG, "n_points must be >= 1");
-    if (N > (int64_t)1 << 30) return set_error(MGT_ERR_ARG, "n_points too large");
+    if (N >= (int64_t)kEntEmpty) return set_error(MGT_ERR_ARG, "n_points must be below 2^30 - 1");
     if (!d->pos || !d->vel || !d->temp || !d->vturb2 || !d->n_coll || !d->n_spec || !d->nbr_offsets || !d->nbrs ||
         !d->dirs || !d->energy_J || !d->g || !d->up || !d->lo || !d->A || !d->freq_Hz)
         return set_error(MGT_ERR_ARG, "a required input pointer is NULL");
@@ -151,7 +153,7 @@ static mgt_status validate(const mgt_model_desc *d)
     for (int64_t i = 0; i < N; ++i)
         if (d->nbr_offsets[i + 1] < d->nbr_offsets[i]) return set_error(MGT_ERR_ARG, "nbr_offsets must not decrease");
     const int64_t nnz = d->nbr_offsets[N];
-    if (nnz >= ((int64_t)1 << 31)) return set_error(MGT_ERR_ARG, "too many neighbour entries");
+    if (nnz + N + 16 >= ((int64_t)1 << 31)) return set_error(MGT_ERR_ARG, "too many neighbour entries");
     for (int64_t k = 0; k < nnz; ++k)
         if (d->nbrs[k] < 0 || d->nbrs[k] >= N) return set_error(MGT_ERR_ARG, "neighbour index out of range");
     if (d->n_boundary < 0 || (d->n_boundary > 0 && !d->boundary)) return set_error(MGT_ERR_ARG, "bad boundary list");
@@ -211,7 +213,7 @@ static mgt_status validate(const mgt_model_desc *d)
 
 static void free_model(mgt_model *m)
 {
-    void *ptrs[] = {m->d_nbr_pos, m->d_nbr_hl, m->d_pos_hl, m->d_vel_hl, m->d_dirs32, m->d_order, m->d_pos, m->d_vel, m->d_temp, m->d_vturb2, m->d_ncoll, m->d_nspec, m->d_w64, m->d_w32,
+    void *ptrs[] = {m->d_nbr_pos, m->d_ent, m->d_ent_off, m->d_pos_hl, m->d_vel_hl, m->d_dirs32, m->d_order, m->d_pos, m->d_vel, m->d_temp, m->d_vturb2, m->d_ncoll, m->d_nspec, m->d_w64, m->d_w32,
                     m->d_nbr_off, m->d_nbrs, m->d_bnd, m->d_dirs, m->d_pairs, m->d_xq, m->d_wq, m->d_line_tab,
                     m->d_line_ul, m->d_level_tab, m->d_coll_tab, m->d_coll_ul, m->d_entry, m->d_pops,
                     m->d_pops_prev, m->d_line32, m->d_line64, m->d_J, m->d_Lst, m->d_err, m->d_count,
@@ -367,7 +369,6 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
     MGT_TRY(dalloc(&m->d_nbr_off, N + 1));
     MGT_TRY(dalloc(&m->d_nbrs, m->nnz));
     MGT_TRY(dalloc(&m->d_nbr_pos, 3 * m->nnz));
-    MGT_TRY(dalloc(&m->d_nbr_hl, 6 * m->nnz));
     MGT_TRY(dalloc(&m->d_pos_hl, 6 * N));
     MGT_TRY(dalloc(&m->d_vel_hl, 6 * N));
     MGT_TRY(dalloc(&m->d_dirs32, (size_t)m->R));
@@ -402,7 +403,6 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
     MGT_TRY(upload(m->d_nbrs, d->nbrs, m->nnz, s));
     {
         std::vector<double> np(3 * (size_t)m->nnz);
-        std::vector<float> hl(6 * (size_t)m->nnz);
         double xmax = 0.0;
         for (int64_t i = 0; i < 3 * N; ++i) xmax = std::max(xmax, std::fabs(d->pos[i]));
         // exact power-of-two scaling that brings coordinates to order one, so
@@ -411,14 +411,7 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
         std::frexp(xmax > 0.0 ? xmax : 1.0, &ex);
         m->pos_scale = std::ldexp(1.0, -ex);
         for (int64_t k = 0; k < m->nnz; ++k)
-            for (int c = 0; c < 3; ++c) {
-                const double x = d->pos[3 * (int64_t)d->nbrs[k] + c];
-                const double xs = x * m->pos_scale;
-                const float hi = (float)xs;
-                np[3 * k + c] = x;
-                hl[6 * k + c] = hi;
-                hl[6 * k + 3 + c] = (float)(xs - (double)hi);
-            }
+            for (int c = 0; c < 3; ++c) np[3 * k + c] = d->pos[3 * (int64_t)d->nbrs[k] + c];
         // |xs - (hi + lo)| <= 2^-24 |lo| <= 2^-48 |xs| <= 2^-48; four times that, for both endpoints
         m->pos_slack = (float)std::ldexp(1.0, -46);
         // per point: the scaled position and v/c, each split into float hi + lo
@@ -434,11 +427,56 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
                 vhl[6 * i + c] = vh;
                 vhl[6 * i + 3 + c] = (float)(vb - (double)vh);
             }
+        // packed walk rows: every point's neighbours in CSR order, the last one
+        // flagged; an empty row holds one kEntEmpty entry; 16 pad entries
+        std::vector<int32_t> eoff(N);
+        int64_t ne = 0;
+        for (int64_t i = 0; i < N; ++i) {
+            eoff[i] = (int32_t)ne;
+            const int64_t deg = d->nbr_offsets[i + 1] - d->nbr_offsets[i];
+            ne += deg > 0 ? deg : 1;
+        }
+        std::vector<float4> ent(2 * (size_t)(ne + 16));
+        auto put = [&](int64_t e, int64_t mpt, uint32_t word) {
+            float v[6] = {0, 0, 0, 0, 0, 0};
+            if (mpt >= 0)
+                for (int c = 0; c < 3; ++c) {
+                    v[c] = phl[6 * mpt + c];
+                    v[3 + c] = phl[6 * mpt + 3 + c];
+                }
+            const int32_t noff = mpt >= 0 ? eoff[mpt] : 0;
+            ent[2 * e] = make_float4(v[0], v[1], v[2], v[3]);
+            float4 b;
+            b.x = v[4];
+            b.y = v[5];
+            std::memcpy(&b.z, &word, 4);
+            std::memcpy(&b.w, &noff, 4);
+            ent[2 * e + 1] = b;
+        };
+        for (int64_t i = 0; i < N; ++i) {
+            const int64_t k0 = d->nbr_offsets[i], k1 = d->nbr_offsets[i + 1];
+            if (k1 == k0) {
+                put(eoff[i], -1, kEntEmpty | kEntLast);
+                continue;
+            }
+            for (int64_t k = k0; k < k1; ++k) {
+                const int64_t mpt = d->nbrs[k];
+                uint32_t word = (uint32_t)mpt;
+                if (k == k1 - 1) word |= kEntLast;
+                if (bnd[mpt]) word |= kEntBnd;
+                put(eoff[i] + (k - k0), mpt, word);
+            }
+        }
+        for (int64_t e = ne; e < ne + 16; ++e) put(e, -1, kEntEmpty | kEntLast);
+        m->n_ent = ne + 16;
+        MGT_TRY(dalloc(&m->d_ent, ent.size()));
+        MGT_TRY(dalloc(&m->d_ent_off, (size_t)N));
+        MGT_TRY(upload(m->d_ent, ent.data(), ent.size(), s));
+        MGT_TRY(upload(m->d_ent_off, eoff.data(), (size_t)N, s));
         std::vector<float4> d32(m->R);
         for (int r = 0; r < m->R; ++r)
             d32[r] = make_float4((float)d->dirs[3 * r], (float)d->dirs[3 * r + 1], (float)d->dirs[3 * r + 2], 0.0f);
         MGT_TRY(upload(m->d_nbr_pos, np.data(), np.size(), s));
-        MGT_TRY(upload(m->d_nbr_hl, hl.data(), hl.size(), s));
         MGT_TRY(upload(m->d_pos_hl, phl.data(), phl.size(), s));
         MGT_TRY(upload(m->d_vel_hl, vhl.data(), vhl.size(), s));
         MGT_TRY(upload(m->d_dirs32, d32.data(), d32.size(), s));

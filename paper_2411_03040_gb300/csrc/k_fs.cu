@@ -28,6 +28,17 @@
 // dtau -> 0 is exact and FP32 keeps its relative accuracy.  At the origin,
 // with h = (a_L + a_R)/2 from the two adjacent segments,
 //     u = (S h + Y_L + Y_R) / (h + P_L + P_R),  Lambda*_oo = h / (h + P_L + P_R).
+// The kernels carry half depths (alpha = a/2, beta = b/2) and Pi = 2P, which
+// removes the halving from every row: h = alpha + beta, G = 2h + Pi (= 2H),
+// q = 1/(1 + beta G), Pi <- G q, Y <- (S h + Y) q -- eight FP32 operations
+// and one reciprocal per line and step, from Pi = 2, alpha = 0 at the far end.
+//
+// Staged kernel, per chunk of a half-ray: first every thread of the CTA
+// computes line-independent segment coefficients for a share of the chunk's
+// (bin, step) pairs (Gaussian at both ends, trapezoid/erf switch, erf
+// difference) into shared memory, then each thread eliminates its lines
+// reading one coefficient pair per step.  The line groups of a bin no longer
+// repeat that work.
 #include <algorithm>
 
 #include "mgt_common.cuh"
@@ -191,13 +202,15 @@ __device__ __noinline__ bool trapezoid_fp64(const FSArgs &a, int r, int64_t c_fa
 // when a + b < 0 leaves E unchanged, after which E = erfc(a) - erfc(b) has no
 // cancellation: either both arguments are >= 0 (tails as differences of small
 // erfc values) or they straddle zero and E >= erf(|du|/2) (|du| >= threshold).
+// Both coefficients are returned halved: half the segment's optical depth is
+// cf chi~_far + cn chi~_near.
 template <typename T>
 __device__ __forceinline__ void segment_coefs(bool trap, T dx, T du, T z_f, T g_f, T w_f, T g_n, T w_n, int width_mode,
                                               T &cf, T &cn)
 {
     if (trap) {
-        cf = T(0.5) * dx * g_f;
-        cn = T(0.5) * dx * g_n;
+        cf = T(0.25) * dx * g_f;
+        cn = T(0.25) * dx * g_n;
     } else {
         const T iwbar = width_mode == 0 ? Prec<T>::rsqrt_(T(0.5) * (w_f * w_f + w_n * w_n))
                                         : Prec<T>::rcp(T(0.5) * (w_f + w_n));
@@ -208,31 +221,36 @@ __device__ __forceinline__ void segment_coefs(bool trap, T dx, T du, T z_f, T g_
             b = -t;
         }
         const T E = Prec<T>::erfc_(a) - Prec<T>::erfc_(b);
-        const T kk = dx * T(0.25 * kSqrtPi) * E * iwbar * Prec<T>::rcp(du);
+        const T kk = dx * T(0.125 * kSqrtPi) * E * iwbar * Prec<T>::rcp(du);
         cf = kk * w_f;
         cn = kk * w_n;
     }
 }
 
-// One elimination row for the thread's LPT lines.
+// One elimination row for the thread's LPT lines, in the halved variables:
+// cf, cn halved coefficients; aa[l] = alpha (half depth of the previous
+// segment); P[l] = Pi = 2P.
 template <typename T, int LPT>
 __device__ __forceinline__ void eliminate_row(T cf, T cn, const T (&chi_f)[LPT], const T (&S_f)[LPT],
                                               const T (&chi_n)[LPT], T (&P)[LPT], T (&Y)[LPT], T (&aa)[LPT])
 {
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
-        const T b = cf * chi_f[l] + cn * chi_n[l];
-        const T h = T(0.5) * (aa[l] + b);
-        const T H = h + P[l];
-        const T q = Prec<T>::rcp(T(1) + b * H);
-        P[l] = H * q;
+        const T b = cf * chi_f[l] + cn * chi_n[l];     // beta, half the segment depth
+        const T h = aa[l] + b;
+        const T G = T(2) * h + P[l];
+        const T q = Prec<T>::rcp(b * G + T(1));
+        P[l] = G * q;
         Y[l] = (S_f[l] * h + Y[l]) * q;
         aa[l] = b;
     }
 }
 
-// Combine both halves at the origin and accumulate w_q u and w_q Lambda*
-// (compensated sums kept in shared memory, one column per thread).
+// Combine both halves at the origin and accumulate w_q u (compensated) and
+// w_q Lambda*_oo (plain: at most a few hundred positive terms of similar size,
+// relative error ~1e-6) in shared memory, one column per thread:
+// acc[0] sum of J, acc[1] its compensation, acc[2] sum of Lambda*.  Inputs in
+// the halved variables of eliminate_row.
 template <typename T, int LPT>
 __device__ __forceinline__ void combine_accumulate(T wqn, const T (&So)[LPT], const T (&PL)[LPT], const T (&YL)[LPT],
                                                    const T (&aL)[LPT], const T (&PR)[LPT], const T (&YR)[LPT],
@@ -240,19 +258,16 @@ __device__ __forceinline__ void combine_accumulate(T wqn, const T (&So)[LPT], co
 {
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
-        const T h = T(0.5) * (aL[l] + aR[l]);
-        const T inv = Prec<T>::rcp(h + PL[l] + PR[l]);
+        const T h = aL[l] + aR[l];
+        const T inv = Prec<T>::rcp(h + T(0.5) * (PL[l] + PR[l]));
         const T u = (So[l] * h + YL[l] + YR[l]) * inv;
         const T Ls = h * inv;
         T *sJ = acc + (0 * LPT + l) * bd + tid, *cJ = acc + (1 * LPT + l) * bd + tid;
-        T *sL = acc + (2 * LPT + l) * bd + tid, *cL = acc + (3 * LPT + l) * bd + tid;
-        T y = wqn * u - *cJ, tt = *sJ + y;
+        T *sL = acc + (2 * LPT + l) * bd + tid;
+        const T y = wqn * u - *cJ, tt = *sJ + y;
         *cJ = (tt - *sJ) - y;
         *sJ = tt;
-        y = wqn * Ls - *cL;
-        tt = *sL + y;
-        *cL = (tt - *sL) - y;
-        *sL = tt;
+        *sL += wqn * Ls;
     }
 }
 
@@ -304,7 +319,7 @@ __device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, 
     const int n = (int)(a.ray_off[t + 1] - s0);
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
-        P[l] = T(1);
+        P[l] = T(2);
         Y[l] = Ibg[l];
         aa[l] = T(0);
     }
@@ -357,8 +372,8 @@ template <typename T, int LPT> __global__ void __launch_bounds__(256) k_fs_gathe
     const int bd = blockDim.x, tid = threadIdx.x;
     const int QG = a.Q * a.Gb;
     const int Mb = a.Gb * LPT;
-    T *acc = reinterpret_cast<T *>(smem_raw);                       // [4][LPT][bd]
-    double *red = reinterpret_cast<double *>(acc + 4 * LPT * bd);   // [2][OPB][Mb][Q]
+    T *acc = reinterpret_cast<T *>(smem_raw);                       // [3][LPT][bd]
+    double *red = reinterpret_cast<double *>(acc + 4 * LPT * bd);   // [2][OPB][Mb][Q] (acc rounded up to 4 rows)
 
     const int lo_ = tid / QG, rem = tid - lo_ * QG, gl = rem / a.Q, q = rem - gl * a.Q;
     const int gg = blockIdx.y * a.Gb + gl;
@@ -372,7 +387,7 @@ template <typename T, int LPT> __global__ void __launch_bounds__(256) k_fs_gathe
         background<T, LPT>(a, line0, xq64, wo64, Ibg);
 #pragma unroll
         for (int l = 0; l < LPT; ++l)
-            for (int c = 0; c < 4; ++c) acc[(c * LPT + l) * bd + tid] = T(0);
+            for (int c = 0; c < 3; ++c) acc[(c * LPT + l) * bd + tid] = T(0);
         const T Aq = T(xq64) * T(wo64), Bq = T(1) + Aq;
         const T wqn = T(a.wq[q]);
         const T *line = reinterpret_cast<const T *>(a.line);
@@ -392,7 +407,7 @@ template <typename T, int LPT> __global__ void __launch_bounds__(256) k_fs_gathe
                 red[((0 * a.OPB + lo_) * Mb + lb + l) * a.Q + q] =
                     (double)acc[(0 * LPT + l) * bd + tid] - (double)acc[(1 * LPT + l) * bd + tid];
                 red[((1 * a.OPB + lo_) * Mb + lb + l) * a.Q + q] =
-                    (double)acc[(2 * LPT + l) * bd + tid] - (double)acc[(3 * LPT + l) * bd + tid];
+                    (double)acc[(2 * LPT + l) * bd + tid];
             }
         }
     }
@@ -525,8 +540,74 @@ __device__ __forceinline__ void issue_chunk(const FSArgs &a, int64_t o, const Ch
     }
 }
 
+// Shared-memory carve-out of the staged kernel (bytes from the dynamic base),
+// computed identically on the host (launch size) and the device.
+struct StagedLayout {
+    int stage, coef, ibg, sab, acc, half0, total;
+};
+
+// Staging buffers [2] and coefficient buffers [2] are contiguous; the final
+// FP64 reduction area aliases them once the last chunk is done.
+template <typename T, int LPT, int CH>
+__host__ __device__ inline StagedLayout staged_layout(int Q, int Mb, int RS, int bd)
+{
+    constexpr int SB = sizeof(T) == 4 ? 16 : 32;
+    constexpr int NPT = CH + 1;
+    auto up = [](int x) { return (x + 15) & ~15; };
+    StagedLayout L;
+    const int rowB = RS * (int)sizeof(T);
+    const int stage_bytes = 2 * NPT * (SB + rowB);
+    const int coef_bytes = 2 * CH * Q * 2 * (int)sizeof(T);
+    const int red_bytes = 2 * Mb * Q * (int)sizeof(double);
+    L.stage = 128;
+    L.coef = L.stage + up(stage_bytes);
+    const int pipe_end = L.coef + up(coef_bytes);
+    L.ibg = pipe_end > L.stage + up(red_bytes) ? pipe_end : L.stage + up(red_bytes);
+    L.sab = L.ibg + up(Mb * Q * (int)sizeof(T));
+    L.acc = L.sab + up(2 * Q * (int)sizeof(T));
+    L.half0 = L.acc + up(3 * LPT * bd * (int)sizeof(T));
+    L.total = L.half0 + up(3 * LPT * bd * (int)sizeof(T));
+    return L;
+}
+
+// Line-independent coefficients of every (bin, step) of one chunk, shared by
+// the CTA's line groups: coef[(k - k_lo) * Q + q] = halved {cf, cn} of step k.
+template <typename T>
+__device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, int k_lo, int k_hi,
+                                            const unsigned char *Sb, const T *Rb, const T *sA, const T *sB,
+                                            typename Prec<T>::V2 *coef, int tid, int bd)
+{
+    constexpr int SB = sizeof(T) == 4 ? 16 : 32;
+    const T thr = (T)a.thr;
+    const int items = a.Q * (k_hi - k_lo + 1);
+#pragma unroll 1
+    for (int it = tid; it < items; it += bd) {
+        const int kk = it / a.Q, q = it - kk * a.Q;
+        const int k = k_lo + kk, jf = kk + 1, jn = kk;
+        const StepG<T> sf = step_from<T>(Sb + jf * SB);
+        const T beta_n = k > 1 ? step_from<T>(Sb + jn * SB).beta : T(0);
+        const T *rowf = Rb + jf * a.RS, *rown = Rb + jn * a.RS;
+        const T w_f = rowf[2 * a.Mpad], w_n = rown[2 * a.Mpad];
+        const T Aq = sA[q], Bq = sB[q];
+        const T z_f = Aq + Bq * sf.beta, z_n = Aq + Bq * beta_n;
+        const T g_f = Prec<T>::gauss(z_f * rowf[2 * a.Mpad + 1]);
+        const T g_n = Prec<T>::gauss(z_n * rown[2 * a.Mpad + 1]);
+        const T du = -Bq * sf.dbw;
+        bool trap = fabs(du) < thr;
+        if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(kSwitchBand) * thr) {
+            const int64_t c_f = reinterpret_cast<const int4 *>(Sb + jf * SB)->x;
+            const int64_t c_n = k > 1 ? (int64_t)reinterpret_cast<const int4 *>(Sb + jn * SB)->x : o;
+            trap = trapezoid_fp64(a, r, c_f, c_n, a.xq[q], a.w64[o]);
+        }
+        T cf, cn;
+        segment_coefs<T>(trap, sf.dx, du, z_f, g_f, w_f, g_n, w_n, a.width_mode, cf, cn);
+        coef[kk * a.Q + q] = {cf, cn};
+    }
+}
+
 template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds__(256, MINB) k_fs_staged(FSArgs a)
 {
+    using V2 = typename Prec<T>::V2;
     constexpr int SB = sizeof(T) == 4 ? 16 : 32;
     constexpr int NPT = CH + 1;
     static_assert(NPT <= 32, "one point row per producer lane");
@@ -534,19 +615,18 @@ template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rowB = a.RS * (int)sizeof(T);
     const int Mb = a.Gb * LPT;
+    const StagedLayout lay = staged_layout<T, LPT, CH>(a.Q, Mb, a.RS, bd);
 
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);                   // [2]
     int *abort_flag = reinterpret_cast<int *>(smem + 16);
-    unsigned char *stage = smem + 128;                                    // steps [2][NPT][SB], rows [2][NPT][rowB]
-    unsigned char *steps_s = stage;
-    unsigned char *rows_s = stage + 2 * NPT * SB;
-    const int stage_bytes = 2 * NPT * (SB + rowB);
-    const int red_bytes = 2 * Mb * a.Q * (int)sizeof(double);
-    unsigned char *after = stage + ((max(stage_bytes, red_bytes) + 127) & ~127);
-    T *ibg = reinterpret_cast<T *>(after);                                // [Mb][Q]
-    T *acc = ibg + ((Mb * a.Q + 3) & ~3);                                 // [4][LPT][bd]
-    T *half0 = acc + 4 * LPT * bd;                                        // [3][LPT][bd] first half's P, Y, a
-    double *red = reinterpret_cast<double *>(stage);                      // reuses the staging area at the end
+    unsigned char *steps_s = smem + lay.stage;                            // steps [2][NPT][SB]
+    unsigned char *rows_s = steps_s + 2 * NPT * SB;                       // rows [2][NPT][rowB]
+    V2 *coef = reinterpret_cast<V2 *>(smem + lay.coef);                   // [2][CH][Q]
+    T *ibg = reinterpret_cast<T *>(smem + lay.ibg);                       // [Mb][Q]
+    T *sA = reinterpret_cast<T *>(smem + lay.sab), *sB = sA + a.Q;        // [Q] each
+    T *acc = reinterpret_cast<T *>(smem + lay.acc);                       // [3][LPT][bd]
+    T *half0 = reinterpret_cast<T *>(smem + lay.half0);                   // [3][LPT][bd] first half's P, Y, a
+    double *red = reinterpret_cast<double *>(smem + lay.stage);           // reuses staging + coefficients at the end
 
     const int64_t o = a.order[blockIdx.x];
     const int gl = tid / a.Q, q = tid - gl * a.Q;
@@ -560,14 +640,19 @@ template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    const double xq64 = active ? a.xq[q] : 0.0, wo64 = active ? a.w64[o] : 0.0;
+    const double wo64 = a.w64[o];
+    if (tid < a.Q) {
+        const T Aq = T(a.xq[tid]) * T(wo64);
+        sA[tid] = Aq;
+        sB[tid] = T(1) + Aq;
+    }
     if (active) {
         T Ibg[LPT];
-        background<T, LPT>(a, line0, xq64, wo64, Ibg);
+        background<T, LPT>(a, line0, a.xq[q], wo64, Ibg);
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
             ibg[(gl * LPT + l) * a.Q + q] = Ibg[l];
-            for (int c = 0; c < 4; ++c) acc[(c * LPT + l) * bd + tid] = T(0);
+            for (int c = 0; c < 3; ++c) acc[(c * LPT + l) * bd + tid] = T(0);
         }
     }
     __syncthreads();
@@ -576,13 +661,10 @@ template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds
     const bool any = first_chunk_from(a, o, 0, 0, CH, cur);
     if (any && warp == 0) issue_chunk<T>(a, o, cur, steps_s, rows_s, &bar[0], rowB, lane);
 
-    const T Aq = T(xq64) * T(wo64), Bq = T(1) + Aq;
-    const T thr = (T)a.thr;
     const T wqn = active ? T(a.wq[q]) : T(0);
     int ci = 0;                 // chunks consumed
     bool ok = true;
     T P[LPT], Y[LPT], aa[LPT];
-    T z_f = 0, g_f = 0, w_f = 1;
     for (int p = 0; p < a.P; ++p) {
         const int2 pr = a.pairs[p];
         for (int h = 0; h < 2; ++h) {
@@ -592,14 +674,21 @@ template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds
             half_extent(a, o, p, h, s0, n);
 #pragma unroll
             for (int l = 0; l < LPT; ++l) {
-                P[l] = T(1);
+                P[l] = T(2);
                 Y[l] = active ? ibg[(gl * LPT + l) * a.Q + q] : T(0);
                 aa[l] = T(0);
             }
             for (int k_hi = n; k_hi >= 1; k_hi -= CH) {
                 const int k_lo = max(1, k_hi - CH + 1);
-                // everyone is done with the buffer about to be refilled; stop
-                // together if any wait gave up
+                ok = mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1);
+                const unsigned char *Sb = steps_s + (ci & 1) * NPT * SB;
+                const T *Rb = reinterpret_cast<const T *>(rows_s + (ci & 1) * NPT * rowB);
+                V2 *cf_buf = coef + (ci & 1) * CH * a.Q;
+                if (ok) chunk_coefs<T>(a, o, r, k_lo, k_hi, Sb, Rb, sA, sB, cf_buf, tid, bd);
+                // one barrier per chunk: this chunk's coefficients are complete, and
+                // everyone is done with the previous chunk (its staging buffer is
+                // refilled next, its coefficient buffer on the following chunk);
+                // stop together if any wait gave up
                 if (__syncthreads_or(!ok)) {
                     if (tid == 0) *abort_flag = 1;
                     goto done;
@@ -611,42 +700,17 @@ template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds
                         issue_chunk<T>(a, o, nx, steps_s + ((ci + 1) & 1) * NPT * SB,
                                        rows_s + ((ci + 1) & 1) * NPT * rowB, &bar[(ci + 1) & 1], rowB, lane);
                 }
-                ok = mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1);
-                if (ok && active) {
-                    const unsigned char *Sb = steps_s + (ci & 1) * NPT * SB;
-                    const T *Rb = reinterpret_cast<const T *>(rows_s + (ci & 1) * NPT * rowB);
-                    if (k_hi == n) {            // far end of the half-ray
-                        const int jf = k_hi - k_lo + 1;
-                        const T *row = Rb + jf * a.RS;
-                        w_f = row[2 * a.Mpad];
-                        z_f = Aq + Bq * step_from<T>(Sb + jf * SB).beta;
-                        g_f = Prec<T>::gauss(z_f * row[2 * a.Mpad + 1]);
-                    }
+                if (active) {
+#pragma unroll 1
                     for (int k = k_hi; k >= k_lo; --k) {
                         const int jf = k - k_lo + 1, jn = jf - 1;
-                        const StepG<T> sf = step_from<T>(Sb + jf * SB);
-                        const T beta_n = k > 1 ? step_from<T>(Sb + jn * SB).beta : T(0);
+                        const V2 cc = cf_buf[(k - k_lo) * a.Q + q];
                         const T *rowf = Rb + jf * a.RS, *rown = Rb + jn * a.RS;
                         T chi_f[LPT], S_f[LPT], chi_n[LPT];
                         load_vec<LPT>(rowf + line0, chi_f);
                         load_vec<LPT>(rowf + a.Mpad + line0, S_f);
                         load_vec<LPT>(rown + line0, chi_n);
-                        const T w_n = rown[2 * a.Mpad];
-                        const T z_n = Aq + Bq * beta_n;
-                        const T g_n = Prec<T>::gauss(z_n * rown[2 * a.Mpad + 1]);
-                        const T du = -Bq * sf.dbw;
-                        bool trap = fabs(du) < thr;
-                        if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(kSwitchBand) * thr) {
-                            const int64_t c_f = __ldg(&a.s32[s0 + k - 1].x);
-                            const int64_t c_n = k > 1 ? (int64_t)__ldg(&a.s32[s0 + k - 2].x) : o;
-                            trap = trapezoid_fp64(a, r, c_f, c_n, xq64, wo64);
-                        }
-                        T cf, cn;
-                        segment_coefs<T>(trap, sf.dx, du, z_f, g_f, w_f, g_n, w_n, a.width_mode, cf, cn);
-                        eliminate_row<T, LPT>(cf, cn, chi_f, S_f, chi_n, P, Y, aa);
-                        z_f = z_n;
-                        g_f = g_n;
-                        w_f = w_n;
+                        eliminate_row<T, LPT>(cc.x, cc.y, chi_f, S_f, chi_n, P, Y, aa);
                     }
                 }
                 ++ci;
@@ -678,7 +742,11 @@ done:
     if (*abort_flag) {
         // give in-flight copies a bounded chance to land before the CTA exits
         if (tid == 0) {
-            atomicCAS(a.err, 0, (int)kDevTimeout);
+            if (atomicCAS(a.err, 0, (int)kDevTimeout) == 0) {
+                a.err[1] = 3;
+                a.err[2] = (int)blockIdx.x;
+                a.err[3] = ci;
+            }
             mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1);
             mbar_wait_bounded(&bar[(ci + 1) & 1], ((ci + 1) >> 1) & 1);
         }
@@ -692,7 +760,7 @@ done:
                 red[(0 * Mb + lb + l) * a.Q + q] =
                     (double)acc[(0 * LPT + l) * bd + tid] - (double)acc[(1 * LPT + l) * bd + tid];
                 red[(1 * Mb + lb + l) * a.Q + q] =
-                    (double)acc[(2 * LPT + l) * bd + tid] - (double)acc[(3 * LPT + l) * bd + tid];
+                    (double)acc[(2 * LPT + l) * bd + tid];
             }
         }
     }
@@ -742,12 +810,7 @@ template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_
         a.OPB = 1;
         const int threads = a.Q * a.Gb;
         const int bd = ((threads + 31) / 32) * 32;
-        constexpr int SB = sizeof(T) == 4 ? 16 : 32;
-        const int rowB = a.RS * (int)sizeof(T);
-        const int stage_bytes = 2 * (kChunk + 1) * (SB + rowB);
-        const int red_bytes = 2 * Mb * a.Q * (int)sizeof(double);
-        const size_t smem = 128 + ((std::max(stage_bytes, red_bytes) + 127) & ~127) +
-                            sizeof(T) * (((Mb * a.Q + 3) & ~3) + 7 * LPT * bd);
+        const size_t smem = (size_t)staged_layout<T, LPT, kChunk>(a.Q, Mb, a.RS, bd).total;
         dim3 grid((unsigned)m->N, (unsigned)ceil_div(a.Gtot, a.Gb));
         if (schedule == 3) {
             MGT_CUDA(cudaFuncSetAttribute(k_fs_staged<T, LPT, kChunk, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -145,16 +145,36 @@ struct WalkArgs {
     const int32_t *off;
     const int32_t *nb;
     const double *nb_pos;     // [nnz][3] position of each neighbour entry (contiguous per point)
-    const float *nb_hl;       // [nnz][6] the same positions times pos_scale, split into float hi + lo
     double pos_scale;         // power of two near 1 / (largest coordinate): exact scaling
     const uint8_t *bnd;
     const double *dirs;
+    const float4 *ent;        // packed neighbour entries, two float4 each (WalkEntry layout)
+    const int32_t *ent_off;   // [N] first packed entry of each point's row
     const float *pos_hl;      // [N][6] positions times pos_scale, split into float hi + lo
     const float4 *dirs32;     // [R] directions in FP32
     const int32_t *order;     // walks of one direction are visited in this point order
     float pos_slack;          // bound on |x - (hi + lo)| over all coordinates
     unsigned long long *n_exact;   // steps decided by the FP64 predicates
+    int32_t max_row_chunks;   // bound on the 16-entry chunks of one row scan (packed entries / 16 + 2)
+    int64_t n_ent;            // packed entries (index bound)
 };
+
+__device__ __forceinline__ uint64_t walk_clock_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// First device error wins; err[1..3] say where (site) and which walk / step.
+__device__ __forceinline__ void walk_give_up(int *err, int site, int64_t wg, int64_t n)
+{
+    if (atomicCAS(err, 0, (int)kDevTimeout) == 0) {
+        err[1] = site;
+        err[2] = (int)wg;
+        err[3] = (int)n;
+    }
+}
 
 __device__ __forceinline__ double dot3_exact(double ax, double ay, double az, double bx, double by, double bz)
 {
@@ -215,16 +235,57 @@ __device__ __forceinline__ WalkFrame make_frame(const WalkArgs &a, int64_t o, in
     return f;
 }
 
-__device__ __forceinline__ float warp_min(float v)
+
+// Step records of `cnt` consecutive steps, one per lane of a 16-lane group
+// (the whole warp calls; cnt = 0 in a group with nothing to write): lane j < cnt writes the record of the step
+// ending at its point my_pt, the step starting at the previous lane's point
+// (prev_last for lane 0).  All in FP32: dx from the hi + lo scaled positions,
+// beta = n.(v_c - v_o)/c and dbeta = n.(v_c - v_prev)/c from hi + lo values
+// of v/c (relative error about 1e-7 of |v_c - v_o|/c), the averaged width of
+// the segment.
+__device__ __forceinline__ void write_step_records(const WalkArgs &a, int64_t o, int r, int64_t prev_last,
+                                                   int32_t my_pt, int cnt, const float *__restrict__ vel_hl,
+                                                   const float2 *__restrict__ w32, float inv_Lunit, int width_mode,
+                                                   Step32 *__restrict__ out, int sl)
+{
+    int64_t prev = __shfl_up_sync(0xffffffffu, my_pt, 1, 16);
+    if (sl == 0) prev = prev_last;
+    if (sl >= cnt) return;
+    const int64_t c = my_pt;
+    const float *pc = a.pos_hl + 6 * c, *pp = a.pos_hl + 6 * prev;
+    const float *vc = vel_hl + 6 * c, *vp = vel_hl + 6 * prev, *vo = vel_hl + 6 * o;
+    const float4 n = a.dirs32[r];
+    float e[3], db[3], dp[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        e[d] = (pc[d] - pp[d]) + (pc[3 + d] - pp[3 + d]);
+        db[d] = (vc[d] - vo[d]) + (vc[3 + d] - vo[3 + d]);
+        dp[d] = (vc[d] - vp[d]) + (vc[3 + d] - vp[3 + d]);
+    }
+    const float dxs = sqrtf(fmaf(e[2], e[2], fmaf(e[1], e[1], e[0] * e[0]))) * inv_Lunit;
+    const float beta = fmaf(n.z, db[2], fmaf(n.y, db[1], n.x * db[0]));
+    const float dbeta = fmaf(n.z, dp[2], fmaf(n.y, dp[1], n.x * dp[0]));
+    const float wc = w32[c].x, wp = w32[prev].x;
+    const float wbar = width_mode == 0 ? sqrtf(0.5f * (wc * wc + wp * wp)) : 0.5f * (wc + wp);
+    out[sl] = make_int4((int)c, __float_as_int(dxs), __float_as_int(beta), __float_as_int(dbeta / wbar));
+}
+
+__device__ __forceinline__ float group16_min(float v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 8; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
 // ---------------------------------------------------------------------------
-// One warp per walk.  At each step the lanes evaluate the neighbours of the
-// current point c in parallel with FP32 arithmetic and error bounds that
+// Two walks per warp, one per 16-lane group.  Each step reads the current
+// point's row of packed neighbour entries (WalkEntry: the neighbour's scaled
+// position as float hi + lo, its index with its boundary flag and a
+// last-of-row flag, and the offset of its own row), 16 entries per load, so
+// the next step's row offset, the winner's index and its boundary flag arrive
+// with the candidates: one dependent L2 round trip per step.
+//
+// The lanes evaluate the candidates with FP32 arithmetic and error bounds that
 // cover both the FP32 and the FP64 rounding (generous multiples of the
 // rounding analysis):
 //   offsets    |d32 - d64| <= ed = 2e-6 (|d32|_max + slack)
@@ -238,61 +299,94 @@ __device__ __forceinline__ float warp_min(float v)
 // lane) is accepted only if its upper d2 bound is below every other
 // candidate's lower bound, so near-ties never decide.  Undecided steps run
 // walk_next_exact, the FP64 predicates themselves (exact Z_c recomputed by
-// the same expression).  The point lists are therefore those of the FP64 rule.
+// the same expression), on lane 0 of the group.  The point lists are
+// therefore those of the FP64 rule.
 //
 // FILL = false: half-ray length and stall count.  FILL = true: also the step
-// records (see Step32), all in FP32: dx from the hi/lo positions, the
-// velocity projections beta and dbeta from hi/lo values of v/c, the widths.
+// records (see Step32), 16 at a time, one per lane of the group.
 // ---------------------------------------------------------------------------
 template <bool FILL>
-__global__ void __launch_bounds__(256) k_trace_warp(WalkArgs a, int64_t *__restrict__ len_or_off,
-                                                    unsigned long long *__restrict__ n_stall,
-                                                    const float *__restrict__ vel_hl, const float2 *__restrict__ w32,
-                                                    float inv_Lunit, int width_mode, Step32 *__restrict__ steps,
-                                                    int *__restrict__ err)
+__global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ len_or_off,
+                                              unsigned long long *__restrict__ n_stall,
+                                              const float *__restrict__ vel_hl, const float2 *__restrict__ w32,
+                                              float inv_Lunit, int width_mode, Step32 *__restrict__ steps,
+                                              int *__restrict__ err)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (wg >= (int64_t)a.R * a.N) return;                      // whole warp
-    const int r = (int)(wg / a.N);
-    const int64_t o = a.order[wg - (int64_t)r * a.N];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, sl = lane & 15, grp = lane >> 4;
+    const unsigned gmask = 0xffffu << (16 * grp);
+    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 4;   // walk id
+    const int64_t W = (int64_t)a.R * a.N;
+    if ((wg & ~(int64_t)1) >= W) return;                       // both walks of the warp absent
+    bool live = wg < W;
+    const int r = live ? (int)(wg / a.N) : 0;
+    int64_t o = live ? (int64_t)a.order[wg - (int64_t)r * a.N] : 0;
+    if (o < 0 || o >= a.N) {                                  // index check: record and skip
+        walk_give_up(err, 13, wg, o);
+        o = 0;
+        live = false;
+    }
     const int64_t wi = (int64_t)r * a.N + o;
     const WalkFrame f = make_frame(a, o, r);
     int64_t base = 0, cap = a.N;
-    if (FILL) {
+    if (FILL && live) {
         base = len_or_off[wi];
         cap = len_or_off[wi + 1] - base;
     }
-    // previous point (for the step records, lane 0): scaled position and
-    // v/c as float hi + lo, relative width; the origin's v/c
-    float ph[3] = {f.ohx, f.ohy, f.ohz}, pl[3] = {f.olx, f.oly, f.olz};
-    float pvh[3] = {0, 0, 0}, pvl[3] = {0, 0, 0}, voh[3] = {0, 0, 0}, vol[3] = {0, 0, 0};
-    float pw = 0.0f;
-    if (FILL && lane == 0) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            voh[d] = pvh[d] = vel_hl[6 * o + d];
-            vol[d] = pvl[d] = vel_hl[6 * o + 3 + d];
-        }
-        pw = w32[o].x;
-    }
+    // step records are built 16 at a time: lane j of the group keeps the point
+    // of step (chunk start + j); prev_last is the point before the chunk
+    int32_t my_pt = 0;
+    int64_t prev_last = o;
     int64_t c = o, n = 0;
-    float Zc = 0.0f, eZc = 0.0f;        // Z of o is exactly 0
-    for (;;) {
-        const int32_t k0 = a.off[c], k1 = a.off[c + 1];
+    int32_t c_off = live ? a.ent_off[o] : 0;   // the current point's row of packed entries
+    float Zc = 0.0f, eZc = 0.0f;                // Z of o is exactly 0
+    bool done = !live;
+    // every loop below is bounded: the walk by the point count and a 2 s
+    // clock, a row scan by the number of packed entries; running out records
+    // the site and returns
+    const uint64_t t_start = walk_clock_ns();
+    bool gave_up = false;
+    while (!__all_sync(full, done)) {
+        if (__any_sync(full, walk_clock_ns() - t_start > 2000000000ull)) {
+            if (sl == 0 && !done) walk_give_up(err, 1, wg, n);
+            gave_up = true;
+            break;
+        }
         float bd2 = 3.0e38f, bU = 0.0f, bL = 0.0f, bZ = 0.0f, beZ = 0.0f, minLother = 3.0e38f;
-        int32_t bk = -1;
-        bool undecided = false;
-        for (int32_t kb = k0; kb < k1; kb += 32) {
-            const int32_t k = kb + lane;
-            bool cand = false;
+        uint32_t bword = 0u;
+        int32_t boff = 0;
+        bool have = false, undecided = false, row_open = !done;
+        int32_t chunks = 0;
+        for (int32_t kb = c_off; __any_sync(full, row_open); kb += 16) {
+            if (++chunks > a.max_row_chunks) {
+                if (sl == 0 && row_open) walk_give_up(err, 2, wg, n);
+                gave_up = true;
+                break;
+            }
+            bool cand = false, und = false, last = false;
             float d2 = 3.0e38f, U = 0.0f, Lo = 3.0e38f, Z = 0.0f, eZ = 0.0f;
-            bool und = false;
-            if (k < k1) {
-                const float *hl = a.nb_hl + 6 * (int64_t)k;
-                const float dx = (hl[0] - f.ohx) + (hl[3] - f.olx);
-                const float dy = (hl[1] - f.ohy) + (hl[4] - f.oly);
-                const float dz = (hl[2] - f.ohz) + (hl[5] - f.olz);
+            uint32_t word = 0u;
+            int32_t eoff = 0;
+            float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = e0;
+            if (row_open && (kb + sl < 0 || kb + sl >= a.n_ent)) {   // index check: record and skip
+                walk_give_up(err, 10, wg, kb + sl);
+                row_open = false;
+            }
+            if (row_open) {
+                const float4 *ep = reinterpret_cast<const float4 *>(a.ent + 2 * (int64_t)(kb + sl));
+                e0 = ep[0];
+                e1 = ep[1];
+                word = __float_as_uint(e1.z);
+                eoff = __float_as_int(e1.w);
+                last = (word & kEntLast) != 0u;
+            }
+            // entries up to the group's first last-of-row flag belong to the row
+            const unsigned lastbits = (__ballot_sync(full, last) & gmask) >> (16 * grp);
+            const bool inrow = row_open && (lastbits & ((1u << sl) - 1u)) == 0u;
+            if (inrow && (word & kEntIdx) != kEntEmpty) {
+                const float dx = (e0.x - f.ohx) + (e0.w - f.olx);
+                const float dy = (e0.y - f.ohy) + (e1.x - f.oly);
+                const float dz = (e0.z - f.ohz) + (e1.y - f.olz);
                 const float adx = fabsf(dx), ady = fabsf(dy), adz = fabsf(dz);
                 const float ed = 2e-6f * (fmaxf(adx, fmaxf(ady, adz)) + a.pos_slack);
                 Z = fmaf(dz, f.f2, fmaf(dy, f.f1, dx * f.f0));
@@ -309,115 +403,116 @@ __global__ void __launch_bounds__(256) k_trace_warp(WalkArgs a, int64_t *__restr
                     und = true;
                 }
             }
-            if (__any_sync(0xffffffffu, und)) {
-                undecided = true;
-                break;
+            // (the ballot must run in every lane: no short-circuit around it)
+            const bool und_grp = (__ballot_sync(full, und) & gmask) != 0u;
+            undecided = undecided || und_grp;
+            const float m = group16_min(cand ? d2 : 3.0e38f);
+            const unsigned wins = (__ballot_sync(full, cand && d2 == m) & gmask) >> (16 * grp);
+            const int wl = wins ? __ffs(wins) - 1 : sl;
+            const int src = 16 * grp + wl;
+            const float cU = __shfl_sync(full, U, src), cL = __shfl_sync(full, Lo, src);
+            const float cZ = __shfl_sync(full, Z, src), ceZ = __shfl_sync(full, eZ, src);
+            const uint32_t cword = __shfl_sync(full, word, src);
+            const int32_t coff = __shfl_sync(full, eoff, src);
+            const float oL = group16_min((cand && sl != wl) ? Lo : 3.0e38f);
+            if (wins) {
+                if (!have || m < bd2) {
+                    if (have) minLother = fminf(minLother, bL);
+                    minLother = fminf(minLother, oL);
+                    have = true;
+                    bd2 = m;
+                    bU = cU;
+                    bL = cL;
+                    bZ = cZ;
+                    beZ = ceZ;
+                    bword = cword;
+                    boff = coff;
+                } else {
+                    minLother = fminf(minLother, fminf(cL, oL));
+                }
             }
-            const float m = warp_min(cand ? d2 : 3.0e38f);
-            const unsigned wins = __ballot_sync(0xffffffffu, cand && d2 == m);
-            if (wins == 0u) continue;                          // no candidate in this chunk
-            const int wl = __ffs(wins) - 1;
-            const float cU = __shfl_sync(0xffffffffu, U, wl), cL = __shfl_sync(0xffffffffu, Lo, wl);
-            const float cZ = __shfl_sync(0xffffffffu, Z, wl), ceZ = __shfl_sync(0xffffffffu, eZ, wl);
-            const float oL = warp_min((cand && lane != wl) ? Lo : 3.0e38f);
-            if (bk < 0 || m < bd2) {
-                if (bk >= 0) minLother = fminf(minLother, bL);
-                minLother = fminf(minLother, oL);
-                bk = kb + wl;
-                bd2 = m;
-                bU = cU;
-                bL = cL;
-                bZ = cZ;
-                beZ = ceZ;
+            row_open = row_open && lastbits == 0u;
+        }
+        if (gave_up) break;
+        // The decision runs in both groups in lockstep (a finished group only
+        // predicates itself off), so every warp intrinsic below names the
+        // whole warp.
+        const bool exact = !done && (undecided || (have && !(bU < minLother)));
+        int64_t v = -1;
+        double Zn = 0.0;
+        if (exact && sl == 0) {
+            // FP64 predicates, evaluated by lane 0 of the group
+            atomicAdd(a.n_exact, 1ULL);
+            const double xo = a.pos[3 * o], yo = a.pos[3 * o + 1], zo = a.pos[3 * o + 2];
+            const double n0 = a.dirs[3 * r], n1 = a.dirs[3 * r + 1], n2 = a.dirs[3 * r + 2];
+            double Zc64 = 0.0;
+            if (c != o) {
+                const double *q = a.pos + 3 * c;
+                Zc64 = dot3_exact(__dsub_rn(q[0], xo), __dsub_rn(q[1], yo), __dsub_rn(q[2], zo), n0, n1, n2);
+            }
+            v = walk_next_exact(a, c, xo, yo, zo, n0, n1, n2, Zc64, &Zn);
+        }
+        v = __shfl_sync(full, v, 16 * grp);
+        Zn = __shfl_sync(full, Zn, 16 * grp);
+        int64_t nx = -1;
+        bool nx_bnd = false;
+        if (!done) {
+            if (exact) {
+                nx = v;
+                if (nx >= a.N) {
+                    walk_give_up(err, 11, wg, nx);
+                    nx = -1;
+                }
+                Zc = (float)(Zn * a.pos_scale);      // the filter works in scaled units (exact factor)
+                eZc = 1e-7f * fabsf(Zc) + 1e-30f;
+                nx_bnd = nx >= 0 && a.bnd[nx] != 0;
+                if (nx >= 0) c_off = a.ent_off[nx];
+            } else if (have) {
+                nx = (int64_t)(bword & kEntIdx);
+                if (nx >= a.N || boff < 0 || boff >= a.n_ent) {
+                    walk_give_up(err, 12, wg, nx);
+                    nx = -1;
+                    have = false;
+                }
+                nx_bnd = (bword & kEntBnd) != 0u;
+                c_off = boff;
+                Zc = bZ;
+                eZc = beZ;
+            }
+        }
+        bool flush_full = false, flush_last = false;   // FILL: a full chunk of 16 records / the walk's tail
+        if (!done) {
+            if (nx < 0) {
+                if (!FILL && sl == 0 && !(c == o && a.bnd[o])) atomicAdd(n_stall, 1ULL);
+                done = true;
+                flush_last = FILL && (n & 15) != 0;
+            } else if (FILL && n >= cap) {       // cannot happen for a deterministic walk
+                if (sl == 0) atomicCAS(err, 0, (int)kDevBounds);
+                done = true;
             } else {
-                minLother = fminf(minLother, fminf(cL, oL));
-            }
-        }
-        int64_t nx;
-        if (undecided || (bk >= 0 && !(bU < minLother))) {
-            // FP64 predicates, evaluated by lane 0
-            int64_t v = -1;
-            double Zn = 0.0;
-            if (lane == 0) {
-                atomicAdd(a.n_exact, 1ULL);
-                const double xo = a.pos[3 * o], yo = a.pos[3 * o + 1], zo = a.pos[3 * o + 2];
-                const double n0 = a.dirs[3 * r], n1 = a.dirs[3 * r + 1], n2 = a.dirs[3 * r + 2];
-                double Zc64 = 0.0;
-                if (c != o) {
-                    const double *q = a.pos + 3 * c;
-                    Zc64 = dot3_exact(__dsub_rn(q[0], xo), __dsub_rn(q[1], yo), __dsub_rn(q[2], zo), n0, n1, n2);
-                }
-                v = walk_next_exact(a, c, xo, yo, zo, n0, n1, n2, Zc64, &Zn);
-            }
-            nx = __shfl_sync(0xffffffffu, v, 0);
-            Zn = __shfl_sync(0xffffffffu, Zn, 0);
-            Zc = (float)(Zn * a.pos_scale);          // the filter works in scaled units (exact factor)
-            eZc = 1e-7f * fabsf(Zc) + 1e-30f;
-            if (nx >= 0) {
-                bk = -1;                                       // locate the winner's entry for FILL
-                for (int32_t kb = k0; kb < k1; kb += 32) {
-                    const unsigned hit = __ballot_sync(0xffffffffu, kb + lane < k1 && a.nb[kb + lane] == nx);
-                    if (hit) {
-                        bk = kb + __ffs(hit) - 1;
-                        break;
-                    }
+                if (FILL && sl == (int)(n & 15)) my_pt = (int32_t)nx;
+                flush_full = FILL && (n & 15) == 15;
+                ++n;
+                c = nx;
+                if (nx_bnd || n >= a.N) {
+                    done = true;
+                    flush_last = FILL && (n & 15) != 0;
                 }
             }
-        } else if (bk < 0) {
-            nx = -1;
-        } else {
-            nx = a.nb[bk];
-            Zc = bZ;
-            eZc = beZ;
         }
-        if (nx < 0) {
-            if (!FILL && lane == 0 && !(c == o && a.bnd[o])) atomicAdd(n_stall, 1ULL);
-            break;
+        if (FILL && __any_sync(full, flush_full || flush_last)) {
+            // records of the group's buffered steps: n already counts the newest
+            const int cnt = flush_full ? 16 : (int)(n & 15);
+            const int64_t first = flush_full ? n - 16 : (n & ~(int64_t)15);
+            write_step_records(a, o, r, prev_last, my_pt, (flush_full || flush_last) ? cnt : 0, vel_hl, w32,
+                               inv_Lunit, width_mode, steps + base + first, sl);
+            if (flush_full) prev_last = nx;
         }
-        if (FILL && lane == 0) {
-            if (n >= cap) {                      // cannot happen for a deterministic walk
-                atomicCAS(err, 0, (int)kDevBounds);
-                break;
-            }
-            const float *hl = a.nb_hl + 6 * (int64_t)bk;
-            const float ex = (hl[0] - ph[0]) + (hl[3] - pl[0]);
-            const float ey = (hl[1] - ph[1]) + (hl[4] - pl[1]);
-            const float ez = (hl[2] - ph[2]) + (hl[5] - pl[2]);
-            const float dxs = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex))) * inv_Lunit;
-            // velocity differences from hi + lo floats: relative error ~1e-7 of
-            // |v_c - v_o| / c, well inside the FP32 path's tolerance
-            const float *vq = vel_hl + 6 * nx;
-            float vh[3], vl[3], db[3], dp[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                vh[d] = vq[d];
-                vl[d] = vq[3 + d];
-                db[d] = (vh[d] - voh[d]) + (vl[d] - vol[d]);
-                dp[d] = (vh[d] - pvh[d]) + (vl[d] - pvl[d]);
-            }
-            const float beta = fmaf(f.f2, db[2], fmaf(f.f1, db[1], f.f0 * db[0]));
-            const float dbeta = fmaf(f.f2, dp[2], fmaf(f.f1, dp[1], f.f0 * dp[0]));
-            const float wq = w32[nx].x;
-            const float wbar = width_mode == 0 ? sqrtf(0.5f * (wq * wq + pw * pw)) : 0.5f * (wq + pw);
-            steps[base + n] = make_int4((int)nx, __float_as_int(dxs), __float_as_int(beta),
-                                        __float_as_int(dbeta / wbar));
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                ph[d] = hl[d];
-                pl[d] = hl[3 + d];
-                pvh[d] = vh[d];
-                pvl[d] = vl[d];
-            }
-            pw = wq;
-        }
-        ++n;
-        c = nx;
-        if (a.bnd[nx] || n >= a.N) break;
     }
-    if (lane == 0) {
+    if (live && sl == 0) {
         if (!FILL)
-            len_or_off[wi] = n;
-        else if (n != cap)
+            len_or_off[wi] = gave_up ? 0 : n;
+        else if (n != cap && !gave_up)
             atomicCAS(err, 0, (int)kDevBounds);
     }
 }
@@ -458,16 +553,17 @@ __global__ void k_steps64(int64_t N, int32_t R, const int64_t *__restrict__ off,
 mgt_status trace_all(mgt_model *m, cudaStream_t s)
 {
     const int64_t W = (int64_t)m->R * m->N;
-    WalkArgs a{m->N,        m->R,         m->d_pos,    m->d_nbr_off, m->d_nbrs,  m->d_nbr_pos,
-               m->d_nbr_hl, m->pos_scale, m->d_bnd,    m->d_dirs,    m->d_pos_hl, m->d_dirs32,
-               m->d_order,  m->pos_slack, m->d_count + 2};
+    WalkArgs a{m->N,        m->R,          m->d_pos,  m->d_nbr_off, m->d_nbrs,   m->d_nbr_pos,
+               m->pos_scale, m->d_bnd,     m->d_dirs, m->d_ent,     m->d_ent_off, m->d_pos_hl,
+               m->d_dirs32,  m->d_order,   m->pos_slack, m->d_count + 2,
+               (int32_t)((m->n_ent + 15) / 16 + 2), m->n_ent};
     if (!m->d_ray_off) MGT_CUDA(cudaMalloc(&m->d_ray_off, sizeof(int64_t) * (W + 1)));
     int64_t *d_len = nullptr;
     MGT_CUDA(cudaMallocAsync(&d_len, sizeof(int64_t) * (W + 1), s));
     MGT_CUDA(cudaMemsetAsync(m->d_count + 1, 0, 2 * sizeof(unsigned long long), s));
-    k_trace_warp<false><<<ceil_div(W * 32, 256), 256, 0, s>>>(a, d_len, m->d_count + 1, nullptr, nullptr, 0.0f, 0,
-                                                              nullptr, m->d_err);
-    MGT_LAUNCH_CHECK("k_trace_warp<count>");
+    k_walk<false><<<ceil_div(W * 16, 256), 256, 0, s>>>(a, d_len, m->d_count + 1, nullptr, nullptr, 0.0f, 0,
+                                                        nullptr, m->d_err);
+    MGT_LAUNCH_CHECK("k_walk<count>");
     MGT_CUDA(cudaMemsetAsync(d_len + W, 0, sizeof(int64_t), s));
     size_t tmp_bytes = 0;
     MGT_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, d_len, m->d_ray_off, W + 1, s));
@@ -489,6 +585,16 @@ mgt_status trace_all(mgt_model *m, cudaStream_t s)
     MGT_CUDA(cudaMemcpyAsync(&stalls, m->d_count + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     MGT_CUDA(cudaMemcpyAsync(&exact_steps, m->d_count + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     MGT_CUDA(cudaStreamSynchronize(s));
+    {
+        const mgt_status st = check_device_error(m, s);     // a walk that gave up leaves lengths unusable
+        if (st != MGT_OK) {
+            cudaFreeAsync(tmp, s);
+            cudaFreeAsync(tmpb, s);
+            cudaFreeAsync(d_max, s);
+            cudaFreeAsync(d_len, s);
+            return st;
+        }
+    }
     MGT_CUDA(cudaFreeAsync(tmp, s));
     MGT_CUDA(cudaFreeAsync(tmpb, s));
     MGT_CUDA(cudaFreeAsync(d_max, s));
@@ -511,11 +617,11 @@ mgt_status trace_all(mgt_model *m, cudaStream_t s)
     m->n_stalls = (int64_t)stalls;
     m->n_exact_steps = (int64_t)exact_steps;   // pass 1 only
     if (total > 0) {
-        k_trace_warp<true><<<ceil_div(W * 32, 256), 256, 0, s>>>(a, m->d_ray_off, nullptr, m->d_vel_hl, m->d_w32,
+        k_walk<true><<<ceil_div(W * 16, 256), 256, 0, s>>>(a, m->d_ray_off, nullptr, m->d_vel_hl, m->d_w32,
                                                                  (float)(1.0 / (m->pos_scale * m->L_unit)),
                                                                  m->opts.width_mode,
                                                                  m->d_steps32, m->d_err);
-        MGT_LAUNCH_CHECK("k_trace_warp<fill>");
+        MGT_LAUNCH_CHECK("k_walk<fill>");
     }
     m->steps_width_mode = m->opts.width_mode;
     m->traced = true;

@@ -52,11 +52,12 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) k_se(SEArgs a)
     extern __shared__ __align__(16) double sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int L = a.L, LL = L * L;
-    const int per_warp = LL + 2 * L + 2 * a.Mpad;
+    const int per_warp = LL + 3 * L + 2 * a.Mpad;
     double *R = sm + warp * per_warp;     // R[i*L + j]: rate i -> j
     double *Sn = R + LL;                  // [L] pivots
     double *xx = Sn + L;                  // [L] unnormalised populations
-    double *rdown = xx + L;               // [Mpad] radiative u -> l rate per line
+    double *bz = xx + L;                  // [L] Boltzmann factors g_i exp(-(E_i - E_0)/kT)
+    double *rdown = bz + L;               // [Mpad] radiative u -> l rate per line
     double *rup = rdown + a.Mpad;         // [Mpad] radiative l -> u rate per line
     const int64_t p = (int64_t)blockIdx.x * a.wpb + warp;
     if (p >= a.N) return;                 // whole warp leaves together
@@ -77,9 +78,12 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) k_se(SEArgs a)
         rdown[k] = fmax(A * (1.0 - Ls) + Bul * Jeff, 0.0);
         rup[k] = fmax(Blu * Jeff, 0.0);
     }
-    __syncwarp();
     const double *E = a.level_tab, *g = a.level_tab + L;
     const double ikT = 1.0 / (kKB * Tp);
+    // one exponential per level instead of one per collisional pair: the
+    // upward rate C_lu = C_ul (g_u/g_l) exp(-(E_u - E_l)/kT) = C_ul bz_u / bz_l
+    for (int i = lane; i < L; i += 32) bz[i] = g[i] * exp(-(E[i] - E[0]) * ikT);
+    __syncwarp();
     for (int e = lane; e < LL; e += 32) {
         const int i = e / L, j = e - i * L;
         double v = 0.0;
@@ -92,7 +96,9 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) k_se(SEArgs a)
                 const double Cul = nc * a.Kul[kc];
                 if (i == cu)
                     v += Cul;
-                else
+                else if (bz[cl] > 1e-290 && bz[cu] > 1e-290)
+                    v += Cul * bz[cu] / bz[cl];
+                else   // a factor near the bottom of the FP64 range: the pair's own exponential
                     v += Cul * g[cu] / g[cl] * exp(-(E[cu] - E[cl]) * ikT);
             }
         }
@@ -107,7 +113,8 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) k_se(SEArgs a)
         s = s > 0.0 ? s : 1e-300;
         if (lane == 0) Sn[n] = s;
         __syncwarp();
-        for (int j = lane; j < n; j += 32) R[n * L + j] = R[n * L + j] / s;
+        const double rs = 1.0 / s;
+        for (int j = lane; j < n; j += 32) R[n * L + j] *= rs;
         __syncwarp();
         const int nn = n * n;
         for (int e = lane; e < nn; e += 32) {
@@ -155,7 +162,7 @@ mgt_status launch_stat_eq(mgt_model *m, cudaStream_t s)
     a.coll_ul = m->d_coll_ul;
     a.entry = m->d_entry;
     a.pops_out = m->d_pops;
-    const size_t per_warp = sizeof(double) * ((size_t)m->L * m->L + 2 * m->L + 2 * m->Mpad);
+    const size_t per_warp = sizeof(double) * ((size_t)m->L * m->L + 3 * m->L + 2 * m->Mpad);
     const size_t max_smem = 227 * 1024;
     int wpb = (int)std::min<size_t>(kMaxWarpsPerBlock, max_smem / per_warp);
     if (wpb < 1) return set_error(MGT_ERR_ARG, "statistical equilibrium: too many levels/lines for shared memory");

@@ -34,6 +34,18 @@ constexpr int kMaxNgHist = 16;
 // c_0 = o, beta_0 = 0.
 using Step32 = int4;
 
+// Packed neighbour entry of the ray walk, 32 bytes (two float4):
+//   {hx, hy, hz, lx}, {ly, lz, word, off}
+// h + l = the neighbour's position times pos_scale (float hi + lo); word holds
+// the neighbour's index (bits 0-29), a last-entry-of-this-row flag (bit 30)
+// and the neighbour's boundary flag (bit 31); off is the first entry of the
+// neighbour's own row.  A point without neighbours has one entry with index
+// kEntEmpty; 16 such entries pad the array's end.
+constexpr uint32_t kEntLast = 1u << 30;
+constexpr uint32_t kEntBnd = 1u << 31;
+constexpr uint32_t kEntIdx = kEntLast - 1u;
+constexpr uint32_t kEntEmpty = kEntIdx;
+
 // Double-precision geometry of the same step: {dx, beta, dbeta/wbar, unused}.
 struct alignas(32) Step64 {
     double dx, beta, dbw, pad;
@@ -76,7 +88,9 @@ struct mgt_model {
     float2 *d_w32 = nullptr;                   // {w, 1/w}
     int32_t *d_nbr_off = nullptr, *d_nbrs = nullptr;
     double *d_nbr_pos = nullptr;               // [nnz][3] position of each neighbour entry
-    float *d_nbr_hl = nullptr;                 // [nnz][6] the same times pos_scale, split into float hi + lo
+    float4 *d_ent = nullptr;                   // packed neighbour rows for the walk (see WalkEntry)
+    int32_t *d_ent_off = nullptr;              // [N] first packed entry of each point's row
+    int64_t n_ent = 0;                         // packed entries, including the 16 pad entries
     float *d_pos_hl = nullptr;                 // [N][6] positions times pos_scale, float hi + lo
     float *d_vel_hl = nullptr;                 // [N][6] velocities / c, float hi + lo
     float4 *d_dirs32 = nullptr;                // [R] directions in FP32 {n0, n1, n2, 0}
