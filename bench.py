@@ -34,7 +34,10 @@ if ROOT not in sys.path:
 
 METRIC = "point·ray·freq formal solutions/s (J̄+Λ*), FP32-mixed vs FP64 at 1e-4 J̄"
 UNIT = "formal solutions/s"
-OPS_PER_LINE_STEP = 10      # FP32 ops of one elimination row for one line (see the formal-solve kernel)
+# Algorithmic work of one line-step (one line, one bin, one ray step of one
+# formal solution): the elimination row of the formal-solve kernel, 8 FP32
+# operations and 1 reciprocal (MUFU); each takes one issue slot per lane.
+OPS_PER_LINE_STEP = 9
 
 
 def parse():
@@ -155,9 +158,13 @@ def fs_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_record(units_per_launch_key):
-    """Per-launch DRAM bytes of the formal-solve kernel from a committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+def traffic_record():
+    """DRAM bytes per traced ray step of the formal-solve kernel from a
+    committed ncu capture, if it was taken on the current kernel source; else
+    None.  The capture is of a smaller workload of the same kind; its traffic
+    grows with the number of traced steps (the step records stream from DRAM,
+    the per-point rows stay in L2), so the bench scales it by the launch's
+    step count."""
     p = os.path.join(ROOT, "profiles", "k_fs_dram_traffic.json")
     if not os.path.exists(p):
         return None
@@ -328,13 +335,14 @@ def run_mine(args, model, cfg):
     line_steps = tst["total_steps"] * model.lines.n_lines * model.n_quad
     achieved = OPS_PER_LINE_STEP * line_steps / (fs_ms * 1e-3) / 1e12
     peak = 152 * 4 * 32 * sm_max * 1e6 / 1e12
-    tr = traffic_record("line_steps")
+    tr = traffic_record()
     out["roofline"] = {
-        "bound": "alu", "kernel": "k_fs<float,8> (formal solution + J-bar/Lambda* reduction)",
+        "bound": "alu", "kernel": "k_fs_staged<float,8,31,2> (formal solution + J-bar/Lambda* reduction)",
         "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak,
-        "traffic": (tr["dram_bytes_per_launch"] if tr else None),
-        "peak_source": f"{src}: 152 SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz (one FP32/MUFU op per lane "
-                       "per cycle)",
+        "traffic": (tr["dram_bytes_per_traced_step"] * tst["total_steps"] if tr else None),
+        "traffic_source": (tr["source"] if tr else None),
+        "peak_source": f"{src} SM clock: issue roof 152 SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz "
+                       "(one FP32 or MUFU lane-op per issue slot)",
         "ops_per_launch": OPS_PER_LINE_STEP * line_steps, "line_steps_per_launch": line_steps,
         "launch_ms": fs_ms, "step_ms": ms, "share_of_step": fs_ms / ms}
     out["gpu_launches"] = launches
