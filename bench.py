@@ -153,7 +153,7 @@ def allreduce_max(world, v):
 
 def fs_source_hash():
     h = hashlib.sha256()
-    for f in ("k_fs.cu", "mgt_common.cuh"):
+    for f in ("k_fs.cu",):
         h.update(open(os.path.join(ROOT, "paper_2411_03040_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -302,11 +302,19 @@ __device__ __forceinline__ float group16_min(float v)
 // the same expression), on lane 0 of the group.  The point lists are
 // therefore those of the FP64 rule.
 //
-// FILL = false: half-ray length and stall count.  FILL = true: also the step
-// records (see Step32), 16 at a time, one per lane of the group.
+// Two modes share the walk:
+//  * kWalkFused: every walk of the grid.  Writes the half-ray length, counts
+//    stalls, and writes the step records (see Step32), 16 at a time, into a
+//    fixed-stride scratch area (K records per walk); records of steps >= K are
+//    not kept (such walks are redone by the list mode).
+//  * kWalkList: the walks named in `list` only, records written to their final
+//    place (ray offsets known).
 // ---------------------------------------------------------------------------
-template <bool FILL>
-__global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ len_or_off,
+constexpr int kWalkFused = 0, kWalkList = 1;
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ lens, const int64_t *__restrict__ ray_off,
+                                              const int64_t *__restrict__ list, int64_t n_list, int32_t K,
                                               unsigned long long *__restrict__ n_stall,
                                               const float *__restrict__ vel_hl, const float2 *__restrict__ w32,
                                               float inv_Lunit, int width_mode, Step32 *__restrict__ steps,
@@ -315,23 +323,36 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, sl = lane & 15, grp = lane >> 4;
     const unsigned gmask = 0xffffu << (16 * grp);
-    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 4;   // walk id
-    const int64_t W = (int64_t)a.R * a.N;
+    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 4;   // walk slot
+    const int64_t W = MODE == kWalkFused ? (int64_t)a.R * a.N : n_list;
     if ((wg & ~(int64_t)1) >= W) return;                       // both walks of the warp absent
     bool live = wg < W;
-    const int r = live ? (int)(wg / a.N) : 0;
-    int64_t o = live ? (int64_t)a.order[wg - (int64_t)r * a.N] : 0;
-    if (o < 0 || o >= a.N) {                                  // index check: record and skip
+    int r = 0;
+    int64_t o = 0;
+    if (live) {
+        if (MODE == kWalkFused) {
+            r = (int)(wg / a.N);
+            o = a.order[wg - (int64_t)r * a.N];
+        } else {
+            const int64_t t = list[wg];
+            r = (int)(t / a.N);
+            o = t - (int64_t)r * a.N;
+        }
+    }
+    if (o < 0 || o >= a.N || r < 0 || r >= a.R) {            // index check: record and skip
         walk_give_up(err, 13, wg, o);
         o = 0;
+        r = 0;
         live = false;
     }
     const int64_t wi = (int64_t)r * a.N + o;
     const WalkFrame f = make_frame(a, o, r);
-    int64_t base = 0, cap = a.N;
-    if (FILL && live) {
-        base = len_or_off[wi];
-        cap = len_or_off[wi + 1] - base;
+    // records go to out[0 .. cap): the walk's scratch slot, or its final place
+    int64_t cap = K;
+    Step32 *out = steps + wi * (int64_t)K;
+    if (MODE == kWalkList && live) {
+        out = steps + ray_off[wi];
+        cap = ray_off[wi + 1] - ray_off[wi];
     }
     // step records are built 16 at a time: lane j of the group keeps the point
     // of step (chunk start + j); prev_last is the point before the chunk
@@ -480,41 +501,67 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
                 eZc = beZ;
             }
         }
-        bool flush_full = false, flush_last = false;   // FILL: a full chunk of 16 records / the walk's tail
+        bool flush_full = false, flush_last = false;   // a full chunk of 16 records / the walk's tail
         if (!done) {
             if (nx < 0) {
-                if (!FILL && sl == 0 && !(c == o && a.bnd[o])) atomicAdd(n_stall, 1ULL);
+                if (MODE == kWalkFused && sl == 0 && !(c == o && a.bnd[o])) atomicAdd(n_stall, 1ULL);
                 done = true;
-                flush_last = FILL && (n & 15) != 0;
-            } else if (FILL && n >= cap) {       // cannot happen for a deterministic walk
+                flush_last = (n & 15) != 0;
+            } else if (MODE == kWalkList && n >= cap) {   // cannot happen for a deterministic walk
                 if (sl == 0) atomicCAS(err, 0, (int)kDevBounds);
                 done = true;
             } else {
-                if (FILL && sl == (int)(n & 15)) my_pt = (int32_t)nx;
-                flush_full = FILL && (n & 15) == 15;
+                if (sl == (int)(n & 15)) my_pt = (int32_t)nx;
+                flush_full = (n & 15) == 15;
                 ++n;
                 c = nx;
                 if (nx_bnd || n >= a.N) {
                     done = true;
-                    flush_last = FILL && (n & 15) != 0;
+                    flush_last = (n & 15) != 0;
                 }
             }
         }
-        if (FILL && __any_sync(full, flush_full || flush_last)) {
-            // records of the group's buffered steps: n already counts the newest
+        if (__any_sync(full, flush_full || flush_last)) {
+            // records of the group's buffered steps (n already counts the newest);
+            // chunks start at multiples of 16 and cap is one (fused mode) or
+            // exactly the walk's length (list mode), so a chunk is kept whole or
+            // not at all
             const int cnt = flush_full ? 16 : (int)(n & 15);
             const int64_t first = flush_full ? n - 16 : (n & ~(int64_t)15);
-            write_step_records(a, o, r, prev_last, my_pt, (flush_full || flush_last) ? cnt : 0, vel_hl, w32,
-                               inv_Lunit, width_mode, steps + base + first, sl);
+            const bool keep = (flush_full || flush_last) && first < cap;
+            write_step_records(a, o, r, prev_last, my_pt, keep ? cnt : 0, vel_hl, w32, inv_Lunit, width_mode,
+                               out + first, sl);
             if (flush_full) prev_last = nx;
         }
     }
     if (live && sl == 0) {
-        if (!FILL)
-            len_or_off[wi] = gave_up ? 0 : n;
+        if (MODE == kWalkFused)
+            lens[wi] = gave_up ? 0 : n;
         else if (n != cap && !gave_up)
             atomicCAS(err, 0, (int)kDevBounds);
     }
+}
+
+// Walks whose records did not fit their scratch slot (length > K).
+__global__ void k_walk_overflow(int64_t W, const int64_t *__restrict__ lens, int32_t K, int64_t *__restrict__ list,
+                                unsigned long long *__restrict__ count)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= W || lens[t] <= K) return;
+    list[atomicAdd(count, 1ULL)] = t;
+}
+
+// Move each walk's records (at most K) from its scratch slot to its final
+// place: one warp per walk, 16-byte records.
+__global__ void k_walk_compact(int64_t W, const int64_t *__restrict__ ray_off, int32_t K,
+                               const Step32 *__restrict__ scratch, Step32 *__restrict__ steps)
+{
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= W) return;
+    const int64_t b = ray_off[t], n = ray_off[t + 1] - b;
+    const int64_t m = n < K ? n : K;
+    for (int64_t j = lane; j < m; j += 32) steps[b + j] = scratch[t * (int64_t)K + j];
 }
 
 // Double-precision step geometry for the FP64 formal solution, from the
@@ -558,47 +605,68 @@ mgt_status trace_all(mgt_model *m, cudaStream_t s)
                m->d_dirs32,  m->d_order,   m->pos_slack, m->d_count + 2,
                (int32_t)((m->n_ent + 15) / 16 + 2), m->n_ent};
     if (!m->d_ray_off) MGT_CUDA(cudaMalloc(&m->d_ray_off, sizeof(int64_t) * (W + 1)));
-    int64_t *d_len = nullptr;
+    // Scratch slot per walk: K records, a multiple of 16; the longest half-ray
+    // of this model's previous trace when there was one (64 otherwise), kept
+    // within a third of the free device memory.  Longer walks are redone.
+    int64_t K = m->max_half > 0 ? (m->max_half + 15) / 16 * 16 : 64;
+    {
+        size_t freeb = 0, totalb = 0;
+        MGT_CUDA(cudaMemGetInfo(&freeb, &totalb));
+        while (K > 16 && (size_t)(W * K) * sizeof(Step32) > freeb / 3) K -= 16;
+    }
+    int64_t *d_len = nullptr, *d_list = nullptr, *d_max = nullptr;
+    Step32 *d_scratch = nullptr;
+    unsigned long long *d_nover = nullptr;
+    void *tmp = nullptr, *tmpb = nullptr;
+    auto release = [&]() {
+        if (tmp) cudaFreeAsync(tmp, s);
+        if (tmpb) cudaFreeAsync(tmpb, s);
+        if (d_max) cudaFreeAsync(d_max, s);
+        if (d_len) cudaFreeAsync(d_len, s);
+        if (d_list) cudaFreeAsync(d_list, s);
+        if (d_nover) cudaFreeAsync(d_nover, s);
+        if (d_scratch) cudaFreeAsync(d_scratch, s);
+    };
+    struct Guard {
+        decltype(release) &f;
+        ~Guard() { f(); }
+    } guard{release};
     MGT_CUDA(cudaMallocAsync(&d_len, sizeof(int64_t) * (W + 1), s));
+    MGT_CUDA(cudaMallocAsync(&d_list, sizeof(int64_t) * W, s));
+    MGT_CUDA(cudaMallocAsync(&d_nover, sizeof(unsigned long long), s));
+    if (cudaMallocAsync(&d_scratch, sizeof(Step32) * W * K, s) != cudaSuccess) {
+        d_scratch = nullptr;
+        return set_error(MGT_ERR_OOM, "cannot allocate the walk scratch");
+    }
     MGT_CUDA(cudaMemsetAsync(m->d_count + 1, 0, 2 * sizeof(unsigned long long), s));
-    k_walk<false><<<ceil_div(W * 16, 256), 256, 0, s>>>(a, d_len, m->d_count + 1, nullptr, nullptr, 0.0f, 0,
-                                                        nullptr, m->d_err);
-    MGT_LAUNCH_CHECK("k_walk<count>");
+    MGT_CUDA(cudaMemsetAsync(d_nover, 0, sizeof(unsigned long long), s));
+    const float inv_Lunit = (float)(1.0 / (m->pos_scale * m->L_unit));
+    k_walk<kWalkFused><<<ceil_div(W * 16, 256), 256, 0, s>>>(a, d_len, nullptr, nullptr, 0, (int32_t)K,
+                                                             m->d_count + 1, m->d_vel_hl, m->d_w32, inv_Lunit,
+                                                             m->opts.width_mode, d_scratch, m->d_err);
+    MGT_LAUNCH_CHECK("k_walk<fused>");
     MGT_CUDA(cudaMemsetAsync(d_len + W, 0, sizeof(int64_t), s));
     size_t tmp_bytes = 0;
     MGT_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, d_len, m->d_ray_off, W + 1, s));
-    void *tmp = nullptr;
     MGT_CUDA(cudaMallocAsync(&tmp, tmp_bytes, s));
     MGT_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, d_len, m->d_ray_off, W + 1, s));
     // longest half-ray
-    int64_t *d_max = nullptr;
     MGT_CUDA(cudaMallocAsync(&d_max, sizeof(int64_t), s));
     size_t tmp2 = 0;
     MGT_CUDA(cub::DeviceReduce::Max(nullptr, tmp2, d_len, d_max, W, s));
-    void *tmpb = nullptr;
     MGT_CUDA(cudaMallocAsync(&tmpb, tmp2, s));
     MGT_CUDA(cub::DeviceReduce::Max(tmpb, tmp2, d_len, d_max, W, s));
+    k_walk_overflow<<<ceil_div(W, 256), 256, 0, s>>>(W, d_len, (int32_t)K, d_list, d_nover);
+    MGT_LAUNCH_CHECK("k_walk_overflow");
     int64_t total = 0, mx = 0;
-    unsigned long long stalls = 0, exact_steps = 0;
+    unsigned long long stalls = 0, exact_steps = 0, n_over = 0;
     MGT_CUDA(cudaMemcpyAsync(&total, m->d_ray_off + W, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     MGT_CUDA(cudaMemcpyAsync(&mx, d_max, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     MGT_CUDA(cudaMemcpyAsync(&stalls, m->d_count + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     MGT_CUDA(cudaMemcpyAsync(&exact_steps, m->d_count + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    MGT_CUDA(cudaMemcpyAsync(&n_over, d_nover, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     MGT_CUDA(cudaStreamSynchronize(s));
-    {
-        const mgt_status st = check_device_error(m, s);     // a walk that gave up leaves lengths unusable
-        if (st != MGT_OK) {
-            cudaFreeAsync(tmp, s);
-            cudaFreeAsync(tmpb, s);
-            cudaFreeAsync(d_max, s);
-            cudaFreeAsync(d_len, s);
-            return st;
-        }
-    }
-    MGT_CUDA(cudaFreeAsync(tmp, s));
-    MGT_CUDA(cudaFreeAsync(tmpb, s));
-    MGT_CUDA(cudaFreeAsync(d_max, s));
-    MGT_CUDA(cudaFreeAsync(d_len, s));
+    MGT_TRY_STATUS(check_device_error(m, s));     // a walk that gave up leaves the lengths unusable
     if (m->d_steps32 && total > m->total_steps) {
         MGT_CUDA(cudaFree(m->d_steps32));
         m->d_steps32 = nullptr;
@@ -615,13 +683,16 @@ mgt_status trace_all(mgt_model *m, cudaStream_t s)
     m->total_steps = total;
     m->max_half = (int32_t)mx;
     m->n_stalls = (int64_t)stalls;
-    m->n_exact_steps = (int64_t)exact_steps;   // pass 1 only
+    m->n_exact_steps = (int64_t)exact_steps;   // the walks of the fused pass
     if (total > 0) {
-        k_walk<true><<<ceil_div(W * 16, 256), 256, 0, s>>>(a, m->d_ray_off, nullptr, m->d_vel_hl, m->d_w32,
-                                                                 (float)(1.0 / (m->pos_scale * m->L_unit)),
-                                                                 m->opts.width_mode,
-                                                                 m->d_steps32, m->d_err);
-        MGT_LAUNCH_CHECK("k_walk<fill>");
+        k_walk_compact<<<ceil_div(W * 32, 256), 256, 0, s>>>(W, m->d_ray_off, (int32_t)K, d_scratch, m->d_steps32);
+        MGT_LAUNCH_CHECK("k_walk_compact");
+        if (n_over > 0) {
+            k_walk<kWalkList><<<ceil_div((int64_t)n_over * 16, 256), 256, 0, s>>>(
+                a, nullptr, m->d_ray_off, d_list, (int64_t)n_over, 0, nullptr, m->d_vel_hl, m->d_w32, inv_Lunit,
+                m->opts.width_mode, m->d_steps32, m->d_err);
+            MGT_LAUNCH_CHECK("k_walk<list>");
+        }
     }
     m->steps_width_mode = m->opts.width_mode;
     m->traced = true;

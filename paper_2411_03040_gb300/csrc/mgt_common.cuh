@@ -174,6 +174,12 @@ __host__ __device__ inline int row_stride64(int Mpad) { return 2 * Mpad + 2; }  
         if (e_ != cudaSuccess) return ::mgt::cuda_status(e_, #call);        \
     } while (0)
 
+#define MGT_TRY_STATUS(x)                                                   \
+    do {                                                                    \
+        mgt_status st_ = (x);                                               \
+        if (st_ != MGT_OK) return st_;                                      \
+    } while (0)
+
 #define MGT_LAUNCH_CHECK(what)                                              \
     do {                                                                    \
         cudaError_t e_ = cudaGetLastError();                                \
