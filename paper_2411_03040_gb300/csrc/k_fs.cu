@@ -231,8 +231,8 @@ __device__ __forceinline__ void segment_coefs(bool trap, T dx, T du, T z_f, T g_
 // cf, cn halved coefficients; aa[l] = alpha (half depth of the previous
 // segment); P[l] = Pi = 2P.
 template <typename T, int LPT>
-__device__ __forceinline__ void eliminate_row(T cf, T cn, const T (&chi_f)[LPT], const T (&S_f)[LPT],
-                                              const T (&chi_n)[LPT], T (&P)[LPT], T (&Y)[LPT], T (&aa)[LPT])
+__device__ __forceinline__ void eliminate_row_scalar(T cf, T cn, const T (&chi_f)[LPT], const T (&S_f)[LPT],
+                                                     const T (&chi_n)[LPT], T (&P)[LPT], T (&Y)[LPT], T (&aa)[LPT])
 {
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
@@ -244,6 +244,46 @@ __device__ __forceinline__ void eliminate_row(T cf, T cn, const T (&chi_f)[LPT],
         Y[l] = (S_f[l] * h + Y[l]) * q;
         aa[l] = b;
     }
+}
+
+// The same row in FP32 on line pairs with Blackwell's packed FP32 operations
+// (two lanes of arithmetic per issue slot): four packed operations and two
+// reciprocals per pair of lines, so 5 issue slots per line and step instead of 9.
+template <int LPT>
+__device__ __forceinline__ void eliminate_row_packed(float cf, float cn, const float (&chi_f)[LPT],
+                                                     const float (&S_f)[LPT], const float (&chi_n)[LPT],
+                                                     float (&P)[LPT], float (&Y)[LPT], float (&aa)[LPT])
+{
+    static_assert(LPT % 2 == 0, "line pairs");
+    const float2 cf2 = make_float2(cf, cf), cn2 = make_float2(cn, cn);
+    const float2 two = make_float2(2.0f, 2.0f), one = make_float2(1.0f, 1.0f);
+#pragma unroll
+    for (int l = 0; l < LPT; l += 2) {
+        const float2 cx = make_float2(chi_f[l], chi_f[l + 1]), nx = make_float2(chi_n[l], chi_n[l + 1]);
+        const float2 b = __ffma2_rn(cf2, cx, __fmul2_rn(cn2, nx));
+        const float2 h = __fadd2_rn(make_float2(aa[l], aa[l + 1]), b);
+        const float2 G = __ffma2_rn(two, h, make_float2(P[l], P[l + 1]));
+        const float2 den = __ffma2_rn(b, G, one);
+        const float2 q = make_float2(Prec<float>::rcp(den.x), Prec<float>::rcp(den.y));
+        const float2 Pn = __fmul2_rn(G, q);
+        const float2 Yn = __fmul2_rn(__ffma2_rn(make_float2(S_f[l], S_f[l + 1]), h, make_float2(Y[l], Y[l + 1])), q);
+        P[l] = Pn.x;
+        P[l + 1] = Pn.y;
+        Y[l] = Yn.x;
+        Y[l + 1] = Yn.y;
+        aa[l] = b.x;
+        aa[l + 1] = b.y;
+    }
+}
+
+template <typename T, int LPT>
+__device__ __forceinline__ void eliminate_row(T cf, T cn, const T (&chi_f)[LPT], const T (&S_f)[LPT],
+                                              const T (&chi_n)[LPT], T (&P)[LPT], T (&Y)[LPT], T (&aa)[LPT])
+{
+    if constexpr (sizeof(T) == 4)
+        eliminate_row_packed<LPT>(cf, cn, chi_f, S_f, chi_n, P, Y, aa);
+    else
+        eliminate_row_scalar<T, LPT>(cf, cn, chi_f, S_f, chi_n, P, Y, aa);
 }
 
 // Combine both halves at the origin and accumulate w_q u (compensated) and
