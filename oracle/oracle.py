@@ -76,6 +76,11 @@ def _load():
             lib.oracle_formal_solve.argtypes = [i64, P, P, P, P, f64, i32, P, i32, P, P, P,
                                                 i32, P, P, P, i32, P, P, f64, f64, f64, ctypes.c_int,
                                                 i64, P, P, P]
+            lib.oracle_image_weights.argtypes = [f64, P, P, P]
+            lib.oracle_image_frame.argtypes = [i64, P, P, i32, i32, P, P, P]
+            lib.oracle_image_rays.argtypes = [i64, P, P, P, P, P, i64, P, P, P, P, P, P]
+            lib.oracle_image_solve.argtypes = [i64, P, P, P, P, f64, P, i32, P, P, P, f64, f64, i64, P, P,
+                                               i32, P, P]
             _lib = lib
     return _lib
 
@@ -481,3 +486,76 @@ def ali_solve(model, rays=None, n_iter=20, ng=None, pops0=None, tau_min=1e-150, 
         if callback is not None:
             callback(it, pops)
     return pops, changes
+
+
+# --------------------------------------------------------------------------
+# Synthetic image (Listing 3, compute_image_new), readings in oracle_c.c
+# --------------------------------------------------------------------------
+def image_weights(t):
+    """(e^-t, w0, w1) of the piecewise-linear source update over depth t."""
+    E, w0, w1 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _load().oracle_image_weights(t, ctypes.byref(E), ctypes.byref(w0), ctypes.byref(w1))
+    return E.value, w0.value, w1.value
+
+
+def image_frequencies(nfreq, fmin, fmax):
+    """Channel frequencies: nfreq points from fmin to fmax inclusive
+    (compute_spectral_discretisation(fmin, fmax, N)); one channel is fmin."""
+    if nfreq == 1:
+        return np.array([float(fmin)])
+    return fmin + np.arange(nfreq, dtype=np.float64) * ((fmax - fmin) / (nfreq - 1))
+
+
+@dataclass
+class ImageRays:
+    ref: np.ndarray      # [npix][3] pixel reference points (image plane through the model)
+    anchor: np.ndarray   # [npix] point closest to each pixel line
+    off: np.ndarray      # [npix+1] offsets of the full rays in pts
+    pts: np.ndarray      # full rays, far end first
+    e1: np.ndarray
+    e2: np.ndarray
+
+
+def image_rays(model, direction, npx, npy) -> ImageRays:
+    lib = _load()
+    N = model.n_points
+    n = np.ascontiguousarray(direction, np.float64)
+    pos = np.ascontiguousarray(model.pos, np.float64)
+    e1, e2 = np.zeros(3), np.zeros(3)
+    npix = npx * npy
+    ref = np.zeros((npix, 3))
+    lib.oracle_image_frame(N, _p(pos), _p(n), npx, npy, _p(e1), _p(e2), _p(ref))
+    off = np.ascontiguousarray(model.nbr_offsets, np.int64)
+    nb = np.ascontiguousarray(model.nbrs, np.int32)
+    bnd = np.zeros(N, np.uint8)
+    bnd[model.boundary] = 1
+    anchor = np.zeros(npix, np.int32)
+    nfar = np.zeros(npix, np.int64)
+    nnear = np.zeros(npix, np.int64)
+    lib.oracle_image_rays(N, _p(pos), _p(off), _p(nb), _p(bnd), _p(n), npix, _p(ref), _p(anchor), _p(nfar),
+                          _p(nnear), None, None)
+    ray_off = np.zeros(npix + 1, np.int64)
+    np.cumsum(nfar + nnear + 1, out=ray_off[1:])
+    pts = np.zeros(int(ray_off[-1]), np.int32)
+    lib.oracle_image_rays(N, _p(pos), _p(off), _p(nb), _p(bnd), _p(n), npix, _p(ref), _p(anchor), _p(nfar),
+                          _p(nnear), _p(ray_off), _p(pts))
+    return ImageRays(ref, anchor, ray_off, pts, e1, e2)
+
+
+def image(model, pops, direction, npx, npy, nfreq, fmin, fmax, thr=0.35, rays=None):
+    """Intensity toward the observer [nfreq][npy][npx] (W m^-2 Hz^-1 sr^-1)
+    from the level populations ``pops`` [N][L]; each channel uses the line
+    nearest to it.  Returns (image, rays)."""
+    lib = _load()
+    if rays is None:
+        rays = image_rays(model, direction, npx, npy)
+    chi, S, _ = line_chi_S(pops, model.lines)
+    nu_f = image_frequencies(nfreq, fmin, fmax)
+    arr = lambda a, t=np.float64: np.ascontiguousarray(a, t)
+    npix = npx * npy
+    out = np.zeros((nfreq, npix))
+    lib.oracle_image_solve(model.n_points, _p(arr(model.pos)), _p(arr(model.vel)), _p(arr(model.temp)),
+                           _p(arr(model.vturb2)), float(model.lines.mol_mass_kg), _p(arr(direction)),
+                           model.lines.n_lines, _p(arr(model.lines.freq_Hz)), _p(arr(chi)), _p(arr(S)),
+                           float(model.T_bg), thr, npix, _p(rays.off), _p(rays.pts), nfreq, _p(nu_f), _p(out))
+    return out.reshape(nfreq, npy, npx), rays

@@ -341,3 +341,199 @@ void oracle_formal_solve(int64_t N, const double *pos, const double *vel, const 
         free(pt); free(beta); free(dx); free(dnu); free(off); free(dtau); free(Sd);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Synthetic image (Listing 3, compute_image_new: an image along a ray      */
+/* direction with N_pix_x x N_pix_y pixels).  The paper gives no algorithm; */
+/* readings used here:                                                       */
+/*  - n is the unit direction toward the observer; the image plane basis is  */
+/*    e1 = unit(a x n) with a the coordinate axis least aligned with n       */
+/*    (lowest index on ties), e2 = n x e1;                                   */
+/*  - the pixel grid is square and covers the projections of all points:     */
+/*    centre (c1, c2) = mid-range of the projections, half-width H = half    */
+/*    the larger range; pixel (i, j) has reference point                     */
+/*    p = (c1 - H + (i + 1/2) 2H/npx) e1 + (c2 - H + (j + 1/2) 2H/npy) e2;   */
+/*  - the pixel's anchor is the point closest to the pixel line (p, n)       */
+/*    (squared perpendicular distance, ties to the smaller index);           */
+/*  - the pixel ray is the walk (rule of walk() above, distances to the      */
+/*    pixel line, Z measured from p) from the anchor along -n, reversed,     */
+/*    then the anchor, then the walk along +n.                               */
+/* Everything in FP64, expressions in the order written, no FMA.             */
+/* ------------------------------------------------------------------------ */
+void oracle_image_frame(int64_t N, const double *pos, const double *n, int32_t npx, int32_t npy,
+                        double *e1, double *e2, double *ref /* [npy*npx][3] */)
+{
+    int ax = 0;
+    for (int k = 1; k < 3; ++k)
+        if (fabs(n[k]) < fabs(n[ax])) ax = k;
+    double a[3] = {0.0, 0.0, 0.0};
+    a[ax] = 1.0;
+    double c[3] = {a[1] * n[2] - a[2] * n[1], a[2] * n[0] - a[0] * n[2], a[0] * n[1] - a[1] * n[0]};
+    double cl = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    for (int k = 0; k < 3; ++k) e1[k] = c[k] / cl;
+    e2[0] = n[1] * e1[2] - n[2] * e1[1];
+    e2[1] = n[2] * e1[0] - n[0] * e1[2];
+    e2[2] = n[0] * e1[1] - n[1] * e1[0];
+    double lo1 = 1e300, hi1 = -1e300, lo2 = 1e300, hi2 = -1e300;
+    for (int64_t i = 0; i < N; ++i) {
+        double s1 = pos[3 * i] * e1[0] + pos[3 * i + 1] * e1[1] + pos[3 * i + 2] * e1[2];
+        double s2 = pos[3 * i] * e2[0] + pos[3 * i + 1] * e2[1] + pos[3 * i + 2] * e2[2];
+        if (s1 < lo1) lo1 = s1;
+        if (s1 > hi1) hi1 = s1;
+        if (s2 < lo2) lo2 = s2;
+        if (s2 > hi2) hi2 = s2;
+    }
+    double c1 = 0.5 * (lo1 + hi1), c2 = 0.5 * (lo2 + hi2);
+    double H = 0.5 * ((hi1 - lo1) > (hi2 - lo2) ? (hi1 - lo1) : (hi2 - lo2));
+    for (int32_t j = 0; j < npy; ++j)
+        for (int32_t i = 0; i < npx; ++i) {
+            double t1 = c1 - H + (i + 0.5) * (2.0 * H / npx);
+            double t2 = c2 - H + (j + 0.5) * (2.0 * H / npy);
+            double *p = ref + 3 * ((int64_t)j * npx + i);
+            for (int k = 0; k < 3; ++k) p[k] = t1 * e1[k] + t2 * e2[k];
+        }
+}
+
+/* Walk of an image half-ray: reference point p, direction d (unit), start
+ * point a with projection Za = (x_a - p).d; same rule as walk(). */
+static int64_t walk_ref(int64_t a, const double *p, const double *d, double Za, const double *pos,
+                        const int64_t *off, const int32_t *nb, const uint8_t *bnd, int64_t N, int32_t *out)
+{
+    int64_t c = a, len = 0;
+    double Zc = Za;
+    for (;;) {
+        int64_t best = -1;
+        double bestd = 0.0, bestZ = 0.0;
+        for (int64_t k = off[c]; k < off[c + 1]; ++k) {
+            int64_t m = nb[k];
+            double dx = pos[3 * m] - p[0];
+            double dy = pos[3 * m + 1] - p[1];
+            double dz = pos[3 * m + 2] - p[2];
+            double Z = dx * d[0] + dy * d[1] + dz * d[2];
+            if (!(Z > Zc)) continue;
+            double px = dx - Z * d[0];
+            double py = dy - Z * d[1];
+            double pz = dz - Z * d[2];
+            double d2 = px * px + py * py + pz * pz;
+            if (best < 0 || d2 < bestd || (d2 == bestd && m < best)) {
+                best = m;
+                bestd = d2;
+                bestZ = Z;
+            }
+        }
+        if (best < 0) return len;
+        if (out) out[len] = (int32_t)best;
+        ++len;
+        c = best;
+        Zc = bestZ;
+        if (bnd[best] || len > N) return len;
+    }
+}
+
+/* Anchor (closest point to the pixel line) and the two half-ray lengths of
+ * each pixel; with `pts` the full rays are written at ray_off. */
+void oracle_image_rays(int64_t N, const double *pos, const int64_t *off, const int32_t *nb, const uint8_t *bnd,
+                       const double *n, int64_t npix, const double *ref, int32_t *anchor, int64_t *nfar,
+                       int64_t *nnear, const int64_t *ray_off, int32_t *pts)
+{
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < npix; ++q) {
+        const double *p = ref + 3 * q;
+        int64_t best = -1;
+        double bestd = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            double dx = pos[3 * i] - p[0];
+            double dy = pos[3 * i + 1] - p[1];
+            double dz = pos[3 * i + 2] - p[2];
+            double Z = dx * n[0] + dy * n[1] + dz * n[2];
+            double px = dx - Z * n[0];
+            double py = dy - Z * n[1];
+            double pz = dz - Z * n[2];
+            double d2 = px * px + py * py + pz * pz;
+            if (best < 0 || d2 < bestd) {
+                best = i;
+                bestd = d2;
+            }
+        }
+        anchor[q] = (int32_t)best;
+        double m[3] = {-n[0], -n[1], -n[2]};
+        const double *xa = pos + 3 * best;
+        double Zf = (xa[0] - p[0]) * m[0] + (xa[1] - p[1]) * m[1] + (xa[2] - p[2]) * m[2];
+        double Zn = (xa[0] - p[0]) * n[0] + (xa[1] - p[1]) * n[1] + (xa[2] - p[2]) * n[2];
+        if (!pts) {
+            nfar[q] = walk_ref(best, p, m, Zf, pos, off, nb, bnd, N, NULL);
+            nnear[q] = walk_ref(best, p, n, Zn, pos, off, nb, bnd, N, NULL);
+        } else {
+            int32_t *r = pts + ray_off[q];
+            int64_t nf = walk_ref(best, p, m, Zf, pos, off, nb, bnd, N, r);
+            for (int64_t k = 0; k < nf / 2; ++k) {          /* far half outward -> inward */
+                int32_t t = r[k];
+                r[k] = r[nf - 1 - k];
+                r[nf - 1 - k] = t;
+            }
+            r[nf] = (int32_t)best;
+            walk_ref(best, p, n, Zn, pos, off, nb, bnd, N, r + nf + 1);
+        }
+    }
+}
+
+/* First-order (short-characteristics) formal solution toward the observer
+ * along one image ray for one channel.  Points P_0 (far) .. P_D (near);
+ * with piecewise-linear S in optical depth the exact update over a segment
+ * of depth t is I <- e^-t I + w0(t) S_far + w1(t) S_near,
+ *   w0 = (1 - e^-t)/t - e^-t,  w1 = 1 - (1 - e^-t)/t,
+ * evaluated by their Taylor series for t < 1e-3.  The segment depth follows
+ * oracle_segment_dtau at the comoving offsets nu_f (1 - n.v/c) - nu_line. */
+void oracle_image_weights(double t, double *E, double *w0, double *w1)
+{
+    *E = exp(-t);
+    if (t < 1e-3) {
+        /* (1 - e^-t)/t = 1 - t/2 + t^2/6 - t^3/24 + t^4/120 */
+        double g = 1.0 - t / 2.0 + t * t / 6.0 - t * t * t / 24.0 + t * t * t * t / 120.0;
+        *w0 = g - *E;
+        *w1 = 1.0 - g;
+    } else {
+        double g = (1.0 - *E) / t;
+        *w0 = g - *E;
+        *w1 = 1.0 - g;
+    }
+}
+
+void oracle_image_solve(int64_t N, const double *pos, const double *vel, const double *temp, const double *vturb2,
+                        double mol_mass, const double *n, int32_t M, const double *nu_line, const double *chi,
+                        const double *S, double T_bg, double thr, int64_t npix, const int64_t *ray_off,
+                        const int32_t *pts, int32_t nfreq, const double *nu_f, double *image /* [nfreq][npix] */)
+{
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < npix; ++q) {
+        const int32_t *r = pts + ray_off[q];
+        int64_t D = ray_off[q + 1] - ray_off[q] - 1;   /* segments */
+        for (int32_t f = 0; f < nfreq; ++f) {
+            double nu = nu_f[f];
+            int32_t l = 0;                              /* nearest line */
+            for (int32_t k = 1; k < M; ++k)
+                if (fabs(nu - nu_line[k]) < fabs(nu - nu_line[l])) l = k;
+            double nl = nu_line[l];
+            double I = oracle_planck(nu, T_bg);
+            for (int64_t d = 0; d < D; ++d) {
+                int64_t a = r[d], b = r[d + 1];
+                double ex = pos[3 * b] - pos[3 * a], ey = pos[3 * b + 1] - pos[3 * a + 1],
+                       ez = pos[3 * b + 2] - pos[3 * a + 2];
+                double dx = sqrt(ex * ex + ey * ey + ez * ez);
+                double va = (n[0] * vel[3 * a] + n[1] * vel[3 * a + 1] + n[2] * vel[3 * a + 2]) / OR_C;
+                double vb = (n[0] * vel[3 * b] + n[1] * vel[3 * b + 1] + n[2] * vel[3 * b + 2]) / OR_C;
+                double offa = nu * (1.0 - va) - nl, offb = nu * (1.0 - vb) - nl;
+                double dna = nl / OR_C * sqrt(2.0 * OR_KB * temp[a] / mol_mass + vturb2[a]);
+                double dnb = nl / OR_C * sqrt(2.0 * OR_KB * temp[b] / mol_mass + vturb2[b]);
+                double Tb = 0.5 * (temp[a] + temp[b]), vb2 = 0.5 * (vturb2[a] + vturb2[b]);
+                double dnbar = nl / OR_C * sqrt(2.0 * OR_KB * Tb / mol_mass + vb2);
+                double t = oracle_segment_dtau(dx, chi[(int64_t)l * N + a], chi[(int64_t)l * N + b], dna, dnb, dnbar,
+                                               offa, offb, thr);
+                double E, w0, w1;
+                oracle_image_weights(t, &E, &w0, &w1);
+                I = E * I + w0 * S[(int64_t)l * N + a] + w1 * S[(int64_t)l * N + b];
+            }
+            image[(int64_t)f * npix + q] = I;
+        }
+    }
+}
