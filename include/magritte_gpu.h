@@ -242,6 +242,73 @@ mgt_status mgt_ng_accelerate(mgt_model *m, const mgt_ng_opts *opts, int *accepte
 mgt_status mgt_ali_solve(mgt_model *m, const mgt_ali_opts *opts, mgt_ali_stats *stats, void *stream);
 
 /*
+ * Synthetic image along a line of sight (Listing 3, compute_image_new(rx, ry,
+ * rz, N_pix_x, N_pix_y), with the channels of compute_spectral_discretisation(
+ * fmin, fmax, N)).  The paper gives no algorithm; the definition used here:
+ *  - dir (host, [3]) is the unit direction toward the observer; the image
+ *    plane has basis e1 = unit(a x dir), a the coordinate axis least aligned
+ *    with dir (lowest index on ties), e2 = dir x e1; the square pixel grid
+ *    covers the projections of all points (centre: mid-range of the
+ *    projections, half-width: half the larger range); pixel (i, j) has the
+ *    reference point p = (c1 - H + (i + 1/2) 2H/npx) e1 + (c2 - H + (j + 1/2)
+ *    2H/npy) e2;
+ *  - the pixel ray starts from the pixel's anchor, the point closest to the
+ *    line (p, dir) (ties to the smaller index), and walks along -dir and +dir
+ *    by the rule of mgt_trace_rays with distances to that line and Z measured
+ *    from p; the ray runs from its far end to its near end;
+ *  - channel f has observer-frame frequency fmin + f (fmax - fmin)/(nfreq - 1)
+ *    (fmin for nfreq = 1) and sees the line nearest to it; a point moving with
+ *    v sees the comoving frequency nu_f (1 - dir.v/c);
+ *  - segment optical depths follow mgt_formal_solve (Sec. 4.3: trapezoid, or
+ *    the semi-analytic erf form at or above switch_threshold); the intensity
+ *    toward the observer is integrated with a source function linear in
+ *    optical depth over each segment, from B_nu_f(T_bg) at the far end.
+ * Uses the current populations.  out: [nfreq][npy][npx] f32 intensities in
+ * W m^-2 Hz^-1 sr^-1, host or device per on_device.  Pixel rays are traced on
+ * the first call for a (dir, npx, npy) and kept.  The image is computed in
+ * FP32.  MGT_ERR_ARG for a non-unit or non-finite dir, npx * npy > 2^26,
+ * nfreq outside 1..65536 or not 0 < fmin <= fmax.
+ */
+mgt_status mgt_image(mgt_model *m, const double dir[3], int32_t npx, int32_t npy, int32_t nfreq, double fmin,
+                     double fmax, float *out, int on_device, void *stream);
+
+/*
+ * Gradient of a loss of the image with respect to the per-point fields
+ * (the hand-written adjoint of mgt_image; the paper has no counterpart, its
+ * differentiation is asked for by this library's users).  grad_out [nfreq][npy]
+ * [npx] f32 holds dL/dI (host or device per on_device).  Outputs (same memory
+ * kind, any may be NULL): g_logT [N] = dL/d log T, g_logn [N] = dL/d log n_spec,
+ * g_vel [N][3] = dL/dv in (W m^-2 Hz^-1 sr^-1)^-1 L per m/s.  Level populations
+ * are held as fractions of n_spec (so the opacity scales with n_spec and the
+ * source function does not); T enters through the Doppler width.  The branch
+ * of each segment's optical depth (trapezoid or erf form) is held fixed.
+ * Rays longer than 4096 segments give MGT_ERR_ARG.  Arguments as mgt_image.
+ */
+mgt_status mgt_image_adjoint(mgt_model *m, const double dir[3], int32_t npx, int32_t npy, int32_t nfreq,
+                             double fmin, double fmax, const float *grad_out, double *g_logT, double *g_logn,
+                             double *g_vel, int on_device, void *stream);
+
+/*
+ * The pixel rays of mgt_image for (dir, npx, npy), copied to host memory:
+ * anchor [npx*npy], ray_off [npx*npy+1] (offsets into pts), pts [ray_off[npix]]
+ * point indices, far end first.  Any pointer may be NULL.
+ */
+mgt_status mgt_image_rays(mgt_model *m, const double dir[3], int32_t npx, int32_t npy, int32_t *anchor,
+                          int64_t *ray_off, int32_t *pts, void *stream);
+
+/*
+ * Replace per-point fields (Sec. 3.2, Listing 2 inputs): temp [N] K, n_spec
+ * [N] m^-3, vel [N][3] m/s; NULL leaves a field unchanged.  Level populations
+ * keep their fractions n_i / n_spec.  Host inputs are validated (finite,
+ * T > 0, n_spec > 0); device inputs (on_device nonzero) are not.  Changing T or
+ * v makes the traced rays stale: mgt_trace_rays must run again before
+ * mgt_formal_solve.  Pixel rays of mgt_image stay valid (positions do not
+ * change).
+ */
+mgt_status mgt_set_point_fields(mgt_model *m, const double *temp, const double *n_spec, const double *vel,
+                                int on_device, void *stream);
+
+/*
  * Ng extrapolation without any device allocation.  The paper has no
  * counterpart: this is a service for callers that cannot allocate device
  * memory -- an application whose own allocator owns the whole GPU (a pool

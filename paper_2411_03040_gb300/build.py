@@ -12,10 +12,12 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmgt.so")
-SOURCES = ["api.cu", "k_geom.cu", "k_fs.cu", "k_se.cu", "k_ng.cu", "k_ng_noalloc.cu"]
+SOURCES = ["api.cu", "k_geom.cu", "k_fs.cu", "k_se.cu", "k_ng.cu", "k_ng_noalloc.cu", "k_image.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code without multiply-add contraction: the image frame must round like
+# its definition (the same expressions as the oracle's)
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr"]
+         "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr"]
 
 
 def _nvcc() -> str:

@@ -221,6 +221,7 @@ static void free_model(mgt_model *m)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     ng_free(m);
+    image_free(m);
     delete m;
 }
 

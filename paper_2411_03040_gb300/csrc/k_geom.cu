@@ -2,6 +2,10 @@
 // function, and the ray walk through the neighbour graph.
 #include <cub/cub.cuh>
 
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
 #include "mgt_common.cuh"
 
 namespace mgt {
@@ -309,8 +313,23 @@ __device__ __forceinline__ float group16_min(float v)
 //    not kept (such walks are redone by the list mode).
 //  * kWalkList: the walks named in `list` only, records written to their final
 //    place (ray offsets known).
+//  * kWalkImgCount / kWalkImgFill: the two half-rays of every image pixel
+//    (walk 2q + h: h = 0 along -n, h = 1 along +n, n toward the observer),
+//    from the pixel's anchor point, distances to the pixel line, Z measured
+//    from the pixel's reference point; the count mode writes the lengths, the
+//    fill mode the point indices of the full ray (far half reversed, anchor,
+//    near half).
 // ---------------------------------------------------------------------------
-constexpr int kWalkFused = 0, kWalkList = 1;
+constexpr int kWalkFused = 0, kWalkList = 1, kWalkImgCount = 2, kWalkImgFill = 3;
+
+struct ImgWalkArgs {
+    const double *ref;        // [npix][3] pixel reference points
+    const int32_t *anchor;    // [npix] start point of both half-rays
+    const int64_t *off;       // [npix+1] full-ray offsets (fill mode)
+    int32_t *pts;             // full rays (fill mode)
+    int64_t npix;
+    double n[3];              // unit direction toward the observer
+};
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ lens, const int64_t *__restrict__ ray_off,
@@ -318,13 +337,14 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
                                               unsigned long long *__restrict__ n_stall,
                                               const float *__restrict__ vel_hl, const float2 *__restrict__ w32,
                                               float inv_Lunit, int width_mode, Step32 *__restrict__ steps,
-                                              int *__restrict__ err)
+                                              int *__restrict__ err, ImgWalkArgs im)
 {
+    constexpr bool IMG = MODE == kWalkImgCount || MODE == kWalkImgFill;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, sl = lane & 15, grp = lane >> 4;
     const unsigned gmask = 0xffffu << (16 * grp);
     const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 4;   // walk slot
-    const int64_t W = MODE == kWalkFused ? (int64_t)a.R * a.N : n_list;
+    const int64_t W = MODE == kWalkFused ? (int64_t)a.R * a.N : IMG ? 2 * im.npix : n_list;
     if ((wg & ~(int64_t)1) >= W) return;                       // both walks of the warp absent
     bool live = wg < W;
     int r = 0;
@@ -333,20 +353,45 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
         if (MODE == kWalkFused) {
             r = (int)(wg / a.N);
             o = a.order[wg - (int64_t)r * a.N];
+        } else if (IMG) {
+            r = (int)(wg & 1);
+            o = im.anchor[wg >> 1];
         } else {
             const int64_t t = list[wg];
             r = (int)(t / a.N);
             o = t - (int64_t)r * a.N;
         }
     }
-    if (o < 0 || o >= a.N || r < 0 || r >= a.R) {            // index check: record and skip
+    if (o < 0 || o >= a.N || r < 0 || r >= (IMG ? 2 : a.R)) {   // index check: record and skip
         walk_give_up(err, 13, wg, o);
         o = 0;
         r = 0;
         live = false;
     }
     const int64_t wi = (int64_t)r * a.N + o;
-    const WalkFrame f = make_frame(a, o, r);
+    // the walk's frame: origin o and direction r, or for image walks the pixel's
+    // reference point and -n / +n (FP64 values are loaded again where needed)
+    WalkFrame f;
+    double img_Z0 = 0.0;                        // image walks: Z of the anchor
+    if (IMG) {
+        const double sg = r == 0 ? -1.0 : 1.0;
+        const double *pr = im.ref + 3 * (wg >> 1);
+        const double sx = pr[0] * a.pos_scale, sy = pr[1] * a.pos_scale, sz = pr[2] * a.pos_scale;
+        f.ohx = (float)sx;
+        f.ohy = (float)sy;
+        f.ohz = (float)sz;
+        f.olx = (float)(sx - (double)f.ohx);
+        f.oly = (float)(sy - (double)f.ohy);
+        f.olz = (float)(sz - (double)f.ohz);
+        f.f0 = (float)(sg * im.n[0]);
+        f.f1 = (float)(sg * im.n[1]);
+        f.f2 = (float)(sg * im.n[2]);
+        const double *q = a.pos + 3 * o;
+        img_Z0 = dot3_exact(__dsub_rn(q[0], pr[0]), __dsub_rn(q[1], pr[1]), __dsub_rn(q[2], pr[2]), sg * im.n[0],
+                            sg * im.n[1], sg * im.n[2]);
+    } else {
+        f = make_frame(a, o, r);
+    }
     // records go to out[0 .. cap): the walk's scratch slot, or its final place
     int64_t cap = K;
     Step32 *out = steps + wi * (int64_t)K;
@@ -354,13 +399,24 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
         out = steps + ray_off[wi];
         cap = ray_off[wi + 1] - ray_off[wi];
     }
+    if (IMG) cap = a.N;
+    int64_t img_nfar = 0, img_base = 0;         // fill: far-half length and the pixel's ray offset
+    if (MODE == kWalkImgFill && live) {
+        img_nfar = lens[wg & ~(int64_t)1];
+        img_base = im.off[wg >> 1];
+        cap = lens[wg];
+    }
     // step records are built 16 at a time: lane j of the group keeps the point
     // of step (chunk start + j); prev_last is the point before the chunk
     int32_t my_pt = 0;
     int64_t prev_last = o;
     int64_t c = o, n = 0;
     int32_t c_off = live ? a.ent_off[o] : 0;   // the current point's row of packed entries
-    float Zc = 0.0f, eZc = 0.0f;                // Z of o is exactly 0
+    float Zc = 0.0f, eZc = 0.0f;                // Z of o is exactly 0 (image walks: the anchor's Z)
+    if (IMG) {
+        Zc = (float)(img_Z0 * a.pos_scale);     // the filter works in scaled units (exact factor)
+        eZc = 1e-7f * fabsf(Zc) + 1e-30f;
+    }
     bool done = !live;
     // every loop below is bounded: the walk by the point count and a 2 s
     // clock, a row scan by the number of packed entries; running out records
@@ -463,11 +519,27 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
         double Zn = 0.0;
         if (exact && sl == 0) {
             // FP64 predicates, evaluated by lane 0 of the group
-            atomicAdd(a.n_exact, 1ULL);
-            const double xo = a.pos[3 * o], yo = a.pos[3 * o + 1], zo = a.pos[3 * o + 2];
-            const double n0 = a.dirs[3 * r], n1 = a.dirs[3 * r + 1], n2 = a.dirs[3 * r + 2];
+            if (!IMG) atomicAdd(a.n_exact, 1ULL);
+            double xo, yo, zo, n0, n1, n2;
+            if (IMG) {
+                const double *pr = im.ref + 3 * (wg >> 1);
+                const double sg = r == 0 ? -1.0 : 1.0;
+                xo = pr[0];
+                yo = pr[1];
+                zo = pr[2];
+                n0 = sg * im.n[0];
+                n1 = sg * im.n[1];
+                n2 = sg * im.n[2];
+            } else {
+                xo = a.pos[3 * o];
+                yo = a.pos[3 * o + 1];
+                zo = a.pos[3 * o + 2];
+                n0 = a.dirs[3 * r];
+                n1 = a.dirs[3 * r + 1];
+                n2 = a.dirs[3 * r + 2];
+            }
             double Zc64 = 0.0;
-            if (c != o) {
+            if (c != o || IMG) {
                 const double *q = a.pos + 3 * c;
                 Zc64 = dot3_exact(__dsub_rn(q[0], xo), __dsub_rn(q[1], yo), __dsub_rn(q[2], zo), n0, n1, n2);
             }
@@ -507,7 +579,7 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
                 if (MODE == kWalkFused && sl == 0 && !(c == o && a.bnd[o])) atomicAdd(n_stall, 1ULL);
                 done = true;
                 flush_last = (n & 15) != 0;
-            } else if (MODE == kWalkList && n >= cap) {   // cannot happen for a deterministic walk
+            } else if ((MODE == kWalkList || MODE == kWalkImgFill) && n >= cap) {   // cannot happen: deterministic walk
                 if (sl == 0) atomicCAS(err, 0, (int)kDevBounds);
                 done = true;
             } else {
@@ -521,7 +593,19 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
                 }
             }
         }
-        if (__any_sync(full, flush_full || flush_last)) {
+        if (IMG) {
+            // image fill: the group's buffered point indices to their place in
+            // the pixel's full ray (far half reversed, then anchor, then near half)
+            if (MODE == kWalkImgFill && __any_sync(full, flush_full || flush_last)) {
+                const int cnt = flush_full ? 16 : (int)(n & 15);
+                const int64_t first = flush_full ? n - 16 : (n & ~(int64_t)15);
+                if ((flush_full || flush_last) && sl < cnt) {
+                    const int64_t k = first + sl;
+                    const int64_t at = r == 0 ? img_base + img_nfar - 1 - k : img_base + img_nfar + 1 + k;
+                    im.pts[at] = my_pt;
+                }
+            }
+        } else if (__any_sync(full, flush_full || flush_last)) {
             // records of the group's buffered steps (n already counts the newest);
             // chunks start at multiples of 16 and cap is one (fused mode) or
             // exactly the walk's length (list mode), so a chunk is kept whole or
@@ -537,6 +621,8 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
     if (live && sl == 0) {
         if (MODE == kWalkFused)
             lens[wi] = gave_up ? 0 : n;
+        else if (MODE == kWalkImgCount)
+            lens[wg] = gave_up ? 0 : n;
         else if (n != cap && !gave_up)
             atomicCAS(err, 0, (int)kDevBounds);
     }
@@ -643,7 +729,7 @@ mgt_status trace_all(mgt_model *m, cudaStream_t s)
     const float inv_Lunit = (float)(1.0 / (m->pos_scale * m->L_unit));
     k_walk<kWalkFused><<<ceil_div(W * 16, 256), 256, 0, s>>>(a, d_len, nullptr, nullptr, 0, (int32_t)K,
                                                              m->d_count + 1, m->d_vel_hl, m->d_w32, inv_Lunit,
-                                                             m->opts.width_mode, d_scratch, m->d_err);
+                                                             m->opts.width_mode, d_scratch, m->d_err, ImgWalkArgs{});
     MGT_LAUNCH_CHECK("k_walk<fused>");
     MGT_CUDA(cudaMemsetAsync(d_len + W, 0, sizeof(int64_t), s));
     size_t tmp_bytes = 0;
@@ -690,7 +776,7 @@ mgt_status trace_all(mgt_model *m, cudaStream_t s)
         if (n_over > 0) {
             k_walk<kWalkList><<<ceil_div((int64_t)n_over * 16, 256), 256, 0, s>>>(
                 a, nullptr, m->d_ray_off, d_list, (int64_t)n_over, 0, nullptr, m->d_vel_hl, m->d_w32, inv_Lunit,
-                m->opts.width_mode, m->d_steps32, m->d_err);
+                m->opts.width_mode, m->d_steps32, m->d_err, ImgWalkArgs{});
             MGT_LAUNCH_CHECK("k_walk<list>");
         }
     }
@@ -712,6 +798,243 @@ mgt_status build_steps64(mgt_model *m, cudaStream_t s)
                                                m->d_steps64);
     MGT_LAUNCH_CHECK("k_steps64");
     m->steps64_width_mode = m->opts.width_mode;
+    return MGT_OK;
+}
+
+}  // namespace mgt
+
+namespace mgt {
+
+// ---------------------------------------------------------------------------
+// Synthetic image geometry (Listing 3, compute_image_new).  The paper gives
+// no algorithm; the image plane, the pixel reference points, the anchor of a
+// pixel (the point closest to the pixel line) and the two walks from it follow
+// the definition written out in the model-independent form below, in FP64
+// with every expression in the order written (host code is compiled without
+// multiply-add contraction).
+// ---------------------------------------------------------------------------
+void image_frame(const double *pos, int64_t N, const double n[3], int32_t npx, int32_t npy, double e1[3],
+                 double e2[3], std::vector<double> &ref)
+{
+    int ax = 0;
+    for (int k = 1; k < 3; ++k)
+        if (std::fabs(n[k]) < std::fabs(n[ax])) ax = k;
+    double av[3] = {0.0, 0.0, 0.0};
+    av[ax] = 1.0;
+    const double c[3] = {av[1] * n[2] - av[2] * n[1], av[2] * n[0] - av[0] * n[2], av[0] * n[1] - av[1] * n[0]};
+    const double cl = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    for (int k = 0; k < 3; ++k) e1[k] = c[k] / cl;
+    e2[0] = n[1] * e1[2] - n[2] * e1[1];
+    e2[1] = n[2] * e1[0] - n[0] * e1[2];
+    e2[2] = n[0] * e1[1] - n[1] * e1[0];
+    double lo1 = 1e300, hi1 = -1e300, lo2 = 1e300, hi2 = -1e300;
+    for (int64_t i = 0; i < N; ++i) {
+        const double s1 = pos[3 * i] * e1[0] + pos[3 * i + 1] * e1[1] + pos[3 * i + 2] * e1[2];
+        const double s2 = pos[3 * i] * e2[0] + pos[3 * i + 1] * e2[1] + pos[3 * i + 2] * e2[2];
+        if (s1 < lo1) lo1 = s1;
+        if (s1 > hi1) hi1 = s1;
+        if (s2 < lo2) lo2 = s2;
+        if (s2 > hi2) hi2 = s2;
+    }
+    const double c1 = 0.5 * (lo1 + hi1), c2 = 0.5 * (lo2 + hi2);
+    const double H = 0.5 * ((hi1 - lo1) > (hi2 - lo2) ? (hi1 - lo1) : (hi2 - lo2));
+    ref.assign(3 * (size_t)npx * npy, 0.0);
+    for (int32_t j = 0; j < npy; ++j)
+        for (int32_t i = 0; i < npx; ++i) {
+            const double t1 = c1 - H + (i + 0.5) * (2.0 * H / npx);
+            const double t2 = c2 - H + (j + 0.5) * (2.0 * H / npy);
+            double *p = ref.data() + 3 * ((size_t)j * npx + i);
+            for (int k = 0; k < 3; ++k) p[k] = t1 * e1[k] + t2 * e2[k];
+        }
+}
+
+// Anchor of each pixel: the point whose squared distance to the pixel line
+// |(x - p) - ((x - p).n) n|^2 is smallest, ties to the smaller index.  One
+// warp per pixel; FP32 distances from hi + lo positions with the error bounds
+// of the walk, an FP64 scan (the defining expressions) when the bounds do not
+// separate the winner from every other point.
+__global__ void __launch_bounds__(256) k_img_anchor(WalkArgs a, const double *__restrict__ ref, int64_t npix,
+                                                    double n0, double n1, double n2, int32_t *__restrict__ anchor)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (q >= npix) return;                                     // whole warp
+    const double *pr = ref + 3 * q;
+    const double sx = pr[0] * a.pos_scale, sy = pr[1] * a.pos_scale, sz = pr[2] * a.pos_scale;
+    const float ohx = (float)sx, ohy = (float)sy, ohz = (float)sz;
+    const float olx = (float)(sx - (double)ohx), oly = (float)(sy - (double)ohy), olz = (float)(sz - (double)ohz);
+    const float f0 = (float)n0, f1 = (float)n1, f2 = (float)n2;
+    float bd2 = 3.0e38f, bU = 3.0e38f, bL = 3.0e38f, minLo = 3.0e38f;
+    int64_t bi = -1;
+    for (int64_t i = lane; i < a.N; i += 32) {
+        const float *h = a.pos_hl + 6 * i;
+        const float dx = (h[0] - ohx) + (h[3] - olx), dy = (h[1] - ohy) + (h[4] - oly), dz = (h[2] - ohz) + (h[5] - olz);
+        const float adx = fabsf(dx), ady = fabsf(dy), adz = fabsf(dz);
+        const float ed = 2e-6f * (fmaxf(adx, fmaxf(ady, adz)) + a.pos_slack);
+        const float Z = fmaf(dz, f2, fmaf(dy, f1, dx * f0));
+        const float eZ = 2e-6f * (adx + ady + adz) + 2.0f * ed;
+        const float px = fmaf(-Z, f0, dx), py = fmaf(-Z, f1, dy), pz = fmaf(-Z, f2, dz);
+        const float d2 = fmaf(pz, pz, fmaf(py, py, px * px));
+        const float ep = ed + eZ + 2e-7f * (fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz))) + fabsf(Z));
+        const float e2 = 4.0f * sqrtf(d2) * ep + 4.0f * ep * ep + 1e-6f * d2;
+        if (d2 < bd2) {                       // strictly smaller: the lane's earlier index wins ties
+            minLo = fminf(minLo, bL);
+            bd2 = d2;
+            bU = d2 + e2;
+            bL = d2 - e2;
+            bi = i;
+        } else {
+            minLo = fminf(minLo, d2 - e2);
+        }
+    }
+    // warp winner: smallest d2, then smallest index
+    float wd2 = bd2;
+    int64_t wi = bi < 0 ? INT64_MAX : bi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float od = __shfl_xor_sync(full, wd2, o);
+        const int64_t oi = __shfl_xor_sync(full, wi, o);
+        if (od < wd2 || (od == wd2 && oi < wi)) {
+            wd2 = od;
+            wi = oi;
+        }
+    }
+    const bool mine = bi == wi;
+    float oth = fminf(minLo, mine ? 3.0e38f : bL);
+    float wU = mine ? bU : 3.0e38f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        oth = fminf(oth, __shfl_xor_sync(full, oth, o));
+        wU = fminf(wU, __shfl_xor_sync(full, wU, o));
+    }
+    int64_t best = wi;
+    if (!(wU < oth)) {
+        // FP64, the defining expressions
+        double ed2 = 0.0;
+        int64_t ei = -1;
+        for (int64_t i = lane; i < a.N; i += 32) {
+            const double *x = a.pos + 3 * i;
+            const double dx = __dsub_rn(x[0], pr[0]), dy = __dsub_rn(x[1], pr[1]), dz = __dsub_rn(x[2], pr[2]);
+            const double Z = dot3_exact(dx, dy, dz, n0, n1, n2);
+            const double px = __dsub_rn(dx, __dmul_rn(Z, n0)), py = __dsub_rn(dy, __dmul_rn(Z, n1)),
+                         pz = __dsub_rn(dz, __dmul_rn(Z, n2));
+            const double d2 = dot3_exact(px, py, pz, px, py, pz);
+            if (ei < 0 || d2 < ed2) {
+                ed2 = d2;
+                ei = i;
+            }
+        }
+        if (ei < 0) ei = INT64_MAX;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double od = __shfl_xor_sync(full, ed2, o);
+            const int64_t oi = __shfl_xor_sync(full, ei, o);
+            if (oi != INT64_MAX && (ei == INT64_MAX || od < ed2 || (od == ed2 && oi < ei))) {
+                ed2 = od;
+                ei = oi;
+            }
+        }
+        best = ei;
+    }
+    if (lane == 0) anchor[q] = (int32_t)best;
+}
+
+// Full-ray sizes: nfar + anchor + nnear per pixel.
+__global__ void k_img_sizes(int64_t npix, const int64_t *__restrict__ lens, int64_t *__restrict__ sizes)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < npix) sizes[q] = lens[2 * q] + lens[2 * q + 1] + 1;
+}
+
+__global__ void k_img_place_anchor(int64_t npix, const int64_t *__restrict__ lens, const int64_t *__restrict__ off,
+                                   const int32_t *__restrict__ anchor, int32_t *__restrict__ pts)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < npix) pts[off[q] + lens[2 * q]] = anchor[q];
+}
+
+void image_free(mgt_model *m)
+{
+    ImageGeom &g = m->img;
+    if (g.d_ref) cudaFree(g.d_ref);
+    if (g.d_anchor) cudaFree(g.d_anchor);
+    if (g.d_off) cudaFree(g.d_off);
+    if (g.d_pts) cudaFree(g.d_pts);
+    g = ImageGeom{};
+}
+
+mgt_status trace_image(mgt_model *m, const double n[3], int32_t npx, int32_t npy, cudaStream_t s)
+{
+    ImageGeom &g = m->img;
+    if (g.valid && g.npx == npx && g.npy == npy && g.n[0] == n[0] && g.n[1] == n[1] && g.n[2] == n[2])
+        return MGT_OK;
+    image_free(m);
+    const int64_t npix = (int64_t)npx * npy;
+    std::vector<double> pos(3 * (size_t)m->N), ref;
+    MGT_CUDA(cudaMemcpyAsync(pos.data(), m->d_pos, sizeof(double) * 3 * m->N, cudaMemcpyDeviceToHost, s));
+    MGT_CUDA(cudaStreamSynchronize(s));
+    double e1[3], e2[3];
+    image_frame(pos.data(), m->N, n, npx, npy, e1, e2, ref);
+    MGT_CUDA(cudaMalloc(&g.d_ref, sizeof(double) * ref.size()));
+    MGT_CUDA(cudaMalloc(&g.d_anchor, sizeof(int32_t) * npix));
+    MGT_CUDA(cudaMalloc(&g.d_off, sizeof(int64_t) * (npix + 1)));
+    MGT_CUDA(cudaMemcpyAsync(g.d_ref, ref.data(), sizeof(double) * ref.size(), cudaMemcpyHostToDevice, s));
+    WalkArgs a{m->N,        m->R,          m->d_pos,  m->d_nbr_off, m->d_nbrs,   m->d_nbr_pos,
+               m->pos_scale, m->d_bnd,     m->d_dirs, m->d_ent,     m->d_ent_off, m->d_pos_hl,
+               m->d_dirs32,  m->d_order,   m->pos_slack, m->d_count + 3,
+               (int32_t)((m->n_ent + 15) / 16 + 2), m->n_ent};
+    k_img_anchor<<<ceil_div(npix * 32, 256), 256, 0, s>>>(a, g.d_ref, npix, n[0], n[1], n[2], g.d_anchor);
+    MGT_LAUNCH_CHECK("k_img_anchor");
+    int64_t *d_lens = nullptr, *d_sizes = nullptr;
+    void *tmp = nullptr;
+    MGT_CUDA(cudaMallocAsync(&d_lens, sizeof(int64_t) * 2 * npix, s));
+    MGT_CUDA(cudaMallocAsync(&d_sizes, sizeof(int64_t) * (npix + 1), s));
+    ImgWalkArgs im{g.d_ref, g.d_anchor, g.d_off, nullptr, npix, {n[0], n[1], n[2]}};
+    k_walk<kWalkImgCount><<<ceil_div(2 * npix * 16, 256), 256, 0, s>>>(a, d_lens, nullptr, nullptr, 0, 0, nullptr,
+                                                                       nullptr, nullptr, 0.0f, 0, nullptr, m->d_err,
+                                                                       im);
+    MGT_LAUNCH_CHECK("k_walk<image count>");
+    k_img_sizes<<<ceil_div(npix, 256), 256, 0, s>>>(npix, d_lens, d_sizes);
+    MGT_LAUNCH_CHECK("k_img_sizes");
+    MGT_CUDA(cudaMemsetAsync(d_sizes + npix, 0, sizeof(int64_t), s));
+    size_t tb = 0;
+    MGT_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, d_sizes, g.d_off, npix + 1, s));
+    MGT_CUDA(cudaMallocAsync(&tmp, tb, s));
+    MGT_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tb, d_sizes, g.d_off, npix + 1, s));
+    int64_t total = 0;
+    MGT_CUDA(cudaMemcpyAsync(&total, g.d_off + npix, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    std::vector<int64_t> sizes(npix);
+    MGT_CUDA(cudaMemcpyAsync(sizes.data(), d_sizes, sizeof(int64_t) * npix, cudaMemcpyDeviceToHost, s));
+    MGT_CUDA(cudaStreamSynchronize(s));
+    const mgt_status st = check_device_error(m, s);
+    if (st != MGT_OK) {
+        cudaFreeAsync(d_lens, s);
+        cudaFreeAsync(d_sizes, s);
+        cudaFreeAsync(tmp, s);
+        return st;
+    }
+    MGT_CUDA(cudaMalloc(&g.d_pts, sizeof(int32_t) * (total > 0 ? total : 1)));
+    im.pts = g.d_pts;
+    k_walk<kWalkImgFill><<<ceil_div(2 * npix * 16, 256), 256, 0, s>>>(a, d_lens, nullptr, nullptr, 0, 0, nullptr,
+                                                                      nullptr, nullptr, 0.0f, 0, nullptr, m->d_err, im);
+    MGT_LAUNCH_CHECK("k_walk<image fill>");
+    k_img_place_anchor<<<ceil_div(npix, 256), 256, 0, s>>>(npix, d_lens, g.d_off, g.d_anchor, g.d_pts);
+    MGT_LAUNCH_CHECK("k_img_place_anchor");
+    MGT_CUDA(cudaFreeAsync(d_lens, s));
+    MGT_CUDA(cudaFreeAsync(d_sizes, s));
+    MGT_CUDA(cudaFreeAsync(tmp, s));
+    MGT_TRY_STATUS(check_device_error(m, s));
+    int64_t mx = 0;
+    for (int64_t v : sizes) mx = std::max(mx, v);
+    g.total = total;
+    g.max_len = (int32_t)mx;
+    g.n[0] = n[0];
+    g.n[1] = n[1];
+    g.n[2] = n[2];
+    g.npx = npx;
+    g.npy = npy;
+    g.valid = true;
     return MGT_OK;
 }
 

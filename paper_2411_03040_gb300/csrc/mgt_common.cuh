@@ -51,6 +51,19 @@ struct alignas(32) Step64 {
     double dx, beta, dbw, pad;
 };
 
+// Pixel rays of the last image geometry (direction and pixel counts).
+struct ImageGeom {
+    bool valid = false;
+    double n[3] = {0, 0, 0};
+    int32_t npx = 0, npy = 0;
+    int64_t total = 0;                  // points over all pixel rays
+    int32_t max_len = 0;                // longest pixel ray (points)
+    double *d_ref = nullptr;            // [npix][3] pixel reference points
+    int32_t *d_anchor = nullptr;        // [npix]
+    int64_t *d_off = nullptr;           // [npix+1]
+    int32_t *d_pts = nullptr;           // [total] far end first
+};
+
 struct NgState {
     mgt_ng_opts opts{MGT_NG_NONE, 4, 8};
     int n_slots = 0;
@@ -127,6 +140,7 @@ struct mgt_model {
     int steps_width_mode = 0, steps64_width_mode = -1;
 
     mgt::NgState ng;
+    mgt::ImageGeom img;
 };
 
 namespace mgt {
@@ -143,6 +157,11 @@ mgt_status launch_lte(mgt_model *m, cudaStream_t s);
 mgt_status launch_line_data(mgt_model *m, cudaStream_t s);
 mgt_status trace_all(mgt_model *m, cudaStream_t s);
 mgt_status build_steps64(mgt_model *m, cudaStream_t s);
+
+mgt_status trace_image(mgt_model *m, const double n[3], int32_t npx, int32_t npy, cudaStream_t s);
+void image_free(mgt_model *m);
+void image_frame(const double *pos, int64_t N, const double n[3], int32_t npx, int32_t npy, double e1[3],
+                 double e2[3], std::vector<double> &ref);
 
 // formal solution (k_fs.cu)
 mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s);

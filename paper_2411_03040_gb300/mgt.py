@@ -73,6 +73,10 @@ SIGNATURES = {
     "mgt_ng_accelerate": [_P, ctypes.POINTER(mgt_ng_opts), ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(_f64), _P],
     "mgt_ali_solve": [_P, ctypes.POINTER(mgt_ali_opts), ctypes.POINTER(mgt_ali_stats), _P],
+    "mgt_image": [_P, _P, _i32, _i32, _i32, _f64, _f64, _P, ctypes.c_int, _P],
+    "mgt_image_adjoint": [_P, _P, _i32, _i32, _i32, _f64, _f64, _P, _P, _P, _P, ctypes.c_int, _P],
+    "mgt_image_rays": [_P, _P, _i32, _i32, _P, _P, _P, _P],
+    "mgt_set_point_fields": [_P, _P, _P, _P, ctypes.c_int, _P],
     "mgt_ng_extrapolate_noalloc": [_i32, _P, _i64, _P, _P, ctypes.POINTER(_i64), _P],
     "mgt_sync": [_P, _P],
     "mgt_model_sizes": [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
@@ -261,6 +265,63 @@ def mgt_ali_solve(m: Model, n_iter=20, precision=MGT_FP32_MIXED, ng_mode=MGT_NG_
     st = mgt_ali_stats()
     _check(load().mgt_ali_solve(m.handle, ctypes.byref(o), ctypes.byref(st), _stream(stream)), "mgt_ali_solve")
     return dict(iterations=st.iterations, ng_accepted=st.ng_accepted, last_maxrel=st.last_maxrel)
+
+
+def _dir(direction):
+    return np.ascontiguousarray(direction, np.float64)
+
+
+def mgt_image(m: Model, direction, npx, npy, nfreq, fmin, fmax, out=None, stream=None):
+    """Image [nfreq][npy][npx] f32; ``out`` may be a torch CUDA tensor."""
+    d = _dir(direction)
+    if out is None:
+        out = np.zeros((nfreq, npy, npx), np.float32)
+    on_dev = 1 if hasattr(out, "data_ptr") else 0
+    _check(load().mgt_image(m.handle, _ptr(d), npx, npy, nfreq, float(fmin), float(fmax), _ptr(out), on_dev,
+                            _stream(stream)), "mgt_image")
+    return out
+
+
+def mgt_image_adjoint(m: Model, direction, npx, npy, nfreq, fmin, fmax, grad_out, g_logT=None, g_logn=None,
+                      g_vel=None, stream=None):
+    """(g_logT [N], g_logn [N], g_vel [N][3]) for dL/dI = grad_out.  With a
+    torch CUDA ``grad_out`` the outputs must be torch CUDA tensors too."""
+    d = _dir(direction)
+    on_dev = 1 if hasattr(grad_out, "data_ptr") else 0
+    if not on_dev:
+        grad_out = np.ascontiguousarray(grad_out, np.float32)
+        n = mgt_model_sizes(m)["n_points"]
+        g_logT = np.zeros(n) if g_logT is None else g_logT
+        g_logn = np.zeros(n) if g_logn is None else g_logn
+        g_vel = np.zeros((n, 3)) if g_vel is None else g_vel
+    _check(load().mgt_image_adjoint(m.handle, _ptr(d), npx, npy, nfreq, float(fmin), float(fmax), _ptr(grad_out),
+                                    _ptr(g_logT), _ptr(g_logn), _ptr(g_vel), on_dev, _stream(stream)),
+           "mgt_image_adjoint")
+    return g_logT, g_logn, g_vel
+
+
+def mgt_image_rays(m: Model, direction, npx, npy, stream=None):
+    """(anchor, ray_off, pts) of the pixel rays, host arrays."""
+    d = _dir(direction)
+    npix = npx * npy
+    anchor = np.zeros(npix, np.int32)
+    off = np.zeros(npix + 1, np.int64)
+    _check(load().mgt_image_rays(m.handle, _ptr(d), npx, npy, _ptr(anchor), _ptr(off), None, _stream(stream)),
+           "mgt_image_rays")
+    pts = np.zeros(max(int(off[-1]), 1), np.int32)
+    _check(load().mgt_image_rays(m.handle, _ptr(d), npx, npy, None, None, _ptr(pts), _stream(stream)),
+           "mgt_image_rays")
+    return anchor, off, pts[:int(off[-1])]
+
+
+def mgt_set_point_fields(m: Model, temp=None, n_spec=None, vel=None, stream=None):
+    """Replace T [N], n_spec [N] and/or v [N][3] (numpy or torch CUDA tensors)."""
+    arrs = [temp, n_spec, vel]
+    on_dev = 1 if any(hasattr(a, "data_ptr") for a in arrs if a is not None) else 0
+    if not on_dev:
+        arrs = [None if a is None else np.ascontiguousarray(a, np.float64) for a in arrs]
+    _check(load().mgt_set_point_fields(m.handle, *[_ptr(a) for a in arrs], on_dev, _stream(stream)),
+           "mgt_set_point_fields")
 
 
 def mgt_ng_extrapolate_noalloc(iterates, prediction, stream=None):

@@ -1,7 +1,7 @@
 """The FP32 erfc of the formal-solve kernel against scipy (CPU).
 
 The kernel evaluates erfc(|x|) = exp(-x^2) t P(2t - 1), t = 1/(1 + 0.4|x|),
-with the coefficients written in k_fs.cu; here the same coefficients, read
+with the coefficients written in mgt_erfc.cuh; here the same coefficients, read
 from the source, are evaluated in FP32 Horner form and compared with
 scipy.special.erfcx / erfc.
 """
@@ -19,7 +19,7 @@ import fit_erfcx  # noqa: E402
 
 
 def kernel_coefficients():
-    src = open(os.path.join(CSRC, "k_fs.cu")).read()
+    src = open(os.path.join(CSRC, "mgt_erfc.cuh")).read()
     body = src[src.index("__device__ __forceinline__ float erfc_fit(float x)"):]
     body = body[:body.index("return x < 0.0f")]
     vals = [float(v) for v in re.findall(r"([-+]?\d\.\d+e[-+]\d+)f", body)]
