@@ -50,6 +50,12 @@ def parse():
     ap.add_argument("--points", type=int, default=None, help="override the point count (same laws)")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 and CPU-baseline legs")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle origins per CPU sample (0 = auto)")
+    ap.add_argument("--dtau-study", action="store_true",
+                    help="accuracy and cost of the optical-depth rules on a large-velocity-gradient model "
+                         "(paper's switch rule and plain trapezoid against 16x subdivision)")
+    ap.add_argument("--image", action="store_true",
+                    help="time mgt_image and mgt_image_adjoint instead (differentiation workload: 200k-point "
+                         "outflow, 256 x 256 pixels x 100 channels, populations held fixed)")
     return ap.parse_args()
 
 
@@ -393,8 +399,121 @@ def run_mine(args, model, cfg):
         dist.destroy_process_group()
 
 
+def run_image(args):
+    """Synthetic image and its adjoint on the differentiation workload: a
+    200k-point shell outflow (41 levels), 256 x 256 pixels x 100 channels
+    across the J = 2-1 line, populations fixed at LTE (the cost does not depend
+    on their values).  Prints one JSON line."""
+    import torch
+
+    from paper_2411_03040_gb300 import build as B
+    from paper_2411_03040_gb300 import mgt, synth
+    torch.cuda.set_device(0)
+    B.build()
+    mgt.load()
+    n = args.points or 200_000
+    model = synth.shell_model(n, 41, 1, 10, seed=synth.SEED_BASE + 5, name=f"shells-{n}")
+    npx = npy = 256
+    nfreq = 100
+    d = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+    nu = model.lines.freq_Hz[1]
+    lo, hi = nu * (1 - 1e-4), nu * (1 + 1e-4)
+    stream = torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        h = mgt.mgt_model_create(model, stream=stream)
+        a, b = ev(), ev()
+        a.record(stream)
+        _, off, _ = mgt.mgt_image_rays(h, d, npx, npy, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        rays_ms = a.elapsed_time(b)
+        out = torch.empty((nfreq, npy, npx), dtype=torch.float32, device="cuda")
+        g = torch.rand((nfreq, npy, npx), dtype=torch.float32, device="cuda")
+        gT = torch.empty(n, dtype=torch.float64, device="cuda")
+        gn = torch.empty(n, dtype=torch.float64, device="cuda")
+        gv = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        for _ in range(max(1, args.warmup)):
+            mgt.mgt_image(h, d, npx, npy, nfreq, lo, hi, out=out, stream=stream)
+            mgt.mgt_image_adjoint(h, d, npx, npy, nfreq, lo, hi, g, gT, gn, gv, stream=stream)
+        times = {"forward": [], "adjoint": []}
+        for _ in range(args.steps):
+            a, b, c = ev(), ev(), ev()
+            a.record(stream)
+            mgt.mgt_image(h, d, npx, npy, nfreq, lo, hi, out=out, stream=stream)
+            b.record(stream)
+            mgt.mgt_image_adjoint(h, d, npx, npy, nfreq, lo, hi, g, gT, gn, gv, stream=stream)
+            c.record(stream)
+            torch.cuda.synchronize()
+            times["forward"].append(a.elapsed_time(b))
+            times["adjoint"].append(b.elapsed_time(c))
+    units = npx * npy * nfreq
+    segs = int(off[-1]) - npx * npy
+    fwd = float(np.median(times["forward"]))
+    adj = float(np.median(times["adjoint"]))
+    print(json.dumps({
+        "metric": "image pixel-channels/s (mgt_image) and adjoint", "unit": "pixel-channels/s",
+        "value": units / (fwd * 1e-3), "adjoint_value": units / (adj * 1e-3), "forward_ms": fwd, "adjoint_ms": adj,
+        "pixel_rays_ms": rays_ms, "steps": args.steps, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": model.name, "points": n, "levels": 41, "pixels": [npx, npy], "channels": nfreq,
+                   "ray_segments": segs, "segment_channels_per_forward": segs * nfreq}}), flush=True)
+
+
+def run_dtau_study(args):
+    """Sec. 4.3 accuracy study on the workload with large velocity gradients
+    (shell outflow plus a Gaussian random velocity field, sigma 5 km/s,
+    correlation length 0.05), at a reduced point count: J-bar and Lambda* from
+    the paper's switch rule (trapezoid below 0.35 Doppler widths, semi-analytic
+    above) and from the plain trapezoidal rule, against 16x subdivision of
+    every segment; relative-error percentiles and formal-solve times."""
+    import torch
+
+    from paper_2411_03040_gb300 import build as B
+    from paper_2411_03040_gb300 import mgt, synth
+    torch.cuda.set_device(0)
+    B.build()
+    mgt.load()
+    n = args.points or 100_000
+    model = synth.shell_model(n, 41, 2, 40, grf_sigma=5e3, grf_ell=0.05, seed=synth.SEED_BASE + 3,
+                              name=f"shells-grf-{n}")
+    stream = torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    res = {}
+    with torch.cuda.stream(stream):
+        h = mgt.mgt_model_create(model, stream=stream)
+        mgt.mgt_trace_rays(h, stream=stream)
+        for name, kw in (("switch", {}), ("trapezoid", {"switch_threshold": 1e30}), ("subdiv16", {"subdivisions": 16})):
+            mgt.mgt_set_solve_opts(h, **kw)
+            mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED, want=False, stream=stream)
+            a, b = ev(), ev()
+            a.record(stream)
+            mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED, want=False, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            J, L = mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED, stream=stream)
+            res[name] = (a.elapsed_time(b), J, L)
+    ref = res["subdiv16"]
+    out = {"metric": "J-bar / Lambda* relative error against 16x subdivision", "data": "synthetic",
+           "config": {"workload": model.name, "points": n, "rays": int(model.dirs.shape[0]), "lines": 40,
+                      "bins_per_line": 40, "velocity": "outflow + Gaussian random field 5 km/s, l = 0.05"}}
+    for name in ("switch", "trapezoid"):
+        ms, J, L = res[name]
+        eJ = np.abs(J - ref[1]) / np.abs(ref[1])
+        eL = np.abs(L - ref[2]) / np.abs(ref[2])
+        q = lambda e: {p: float(np.percentile(e, p)) for p in (50, 90, 99)} | {"max": float(e.max())}
+        out[name] = {"formal_solve_ms": ms, "Jbar_rel_err": q(eJ), "Lstar_rel_err": q(eL)}
+    out["subdiv16"] = {"formal_solve_ms": ref[0]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.dtau_study:
+        run_dtau_study(args)
+        return
+    if args.image:
+        run_image(args)
+        return
     from paper_2411_03040_gb300 import synth
     model = synth.config_model(args.workload, n_points=args.points)
     cfg = workload_config(model, args.workload)

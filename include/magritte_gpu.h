@@ -107,7 +107,11 @@ typedef struct {
                                  memory (registers capped for two blocks per SM), 3 = staging
                                  with one block per SM; 2 and 3 need one origin to fill a
                                  block (bins x line groups >= 96), else 1 is used */
-    int32_t reserved;         /* must be 0 */
+    int32_t subdivisions;     /* 0 = the switch rule above (default); n = 1..256: every segment's
+                                 optical depth by the trapezoidal rule over n equal pieces with
+                                 chi^{ij}, the width and the comoving offset interpolated linearly
+                                 (the reference of the Sec. 4.3 accuracy study; n = 1 is the plain
+                                 trapezoidal rule) */
 } mgt_solve_opts;
 
 typedef struct {

@@ -75,7 +75,9 @@ def _load():
             lib.oracle_feautrier_at.argtypes = [i64, P, P, f64, f64, i64, P, P]
             lib.oracle_formal_solve.argtypes = [i64, P, P, P, P, f64, i32, P, i32, P, P, P,
                                                 i32, P, P, P, i32, P, P, f64, f64, f64, ctypes.c_int,
-                                                i64, P, P, P]
+                                                ctypes.c_int, i64, P, P, P]
+            lib.oracle_segment_dtau_subdiv.argtypes = [f64] * 7 + [ctypes.c_int]
+            lib.oracle_segment_dtau_subdiv.restype = f64
             lib.oracle_image_weights.argtypes = [f64, P, P, P]
             lib.oracle_image_frame.argtypes = [i64, P, P, i32, i32, P, P, P]
             lib.oracle_image_rays.argtypes = [i64, P, P, P, P, P, i64, P, P, P, P, P, P]
@@ -226,6 +228,10 @@ def segment_dtau(dx, chi0, chi1, dnu0, dnu1, dnubar, off0, off1, thr=0.35):
     return _load().oracle_segment_dtau(dx, chi0, chi1, dnu0, dnu1, dnubar, off0, off1, thr)
 
 
+def segment_dtau_subdiv(dx, chi0, chi1, dnu0, dnu1, off0, off1, n):
+    return _load().oracle_segment_dtau_subdiv(dx, chi0, chi1, dnu0, dnu1, off0, off1, n)
+
+
 def feautrier_at(dtau, S, I_left, I_right, io):
     dtau = np.ascontiguousarray(dtau, np.float64)
     S = np.ascontiguousarray(S, np.float64)
@@ -237,8 +243,10 @@ def feautrier_at(dtau, S, I_left, I_right, io):
 
 
 def formal_solve(model, rays: Rays, chi, S, origins=None, tau_min=1e-150, thr=0.35,
-                 width_mode=0):
-    """J-bar and Lambda* ([n][M], SI) at ``origins`` (default: all points)."""
+                 width_mode=0, subdiv=0):
+    """J-bar and Lambda* ([n][M], SI) at ``origins`` (default: all points).
+    ``subdiv`` > 0 replaces every segment's optical depth by the subdivided
+    trapezoidal rule with that many pieces."""
     lib = _load()
     N = model.n_points
     pairs = direction_pairs(model.dirs)
@@ -254,7 +262,7 @@ def formal_solve(model, rays: Rays, chi, S, origins=None, tau_min=1e-150, thr=0.
     lib.oracle_formal_solve(N, _p(pos), _p(vel), _p(T), _p(vt2), float(model.lines.mol_mass_kg),
                             model.dirs.shape[0], _p(dirs), pairs.shape[0], _p(pr),
                             _p(rays.off), _p(rays.idx), M, _p(nu), _p(chi_), _p(S_),
-                            x.shape[0], _p(x), _p(w), float(model.T_bg), tau_min, thr, width_mode,
+                            x.shape[0], _p(x), _p(w), float(model.T_bg), tau_min, thr, width_mode, int(subdiv),
                             origins.shape[0], _p(origins), _p(J), _p(L))
     return J, L
 

@@ -152,6 +152,25 @@ double oracle_segment_dtau(double dx, double chi0, double chi1, double dnu0, dou
     return dx * 0.5 * (chi0 + chi1) * E / (2.0 * shift);
 }
 
+/* Reference optical depth by subdivision (the accuracy study of Sec. 4.3):   */
+/* the segment is cut into n equal pieces and the trapezoidal rule applied to */
+/* each, with chi^{ij}, the line width and the comoving offset interpolated  */
+/* linearly along the segment.  n = 1 is the plain trapezoidal rule.          */
+double oracle_segment_dtau_subdiv(double dx, double chi0, double chi1, double dnu0, double dnu1, double off0,
+                                  double off1, int n)
+{
+    double sum = 0.0;
+    for (int k = 0; k <= n; ++k) {
+        double x = (double)k / n;
+        double ch = chi0 + x * (chi1 - chi0);
+        double dn = dnu0 + x * (dnu1 - dnu0);
+        double of = off0 + x * (off1 - off0);
+        double wk = (k == 0 || k == n) ? 0.5 : 1.0;
+        sum += wk * ch * profile(of, dn);
+    }
+    return dx / n * sum;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Second-order (Feautrier) two-point system on one ray, solved at point io. */
 /*                                                                           */
@@ -241,7 +260,8 @@ void oracle_feautrier_at(int64_t D, const double *dtau, const double *S,
 /*  - a point c on half-ray h sees the photons travelling toward o at the     */
 /*    comoving frequency nu_q (1 + n_h . (v_c - v_o)/c), so its offset from   */
 /*    line centre is x_q dnu_ij(o) + nu_q n_h . (v_c - v_o)/c;                */
-/*  - segment optical depths follow oracle_segment_dtau, floored at tau_min;  */
+/*  - segment optical depths follow oracle_segment_dtau (or, with subdiv > 0, */
+/*    oracle_segment_dtau_subdiv), floored at tau_min;                        */
 /*  - both ends see the background I_bg = B_nu(T_bg) at nu_q;                 */
 /*  - Jbar  += (2/R) w_q u_o,  Lstar += (2/R) w_q L*_oo  (w_q normalised GH). */
 /* width_mode 0: dnubar from the averaged T and vturb^2; 1: mean of widths.   */
@@ -253,7 +273,7 @@ void oracle_formal_solve(int64_t N, const double *pos, const double *vel, const 
                          const int64_t *ray_off, const int32_t *ray_idx,
                          int32_t M, const double *nu, const double *chi, const double *S,
                          int32_t Q, const double *xq, const double *wq, double T_bg,
-                         double tau_min, double thr, int width_mode,
+                         double tau_min, double thr, int width_mode, int subdiv,
                          int64_t n_orig, const int64_t *orig, double *Jbar, double *Lstar)
 {
     #pragma omp parallel for schedule(dynamic, 1)
@@ -327,8 +347,11 @@ void oracle_formal_solve(int64_t N, const double *pos, const double *vel, const 
                         } else {
                             dnb = 0.5 * (dnu[d] + dnu[d + 1]);
                         }
-                        double t = oracle_segment_dtau(dx[d], chi[(int64_t)m * N + a], chi[(int64_t)m * N + b],
-                                                       dnu[d], dnu[d + 1], dnb, off[d], off[d + 1], thr);
+                        double t = subdiv > 0
+                            ? oracle_segment_dtau_subdiv(dx[d], chi[(int64_t)m * N + a], chi[(int64_t)m * N + b],
+                                                         dnu[d], dnu[d + 1], off[d], off[d + 1], subdiv)
+                            : oracle_segment_dtau(dx[d], chi[(int64_t)m * N + a], chi[(int64_t)m * N + b],
+                                                  dnu[d], dnu[d + 1], dnb, off[d], off[d + 1], thr);
                         dtau[d] = t > tau_min ? t : tau_min;
                     }
                     double u, L;

@@ -586,7 +586,7 @@ mgt_status mgt_set_solve_opts(mgt_model *m, const mgt_solve_opts *o)
     mgt_solve_opts d{0.35, 0, 0, 0, 0};
     if (o) {
         if (o->schedule < 0 || o->schedule > 3) return set_error(MGT_ERR_ARG, "schedule must be 0..3");
-        if (o->reserved != 0) return set_error(MGT_ERR_ARG, "reserved must be 0");
+        if (o->subdivisions < 0 || o->subdivisions > 256) return set_error(MGT_ERR_ARG, "subdivisions must be 0..256");
         if (!(o->switch_threshold >= 0.0) || !std::isfinite(o->switch_threshold))
             return set_error(MGT_ERR_ARG, "switch_threshold must be >= 0");
         if (o->width_mode != 0 && o->width_mode != 1) return set_error(MGT_ERR_ARG, "width_mode must be 0 or 1");

@@ -87,6 +87,7 @@ struct FSArgs {
     const double *vel, *dirs, *w64;
     double thr;
     int width_mode;
+    int subdiv;                // > 0: every segment by the trapezoidal rule over this many pieces
     double *J, *Lst;           // [N][M]
     int *err;
 };
@@ -202,6 +203,27 @@ __device__ __forceinline__ void segment_coefs(bool trap, T dx, T du, T z_f, T g_
         cf = kk * w_f;
         cn = kk * w_n;
     }
+}
+
+// Reference coefficients of the accuracy study (Sec. 4.3): the segment cut
+// into n equal pieces, the trapezoidal rule on each, with the line opacity
+// chi^{ij} = chi~ w (nu sqrt(pi)), the width and the comoving offset
+// interpolated linearly; halved, like segment_coefs.
+template <typename T>
+__device__ __forceinline__ void subdiv_coefs(int n, T dx, T z_f, T w_f, T z_n, T w_n, T &cf, T &cn)
+{
+    T sf = T(0), sn = T(0);
+    const T inv_n = T(1) / T(n);
+    for (int k = 0; k <= n; ++k) {
+        const T x = T(k) * inv_n;
+        const T z = z_f + x * (z_n - z_f), w = w_f + x * (w_n - w_f);
+        const T u = z / w;
+        const T g = Prec<T>::gauss(u) / w * ((k == 0 || k == n) ? T(0.5) : T(1));
+        sf += (T(1) - x) * g;
+        sn += x * g;
+    }
+    cf = T(0.5) * dx * inv_n * w_f * sf;
+    cn = T(0.5) * dx * inv_n * w_n * sn;
 }
 
 // One elimination row for the thread's LPT lines, in the halved variables:
@@ -368,7 +390,10 @@ __device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, 
         bool trap = fabs(du) < thr;
         if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(kSwitchBand) * thr) trap = trapezoid_fp64(a, r, c_f, c_n, xq64, wo64);
         T cf, cn;
-        segment_coefs<T>(trap, sf.dx, du, z_f, g_f, w_f, g_n, w_n, a.width_mode, cf, cn);
+        if (a.subdiv > 0)
+            subdiv_coefs<T>(a.subdiv, sf.dx, z_f, w_f, z_n, w_n, cf, cn);
+        else
+            segment_coefs<T>(trap, sf.dx, du, z_f, g_f, w_f, g_n, w_n, a.width_mode, cf, cn);
         eliminate_row<T, LPT>(cf, cn, chi_f, S_f, chi_n, P, Y, aa);
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
@@ -617,7 +642,10 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
             trap = trapezoid_fp64(a, r, c_f, c_n, a.xq[q], a.w64[o]);
         }
         T cf, cn;
-        segment_coefs<T>(trap, sf.dx, du, z_f, g_f, w_f, g_n, w_n, a.width_mode, cf, cn);
+        if (a.subdiv > 0)
+            subdiv_coefs<T>(a.subdiv, sf.dx, z_f, w_f, z_n, w_n, cf, cn);
+        else
+            segment_coefs<T>(trap, sf.dx, du, z_f, g_f, w_f, g_n, w_n, a.width_mode, cf, cn);
         coef[kk * a.Q + q] = {cf, cn};
     }
 }
@@ -816,6 +844,7 @@ template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_
     a.w64 = m->d_w64;
     a.thr = m->opts.switch_threshold;
     a.width_mode = m->opts.width_mode;
+    a.subdiv = m->opts.subdivisions;
     a.J = m->d_J;
     a.Lst = m->d_Lst;
     a.err = m->d_err;

@@ -39,7 +39,7 @@ class mgt_model_desc(ctypes.Structure):
 
 class mgt_solve_opts(ctypes.Structure):
     _fields_ = [("switch_threshold", _f64), ("width_mode", _i32), ("lines_per_thread", _i32),
-                ("schedule", _i32), ("reserved", _i32)]
+                ("schedule", _i32), ("subdivisions", _i32)]
 
 
 class mgt_trace_stats(ctypes.Structure):
@@ -189,8 +189,9 @@ def mgt_model_sizes(m: Model):
     return dict(n_points=n.value, n_rays=r.value, n_levels=l.value, n_lines=mm.value, n_quad=q.value)
 
 
-def mgt_set_solve_opts(m: Model, switch_threshold=0.35, width_mode=0, lines_per_thread=0, schedule=0):
-    o = mgt_solve_opts(switch_threshold, width_mode, lines_per_thread, schedule, 0)
+def mgt_set_solve_opts(m: Model, switch_threshold=0.35, width_mode=0, lines_per_thread=0, schedule=0,
+                       subdivisions=0):
+    o = mgt_solve_opts(switch_threshold, width_mode, lines_per_thread, schedule, subdivisions)
     _check(load().mgt_set_solve_opts(m.handle, ctypes.byref(o)), "mgt_set_solve_opts")
 
 

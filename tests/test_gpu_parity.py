@@ -296,3 +296,19 @@ def test_full_size_shell_100k_sampled(mgt):
     Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP64)
     assert rel_err(Jg[orig], J) < TOL64
     assert rel_err(Lg[orig], L) < TOL64
+
+
+# ------------------------------------------- subdivision reference (Sec. 4.3 study)
+@pytest.mark.parametrize("prec,tol", [(1, TOL32), (0, TOL64)], ids=["fp32", "fp64"])
+def test_subdivision_reference_mode(mgt, prec, tol):
+    m = synth.shell_model(2500, 5, 1, 7, grf_sigma=5e3, seed=21, name="grf-2500")
+    h = mgt.mgt_model_create(m)
+    mgt.mgt_trace_rays(h)
+    mgt.mgt_set_solve_opts(h, subdivisions=16)
+    J, L = gpu_fields(mgt, h, prec)
+    rays = O.trace(m)
+    pops = O.lte_populations(m.temp, m.n_spec, m.lines.energy_J, m.lines.g)
+    chi, S, _ = O.line_chi_S(pops, m.lines)
+    Jr, Lr = O.formal_solve(m, rays, chi, S, subdiv=16)
+    assert rel_err(J, Jr) < tol
+    assert rel_err(L, Lr) < tol

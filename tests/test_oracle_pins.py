@@ -151,6 +151,24 @@ def test_semi_analytic_vs_fine_subdivision():
     assert abs(trap / fine - 1) > 0.5
 
 
+def test_subdivision_reference_converges_to_the_integral():
+    # the subdivided trapezoid of the study mode: n = 1 is the plain trapezoid,
+    # and it converges at second order to the integral of the linearly
+    # interpolated integrand (Simpson on 100k points as the reference)
+    dnu0, dnu1, chi0, chi1, o0, o1 = 1.0e5, 1.3e5, 1.0, 1.6, -2.0e5, 2.5e5
+    lam = np.linspace(0, 1, 100001)
+    ch = chi0 + lam * (chi1 - chi0)
+    dn = dnu0 + lam * (dnu1 - dnu0)
+    of = o0 + lam * (o1 - o0)
+    fine = integrate.simpson(ch * np.exp(-(of / dn) ** 2) / (dn * math.sqrt(math.pi)), x=lam)
+    t1 = O.segment_dtau_subdiv(1.0, chi0, chi1, dnu0, dnu1, o0, o1, 1)
+    trap = O.segment_dtau(1.0, chi0, chi1, dnu0, dnu1, 0.5 * (dnu0 + dnu1), o0, o1, thr=1e9)
+    assert abs(t1 / trap - 1) < 1e-14
+    errs = [abs(O.segment_dtau_subdiv(1.0, chi0, chi1, dnu0, dnu1, o0, o1, n) / fine - 1) for n in (16, 32, 64)]
+    assert errs[0] < 1e-2
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
 # ----------------------------------------------------- the two-point system
 def _dense_system(dtau, S, Il, Ir):
     D = len(S)
