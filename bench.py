@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3])
     ap.add_argument("--points", type=int, default=None, help="override the point count (same laws)")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 and CPU-baseline legs")
+    ap.add_argument("--pairs-per-batch", type=int, default=None,
+                    help="hold the rays of this many pairs at a time (default: all for workloads 1-2, 8 for 3)")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle origins per CPU sample (0 = auto)")
     ap.add_argument("--dtau-study", action="store_true",
                     help="accuracy and cost of the optical-depth rules on a large-velocity-gradient model "
@@ -269,14 +271,19 @@ def run_mine(args, model, cfg):
     units = model.n_points * (model.dirs.shape[0] // 2) * model.lines.n_lines * model.n_quad
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
+    batch = args.pairs_per_batch if args.pairs_per_batch is not None else (8 if args.workload == 3 else 0)
     with torch.cuda.stream(stream):
         h = mgt.mgt_model_create(model, stream=stream)
+        if batch:
+            mgt.mgt_set_solve_opts(h, pairs_per_batch=batch)
         tst = mgt.mgt_trace_rays(h, stream=stream)
 
         fs_ev = []
 
         def step(record):
-            mgt.mgt_trace_rays(h, stream=stream)
+            # with pair batches the formal solution traces each batch itself
+            if not batch:
+                mgt.mgt_trace_rays(h, stream=stream)
             if record:
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
@@ -310,11 +317,22 @@ def run_mine(args, model, cfg):
         clk = clocks.stop()
         ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
         fs_ms = sum(a.elapsed_time(b) for a, b in fs_ev) / args.steps
+        fs_source = "CUDA events around mgt_formal_solve"
+        if batch:
+            # the batched formal solution includes the trace of each batch:
+            # time the trace of all batches alone and take it off
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mgt.mgt_trace_rays(h, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fs_ms -= a.elapsed_time(b)
+            fs_source = "mgt_formal_solve (pair batches, traces included) minus a separately timed trace of all batches"
         ms = allreduce_max(world, ms)
         value = world * units / (ms * 1e-3)
 
         extras = {}
-        if not args.no_extras and rank == 0:
+        if not args.no_extras and rank == 0 and not batch:
             # FP64 path: one timed solve, and the FP32 vs FP64 difference of J-bar
             J32, L32 = mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED, stream=stream)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -350,13 +368,15 @@ def run_mine(args, model, cfg):
         "peak_source": f"{src} SM clock: issue roof 152 SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz "
                        "(one FP32 or MUFU lane-op per issue slot)",
         "ops_per_launch": OPS_PER_LINE_STEP * line_steps, "line_steps_per_launch": line_steps,
-        "launch_ms": fs_ms, "step_ms": ms, "share_of_step": fs_ms / ms}
+        "launch_ms": fs_ms, "launch_ms_source": fs_source, "step_ms": ms, "share_of_step": fs_ms / ms}
+    if batch:
+        out["config"]["pairs_per_batch"] = batch
     out["gpu_launches"] = launches
     out["clocks"] = clk
     out["trace"] = tst
     out.update(extras)
 
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and rank == 0 and not batch:
         # end to end through the C-ABI with host buffers (pinned), copies inside
         pm = pinned_copy(model)
         pops_host = torch.empty((model.n_points, model.lines.n_levels), dtype=torch.float64,
@@ -383,10 +403,11 @@ def run_mine(args, model, cfg):
                       "ms_per_step": 1e3 * e2e_s,
                       "path": "mgt_model_create from pinned host arrays -> trace -> formal solve -> SE (populations "
                               "to host) -> Ng -> destroy"}
+    if not args.no_extras and rank == 0:
         # the oracle on the host cores, bounded sample
         import oracle as O
         O.build()
-        n = args.cpu_sample or max(8, min(model.n_points, 640))
+        n = args.cpu_sample or max(8, min(model.n_points, 48 if batch else 640))
         u, dt, cores = oracle_sample(model, n, seed=0)
         out["cpu_baseline"] = {"value": u / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{n} random origin points, all {model.dirs.shape[0] // 2} pairs x "

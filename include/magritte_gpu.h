@@ -112,6 +112,11 @@ typedef struct {
                                  chi^{ij}, the width and the comoving offset interpolated linearly
                                  (the reference of the Sec. 4.3 accuracy study; n = 1 is the plain
                                  trapezoidal rule) */
+    int32_t pairs_per_batch;  /* 0 = trace every ray pair once and keep the rays (default);
+                                 B > 0 = hold the rays of at most B pairs at a time: the formal
+                                 solution traces and solves the pairs batch by batch, summing J-bar
+                                 and Lambda* (for models whose rays do not fit in device memory);
+                                 mgt_get_rays is then unavailable */
 } mgt_solve_opts;
 
 typedef struct {

@@ -213,7 +213,7 @@ static mgt_status validate(const mgt_model_desc *d)
 
 static void free_model(mgt_model *m)
 {
-    void *ptrs[] = {m->d_nbr_pos, m->d_ent, m->d_ent_off, m->d_pos_hl, m->d_vel_hl, m->d_dirs32, m->d_order, m->d_pos, m->d_vel, m->d_temp, m->d_vturb2, m->d_ncoll, m->d_nspec, m->d_w64, m->d_w32,
+    void *ptrs[] = {m->d_dir_map, m->d_batch_pairs, m->d_nbr_pos, m->d_ent, m->d_ent_off, m->d_pos_hl, m->d_vel_hl, m->d_dirs32, m->d_order, m->d_pos, m->d_vel, m->d_temp, m->d_vturb2, m->d_ncoll, m->d_nspec, m->d_w64, m->d_w32,
                     m->d_nbr_off, m->d_nbrs, m->d_bnd, m->d_dirs, m->d_pairs, m->d_xq, m->d_wq, m->d_line_tab,
                     m->d_line_ul, m->d_level_tab, m->d_coll_tab, m->d_coll_ul, m->d_entry, m->d_pops,
                     m->d_pops_prev, m->d_line32, m->d_line64, m->d_J, m->d_Lst, m->d_err, m->d_count,
@@ -377,6 +377,8 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
     MGT_TRY(dalloc(&m->d_bnd, N));
     MGT_TRY(dalloc(&m->d_dirs, 3 * (size_t)m->R));
     MGT_TRY(dalloc(&m->d_pairs, m->P));
+    MGT_TRY(dalloc(&m->d_dir_map, (size_t)m->R));
+    MGT_TRY(dalloc(&m->d_batch_pairs, (size_t)m->P));
     MGT_TRY(dalloc(&m->d_xq, m->Q));
     MGT_TRY(dalloc(&m->d_wq, m->Q));
     MGT_TRY(dalloc(&m->d_line_tab, tab.size()));
@@ -518,10 +520,13 @@ __global__ void k_transpose_out(int64_t N, int M, const double *__restrict__ in,
     out[t] = in[o * M + k];
 }
 
+static bool batched(const mgt_model *m) { return m->opts.pairs_per_batch > 0 && m->opts.pairs_per_batch < m->P; }
+
 static mgt_status ensure_steps(mgt_model *m, mgt_precision p, cudaStream_t s)
 {
     if (!m->traced) return set_error(MGT_ERR_STATE, "mgt_trace_rays must be called first");
-    if (m->steps_width_mode != m->opts.width_mode) MGT_TRY(trace_all(m, s));
+    const bool all = m->rays_p0 == 0 && m->rays_np == m->P;
+    if (!all || m->steps_width_mode != m->opts.width_mode) MGT_TRY(trace_all(m, s));
     if (p == MGT_FP64 && (!m->d_steps64 || m->steps64_width_mode != m->opts.width_mode))
         MGT_TRY(build_steps64(m, s));
     return MGT_OK;
@@ -530,9 +535,25 @@ static mgt_status ensure_steps(mgt_model *m, mgt_precision p, cudaStream_t s)
 static mgt_status formal_solve_device(mgt_model *m, mgt_precision p, cudaStream_t s)
 {
     if (p != MGT_FP64 && p != MGT_FP32_MIXED) return set_error(MGT_ERR_ARG, "unknown precision");
+    if (batched(m)) {
+        // rays of at most B pairs at a time: trace, solve, add, next batch
+        if (!m->traced) return set_error(MGT_ERR_STATE, "mgt_trace_rays must be called first");
+        if (m->line_dirty) MGT_TRY(launch_line_data(m, s));
+        const int32_t B = m->opts.pairs_per_batch;
+        for (int32_t p0 = 0; p0 < m->P; p0 += B) {
+            const int32_t np = std::min(B, m->P - p0);
+            if (!(m->rays_p0 == p0 && m->rays_np == np && m->steps_width_mode == m->opts.width_mode))
+                MGT_TRY(trace_range(m, s, p0, np));
+            if (p == MGT_FP64 && (!m->d_steps64 || m->steps64_width_mode != m->opts.width_mode))
+                MGT_TRY(build_steps64(m, s));
+            MGT_TRY(launch_formal_solve(m, p, s, p0 > 0));
+        }
+        m->have_J = true;
+        return MGT_OK;
+    }
     MGT_TRY(ensure_steps(m, p, s));
     if (m->line_dirty) MGT_TRY(launch_line_data(m, s));
-    MGT_TRY(launch_formal_solve(m, p, s));
+    MGT_TRY(launch_formal_solve(m, p, s, false));
     m->have_J = true;
     return MGT_OK;
 }
@@ -583,10 +604,11 @@ mgt_status mgt_model_destroy(mgt_model *m)
 mgt_status mgt_set_solve_opts(mgt_model *m, const mgt_solve_opts *o)
 {
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
-    mgt_solve_opts d{0.35, 0, 0, 0, 0};
+    mgt_solve_opts d{0.35, 0, 0, 0, 0, 0};
     if (o) {
         if (o->schedule < 0 || o->schedule > 3) return set_error(MGT_ERR_ARG, "schedule must be 0..3");
         if (o->subdivisions < 0 || o->subdivisions > 256) return set_error(MGT_ERR_ARG, "subdivisions must be 0..256");
+        if (o->pairs_per_batch < 0) return set_error(MGT_ERR_ARG, "pairs_per_batch must be >= 0");
         if (!(o->switch_threshold >= 0.0) || !std::isfinite(o->switch_threshold))
             return set_error(MGT_ERR_ARG, "switch_threshold must be >= 0");
         if (o->width_mode != 0 && o->width_mode != 1) return set_error(MGT_ERR_ARG, "width_mode must be 0 or 1");
@@ -602,14 +624,20 @@ mgt_status mgt_trace_rays(mgt_model *m, mgt_trace_stats *stats, void *stream)
 {
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    MGT_TRY(trace_all(m, s));
+    mgt_trace_stats st{};
+    const int32_t B = batched(m) ? m->opts.pairs_per_batch : m->P;
+    for (int32_t p0 = 0; p0 < m->P; p0 += B) {
+        MGT_TRY(trace_range(m, s, p0, std::min(B, m->P - p0)));
+        st.total_steps += m->total_steps;
+        st.n_stalls += m->n_stalls;
+        st.max_half_ray = std::max(st.max_half_ray, m->max_half);
+        st.n_fp64_steps += m->n_exact_steps;
+    }
+    st.mean_half_ray = (double)st.total_steps / ((double)m->N * m->R);
+    m->stats = st;
     if (stats) {
         MGT_TRY(check_device_error(m, s));
-        stats->total_steps = m->total_steps;
-        stats->n_stalls = m->n_stalls;
-        stats->max_half_ray = m->max_half;
-        stats->mean_half_ray = (double)m->total_steps / ((double)m->N * m->R);
-        stats->n_fp64_steps = m->n_exact_steps;
+        *stats = st;
     }
     return MGT_OK;
 }
@@ -618,6 +646,8 @@ mgt_status mgt_get_rays(mgt_model *m, int64_t *ray_off, int32_t *idx, void *stre
 {
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
     if (!m->traced) return set_error(MGT_ERR_STATE, "mgt_trace_rays must be called first");
+    if (batched(m)) return set_error(MGT_ERR_STATE, "rays are held one pair batch at a time (pairs_per_batch)");
+    if (!(m->rays_p0 == 0 && m->rays_np == m->P)) MGT_TRY(trace_all(m, (cudaStream_t)stream));
     cudaStream_t s = (cudaStream_t)stream;
     if (ray_off)
         MGT_CUDA(cudaMemcpyAsync(ray_off, m->d_ray_off, sizeof(int64_t) * ((int64_t)m->R * m->N + 1),

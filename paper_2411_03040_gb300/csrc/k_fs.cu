@@ -88,6 +88,8 @@ struct FSArgs {
     double thr;
     int width_mode;
     int subdiv;                // > 0: every segment by the trapezoidal rule over this many pieces
+    const int32_t *dir_map;    // pair directions -> model directions (NULL: the same)
+    int accumulate;            // add to J / Lstar (later pair batches) instead of writing them
     double *J, *Lst;           // [N][M]
     int *err;
 };
@@ -163,7 +165,7 @@ constexpr float kSwitchBand = 2e-4f;
 __device__ __noinline__ bool trapezoid_fp64(const FSArgs &a, int r, int64_t c_far, int64_t c_near, double xq64,
                                             double wo64)
 {
-    const double *n = a.dirs + 3 * r;
+    const double *n = a.dirs + 3 * (a.dir_map ? a.dir_map[r] : r);
     const double *vf = a.vel + 3 * c_far, *vn = a.vel + 3 * c_near;
     const double dbeta = (n[0] * (vf[0] - vn[0]) + n[1] * (vf[1] - vn[1]) + n[2] * (vf[2] - vn[2])) / kC;
     const double wf = a.w64[c_far], wn = a.w64[c_near];
@@ -340,8 +342,14 @@ __device__ __forceinline__ void reduce_out(const FSArgs &a, const double *red, i
             sJ += red[((0 * a.OPB + lo2) * Mb + lb) * a.Q + qq];
             sL += red[((1 * a.OPB + lo2) * Mb + lb) * a.Q + qq];
         }
-        a.J[o2 * a.M + line] = sJ * wdir * a.line_tab[6 * a.Mpad + line];
-        a.Lst[o2 * a.M + line] = sL * wdir;
+        const double vJ = sJ * wdir * a.line_tab[6 * a.Mpad + line], vL = sL * wdir;
+        if (a.accumulate) {
+            a.J[o2 * a.M + line] += vJ;
+            a.Lst[o2 * a.M + line] += vL;
+        } else {
+            a.J[o2 * a.M + line] = vJ;
+            a.Lst[o2 * a.M + line] = vL;
+        }
     }
 }
 
@@ -815,12 +823,13 @@ done:
 
 constexpr int kChunk = 31;
 
-template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_t s, int schedule)
+template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_t s, int schedule, bool accumulate)
 {
     FSArgs a{};
+    const bool all = m->rays_p0 == 0 && m->rays_np == m->P;
     a.N = m->N;
     a.R = m->R;
-    a.P = m->P;
+    a.P = m->rays_np;
     a.Q = m->Q;
     a.M = m->M;
     a.Mpad = m->Mpad;
@@ -830,7 +839,9 @@ template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_
     while (gb > 1 && a.Q * gb > 256) --gb;
     a.Gb = gb;
     a.OPB = (a.Q * a.Gb >= 256) ? 1 : 256 / (a.Q * a.Gb);
-    a.pairs = m->d_pairs;
+    a.pairs = all ? m->d_pairs : m->d_batch_pairs;
+    a.dir_map = all ? nullptr : m->d_dir_map;
+    a.accumulate = accumulate ? 1 : 0;
     a.ray_off = m->d_ray_off;
     a.s32 = m->d_steps32;
     a.s64 = m->d_steps64;
@@ -890,14 +901,14 @@ int fs_lines_per_thread(const mgt_model *m, mgt_precision p)
     return m->M <= 4 ? 4 : 8;
 }
 
-mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s)
+mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s, bool accumulate)
 {
     const int lpt = fs_lines_per_thread(m, p);
     if (m->Mpad % lpt != 0) return set_error(MGT_ERR_STATE, "line padding does not match the schedule");
     // 0: automatic, 1: gather kernel, 2: staged (two blocks per SM), 3: staged (one block per SM)
     const int sch = m->opts.schedule;
-    if (p == MGT_FP64) return launch_typed<double, 4>(m, s, sch);
-    return lpt == 4 ? launch_typed<float, 4>(m, s, sch) : launch_typed<float, 8>(m, s, sch);
+    if (p == MGT_FP64) return launch_typed<double, 4>(m, s, sch, accumulate);
+    return lpt == 4 ? launch_typed<float, 4>(m, s, sch, accumulate) : launch_typed<float, 8>(m, s, sch, accumulate);
 }
 
 }  // namespace mgt

@@ -161,6 +161,7 @@ struct WalkArgs {
     unsigned long long *n_exact;   // steps decided by the FP64 predicates
     int32_t max_row_chunks;   // bound on the 16-entry chunks of one row scan (packed entries / 16 + 2)
     int64_t n_ent;            // packed entries (index bound)
+    const int32_t *dir_map;   // walk direction r -> model direction (NULL: the same); R counts walk directions
 };
 
 __device__ __forceinline__ uint64_t walk_clock_ns()
@@ -369,6 +370,7 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
         live = false;
     }
     const int64_t wi = (int64_t)r * a.N + o;
+    const int rg = (!IMG && a.dir_map) ? a.dir_map[r] : r;   // the model's direction index
     // the walk's frame: origin o and direction r, or for image walks the pixel's
     // reference point and -n / +n (FP64 values are loaded again where needed)
     WalkFrame f;
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
         img_Z0 = dot3_exact(__dsub_rn(q[0], pr[0]), __dsub_rn(q[1], pr[1]), __dsub_rn(q[2], pr[2]), sg * im.n[0],
                             sg * im.n[1], sg * im.n[2]);
     } else {
-        f = make_frame(a, o, r);
+        f = make_frame(a, o, rg);
     }
     // records go to out[0 .. cap): the walk's scratch slot, or its final place
     int64_t cap = K;
@@ -534,9 +536,9 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
                 xo = a.pos[3 * o];
                 yo = a.pos[3 * o + 1];
                 zo = a.pos[3 * o + 2];
-                n0 = a.dirs[3 * r];
-                n1 = a.dirs[3 * r + 1];
-                n2 = a.dirs[3 * r + 2];
+                n0 = a.dirs[3 * rg];
+                n1 = a.dirs[3 * rg + 1];
+                n2 = a.dirs[3 * rg + 2];
             }
             double Zc64 = 0.0;
             if (c != o || IMG) {
@@ -613,7 +615,7 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ 
             const int cnt = flush_full ? 16 : (int)(n & 15);
             const int64_t first = flush_full ? n - 16 : (n & ~(int64_t)15);
             const bool keep = (flush_full || flush_last) && first < cap;
-            write_step_records(a, o, r, prev_last, my_pt, keep ? cnt : 0, vel_hl, w32, inv_Lunit, width_mode,
+            write_step_records(a, o, rg, prev_last, my_pt, keep ? cnt : 0, vel_hl, w32, inv_Lunit, width_mode,
                                out + first, sl);
             if (flush_full) prev_last = nx;
         }
@@ -654,14 +656,16 @@ __global__ void k_walk_compact(int64_t W, const int64_t *__restrict__ ray_off, i
 // traced point lists (one thread per half-ray).
 __global__ void k_steps64(int64_t N, int32_t R, const int64_t *__restrict__ off, const Step32 *__restrict__ s32,
                           const double *__restrict__ pos, const double *__restrict__ vel,
-                          const double *__restrict__ w64, const double *__restrict__ dirs, double inv_Lunit,
-                          int width_mode, Step64 *__restrict__ s64)
+                          const double *__restrict__ w64, const double *__restrict__ dirs,
+                          const int32_t *__restrict__ dir_map, double inv_Lunit, int width_mode,
+                          Step64 *__restrict__ s64)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)R * N) return;
     int r = (int)(t / N);
     int64_t o = t - (int64_t)r * N;
-    double n0 = dirs[3 * r], n1 = dirs[3 * r + 1], n2 = dirs[3 * r + 2];
+    const int rg = dir_map ? dir_map[r] : r;
+    double n0 = dirs[3 * rg], n1 = dirs[3 * rg + 1], n2 = dirs[3 * rg + 2];
     const double vox = vel[3 * o], voy = vel[3 * o + 1], voz = vel[3 * o + 2];
     double px = pos[3 * o], py = pos[3 * o + 1], pz = pos[3 * o + 2];
     double pvx = vox, pvy = voy, pvz = voz, pw = w64[o];
@@ -683,14 +687,34 @@ __global__ void k_steps64(int64_t N, int32_t R, const int64_t *__restrict__ off,
     }
 }
 
-mgt_status trace_all(mgt_model *m, cudaStream_t s)
+mgt_status trace_all(mgt_model *m, cudaStream_t s) { return trace_range(m, s, 0, m->P); }
+
+// Trace the rays of pairs [p0, p0 + np).  All pairs: walk direction = model
+// direction, ray offsets direction-major over all R directions.  A batch:
+// walk directions 2i and 2i+1 are the two directions of pair p0 + i (see
+// d_dir_map, d_batch_pairs), ray offsets over the batch's 2 np directions.
+mgt_status trace_range(mgt_model *m, cudaStream_t s, int32_t p0, int32_t np)
 {
-    const int64_t W = (int64_t)m->R * m->N;
-    WalkArgs a{m->N,        m->R,          m->d_pos,  m->d_nbr_off, m->d_nbrs,   m->d_nbr_pos,
+    const bool all = p0 == 0 && np == m->P;
+    const int32_t Rw = all ? m->R : 2 * np;
+    if (!all) {
+        std::vector<int32_t> map(2 * np);
+        std::vector<int2> bp(np);
+        for (int32_t i = 0; i < np; ++i) {
+            map[2 * i] = m->pairs[2 * (p0 + i)];
+            map[2 * i + 1] = m->pairs[2 * (p0 + i) + 1];
+            bp[i] = make_int2(2 * i, 2 * i + 1);
+        }
+        MGT_CUDA(cudaMemcpyAsync(m->d_dir_map, map.data(), sizeof(int32_t) * map.size(), cudaMemcpyHostToDevice, s));
+        MGT_CUDA(cudaMemcpyAsync(m->d_batch_pairs, bp.data(), sizeof(int2) * bp.size(), cudaMemcpyHostToDevice, s));
+        MGT_CUDA(cudaStreamSynchronize(s));
+    }
+    const int64_t W = (int64_t)Rw * m->N;
+    WalkArgs a{m->N,        Rw,            m->d_pos,  m->d_nbr_off, m->d_nbrs,   m->d_nbr_pos,
                m->pos_scale, m->d_bnd,     m->d_dirs, m->d_ent,     m->d_ent_off, m->d_pos_hl,
                m->d_dirs32,  m->d_order,   m->pos_slack, m->d_count + 2,
-               (int32_t)((m->n_ent + 15) / 16 + 2), m->n_ent};
-    if (!m->d_ray_off) MGT_CUDA(cudaMalloc(&m->d_ray_off, sizeof(int64_t) * (W + 1)));
+               (int32_t)((m->n_ent + 15) / 16 + 2), m->n_ent, all ? nullptr : m->d_dir_map};
+    if (!m->d_ray_off) MGT_CUDA(cudaMalloc(&m->d_ray_off, sizeof(int64_t) * ((int64_t)m->R * m->N + 1)));
     // Scratch slot per walk: K records, a multiple of 16; the longest half-ray
     // of this model's previous trace when there was one (64 otherwise), kept
     // within a third of the free device memory.  Longer walks are redone.
@@ -753,18 +777,15 @@ mgt_status trace_all(mgt_model *m, cudaStream_t s)
     MGT_CUDA(cudaMemcpyAsync(&n_over, d_nover, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     MGT_CUDA(cudaStreamSynchronize(s));
     MGT_TRY_STATUS(check_device_error(m, s));     // a walk that gave up leaves the lengths unusable
-    if (m->d_steps32 && total > m->total_steps) {
+    if (m->d_steps32 && total > m->steps32_cap) {
         MGT_CUDA(cudaFree(m->d_steps32));
         m->d_steps32 = nullptr;
     }
-    if (m->d_steps64) {
-        MGT_CUDA(cudaFree(m->d_steps64));
-        m->d_steps64 = nullptr;
-        m->steps64_width_mode = -1;
-    }
+    m->steps64_width_mode = -1;                // the FP64 geometry describes the previous rays
     if (!m->d_steps32 && total > 0) {
         cudaError_t e = cudaMalloc(&m->d_steps32, sizeof(Step32) * total);
         if (e != cudaSuccess) return set_error(MGT_ERR_OOM, "cannot allocate the ray buffer");
+        m->steps32_cap = total;
     }
     m->total_steps = total;
     m->max_half = (int32_t)mx;
@@ -781,6 +802,8 @@ mgt_status trace_all(mgt_model *m, cudaStream_t s)
         }
     }
     m->steps_width_mode = m->opts.width_mode;
+    m->rays_p0 = p0;
+    m->rays_np = np;
     m->traced = true;
     return MGT_OK;
 }
@@ -788,14 +811,21 @@ mgt_status trace_all(mgt_model *m, cudaStream_t s)
 mgt_status build_steps64(mgt_model *m, cudaStream_t s)
 {
     if (m->total_steps == 0) return MGT_OK;
+    if (m->d_steps64 && m->steps64_cap < m->total_steps) {
+        MGT_CUDA(cudaFree(m->d_steps64));
+        m->d_steps64 = nullptr;
+    }
     if (!m->d_steps64) {
+        m->steps64_cap = m->total_steps;
         cudaError_t e = cudaMalloc(&m->d_steps64, sizeof(Step64) * m->total_steps);
         if (e != cudaSuccess) return set_error(MGT_ERR_OOM, "cannot allocate the FP64 ray geometry");
     }
-    const int64_t W = (int64_t)m->R * m->N;
-    k_steps64<<<ceil_div(W, 128), 128, 0, s>>>(m->N, m->R, m->d_ray_off, m->d_steps32, m->d_pos, m->d_vel,
-                                               m->d_w64, m->d_dirs, 1.0 / m->L_unit, m->opts.width_mode,
-                                               m->d_steps64);
+    const bool all = m->rays_p0 == 0 && m->rays_np == m->P;
+    const int32_t Rw = all ? m->R : 2 * m->rays_np;
+    const int64_t W = (int64_t)Rw * m->N;
+    k_steps64<<<ceil_div(W, 128), 128, 0, s>>>(m->N, Rw, m->d_ray_off, m->d_steps32, m->d_pos, m->d_vel,
+                                               m->d_w64, m->d_dirs, all ? nullptr : m->d_dir_map, 1.0 / m->L_unit,
+                                               m->opts.width_mode, m->d_steps64);
     MGT_LAUNCH_CHECK("k_steps64");
     m->steps64_width_mode = m->opts.width_mode;
     return MGT_OK;
@@ -983,7 +1013,7 @@ mgt_status trace_image(mgt_model *m, const double n[3], int32_t npx, int32_t npy
     WalkArgs a{m->N,        m->R,          m->d_pos,  m->d_nbr_off, m->d_nbrs,   m->d_nbr_pos,
                m->pos_scale, m->d_bnd,     m->d_dirs, m->d_ent,     m->d_ent_off, m->d_pos_hl,
                m->d_dirs32,  m->d_order,   m->pos_slack, m->d_count + 3,
-               (int32_t)((m->n_ent + 15) / 16 + 2), m->n_ent};
+               (int32_t)((m->n_ent + 15) / 16 + 2), m->n_ent, nullptr};
     k_img_anchor<<<ceil_div(npix * 32, 256), 256, 0, s>>>(a, g.d_ref, npix, n[0], n[1], n[2], g.d_anchor);
     MGT_LAUNCH_CHECK("k_img_anchor");
     int64_t *d_lens = nullptr, *d_sizes = nullptr;

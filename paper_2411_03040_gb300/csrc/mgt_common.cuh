@@ -86,7 +86,7 @@ struct mgt_model {
     int32_t R = 0, P = 0, Q = 0, L = 0, M = 0, Mpad = 0, K = 0, n_boundary = 0;
     int64_t nnz = 0;
     double mol_mass = 0, T_bg = 0, L_unit = 1.0;
-    mgt_solve_opts opts{0.35, 0, 0, 0, 0};
+    mgt_solve_opts opts{0.35, 0, 0, 0, 0, 0};
 
     // host copies of the small tables
     std::vector<double> energy, g, A, freq, Kul;
@@ -132,7 +132,12 @@ struct mgt_model {
     int64_t *d_ray_off = nullptr;              // [R*N+1]
     mgt::Step32 *d_steps32 = nullptr;
     mgt::Step64 *d_steps64 = nullptr;
-    int64_t total_steps = 0;
+    int64_t total_steps = 0;                   // steps of the rays currently held
+    int64_t steps32_cap = 0, steps64_cap = 0;  // allocated records
+    int32_t rays_p0 = 0, rays_np = 0;          // pair range whose rays are held (all pairs: 0, P)
+    int32_t *d_dir_map = nullptr;              // [R] walk direction -> model direction of a pair batch
+    int2 *d_batch_pairs = nullptr;             // [P] the batch's pairs in walk directions
+    mgt_trace_stats stats{};                   // of the last mgt_trace_rays over all pairs
     int32_t max_half = 0;
     int64_t n_stalls = 0;
     int64_t n_exact_steps = 0;
@@ -156,6 +161,7 @@ mgt_status launch_widths(mgt_model *m, cudaStream_t s);
 mgt_status launch_lte(mgt_model *m, cudaStream_t s);
 mgt_status launch_line_data(mgt_model *m, cudaStream_t s);
 mgt_status trace_all(mgt_model *m, cudaStream_t s);
+mgt_status trace_range(mgt_model *m, cudaStream_t s, int32_t p0, int32_t np);
 mgt_status build_steps64(mgt_model *m, cudaStream_t s);
 
 mgt_status trace_image(mgt_model *m, const double n[3], int32_t npx, int32_t npy, cudaStream_t s);
@@ -164,7 +170,7 @@ void image_frame(const double *pos, int64_t N, const double n[3], int32_t npx, i
                  double e2[3], std::vector<double> &ref);
 
 // formal solution (k_fs.cu)
-mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s);
+mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s, bool accumulate);
 
 // statistical equilibrium (k_se.cu)
 mgt_status launch_stat_eq(mgt_model *m, cudaStream_t s);

@@ -39,7 +39,7 @@ class mgt_model_desc(ctypes.Structure):
 
 class mgt_solve_opts(ctypes.Structure):
     _fields_ = [("switch_threshold", _f64), ("width_mode", _i32), ("lines_per_thread", _i32),
-                ("schedule", _i32), ("subdivisions", _i32)]
+                ("schedule", _i32), ("subdivisions", _i32), ("pairs_per_batch", _i32)]
 
 
 class mgt_trace_stats(ctypes.Structure):
@@ -190,8 +190,8 @@ def mgt_model_sizes(m: Model):
 
 
 def mgt_set_solve_opts(m: Model, switch_threshold=0.35, width_mode=0, lines_per_thread=0, schedule=0,
-                       subdivisions=0):
-    o = mgt_solve_opts(switch_threshold, width_mode, lines_per_thread, schedule, subdivisions)
+                       subdivisions=0, pairs_per_batch=0):
+    o = mgt_solve_opts(switch_threshold, width_mode, lines_per_thread, schedule, subdivisions, pairs_per_batch)
     _check(load().mgt_set_solve_opts(m.handle, ctypes.byref(o)), "mgt_set_solve_opts")
 
 

@@ -312,3 +312,26 @@ def test_subdivision_reference_mode(mgt, prec, tol):
     Jr, Lr = O.formal_solve(m, rays, chi, S, subdiv=16)
     assert rel_err(J, Jr) < tol
     assert rel_err(L, Lr) < tol
+
+
+# ------------------------------------------------------------- pair batches
+@pytest.mark.parametrize("prec,tol", [(1, TOL32), (0, TOL64)], ids=["fp32", "fp64"])
+def test_pair_batches_match_oracle_and_full_trace(mgt, prec, tol):
+    m = synth.shell_model(2500, 5, 2, 7, grf_sigma=5e3, seed=23, name="grf-2500-48")   # 48 rays, 24 pairs
+    h = mgt.mgt_model_create(m)
+    full = mgt.mgt_trace_rays(h)
+    Jf, Lf = gpu_fields(mgt, h, prec)
+    mgt.mgt_set_solve_opts(h, pairs_per_batch=5)                 # batches of 5, 5, 5, 5, 4 pairs
+    st = mgt.mgt_trace_rays(h)
+    for k in ("total_steps", "n_stalls", "max_half_ray", "n_fp64_steps"):
+        assert st[k] == full[k], k
+    J, L = gpu_fields(mgt, h, prec)
+    with pytest.raises(mgt.MgtError):
+        mgt.mgt_get_rays(h)
+    Jr, Lr = oracle_fields(m, O.trace(m))
+    assert rel_err(J, Jr) < tol and rel_err(L, Lr) < tol
+    assert rel_err(J, Jf) < 1e-5 if prec == 1 else rel_err(J, Jf) < 1e-12
+    # back to all pairs at once
+    mgt.mgt_set_solve_opts(h)
+    J2, _ = gpu_fields(mgt, h, prec)
+    assert np.array_equal(J2, Jf)
