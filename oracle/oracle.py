@@ -567,3 +567,57 @@ def image(model, pops, direction, npx, npy, nfreq, fmin, fmax, thr=0.35, rays=No
                            model.lines.n_lines, _p(arr(model.lines.freq_Hz)), _p(arr(chi)), _p(arr(S)),
                            float(model.T_bg), thr, npix, _p(rays.off), _p(rays.pts), nfreq, _p(nu_f), _p(out))
     return out.reshape(nfreq, npy, npx), rays
+
+
+# --------------------------------------------------------------------------
+# Recursive re-meshing (Sec. 4.1)
+# --------------------------------------------------------------------------
+def box_variation(rho):
+    """Sec. 4.1, eq. subdivision criterion: 2 (rho_max - rho_min) / (rho_max + rho_min)."""
+    rmax, rmin = float(np.max(rho)), float(np.min(rho))
+    return 2.0 * ((rmax - rmin) / (rmax + rmin))
+
+
+def remesh(pos, rho, r_max, max_level, n_side):
+    """Recursive re-meshing of a point cloud with tracer rho (Sec. 4.1).
+
+    Start from the bounding box of all points.  A box whose variation exceeds
+    r_max, below level max_level, is divided into 8 equal boxes (a point goes
+    to the upper half of an axis when its coordinate is >= the midpoint); each
+    non-empty part is cropped to the bounding box of its points and treated
+    the same way.  Every other box becomes one point at its centre.  Then an
+    evenly spaced set of boundary points is added on the surface of the
+    outermost box: the n_side^3 lattice over it, surface nodes only.
+
+    Returns (points [K][3], boundary flags [K], leaves) with leaves a list of
+    (lo, hi, level, member indices), in depth-first order, children in octant
+    order (bit d set for the upper half of axis d).
+    """
+    pos = np.asarray(pos, np.float64)
+    rho = np.asarray(rho, np.float64)
+    leaves = []
+    stack = [(np.arange(pos.shape[0]), 0)]
+    root_lo, root_hi = pos.min(axis=0), pos.max(axis=0)
+    while stack:
+        idx, level = stack.pop()
+        p = pos[idx]
+        lo, hi = p.min(axis=0), p.max(axis=0)
+        if level < max_level and box_variation(rho[idx]) > r_max:
+            mid = (lo + hi) * 0.5
+            octant = ((p[:, 0] >= mid[0]).astype(int) | ((p[:, 1] >= mid[1]).astype(int) << 1)
+                      | ((p[:, 2] >= mid[2]).astype(int) << 2))
+            for o in range(7, -1, -1):          # pushed in reverse: popped in octant order
+                sel = idx[octant == o]
+                if sel.size:
+                    stack.append((sel, level + 1))
+        else:
+            leaves.append((lo, hi, level, idx))
+    inner = np.array([(lo + hi) * 0.5 for lo, hi, _, _ in leaves]).reshape(-1, 3)
+    g = np.arange(n_side)
+    I, J, K = np.meshgrid(g, g, g, indexing="ij")
+    on = (I == 0) | (I == n_side - 1) | (J == 0) | (J == n_side - 1) | (K == 0) | (K == n_side - 1)
+    lat = np.stack([I[on], J[on], K[on]], axis=1).astype(np.float64)
+    bnd = root_lo + lat / (n_side - 1) * (root_hi - root_lo)
+    pts = np.concatenate([inner, bnd], axis=0)
+    flags = np.concatenate([np.zeros(inner.shape[0], np.uint8), np.ones(bnd.shape[0], np.uint8)])
+    return pts, flags, leaves
