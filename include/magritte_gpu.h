@@ -318,6 +318,28 @@ mgt_status mgt_set_point_fields(mgt_model *m, const double *temp, const double *
                                 int on_device, void *stream);
 
 /*
+ * Recursive re-meshing of a point cloud (Sec. 4.1), a pre-processing step
+ * before mgt_model_create.  Starting from the bounding box of all points, a
+ * box whose tracer variation 2 (rho_max - rho_min)/(rho_max + rho_min)
+ * (Sec. 4.1, eq. subdivision criterion) exceeds r_max, below recursion level
+ * max_level, is divided into 8 equal boxes (a point goes to the upper half of
+ * an axis when its coordinate is >= the midpoint) and each non-empty part is
+ * cropped to the bounding box of its points; every other box becomes one
+ * point at its centre.  Then evenly spaced boundary points are added on the
+ * surface of the outermost box: the surface nodes of the n_side^3 lattice
+ * over it (6 n_side^2 - 12 n_side + 8 points).
+ *   pos [N][3], rho [N] > 0: host inputs.
+ *   out_pos [capacity][3], out_boundary [capacity] (may be NULL): host
+ *   outputs, box centres first (level by level), then the boundary points
+ *   (flag 1).  *n_out receives the number of output points; with out_pos NULL
+ *   only that count is computed, and a capacity below it gives MGT_ERR_ARG.
+ * Computed on the GPU in FP64 (box bounds and centres are exact).
+ */
+mgt_status mgt_remesh(int64_t n_points, const double *pos, const double *rho, double r_max, int32_t max_level,
+                      int32_t n_side, double *out_pos, uint8_t *out_boundary, int64_t capacity, int64_t *n_out,
+                      void *stream);
+
+/*
  * Ng extrapolation without any device allocation.  The paper has no
  * counterpart: this is a service for callers that cannot allocate device
  * memory -- an application whose own allocator owns the whole GPU (a pool

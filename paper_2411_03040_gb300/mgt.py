@@ -77,6 +77,7 @@ SIGNATURES = {
     "mgt_image_adjoint": [_P, _P, _i32, _i32, _i32, _f64, _f64, _P, _P, _P, _P, ctypes.c_int, _P],
     "mgt_image_rays": [_P, _P, _i32, _i32, _P, _P, _P, _P],
     "mgt_set_point_fields": [_P, _P, _P, _P, ctypes.c_int, _P],
+    "mgt_remesh": [_i64, _P, _P, _f64, _i32, _i32, _P, _P, _i64, ctypes.POINTER(_i64), _P],
     "mgt_ng_extrapolate_noalloc": [_i32, _P, _i64, _P, _P, ctypes.POINTER(_i64), _P],
     "mgt_sync": [_P, _P],
     "mgt_model_sizes": [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
@@ -323,6 +324,21 @@ def mgt_set_point_fields(m: Model, temp=None, n_spec=None, vel=None, stream=None
         arrs = [None if a is None else np.ascontiguousarray(a, np.float64) for a in arrs]
     _check(load().mgt_set_point_fields(m.handle, *[_ptr(a) for a in arrs], on_dev, _stream(stream)),
            "mgt_set_point_fields")
+
+
+def mgt_remesh(pos, rho, r_max, max_level, n_side, stream=None):
+    """Re-meshed point cloud: (points [K][3], boundary flags [K])."""
+    pos = np.ascontiguousarray(pos, np.float64)
+    rho = np.ascontiguousarray(rho, np.float64)
+    n = pos.shape[0]
+    k = _i64(0)
+    _check(load().mgt_remesh(n, _ptr(pos), _ptr(rho), float(r_max), int(max_level), int(n_side), None, None, 0,
+                             ctypes.byref(k), _stream(stream)), "mgt_remesh")
+    out = np.zeros((k.value, 3), np.float64)
+    flags = np.zeros(k.value, np.uint8)
+    _check(load().mgt_remesh(n, _ptr(pos), _ptr(rho), float(r_max), int(max_level), int(n_side), _ptr(out),
+                             _ptr(flags), k.value, ctypes.byref(k), _stream(stream)), "mgt_remesh")
+    return out, flags
 
 
 def mgt_ng_extrapolate_noalloc(iterates, prediction, stream=None):
