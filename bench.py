@@ -57,6 +57,10 @@ def parse():
                          "(paper's switch rule and plain trapezoid against 16x subdivision)")
     ap.add_argument("--remesh", action="store_true",
                     help="time mgt_remesh (Sec. 4.1) on a 1M-point outflow with r_max = 0.4, l = 12")
+    ap.add_argument("--batch", action="store_true",
+                    help="time ALI iterations of a batch of uneven models (256 spheres, 5k-200k points, 5/11/21/41 "
+                         "levels, 12 or 48 rays, 31 bins) replayed as one CUDA graph per iteration")
+    ap.add_argument("--batch-models", type=int, default=256, help="models in the --batch workload")
     ap.add_argument("--image", action="store_true",
                     help="time mgt_image and mgt_image_adjoint instead (differentiation workload: 200k-point "
                          "outflow, 256 x 256 pixels x 100 channels, populations held fixed)")
@@ -482,6 +486,125 @@ def run_image(args):
                    "ray_segments": segs, "segment_channels_per_forward": segs * nfreq}}), flush=True)
 
 
+def _batch_model(spec):
+    from paper_2411_03040_gb300 import synth
+    return synth.batch_model(spec)
+
+
+def run_batch(args):
+    """ALI iterations of a batch of uneven models through mgt_batch_iterate: per
+    iteration one CUDA-graph replay of {line data, persistent formal solution
+    of every (model, origin, line block), statistical equilibrium of every
+    point} and one adaptive Ng step per model.  Prints one JSON line."""
+    import multiprocessing as mp
+
+    from paper_2411_03040_gb300 import synth
+    specs = synth.batch_specs(args.batch_models, n_max=args.points or 200_000,
+                              n_min=min(5_000, args.points or 5_000))
+    # the models are generated on the host cores before any CUDA call
+    # (spawned workers), largest first
+    t0 = time.perf_counter()
+    order = sorted(range(len(specs)), key=lambda i: -specs[i][0])
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        built = pool.map(_batch_model, [specs[i] for i in order], chunksize=1)
+    models = [None] * len(specs)
+    for i, m in zip(order, built):
+        models[i] = m
+    gen_s = time.perf_counter() - t0
+
+    import torch
+
+    from paper_2411_03040_gb300 import build as B
+    from paper_2411_03040_gb300 import mgt
+    torch.cuda.set_device(0)
+    B.build()
+    mgt.load()
+    stream = torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        hs, steps = [], []
+        t0 = time.perf_counter()
+        for m in models:
+            h = mgt.mgt_model_create(m, stream=stream)
+            steps.append(mgt.mgt_trace_rays(h, stream=stream)["total_steps"])
+            hs.append(h)
+        setup_s = time.perf_counter() - t0
+        # autotuner: lines per thread of the staged schedule per (levels, rays)
+        # class, timed on the class's median-size model
+        classes = {}
+        for i, m in enumerate(models):
+            classes.setdefault((m.lines.n_levels, m.dirs.shape[0]), []).append(i)
+        tuned = {}
+        for key, idx in sorted(classes.items()):
+            idx = sorted(idx, key=lambda i: models[i].n_points)
+            rep = idx[len(idx) // 2]
+            r = mgt.mgt_autotune(hs[rep], mgt.MGT_FP32_MIXED, staged_only=True, reps=2, stream=stream)
+            tuned[f"L{key[0]}-R{key[1]}"] = {"lines_per_thread": r["lines_per_thread"], "model_points":
+                                             models[rep].n_points, "ms": {f"lpt{l}": t for _, l, t in r["tried"]}}
+            for i in idx:
+                mgt.mgt_set_solve_opts(hs[i], lines_per_thread=r["lines_per_thread"], schedule=2)
+        b = mgt.mgt_batch_create(hs, stream=stream)
+        lay = mgt.mgt_batch_get_layout(b)
+
+        def step():
+            mgt.mgt_batch_iterate(b, n_iter=1, ng_mode=mgt.MGT_NG_ADAPTIVE, n_max=8, stream=stream)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        n0 = mgt.mgt_launch_count()
+        times = []
+        for _ in range(args.steps):
+            a, c = ev(), ev()
+            a.record(stream)
+            step()
+            c.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(c))
+        launches = mgt.mgt_launch_count() - n0
+        clk = clocks.stop()
+        # the formal solution alone (line data + persistent kernel), for the roofline
+        fs_times = []
+        for _ in range(max(2, args.steps)):
+            a, c = ev(), ev()
+            a.record(stream)
+            mgt.mgt_batch_formal_solve(b, stream=stream)
+            c.record(stream)
+            torch.cuda.synchronize()
+            fs_times.append(a.elapsed_time(c))
+    ms = float(np.mean(times))
+    fs_ms = float(np.mean(fs_times))
+    units = sum(m.n_points * (m.dirs.shape[0] // 2) * m.lines.n_lines * m.n_quad for m in models)
+    line_steps = sum(st * m.lines.n_lines * m.n_quad for st, m in zip(steps, models))
+    pk, src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    achieved = OPS_PER_LINE_STEP * line_steps / (fs_ms * 1e-3) / 1e12
+    peak = 152 * 4 * 32 * sm_max * 1e6 / 1e12
+    npts = np.array([m.n_points for m in models])
+    print(json.dumps({
+        "metric": "point·ray·freq formal solutions/s (J̄+Λ*), batch of uneven models, one ALI iteration per step",
+        "unit": UNIT, "value": units / (ms * 1e-3), "ms_per_step": ms, "steps": args.steps,
+        "warmup": max(3, args.warmup), "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch of {len(models)} sphere models", "models": len(models),
+                   "points_total": int(npts.sum()), "points_min": int(npts.min()), "points_max": int(npts.max()),
+                   "levels": sorted({int(m.lines.n_levels) for m in models}),
+                   "rays": sorted({int(m.dirs.shape[0]) for m in models}), "bins_per_line": int(models[0].n_quad),
+                   "traced_steps": int(sum(steps)), "formal_solutions_per_step": int(units),
+                   "l2": "inputs larger than L2 (ray records of all models)"},
+        "batch_layout": {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in lay.items() if k != "order"},
+        "autotune": tuned,
+        "roofline": {"bound": "alu", "kernel": "k_fs_batch<float,31> (persistent, all models)",
+                     "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"{src} SM clock: issue roof 152 SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz",
+                     "line_steps_per_launch": line_steps, "launch_ms": fs_ms,
+                     "launch_ms_source": "CUDA events around mgt_batch_formal_solve (line data + formal solution)",
+                     "share_of_step": fs_ms / ms},
+        "gpu_launches": launches, "clocks": clk,
+        "host_setup_s": {"generate": gen_s, "create_and_trace": setup_s}}), flush=True)
+
+
 def run_dtau_study(args):
     """Sec. 4.3 accuracy study on the workload with large velocity gradients
     (shell outflow plus a Gaussian random velocity field, sigma 5 km/s,
@@ -573,6 +696,9 @@ def main():
         return
     if args.image:
         run_image(args)
+        return
+    if args.batch:
+        run_batch(args)
         return
     from paper_2411_03040_gb300 import synth
     model = synth.config_model(args.workload, n_points=args.points)

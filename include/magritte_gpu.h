@@ -102,11 +102,11 @@ typedef struct {
     int32_t width_mode;       /* dnu_bar of a segment: 0 = from the averaged temperature
                                  and turbulence (default), 1 = mean of the endpoint widths */
     int32_t lines_per_thread; /* FP32 kernel schedule: 0 = auto, else 4 or 8 */
-    int32_t schedule;         /* formal-solve kernel: 0 = auto, 1 = per-thread gathers from
-                                 global memory, 2 = bulk-copy staging of ray chunks in shared
-                                 memory (registers capped for two blocks per SM), 3 = staging
-                                 with one block per SM; 2 and 3 need one origin to fill a
-                                 block (bins x line groups >= 96), else 1 is used */
+    int32_t schedule;         /* formal-solve kernel: 0 = auto (2 when one origin's bins x
+                                 line groups fill at least 96 threads, else 1), 1 = per-thread
+                                 gathers from global memory, 2 = bulk-copy staging of ray chunks
+                                 in shared memory (registers capped for two blocks per SM),
+                                 3 = staging with one block per SM */
     int32_t subdivisions;     /* 0 = the switch rule above (default); n = 1..256: every segment's
                                  optical depth by the trapezoidal rule over n equal pieces with
                                  chi^{ij}, the width and the comoving offset interpolated linearly
@@ -210,6 +210,14 @@ mgt_status mgt_get_populations(mgt_model *m, double *pops, int on_device, void *
  */
 mgt_status mgt_formal_solve(mgt_model *m, mgt_precision p, double *Jbar, double *Lstar,
                             int on_device, void *stream);
+
+/*
+ * The model's J-bar and Lambda* of its last formal solution (mgt_formal_solve
+ * or a batched one), without solving again: [M][N] f64 each, host or device
+ * as on_device says, either may be NULL.  MGT_ERR_STATE before any formal
+ * solution.  Synchronises the stream for host outputs.
+ */
+mgt_status mgt_get_jbar(mgt_model *m, double *Jbar, double *Lstar, int on_device, void *stream);
 
 /*
  * Statistical equilibrium (Listing 3, compute_level_populations; the paper's
@@ -373,6 +381,86 @@ mgt_status mgt_remesh(int64_t n_points, const double *pos, const double *rho, do
 #define MGT_NG_NOALLOC_SCRATCH_BYTES 157952
 mgt_status mgt_ng_extrapolate_noalloc(int32_t n_iterates, const double *iterates, int64_t len,
                                       double *prediction, double *coef, int64_t *n_negative, void *stream);
+
+/*
+ * Schedule autotuner.  Times the formal solution of model m in precision p
+ * with every candidate (schedule, lines_per_thread) -- schedules 1, 2, 3 (only
+ * 2, the schedule of batched launches, when staged_only != 0) times 4 or 8
+ * lines per thread (FP32-mixed; 4 only in FP64) -- as the median of `reps`
+ * (1..100) launches after one warm-up, with CUDA events on `stream`, and sets
+ * the fastest in the model's options.  Needs mgt_trace_rays and every ray
+ * pair resident (pairs_per_batch = 0); overwrites the model's J-bar and
+ * Lambda*.  `res` (host, may be NULL) receives the choice and the timings.
+ * Synchronises the stream.
+ */
+typedef struct {
+    int32_t schedule;          /* chosen schedule (also set in the model's options) */
+    int32_t lines_per_thread;  /* chosen lines per thread (likewise) */
+    int32_t n_tried;           /* candidates timed */
+    int32_t schedules[8];      /* candidate i: schedule */
+    int32_t lines[8];          /* candidate i: lines per thread */
+    float ms[8];               /* candidate i: median time of one formal solution, ms */
+} mgt_autotune_result;
+mgt_status mgt_autotune(mgt_model *m, mgt_precision p, int32_t staged_only, int32_t reps, mgt_autotune_result *res,
+                        void *stream);
+
+/*
+ * Batches: the per-iteration work of many models (uneven point, level and ray
+ * counts) in single launches.  The paper solves one model at a time; a batch
+ * keeps the GPU full with models too small to fill it alone.
+ *
+ * mgt_batch_create borrows n_models (1..65536) distinct models (host array
+ * of handles, copied): they must stay alive and on the current device while
+ * the batch is used, be traced (mgt_trace_rays) and hold every ray pair
+ * (pairs_per_batch = 0); otherwise MGT_ERR_STATE / MGT_ERR_ARG and *out stays
+ * NULL.  Limits: bins x line groups of one origin <= 256 threads, and the
+ * statistical-equilibrium workspace of 4 points (8 (L^2 + 3L + 2 Mpad) bytes
+ * each) within 227 KB.  Each model's lines_per_thread option (4 or 8, 0 = the
+ * automatic choice; e.g. set by mgt_autotune with staged_only) picks its
+ * schedule inside the batched formal solution; schedule and precision options
+ * do not apply (batched solutions are FP32-mixed with the staged schedule).
+ * Options, rays or populations of a model may change between batch calls:
+ * every call rebuilds the batch's argument tables and uploads them when they
+ * changed.
+ *
+ * mgt_batch_formal_solve: line data of every model from its current
+ * populations, then J-bar and Lambda* of every model (the values of
+ * mgt_formal_solve in FP32-mixed with schedule 2 and the model's lines per
+ * thread) in one persistent launch: CTAs take (model, origin, line block)
+ * items from a counter; models with the most work per item come first.
+ * mgt_batch_stat_equilibrium: the statistical equilibrium of every point of
+ * every model in one launch (the values of mgt_stat_equilibrium).
+ * mgt_batch_iterate: n_iter ALI iterations of every model.  The first call
+ * captures {line data, formal solution, statistical equilibrium} in a CUDA
+ * graph, and each iteration replays it; then, when ng->mode != MGT_NG_NONE or
+ * stats is not NULL, each model takes its Ng step as mgt_ng_accelerate would
+ * (synchronising the stream once per model).  ng (host) may be NULL (no Ng);
+ * stats (host, [n_models] in the caller's order) may be NULL.  The results
+ * equal those of mgt_ali_solve per model with FP32-mixed precision and
+ * schedule 2.  Returns
+ * MGT_ERR_NOT_CONVERGED when a model's populations became non-finite.
+ * All three are stream-ordered; device errors surface as for the models.
+ */
+typedef struct mgt_batch mgt_batch;
+typedef struct {
+    int32_t n_models;
+    int64_t fs_items;          /* (model, origin, line block) items of the formal solution */
+    int32_t fs_grid;           /* CTAs of the persistent formal-solution launch */
+    int32_t fs_threads;        /* threads per CTA (largest over the models) */
+    int64_t fs_smem_bytes;     /* dynamic shared memory per CTA */
+    int64_t se_blocks;         /* CTAs of the statistical-equilibrium launch */
+    int32_t graph_kernels;     /* kernels per replay of the captured iteration (0 before the
+                                  first mgt_batch_iterate) */
+} mgt_batch_layout;
+mgt_status mgt_batch_create(mgt_batch **out, mgt_model *const *models, int32_t n_models, void *stream);
+mgt_status mgt_batch_destroy(mgt_batch *b);
+mgt_status mgt_batch_formal_solve(mgt_batch *b, void *stream);
+mgt_status mgt_batch_stat_equilibrium(mgt_batch *b, void *stream);
+mgt_status mgt_batch_iterate(mgt_batch *b, int32_t n_iter, const mgt_ng_opts *ng, mgt_ali_stats *stats,
+                             void *stream);
+/* Launch layout, and (order, host [n_models], may be NULL) the caller's index
+ * of each model in launch order. */
+mgt_status mgt_batch_get_layout(const mgt_batch *b, mgt_batch_layout *layout, int32_t *order);
 
 /* Wait for the model's work on `stream` and report any device-side error. */
 mgt_status mgt_sync(mgt_model *m, void *stream);

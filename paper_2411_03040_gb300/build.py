@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmgt.so")
-SOURCES = ["api.cu", "k_geom.cu", "k_fs.cu", "k_se.cu", "k_ng.cu", "k_ng_noalloc.cu", "k_image.cu", "k_remesh.cu"]
+SOURCES = ["api.cu", "k_geom.cu", "k_fs.cu", "k_se.cu", "k_ng.cu", "k_ng_noalloc.cu", "k_image.cu", "k_remesh.cu",
+           "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code without multiply-add contraction: the image frame must round like
 # its definition (the same expressions as the oracle's)

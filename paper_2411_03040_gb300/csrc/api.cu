@@ -17,6 +17,7 @@ static thread_local std::string g_last_error;
 static std::atomic<long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 mgt_status set_error(mgt_status s, const std::string &msg)
 {
@@ -522,7 +523,7 @@ __global__ void k_transpose_out(int64_t N, int M, const double *__restrict__ in,
 
 static bool batched(const mgt_model *m) { return m->opts.pairs_per_batch > 0 && m->opts.pairs_per_batch < m->P; }
 
-static mgt_status ensure_steps(mgt_model *m, mgt_precision p, cudaStream_t s)
+mgt_status ensure_rays(mgt_model *m, mgt_precision p, cudaStream_t s)
 {
     if (!m->traced) return set_error(MGT_ERR_STATE, "mgt_trace_rays must be called first");
     const bool all = m->rays_p0 == 0 && m->rays_np == m->P;
@@ -551,7 +552,7 @@ static mgt_status formal_solve_device(mgt_model *m, mgt_precision p, cudaStream_
         m->have_J = true;
         return MGT_OK;
     }
-    MGT_TRY(ensure_steps(m, p, s));
+    MGT_TRY(ensure_rays(m, p, s));
     if (m->line_dirty) MGT_TRY(launch_line_data(m, s));
     MGT_TRY(launch_formal_solve(m, p, s, false));
     m->have_J = true;
@@ -689,11 +690,8 @@ mgt_status mgt_get_populations(mgt_model *m, double *pops, int on_device, void *
     return check_device_error(m, s);
 }
 
-mgt_status mgt_formal_solve(mgt_model *m, mgt_precision p, double *Jbar, double *Lstar, int on_device, void *stream)
+static mgt_status copy_out_jbar(mgt_model *m, double *Jbar, double *Lstar, int on_device, cudaStream_t s)
 {
-    if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
-    cudaStream_t s = (cudaStream_t)stream;
-    MGT_TRY(formal_solve_device(m, p, s));
     if (!Jbar && !Lstar) return MGT_OK;
     const int64_t n = m->N * m->M;
     double *tmp = nullptr;
@@ -712,6 +710,21 @@ mgt_status mgt_formal_solve(mgt_model *m, mgt_precision p, double *Jbar, double 
         return check_device_error(m, s);
     }
     return MGT_OK;
+}
+
+mgt_status mgt_formal_solve(mgt_model *m, mgt_precision p, double *Jbar, double *Lstar, int on_device, void *stream)
+{
+    if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    MGT_TRY(formal_solve_device(m, p, s));
+    return copy_out_jbar(m, Jbar, Lstar, on_device, s);
+}
+
+mgt_status mgt_get_jbar(mgt_model *m, double *Jbar, double *Lstar, int on_device, void *stream)
+{
+    if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
+    if (!m->have_J) return set_error(MGT_ERR_STATE, "no formal solution yet");
+    return copy_out_jbar(m, Jbar, Lstar, on_device, (cudaStream_t)stream);
 }
 
 mgt_status mgt_stat_equilibrium(mgt_model *m, double *pops_out, void *stream)

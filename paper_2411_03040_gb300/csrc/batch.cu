@@ -1,0 +1,388 @@
+// Batches of models (mgt_batch_*) and the schedule autotuner (mgt_autotune).
+//
+// A batch runs the per-iteration work of many models as three launches:
+// line data of every point of every model, the formal solution of every
+// (model, origin, line block) item in one persistent kernel (items taken from
+// a global counter, models ordered from the most to the least work per item
+// so that the short items fill the tail), and the statistical equilibrium of
+// every point with per-model level counts.  mgt_batch_iterate captures the
+// three launches once in a CUDA graph and replays it per iteration.
+//
+// Each launch reads its per-model arguments from a device table.  The tables
+// are rebuilt from the models before every batch call; when a model changed
+// (new rays, new options) they are uploaded again and the graph is dropped.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "mgt_common.cuh"
+
+struct mgt_batch {
+    int device = 0;
+    std::vector<mgt_model *> models;       // in the caller's order
+    std::vector<int32_t> order;            // table slot -> caller index (most work per item first)
+    // host copies of the argument tables, in table order
+    std::vector<unsigned char> fs_args, se_args, ld_args;
+    std::vector<int64_t> fs_end, se_end, ld_end;
+    int fs_threads = 0, fs_grid = 0;
+    size_t fs_smem = 0, se_smem = 0;
+    // device copies
+    unsigned char *d_fs_args = nullptr, *d_se_args = nullptr, *d_ld_args = nullptr;
+    int64_t *d_fs_end = nullptr, *d_se_end = nullptr, *d_ld_end = nullptr;
+    unsigned long long *d_next = nullptr;
+    // the captured iteration
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_kernels = 0;
+};
+
+namespace mgt {
+
+namespace {
+
+void drop_graph(mgt_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+void free_batch(mgt_batch *b)
+{
+    drop_graph(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (void *p : {(void *)b->d_fs_args, (void *)b->d_se_args, (void *)b->d_ld_args, (void *)b->d_fs_end,
+                    (void *)b->d_se_end, (void *)b->d_ld_end, (void *)b->d_next})
+        if (p) cudaFree(p);
+    delete b;
+}
+
+template <typename X> mgt_status upload(X **d, const std::vector<X> &h, size_t cap_elems, cudaStream_t s)
+{
+    if (!*d) MGT_CUDA(cudaMalloc(d, sizeof(X) * cap_elems));
+    MGT_CUDA(cudaMemcpyAsync(*d, h.data(), sizeof(X) * h.size(), cudaMemcpyHostToDevice, s));
+    return MGT_OK;
+}
+
+// Work of one formal-solution item of model m (for the ordering only).
+double item_cost(const mgt_model *m)
+{
+    const double steps_per_origin = (double)m->total_steps / (double)m->N;
+    return steps_per_origin * m->Q * std::min<int32_t>(m->M, 40);
+}
+
+// Rebuild the argument tables from the models; upload them (and drop the
+// graph) when anything changed.
+mgt_status refresh(mgt_batch *b, cudaStream_t s)
+{
+    const int n = (int)b->models.size();
+    for (mgt_model *m : b->models) MGT_TRY_STATUS(ensure_rays(m, MGT_FP32_MIXED, s));
+    // order: most work per item first, ties by caller index
+    std::vector<double> cost(n);
+    for (int i = 0; i < n; ++i) cost[i] = item_cost(b->models[i]);
+    std::vector<int32_t> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+
+    const size_t fsz = fs_args_bytes(), ssz = se_args_bytes(), lsz = ld_args_bytes();
+    std::vector<unsigned char> fa(fsz * n), sa(ssz * n), la(lsz * n);
+    std::vector<int64_t> fe(n), se(n), le(n);
+    int threads = 32;
+    size_t se_smem = 0;
+    int64_t fi = 0, si = 0, li = 0;
+    for (int k = 0; k < n; ++k) {
+        const mgt_model *m = b->models[order[k]];
+        int bd = 0;
+        int64_t items = 0, sblocks = 0, lblocks = 0;
+        size_t ssm = 0;
+        MGT_TRY_STATUS(fs_batch_args(m, fa.data() + k * fsz, &bd, &items));
+        MGT_TRY_STATUS(se_batch_args(m, sa.data() + k * ssz, &sblocks, &ssm));
+        MGT_TRY_STATUS(ld_batch_args(m, la.data() + k * lsz, &lblocks));
+        threads = std::max(threads, bd);
+        se_smem = std::max(se_smem, ssm);
+        fe[k] = (fi += items);
+        se[k] = (si += sblocks);
+        le[k] = (li += lblocks);
+    }
+    if (li > 0x7fffffffLL || si > 0x7fffffffLL)
+        return set_error(MGT_ERR_ARG, "batch: too many points for one launch");
+    size_t fs_smem = 0;
+    for (int k = 0; k < n; ++k) fs_smem = std::max(fs_smem, fs_batch_smem(fa.data() + k * fsz, threads));
+    if (fs_smem > 227 * 1024) return set_error(MGT_ERR_ARG, "batch: formal-solution shared memory above 227 KB");
+
+    const bool same = order == b->order && fa == b->fs_args && sa == b->se_args && la == b->ld_args &&
+                      threads == b->fs_threads && fs_smem == b->fs_smem && se_smem == b->se_smem;
+    if (same && b->d_next) return MGT_OK;
+    drop_graph(b);
+    b->order = order;
+    b->fs_args = fa;
+    b->se_args = sa;
+    b->ld_args = la;
+    b->fs_end = fe;
+    b->se_end = se;
+    b->ld_end = le;
+    b->fs_threads = threads;
+    b->fs_smem = fs_smem;
+    b->se_smem = se_smem;
+    MGT_TRY_STATUS(fs_batch_grid(threads, fs_smem, &b->fs_grid));
+    MGT_TRY_STATUS(se_batch_prepare(se_smem));
+    MGT_TRY_STATUS(upload(&b->d_fs_args, fa, fa.size(), s));
+    MGT_TRY_STATUS(upload(&b->d_se_args, sa, sa.size(), s));
+    MGT_TRY_STATUS(upload(&b->d_ld_args, la, la.size(), s));
+    MGT_TRY_STATUS(upload(&b->d_fs_end, fe, n, s));
+    MGT_TRY_STATUS(upload(&b->d_se_end, se, n, s));
+    MGT_TRY_STATUS(upload(&b->d_ld_end, le, n, s));
+    if (!b->d_next) MGT_CUDA(cudaMalloc(&b->d_next, sizeof(unsigned long long)));
+    // the host vectors must outlive the copies
+    MGT_CUDA(cudaStreamSynchronize(s));
+    return MGT_OK;
+}
+
+mgt_status launch_fs(mgt_batch *b, cudaStream_t s)
+{
+    const int n = (int)b->models.size();
+    MGT_TRY_STATUS(ld_batch_launch(b->d_ld_args, b->d_ld_end, n, b->ld_end.back(), s));
+    return fs_batch_launch(b->d_fs_args, b->d_fs_end, n, b->fs_end.back(), b->d_next, b->fs_threads, b->fs_smem,
+                           b->fs_grid, s);
+}
+
+mgt_status launch_se(mgt_batch *b, cudaStream_t s)
+{
+    return se_batch_launch(b->d_se_args, b->d_se_end, (int)b->models.size(), b->se_end.back(), b->se_smem, s);
+}
+
+mgt_status capture(mgt_batch *b)
+{
+    if (b->exec) return MGT_OK;
+    int64_t before = 0, after = 0;
+    mgt_launch_count(&before);
+    MGT_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    mgt_status st = launch_fs(b, b->cap);
+    if (st == MGT_OK) st = launch_se(b, b->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    mgt_launch_count(&after);
+    note_launches(before - after);          // nothing ran yet; replays are counted
+    if (st != MGT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+    b->graph = g;
+    b->graph_kernels = (int)(after - before);
+    MGT_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+    return MGT_OK;
+}
+
+void mark_solved(mgt_batch *b)
+{
+    for (mgt_model *m : b->models) {
+        m->have_J = true;
+        m->line_dirty = false;
+    }
+}
+
+void mark_se(mgt_batch *b)
+{
+    for (mgt_model *m : b->models) m->line_dirty = true;
+}
+
+}  // namespace
+
+}  // namespace mgt
+
+using namespace mgt;
+
+extern "C" {
+
+mgt_status mgt_batch_create(mgt_batch **out, mgt_model *const *models, int32_t n_models, void *stream)
+{
+    if (!out) return set_error(MGT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!models || n_models < 1 || n_models > 65536) return set_error(MGT_ERR_ARG, "n_models must be 1..65536");
+    std::vector<mgt_model *> ms(models, models + n_models);
+    for (mgt_model *m : ms)
+        if (!m) return set_error(MGT_ERR_ARG, "a model is NULL");
+    {
+        std::vector<mgt_model *> u(ms);
+        std::sort(u.begin(), u.end());
+        if (std::adjacent_find(u.begin(), u.end()) != u.end())
+            return set_error(MGT_ERR_ARG, "a model appears twice in the batch");
+    }
+    int dev = 0;
+    MGT_CUDA(cudaGetDevice(&dev));
+    for (mgt_model *m : ms) {
+        if (m->device != dev) return set_error(MGT_ERR_ARG, "the models of a batch must live on the current device");
+        if (!m->traced) return set_error(MGT_ERR_STATE, "mgt_trace_rays must be called on every model first");
+        if (m->opts.pairs_per_batch > 0 && m->opts.pairs_per_batch < m->P)
+            return set_error(MGT_ERR_ARG, "a batch needs every model's rays resident (pairs_per_batch = 0)");
+    }
+    mgt_batch *b = new mgt_batch;
+    b->device = dev;
+    b->models = ms;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return cuda_status(e, "cudaStreamCreateWithFlags");
+    }
+    const mgt_status st = refresh(b, s);
+    if (st != MGT_OK) {
+        free_batch(b);
+        return st;
+    }
+    *out = b;
+    return MGT_OK;
+}
+
+mgt_status mgt_batch_destroy(mgt_batch *b)
+{
+    if (!b) return MGT_OK;
+    cudaDeviceSynchronize();
+    free_batch(b);
+    return MGT_OK;
+}
+
+mgt_status mgt_batch_formal_solve(mgt_batch *b, void *stream)
+{
+    if (!b) return set_error(MGT_ERR_ARG, "batch is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MGT_TRY_STATUS(refresh(b, s));
+    MGT_TRY_STATUS(launch_fs(b, s));
+    mark_solved(b);
+    return MGT_OK;
+}
+
+mgt_status mgt_batch_stat_equilibrium(mgt_batch *b, void *stream)
+{
+    if (!b) return set_error(MGT_ERR_ARG, "batch is NULL");
+    for (mgt_model *m : b->models)
+        if (!m->have_J) return set_error(MGT_ERR_STATE, "mgt_batch_formal_solve must be called first");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MGT_TRY_STATUS(refresh(b, s));
+    MGT_TRY_STATUS(launch_se(b, s));
+    mark_se(b);
+    return MGT_OK;
+}
+
+mgt_status mgt_batch_iterate(mgt_batch *b, int32_t n_iter, const mgt_ng_opts *ng, mgt_ali_stats *stats,
+                             void *stream)
+{
+    if (!b) return set_error(MGT_ERR_ARG, "batch is NULL");
+    if (n_iter < 0) return set_error(MGT_ERR_ARG, "n_iter must be >= 0");
+    const int n = (int)b->models.size();
+    const mgt_ng_opts no_ng{MGT_NG_NONE, 4, 8};
+    const mgt_ng_opts &o = ng ? *ng : no_ng;
+    if (o.mode < MGT_NG_NONE || o.mode > MGT_NG_ADAPTIVE) return set_error(MGT_ERR_ARG, "unknown Ng mode");
+    if (o.mode == MGT_NG_CLASSICAL && (o.n_steps < 2 || o.n_steps > kMaxNgHist - 1))
+        return set_error(MGT_ERR_ARG, "n_steps must be 2..15");
+    if (o.mode == MGT_NG_ADAPTIVE && (o.n_max < 3 || o.n_max > kMaxNgHist))
+        return set_error(MGT_ERR_ARG, "n_max must be 3..16");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (stats)
+        for (int i = 0; i < n; ++i) stats[i] = {0, 0, 0.0};
+    MGT_TRY_STATUS(refresh(b, s));
+    MGT_TRY_STATUS(capture(b));
+    for (int it = 0; it < n_iter; ++it) {
+        MGT_CUDA(cudaGraphLaunch(b->exec, s));
+        note_launches(b->graph_kernels);
+        mark_solved(b);
+        mark_se(b);
+        if (o.mode == MGT_NG_NONE && !stats) continue;
+        for (int i = 0; i < n; ++i) {
+            int acc = 0;
+            double mr = 0.0;
+            MGT_TRY_STATUS(ng_step(b->models[i], &o, &acc, &mr, s));
+            if (stats) {
+                stats[i].iterations = it + 1;
+                stats[i].ng_accepted += acc;
+                stats[i].last_maxrel = mr;
+            }
+            if (!std::isfinite(mr)) return set_error(MGT_ERR_NOT_CONVERGED, "populations became non-finite");
+        }
+    }
+    for (mgt_model *m : b->models) MGT_TRY_STATUS(check_device_error(m, s));
+    return MGT_OK;
+}
+
+mgt_status mgt_batch_get_layout(const mgt_batch *b, mgt_batch_layout *layout, int32_t *order)
+{
+    if (!b) return set_error(MGT_ERR_ARG, "batch is NULL");
+    if (layout) {
+        layout->n_models = (int32_t)b->models.size();
+        layout->fs_items = b->fs_end.empty() ? 0 : b->fs_end.back();
+        layout->fs_grid = b->fs_grid;
+        layout->fs_threads = b->fs_threads;
+        layout->fs_smem_bytes = (int64_t)b->fs_smem;
+        layout->se_blocks = b->se_end.empty() ? 0 : b->se_end.back();
+        layout->graph_kernels = b->graph_kernels;
+    }
+    if (order) std::copy(b->order.begin(), b->order.end(), order);
+    return MGT_OK;
+}
+
+mgt_status mgt_autotune(mgt_model *m, mgt_precision p, int32_t staged_only, int32_t reps, mgt_autotune_result *res,
+                        void *stream)
+{
+    if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
+    if (p != MGT_FP64 && p != MGT_FP32_MIXED) return set_error(MGT_ERR_ARG, "unknown precision");
+    if (reps < 1 || reps > 100) return set_error(MGT_ERR_ARG, "reps must be 1..100");
+    if (m->opts.pairs_per_batch > 0 && m->opts.pairs_per_batch < m->P)
+        return set_error(MGT_ERR_ARG, "autotune needs the model's rays resident (pairs_per_batch = 0)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MGT_TRY_STATUS(ensure_rays(m, p, s));
+    if (m->line_dirty) MGT_TRY_STATUS(launch_line_data(m, s));
+    struct Cand {
+        int schedule, lpt;
+    };
+    std::vector<Cand> cands;
+    for (int sch = staged_only ? 2 : 1; sch <= (staged_only ? 2 : 3); ++sch)
+        for (int lpt : {4, 8})
+            if (p == MGT_FP32_MIXED || lpt == 4) cands.push_back({sch, lpt});
+    const mgt_solve_opts saved = m->opts;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MGT_CUDA(cudaEventCreate(&e0));
+    MGT_CUDA(cudaEventCreate(&e1));
+    mgt_autotune_result r{};
+    r.n_tried = (int32_t)cands.size();
+    int best = -1;
+    mgt_status st = MGT_OK;
+    for (size_t c = 0; c < cands.size() && st == MGT_OK; ++c) {
+        m->opts.schedule = cands[c].schedule;
+        m->opts.lines_per_thread = cands[c].lpt;
+        r.schedules[c] = cands[c].schedule;
+        r.lines[c] = cands[c].lpt;
+        st = launch_formal_solve(m, p, s, false);          // warm-up
+        std::vector<float> t;
+        for (int k = 0; k < reps && st == MGT_OK; ++k) {
+            cudaEventRecord(e0, s);
+            st = launch_formal_solve(m, p, s, false);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = cuda_status(cudaGetLastError(), "cudaEventSynchronize");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t.push_back(ms);
+        }
+        if (st != MGT_OK) break;
+        std::sort(t.begin(), t.end());
+        r.ms[c] = t[t.size() / 2];
+        if (best < 0 || r.ms[c] < r.ms[best]) best = (int)c;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->opts = saved;
+    if (st != MGT_OK) return st;
+    m->opts.schedule = cands[best].schedule;
+    m->opts.lines_per_thread = cands[best].lpt;
+    r.schedule = cands[best].schedule;
+    r.lines_per_thread = cands[best].lpt;
+    m->have_J = true;
+    if (res) *res = r;
+    return check_device_error(m, s);
+}
+
+}  // extern "C"

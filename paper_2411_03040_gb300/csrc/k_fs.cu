@@ -40,6 +40,7 @@
 // reading one coefficient pair per step.  The line groups of a bin no longer
 // repeat that work.
 #include <algorithm>
+#include <cstring>
 
 #include "mgt_common.cuh"
 #include "mgt_erfc.cuh"
@@ -90,6 +91,8 @@ struct FSArgs {
     int subdiv;                // > 0: every segment by the trapezoidal rule over this many pieces
     const int32_t *dir_map;    // pair directions -> model directions (NULL: the same)
     int accumulate;            // add to J / Lstar (later pair batches) instead of writing them
+    int lpt;                   // lines per thread of the staged schedule (batched launches)
+    int nblk;                  // line blocks per origin (ceil(Gtot / Gb))
     double *J, *Lst;           // [N][M]
     int *err;
 };
@@ -658,13 +661,19 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
     }
 }
 
-template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds__(256, MINB) k_fs_staged(FSArgs a)
+// One (origin, line block) item of the staged schedule, run by the whole CTA:
+// origin order index oi, line block blk.  The mbarriers at the base of shared
+// memory are initialised once per CTA; `ci` counts the chunks the CTA has
+// consumed so far, so their phases carry over from one item to the next.
+// Returns false if a wait gave up: the error word is set and no copy of this
+// CTA is left in flight.
+template <typename T, int LPT, int CH>
+__device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int blk, unsigned char *smem, int &ci)
 {
     using V2 = typename Prec<T>::V2;
     constexpr int SB = sizeof(T) == 4 ? 16 : 32;
     constexpr int NPT = CH + 1;
     static_assert(NPT <= 32, "one point row per producer lane");
-    extern __shared__ __align__(128) unsigned char smem[];
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rowB = a.RS * (int)sizeof(T);
     const int Mb = a.Gb * LPT;
@@ -681,18 +690,12 @@ template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds
     T *half0 = reinterpret_cast<T *>(smem + lay.half0);                   // [3][LPT][bd] first half's P, Y, a
     double *red = reinterpret_cast<double *>(smem + lay.stage);           // reuses staging + coefficients at the end
 
-    const int64_t o = a.order[blockIdx.x];
+    const int64_t o = a.order[oi];
     const int gl = tid / a.Q, q = tid - gl * a.Q;
-    const int gg = blockIdx.y * a.Gb + gl;
+    const int gg = blk * a.Gb + gl;
     const int line0 = gg * LPT;
     const bool active = tid < a.Q * a.Gb && gg < a.Gtot;
 
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
     const double wo64 = a.w64[o];
     if (tid < a.Q) {
         const T Aq = T(a.xq[tid]) * T(wo64);
@@ -712,10 +715,10 @@ template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds
 
     Chunk cur;
     const bool any = first_chunk_from(a, o, 0, 0, CH, cur);
-    if (any && warp == 0) issue_chunk<T>(a, o, cur, steps_s, rows_s, &bar[0], rowB, lane);
+    if (any && warp == 0) issue_chunk<T>(a, o, cur, steps_s + (ci & 1) * NPT * SB, rows_s + (ci & 1) * NPT * rowB,
+                                         &bar[ci & 1], rowB, lane);
 
     const T wqn = active ? T(a.wq[q]) : T(0);
-    int ci = 0;                 // chunks consumed
     bool ok = true;
     T P[LPT], Y[LPT], aa[LPT];
     for (int p = 0; p < a.P; ++p) {
@@ -797,13 +800,13 @@ done:
         if (tid == 0) {
             if (atomicCAS(a.err, 0, (int)kDevTimeout) == 0) {
                 a.err[1] = 3;
-                a.err[2] = (int)blockIdx.x;
+                a.err[2] = (int)oi;
                 a.err[3] = ci;
             }
             mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1);
             mbar_wait_bounded(&bar[(ci + 1) & 1], ((ci + 1) >> 1) & 1);
         }
-        return;
+        return false;
     }
     if (active) {
         const int lb = gl * LPT;
@@ -818,12 +821,89 @@ done:
         }
     }
     __syncthreads();
-    reduce_out(a, red, Mb, blockIdx.y * Mb, (int64_t)blockIdx.x, true);
+    reduce_out(a, red, Mb, blk * Mb, oi, true);
+    // the next item's bulk copies land where this item's reduction was written
+    // through the generic proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    return true;
+}
+
+__device__ __forceinline__ void staged_init(unsigned char *smem)
+{
+    if (threadIdx.x == 0) {
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        *reinterpret_cast<int *>(smem + 16) = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+}
+
+// One CTA per (origin, line block): blockIdx.x is the origin's place in the
+// visiting order, blockIdx.y the line block.
+template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds__(256, MINB) k_fs_staged(FSArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    staged_init(smem);
+    int ci = 0;
+    fs_staged_item<T, LPT, CH>(a, (int64_t)blockIdx.x, (int)blockIdx.y, smem, ci);
+}
+
+// Many models in one persistent launch.  Items (model, origin, line block)
+// are numbered model after model (models in the order of the table, origins
+// in each model's visiting order, the line blocks of an origin together);
+// each CTA takes the next item from a global counter until none is left.
+// item_end[i] is one past the last item of model i.
+struct FSBatchArgs {
+    const FSArgs *args;        // [n_models]
+    const int64_t *item_end;   // [n_models]
+    int n_models;
+    int64_t n_items;
+    unsigned long long *next;  // item counter, zero at launch
+};
+
+template <typename T, int CH> __global__ void __launch_bounds__(256, 2) k_fs_batch(FSBatchArgs b)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ FSArgs sa;
+    __shared__ int64_t s_item, s_first;
+    __shared__ int s_model;
+    staged_init(smem);
+    int ci = 0, cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int64_t it = (int64_t)atomicAdd(b.next, 1ull);
+            int model = -1;
+            if (it < b.n_items) {
+                int lo = 0, hi = b.n_models - 1;       // first model whose end is past the item
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (b.item_end[mid] > it) hi = mid; else lo = mid + 1;
+                }
+                model = lo;
+                s_first = lo > 0 ? b.item_end[lo - 1] : 0;
+                if (lo != cur) sa = b.args[lo];
+            }
+            s_item = it;
+            s_model = model;
+        }
+        __syncthreads();
+        const int model = s_model;
+        if (model < 0) return;
+        cur = model;
+        const int64_t local = s_item - s_first;
+        const int64_t oi = local / sa.nblk;
+        const int blk = (int)(local - oi * sa.nblk);
+        const bool ok = sa.lpt == 8 ? fs_staged_item<T, 8, CH>(sa, oi, blk, smem, ci)
+                                    : fs_staged_item<T, 4, CH>(sa, oi, blk, smem, ci);
+        if (!ok) return;
+    }
 }
 
 constexpr int kChunk = 31;
 
-template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_t s, int schedule, bool accumulate)
+template <typename T, int LPT> FSArgs fill_fs_args(const mgt_model *m, bool accumulate)
 {
     FSArgs a{};
     const bool all = m->rays_p0 == 0 && m->rays_np == m->P;
@@ -859,14 +939,24 @@ template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_
     a.J = m->d_J;
     a.Lst = m->d_Lst;
     a.err = m->d_err;
+    a.lpt = LPT;
+    a.nblk = ceil_div(a.Gtot, a.Gb);
+    return a;
+}
+
+template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_t s, int schedule, bool accumulate)
+{
+    FSArgs a = fill_fs_args<T, LPT>(m, accumulate);
     const int Mb = a.Gb * LPT;
-    // one origin per CTA when bins x groups fill a CTA: the staged kernel
-    // (schedule 2: register-capped for two blocks per SM, 3: one block per SM)
-    const bool staged = schedule != 1 && a.Q * a.Gb >= 96;
+    // one origin per CTA: the staged kernel (schedule 2: register-capped for
+    // two blocks per SM, 3: one block per SM); automatic choice when bins x
+    // groups fill a CTA
+    const bool staged = schedule == 2 || schedule == 3 || (schedule == 0 && a.Q * a.Gb >= 96);
     if (staged) {
         a.OPB = 1;
         const int threads = a.Q * a.Gb;
         const int bd = ((threads + 31) / 32) * 32;
+        if (bd > 256) return set_error(MGT_ERR_ARG, "formal solve: more than 256 bins per origin");
         const size_t smem = (size_t)staged_layout<T, LPT, kChunk>(a.Q, Mb, a.RS, bd).total;
         dim3 grid((unsigned)m->N, (unsigned)ceil_div(a.Gtot, a.Gb));
         if (schedule == 3) {
@@ -909,6 +999,59 @@ mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s, bo
     const int sch = m->opts.schedule;
     if (p == MGT_FP64) return launch_typed<double, 4>(m, s, sch, accumulate);
     return lpt == 4 ? launch_typed<float, 4>(m, s, sch, accumulate) : launch_typed<float, 8>(m, s, sch, accumulate);
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched launch (k_fs_batch): FP32-mixed, staged schedule, all rays resident.
+// ---------------------------------------------------------------------------
+size_t fs_args_bytes() { return sizeof(FSArgs); }
+
+mgt_status fs_batch_args(const mgt_model *m, void *args, int *threads, int64_t *items)
+{
+    const int lpt = fs_lines_per_thread(m, MGT_FP32_MIXED);
+    if (m->Mpad % lpt != 0) return set_error(MGT_ERR_STATE, "line padding does not match the schedule");
+    FSArgs a = lpt == 4 ? fill_fs_args<float, 4>(m, false) : fill_fs_args<float, 8>(m, false);
+    a.OPB = 1;
+    const int bd = ((a.Q * a.Gb + 31) / 32) * 32;
+    if (bd > 256) return set_error(MGT_ERR_ARG, "batched formal solve: more than 256 bins per origin");
+    *threads = bd;
+    *items = a.N * a.nblk;
+    std::memcpy(args, &a, sizeof a);
+    return MGT_OK;
+}
+
+size_t fs_batch_smem(const void *args, int bd)
+{
+    FSArgs a;
+    std::memcpy(&a, args, sizeof a);
+    const int Mb = a.Gb * a.lpt;
+    return a.lpt == 4 ? (size_t)staged_layout<float, 4, kChunk>(a.Q, Mb, a.RS, bd).total
+                      : (size_t)staged_layout<float, 8, kChunk>(a.Q, Mb, a.RS, bd).total;
+}
+
+mgt_status fs_batch_grid(int bd, size_t smem, int *grid)
+{
+    auto kern = k_fs_batch<float, kChunk>;
+    MGT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    MGT_CUDA(cudaGetDevice(&dev));
+    MGT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MGT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bd, smem));
+    if (per_sm < 1) return set_error(MGT_ERR_ARG, "batched formal solve: a CTA does not fit on an SM");
+    *grid = sms * per_sm;
+    return MGT_OK;
+}
+
+mgt_status fs_batch_launch(const void *d_args, const int64_t *d_item_end, int n_models, int64_t n_items,
+                           unsigned long long *d_next, int bd, size_t smem, int grid, cudaStream_t s)
+{
+    FSBatchArgs b{static_cast<const FSArgs *>(d_args), d_item_end, n_models, n_items, d_next};
+    MGT_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), s));
+    const int64_t g = std::min<int64_t>(grid, n_items);
+    k_fs_batch<float, kChunk><<<(unsigned)g, bd, smem, s>>>(b);
+    MGT_LAUNCH_CHECK("k_fs_batch");
+    return MGT_OK;
 }
 
 }  // namespace mgt

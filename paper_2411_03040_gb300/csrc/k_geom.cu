@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "mgt_common.cuh"
 
@@ -69,36 +70,46 @@ mgt_status launch_lte(mgt_model *m, cudaStream_t s)
 // Row layout (see row_stride32): chi~' of every line, then S' of every line,
 // then w and 1/w of the point.  One thread per (point, line slot).
 // ---------------------------------------------------------------------------
-__global__ void k_line_data(int64_t N, int L, int M, int Mpad, const double *__restrict__ pops,
-                            const double *__restrict__ w64, const double *__restrict__ line_tab,
-                            const int32_t *__restrict__ line_ul, double Lunit,
-                            float *__restrict__ out32, double *__restrict__ out64,
-                            unsigned long long *__restrict__ n_floor)
+struct LDArgs {
+    int64_t N;
+    int L, M, Mpad;
+    const double *pops, *w64, *line_tab;
+    const int32_t *line_ul;
+    double Lunit;
+    float *out32;
+    double *out64;
+    unsigned long long *n_floor;
+};
+
+__device__ __forceinline__ void line_data_slot(const LDArgs &d, int64_t t)
 {
-    const int RS = row_stride32(Mpad), RS64 = row_stride64(Mpad);
+    const int Mpad = d.Mpad, RS = row_stride32(Mpad), RS64 = row_stride64(Mpad);
     const int slots = Mpad + 2;                      // Mpad lines + {w, 1/w} + {0, 0}
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= N * slots) return;
+    if (t >= d.N * slots) return;
+    const double *__restrict__ line_tab = d.line_tab;
+    const int32_t *__restrict__ line_ul = d.line_ul;
+    float *__restrict__ out32 = d.out32;
+    double *__restrict__ out64 = d.out64;
     int64_t p = t / slots;
     int k = (int)(t - p * slots);
     double a0 = 0.0, a1 = 0.0;
-    if (k < M) {
+    if (k < d.M) {
         int u = line_ul[k], l = line_ul[Mpad + k];
         double Bul = line_tab[2 * Mpad + k], Blu = line_tab[3 * Mpad + k];
         double nbgmax = line_tab[4 * Mpad + k];
-        double nu_ = pops[p * L + u], nl_ = pops[p * L + l];
+        double nu_ = d.pops[p * d.L + u], nl_ = d.pops[p * d.L + l];
         double a = nl_ * Blu, b = nu_ * Bul;
         double net = a - b, floor_ = 1e-30 * (a + b);
         if (net < floor_) {
             net = floor_;
-            atomicAdd(n_floor, 1ULL);
+            atomicAdd(d.n_floor, 1ULL);
         }
         if (net > 0.0) {
-            a0 = kH * net * Lunit / (4.0 * kPi * kSqrtPi * w64[p]);
+            a0 = kH * net * d.Lunit / (4.0 * kPi * kSqrtPi * d.w64[p]);
             a1 = b / (net * nbgmax);
         }
     } else if (k == Mpad) {
-        a0 = w64[p];
+        a0 = d.w64[p];
         a1 = 1.0 / a0;
     }
     float *r32 = out32 + p * RS;
@@ -122,14 +133,57 @@ __global__ void k_line_data(int64_t N, int L, int M, int Mpad, const double *__r
     }
 }
 
+__global__ void k_line_data(LDArgs d) { line_data_slot(d, blockIdx.x * (int64_t)blockDim.x + threadIdx.x); }
+
+// Many models in one launch: blk_end[i] is one past the last CTA of model i.
+__global__ void k_line_data_batch(const LDArgs *__restrict__ args, const int64_t *__restrict__ blk_end, int n_models)
+{
+    __shared__ LDArgs sd;
+    __shared__ int64_t s_first;
+    if (threadIdx.x == 0) {
+        const int64_t b = blockIdx.x;
+        int lo = 0, hi = n_models - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (blk_end[mid] > b) hi = mid; else lo = mid + 1;
+        }
+        sd = args[lo];
+        s_first = lo > 0 ? blk_end[lo - 1] : 0;
+    }
+    __syncthreads();
+    line_data_slot(sd, ((int64_t)blockIdx.x - s_first) * blockDim.x + threadIdx.x);
+}
+
+static LDArgs fill_ld_args(const mgt_model *m)
+{
+    return LDArgs{m->N, m->L, m->M, m->Mpad, m->d_pops, m->d_w64, m->d_line_tab, m->d_line_ul, m->L_unit,
+                  m->d_line32, m->d_line64, m->d_count + 0};
+}
+
 mgt_status launch_line_data(mgt_model *m, cudaStream_t s)
 {
     int64_t n = m->N * (m->Mpad + 2);
-    k_line_data<<<ceil_div(n, 256), 256, 0, s>>>(m->N, m->L, m->M, m->Mpad, m->d_pops, m->d_w64, m->d_line_tab,
-                                                m->d_line_ul, m->L_unit, m->d_line32, m->d_line64,
-                                                m->d_count + 0);
+    k_line_data<<<ceil_div(n, 256), 256, 0, s>>>(fill_ld_args(m));
     MGT_LAUNCH_CHECK("k_line_data");
     m->line_dirty = false;
+    return MGT_OK;
+}
+
+size_t ld_args_bytes() { return sizeof(LDArgs); }
+
+mgt_status ld_batch_args(const mgt_model *m, void *args, int64_t *blocks)
+{
+    const LDArgs a = fill_ld_args(m);
+    std::memcpy(args, &a, sizeof a);
+    *blocks = (m->N * (m->Mpad + 2) + 255) / 256;
+    return MGT_OK;
+}
+
+mgt_status ld_batch_launch(const void *d_args, const int64_t *d_blk_end, int n_models, int64_t n_blocks,
+                           cudaStream_t s)
+{
+    k_line_data_batch<<<(unsigned)n_blocks, 256, 0, s>>>(static_cast<const LDArgs *>(d_args), d_blk_end, n_models);
+    MGT_LAUNCH_CHECK("k_line_data_batch");
     return MGT_OK;
 }
 

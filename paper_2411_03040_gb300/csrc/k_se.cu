@@ -15,6 +15,7 @@
 // relative accuracy.  All warp reductions run in a fixed lane order, so the
 // result is bitwise reproducible.
 #include <algorithm>
+#include <cstring>
 
 #include "mgt_common.cuh"
 
@@ -34,7 +35,8 @@ struct SEArgs {
     const double *Kul;        // [K]
     const int32_t *coll_ul;   // [2][K]
     const int16_t *entry;     // [3][L*L]
-    double *pops_out;         // [N][L]
+    double *pops_out;         // [N][L] (may be pops_old: each warp reads its row before writing it)
+    double *pops_prev;        // [N][L] copy of pops_old, or NULL
     int wpb;                  // warps (points) per block
 };
 
@@ -47,22 +49,20 @@ __device__ __forceinline__ double warp_sum(double v)
 
 constexpr int kMaxWarpsPerBlock = 4;
 
-__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) k_se(SEArgs a)
+// Point p, solved by one warp in its shared-memory slice sm (LL + 3L + 2 Mpad doubles).
+__device__ __forceinline__ void se_point(const SEArgs &a, int64_t p, double *sm, int lane)
 {
-    extern __shared__ __align__(16) double sm[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int L = a.L, LL = L * L;
-    const int per_warp = LL + 3 * L + 2 * a.Mpad;
-    double *R = sm + warp * per_warp;     // R[i*L + j]: rate i -> j
+    double *R = sm;                       // R[i*L + j]: rate i -> j
     double *Sn = R + LL;                  // [L] pivots
     double *xx = Sn + L;                  // [L] unnormalised populations
     double *bz = xx + L;                  // [L] Boltzmann factors g_i exp(-(E_i - E_0)/kT)
     double *rdown = bz + L;               // [Mpad] radiative u -> l rate per line
     double *rup = rdown + a.Mpad;         // [Mpad] radiative l -> u rate per line
-    const int64_t p = (int64_t)blockIdx.x * a.wpb + warp;
-    if (p >= a.N) return;                 // whole warp leaves together
 
     const double *po = a.pops_old + p * L;
+    if (a.pops_prev)
+        for (int i = lane; i < L; i += 32) a.pops_prev[p * L + i] = po[i];
     const double Tp = a.T[p], nc = a.ncoll[p];
     // per-line preconditioned radiative rates
     for (int k = lane; k < a.M; k += 32) {
@@ -139,9 +139,43 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) k_se(SEArgs a)
     for (int i = lane; i < L; i += 32) a.pops_out[p * L + i] = xx[i] * f;
 }
 
-}  // namespace
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) k_se(SEArgs a)
+{
+    extern __shared__ __align__(16) double sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per_warp = a.L * a.L + 3 * a.L + 2 * a.Mpad;
+    const int64_t p = (int64_t)blockIdx.x * a.wpb + warp;
+    if (p >= a.N) return;                 // whole warp leaves together
+    se_point(a, p, sm + warp * per_warp, lane);
+}
 
-mgt_status launch_stat_eq(mgt_model *m, cudaStream_t s)
+// Many models in one launch, kMaxWarpsPerBlock points of one model per CTA:
+// blk_end[i] is one past the last CTA of model i.
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) k_se_batch(const SEArgs *__restrict__ args,
+                                                                     const int64_t *__restrict__ blk_end, int n_models)
+{
+    extern __shared__ __align__(16) double sm[];
+    __shared__ SEArgs sa;
+    __shared__ int64_t s_first;
+    if (threadIdx.x == 0) {
+        const int64_t b = blockIdx.x;
+        int lo = 0, hi = n_models - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (blk_end[mid] > b) hi = mid; else lo = mid + 1;
+        }
+        sa = args[lo];
+        s_first = lo > 0 ? blk_end[lo - 1] : 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per_warp = sa.L * sa.L + 3 * sa.L + 2 * sa.Mpad;
+    const int64_t p = ((int64_t)blockIdx.x - s_first) * kMaxWarpsPerBlock + warp;
+    if (p >= sa.N) return;
+    se_point(sa, p, sm + warp * per_warp, lane);
+}
+
+SEArgs fill_se_args(const mgt_model *m)
 {
     SEArgs a{};
     a.N = m->N;
@@ -162,6 +196,16 @@ mgt_status launch_stat_eq(mgt_model *m, cudaStream_t s)
     a.coll_ul = m->d_coll_ul;
     a.entry = m->d_entry;
     a.pops_out = m->d_pops;
+    return a;
+}
+
+size_t se_warp_bytes(const mgt_model *m) { return sizeof(double) * ((size_t)m->L * m->L + 3 * m->L + 2 * m->Mpad); }
+
+}  // namespace
+
+mgt_status launch_stat_eq(mgt_model *m, cudaStream_t s)
+{
+    SEArgs a = fill_se_args(m);
     const size_t per_warp = sizeof(double) * ((size_t)m->L * m->L + 3 * m->L + 2 * m->Mpad);
     const size_t max_smem = 227 * 1024;
     int wpb = (int)std::min<size_t>(kMaxWarpsPerBlock, max_smem / per_warp);
@@ -171,6 +215,39 @@ mgt_status launch_stat_eq(mgt_model *m, cudaStream_t s)
     MGT_CUDA(cudaFuncSetAttribute(k_se, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_se<<<ceil_div(m->N, wpb), 32 * wpb, smem, s>>>(a);
     MGT_LAUNCH_CHECK("k_se");
+    return MGT_OK;
+}
+
+// Batched statistical equilibrium: the model's arguments with the previous
+// populations read from and written back to d_pops (the copy for Ng made by
+// the same warp into d_pops_prev).
+size_t se_args_bytes() { return sizeof(SEArgs); }
+
+mgt_status se_batch_args(const mgt_model *m, void *args, int64_t *blocks, size_t *smem)
+{
+    SEArgs a = fill_se_args(m);
+    a.pops_old = m->d_pops;
+    a.pops_prev = m->d_pops_prev;
+    a.wpb = kMaxWarpsPerBlock;
+    *smem = se_warp_bytes(m) * kMaxWarpsPerBlock;
+    if (*smem > 227 * 1024) return set_error(MGT_ERR_ARG, "batched statistical equilibrium: too many levels");
+    *blocks = (m->N + kMaxWarpsPerBlock - 1) / kMaxWarpsPerBlock;
+    std::memcpy(args, &a, sizeof a);
+    return MGT_OK;
+}
+
+mgt_status se_batch_prepare(size_t smem)
+{
+    MGT_CUDA(cudaFuncSetAttribute(k_se_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return MGT_OK;
+}
+
+mgt_status se_batch_launch(const void *d_args, const int64_t *d_blk_end, int n_models, int64_t n_blocks, size_t smem,
+                           cudaStream_t s)
+{
+    k_se_batch<<<(unsigned)n_blocks, 32 * kMaxWarpsPerBlock, smem, s>>>(static_cast<const SEArgs *>(d_args), d_blk_end,
+                                                                       n_models);
+    MGT_LAUNCH_CHECK("k_se_batch");
     return MGT_OK;
 }
 

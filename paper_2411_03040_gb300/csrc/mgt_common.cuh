@@ -169,8 +169,31 @@ void image_free(mgt_model *m);
 void image_frame(const double *pos, int64_t N, const double n[3], int32_t npx, int32_t npy, double e1[3],
                  double e2[3], std::vector<double> &ref);
 
+// rays of every pair held and current for the model's options (api.cu)
+mgt_status ensure_rays(mgt_model *m, mgt_precision p, cudaStream_t s);
+void note_launches(long long n);
+
 // formal solution (k_fs.cu)
 mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s, bool accumulate);
+int fs_lines_per_thread(const mgt_model *m, mgt_precision p);
+
+// batched launches over many models (argument tables built per model, read on
+// the device by table slot; see batch.cu)
+size_t fs_args_bytes();
+mgt_status fs_batch_args(const mgt_model *m, void *args, int *threads, int64_t *items);
+size_t fs_batch_smem(const void *args, int threads);
+mgt_status fs_batch_grid(int threads, size_t smem, int *grid);
+mgt_status fs_batch_launch(const void *d_args, const int64_t *d_item_end, int n_models, int64_t n_items,
+                           unsigned long long *d_next, int threads, size_t smem, int grid, cudaStream_t s);
+size_t se_args_bytes();
+mgt_status se_batch_args(const mgt_model *m, void *args, int64_t *blocks, size_t *smem);
+mgt_status se_batch_prepare(size_t smem);
+mgt_status se_batch_launch(const void *d_args, const int64_t *d_blk_end, int n_models, int64_t n_blocks, size_t smem,
+                           cudaStream_t s);
+size_t ld_args_bytes();
+mgt_status ld_batch_args(const mgt_model *m, void *args, int64_t *blocks);
+mgt_status ld_batch_launch(const void *d_args, const int64_t *d_blk_end, int n_models, int64_t n_blocks,
+                           cudaStream_t s);
 
 // statistical equilibrium (k_se.cu)
 mgt_status launch_stat_eq(mgt_model *m, cudaStream_t s);

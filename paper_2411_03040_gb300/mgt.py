@@ -59,6 +59,16 @@ class mgt_ali_stats(ctypes.Structure):
     _fields_ = [("iterations", _i32), ("ng_accepted", _i32), ("last_maxrel", _f64)]
 
 
+class mgt_autotune_result(ctypes.Structure):
+    _fields_ = [("schedule", _i32), ("lines_per_thread", _i32), ("n_tried", _i32),
+                ("schedules", _i32 * 8), ("lines", _i32 * 8), ("ms", ctypes.c_float * 8)]
+
+
+class mgt_batch_layout(ctypes.Structure):
+    _fields_ = [("n_models", _i32), ("fs_items", _i64), ("fs_grid", _i32), ("fs_threads", _i32),
+                ("fs_smem_bytes", _i64), ("se_blocks", _i64), ("graph_kernels", _i32)]
+
+
 # name -> argtypes (every function returns an int status, except mgt_last_error)
 SIGNATURES = {
     "mgt_model_create": [ctypes.POINTER(_P), ctypes.POINTER(mgt_model_desc), _P],
@@ -70,6 +80,7 @@ SIGNATURES = {
     "mgt_get_populations": [_P, _P, ctypes.c_int, _P],
     "mgt_formal_solve": [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P],
     "mgt_stat_equilibrium": [_P, _P, _P],
+    "mgt_get_jbar": [_P, _P, _P, ctypes.c_int, _P],
     "mgt_ng_accelerate": [_P, ctypes.POINTER(mgt_ng_opts), ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(_f64), _P],
     "mgt_ali_solve": [_P, ctypes.POINTER(mgt_ali_opts), ctypes.POINTER(mgt_ali_stats), _P],
@@ -79,6 +90,13 @@ SIGNATURES = {
     "mgt_set_point_fields": [_P, _P, _P, _P, ctypes.c_int, _P],
     "mgt_remesh": [_i64, _P, _P, _f64, _i32, _i32, _P, _P, _i64, ctypes.POINTER(_i64), _P],
     "mgt_ng_extrapolate_noalloc": [_i32, _P, _i64, _P, _P, ctypes.POINTER(_i64), _P],
+    "mgt_autotune": [_P, ctypes.c_int, _i32, _i32, ctypes.POINTER(mgt_autotune_result), _P],
+    "mgt_batch_create": [ctypes.POINTER(_P), ctypes.POINTER(_P), _i32, _P],
+    "mgt_batch_destroy": [_P],
+    "mgt_batch_formal_solve": [_P, _P],
+    "mgt_batch_stat_equilibrium": [_P, _P],
+    "mgt_batch_iterate": [_P, _i32, ctypes.POINTER(mgt_ng_opts), _P, _P],
+    "mgt_batch_get_layout": [_P, ctypes.POINTER(mgt_batch_layout), _P],
     "mgt_sync": [_P, _P],
     "mgt_model_sizes": [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                         ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
@@ -243,6 +261,18 @@ def mgt_formal_solve(m: Model, precision=MGT_FP32_MIXED, Jbar=None, Lstar=None, 
     return Jbar, Lstar
 
 
+def mgt_get_jbar(m: Model, Jbar=None, Lstar=None, stream=None):
+    """The model's last J-bar and Lambda*, [M][N] (host, or the given torch CUDA tensors)."""
+    s = mgt_model_sizes(m)
+    if Jbar is None:
+        Jbar = np.zeros((s["n_lines"], s["n_points"]), np.float64)
+    if Lstar is None:
+        Lstar = np.zeros((s["n_lines"], s["n_points"]), np.float64)
+    on_dev = 1 if hasattr(Jbar, "data_ptr") else 0
+    _check(load().mgt_get_jbar(m.handle, _ptr(Jbar), _ptr(Lstar), on_dev, _stream(stream)), "mgt_get_jbar")
+    return Jbar, Lstar
+
+
 def mgt_stat_equilibrium(m: Model, want=True, stream=None):
     out = None
     if want:
@@ -352,6 +382,72 @@ def mgt_ng_extrapolate_noalloc(iterates, prediction, stream=None):
     _check(load().mgt_ng_extrapolate_noalloc(n, _ptr(iterates), ln, _ptr(prediction), _ptr(coef),
                                              ctypes.byref(neg), _stream(stream)), "mgt_ng_extrapolate_noalloc")
     return coef[:n - 1], neg.value
+
+
+def mgt_autotune(m: Model, precision=MGT_FP32_MIXED, staged_only=False, reps=3, stream=None) -> dict:
+    """Time the candidate schedules, set the fastest in the model's options."""
+    r = mgt_autotune_result()
+    _check(load().mgt_autotune(m.handle, precision, int(bool(staged_only)), reps, ctypes.byref(r), _stream(stream)),
+           "mgt_autotune")
+    n = r.n_tried
+    return dict(schedule=r.schedule, lines_per_thread=r.lines_per_thread,
+                tried=[(r.schedules[i], r.lines[i], r.ms[i]) for i in range(n)])
+
+
+class Batch:
+    """Owns one mgt_batch handle and keeps its models alive while in use."""
+
+    def __init__(self, handle, models):
+        self.handle = handle
+        self.models = list(models)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().mgt_batch_destroy(self.handle)
+        except Exception:
+            pass
+        self.handle = None
+
+    def close(self):
+        if self.handle:
+            _check(load().mgt_batch_destroy(self.handle), "mgt_batch_destroy")
+            self.handle = None
+
+
+def mgt_batch_create(models, stream=None) -> Batch:
+    lib = load()
+    arr = (_P * len(models))(*[m.handle for m in models])
+    h = _P()
+    _check(lib.mgt_batch_create(ctypes.byref(h), arr, len(models), _stream(stream)), "mgt_batch_create")
+    return Batch(h, models)
+
+
+def mgt_batch_formal_solve(b: Batch, stream=None):
+    _check(load().mgt_batch_formal_solve(b.handle, _stream(stream)), "mgt_batch_formal_solve")
+
+
+def mgt_batch_stat_equilibrium(b: Batch, stream=None):
+    _check(load().mgt_batch_stat_equilibrium(b.handle, _stream(stream)), "mgt_batch_stat_equilibrium")
+
+
+def mgt_batch_iterate(b: Batch, n_iter=1, ng_mode=MGT_NG_NONE, n_steps=4, n_max=8, want_stats=False, stream=None):
+    """n_iter ALI iterations of every model; per-model stats (caller's order) if asked."""
+    o = mgt_ng_opts(ng_mode, n_steps, n_max)
+    st = (mgt_ali_stats * len(b.models))() if want_stats else None
+    _check(load().mgt_batch_iterate(b.handle, n_iter, ctypes.byref(o), st, _stream(stream)), "mgt_batch_iterate")
+    if not want_stats:
+        return None
+    return [dict(iterations=x.iterations, ng_accepted=x.ng_accepted, last_maxrel=x.last_maxrel) for x in st]
+
+
+def mgt_batch_get_layout(b: Batch) -> dict:
+    lay = mgt_batch_layout()
+    order = np.zeros(len(b.models), dtype=np.int32)
+    _check(load().mgt_batch_get_layout(b.handle, ctypes.byref(lay), _ptr(order)), "mgt_batch_get_layout")
+    d = {k: getattr(lay, k) for k, _ in mgt_batch_layout._fields_}
+    d["order"] = order
+    return d
 
 
 def mgt_sync(m: Model, stream=None):

@@ -134,9 +134,8 @@ def delaunay_graph(pos: np.ndarray):
     off = np.asarray(indptr, dtype=np.int64)
     nb = np.asarray(indices, dtype=np.int32)
     # sort each neighbour list (deterministic, independent of qhull's order)
-    for i in range(pos.shape[0]):
-        a, b = off[i], off[i + 1]
-        nb[a:b].sort()
+    row = np.repeat(np.arange(pos.shape[0], dtype=np.int64), np.diff(off))
+    nb = nb[np.lexsort((nb, row))]
     return off, nb, hull
 
 
@@ -282,6 +281,28 @@ def lattice_model(n_side=9, spacing_m=1e11, n_levels=2, n_quad=11, temp=100.0,
     return Model(name, pu * spacing_m, np.zeros_like(pu), np.full(N, temp), np.zeros(N),
                  np.full(N, n_coll), np.full(N, n_spec), off, nb, face, np.asarray(dirs, np.float64),
                  n_quad, lines)
+
+
+# --------------------------------------------------------------------------
+# Batches of uneven models
+# --------------------------------------------------------------------------
+def batch_specs(n_models=256, n_min=5_000, n_max=200_000, levels=(5, 11, 21, 41), nsides=(1, 2), n_quad=31,
+                seed=None):
+    """Seeded sizes of a batch of independent sphere models: point counts
+    log-uniform in [n_min, n_max], level counts drawn from ``levels``, HEALPix
+    nside from ``nsides`` (12 or 48 rays).  Returns (points, levels, nside,
+    bins, seed) tuples; ``batch_model`` builds one."""
+    rng = np.random.default_rng(SEED_BASE + 40 if seed is None else seed)
+    n = np.exp(rng.uniform(math.log(n_min), math.log(n_max), size=n_models)).astype(np.int64)
+    lv = rng.choice(np.asarray(levels), size=n_models)
+    ns = rng.choice(np.asarray(nsides), size=n_models)
+    base = int(rng.integers(1 << 30))
+    return [(int(n[i]), int(lv[i]), int(ns[i]), int(n_quad), base + i) for i in range(n_models)]
+
+
+def batch_model(spec) -> Model:
+    n, L, nside, q, seed = spec
+    return sphere_model(n, L, nside, q, seed=seed, name=f"sphere-{n}-L{L}-R{12 * nside * nside}")
 
 
 # --------------------------------------------------------------------------
