@@ -15,6 +15,8 @@
 //    current chunk from shared memory.
 //  * k_fs_gather: several origins per CTA (small bin x line counts); every
 //    thread gathers its rows straight from global memory.
+//  * k_fs_batch: the staged body for the items (model, origin, line block) of
+//    many models in one persistent launch.
 //
 // Second-order (Feautrier) system along a ray with points d = 0..D-1 and
 // segment optical depths, rows -A u_{d-1} + (1 + A + C) u_d - C u_{d+1} = S_d,
