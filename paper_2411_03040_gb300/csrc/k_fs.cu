@@ -627,26 +627,26 @@ __host__ __device__ inline StagedLayout staged_layout(int Q, int Mb, int RS, int
 
 // Line-independent coefficients of every (bin, step) of one chunk, shared by
 // the CTA's line groups: coef[(k - k_lo) * Q + q] = halved {cf, cn} of step k.
-template <typename T>
+// Two ways to share the items among the CTA's threads:
+//  * strided (CARRY false): item kk * Q + q to thread (kk * Q + q) mod bd;
+//  * runs (CARRY true): thread t takes bin t mod Q and a run of consecutive
+//    steps; the near point of a step is the far point of the step before, so
+//    its Gaussian is carried instead of recomputed.  This pays where the
+//    pre-pass dominates (few lines per origin, 4 lines per thread), while with
+//    many lines the extra live registers cost more than the saved exponentials.
+template <typename T, bool CARRY>
 __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, int k_lo, int k_hi,
                                             const unsigned char *Sb, const T *Rb, const T *sA, const T *sB,
                                             typename Prec<T>::V2 *coef, int tid, int bd)
 {
     constexpr int SB = sizeof(T) == 4 ? 16 : 32;
     const T thr = (T)a.thr;
-    const int items = a.Q * (k_hi - k_lo + 1);
-#pragma unroll 1
-    for (int it = tid; it < items; it += bd) {
-        const int kk = it / a.Q, q = it - kk * a.Q;
+    const int nst = k_hi - k_lo + 1;
+    // one segment's coefficients from its far and near point data
+    auto one = [&](int kk, int q, T Aq, T Bq, T g_n, const StepG<T> &sf, T z_f, T g_f) {
         const int k = k_lo + kk, jf = kk + 1, jn = kk;
-        const StepG<T> sf = step_from<T>(Sb + jf * SB);
-        const T beta_n = k > 1 ? step_from<T>(Sb + jn * SB).beta : T(0);
         const T *rowf = Rb + jf * a.RS, *rown = Rb + jn * a.RS;
         const T w_f = rowf[2 * a.Mpad], w_n = rown[2 * a.Mpad];
-        const T Aq = sA[q], Bq = sB[q];
-        const T z_f = Aq + Bq * sf.beta, z_n = Aq + Bq * beta_n;
-        const T g_f = Prec<T>::gauss(z_f * rowf[2 * a.Mpad + 1]);
-        const T g_n = Prec<T>::gauss(z_n * rown[2 * a.Mpad + 1]);
         const T du = -Bq * sf.dbw;
         bool trap = fabs(du) < thr;
         if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(kSwitchBand) * thr) {
@@ -655,11 +655,48 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
             trap = trapezoid_fp64(a, r, c_f, c_n, a.xq[q], a.w64[o]);
         }
         T cf, cn;
-        if (a.subdiv > 0)
+        if (a.subdiv > 0) {
+            const T z_n = Aq + Bq * (k > 1 ? step_from<T>(Sb + jn * SB).beta : T(0));
             subdiv_coefs<T>(a.subdiv, sf.dx, z_f, w_f, z_n, w_n, cf, cn);
-        else
+        } else {
             segment_coefs<T>(trap, sf.dx, du, z_f, g_f, w_f, g_n, w_n, a.width_mode, cf, cn);
+        }
         coef[kk * a.Q + q] = {cf, cn};
+    };
+    if constexpr (CARRY) {
+        const int nseg = bd / a.Q;                     // Q <= bd: bins x line groups fit the CTA
+        const int seg = tid / a.Q, q = tid - seg * a.Q;
+        const int sps = (nst + nseg - 1) / nseg;
+        const int kk0 = seg * sps, kk1 = min(nst, kk0 + sps);
+        if (seg >= nseg || kk0 >= kk1) return;
+        const T Aq = sA[q], Bq = sB[q];
+        T g_n;
+        {
+            const T z_n = Aq + Bq * (k_lo + kk0 > 1 ? step_from<T>(Sb + kk0 * SB).beta : T(0));
+            g_n = Prec<T>::gauss(z_n * Rb[kk0 * a.RS + 2 * a.Mpad + 1]);
+        }
+#pragma unroll 1
+        for (int kk = kk0; kk < kk1; ++kk) {
+            const StepG<T> sf = step_from<T>(Sb + (kk + 1) * SB);
+            const T z_f = Aq + Bq * sf.beta;
+            const T g_f = Prec<T>::gauss(z_f * Rb[(kk + 1) * a.RS + 2 * a.Mpad + 1]);
+            one(kk, q, Aq, Bq, g_n, sf, z_f, g_f);
+            g_n = g_f;
+        }
+    } else {
+        const int items = a.Q * nst;
+#pragma unroll 1
+        for (int it = tid; it < items; it += bd) {
+            const int kk = it / a.Q, q = it - kk * a.Q;
+            const int k = k_lo + kk;
+            const StepG<T> sf = step_from<T>(Sb + (kk + 1) * SB);
+            const T beta_n = k > 1 ? step_from<T>(Sb + kk * SB).beta : T(0);
+            const T Aq = sA[q], Bq = sB[q];
+            const T z_f = Aq + Bq * sf.beta, z_n = Aq + Bq * beta_n;
+            const T g_f = Prec<T>::gauss(z_f * Rb[(kk + 1) * a.RS + 2 * a.Mpad + 1]);
+            const T g_n = Prec<T>::gauss(z_n * Rb[kk * a.RS + 2 * a.Mpad + 1]);
+            one(kk, q, Aq, Bq, g_n, sf, z_f, g_f);
+        }
     }
 }
 
@@ -742,7 +779,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                 const unsigned char *Sb = steps_s + (ci & 1) * NPT * SB;
                 const T *Rb = reinterpret_cast<const T *>(rows_s + (ci & 1) * NPT * rowB);
                 V2 *cf_buf = coef + (ci & 1) * CH * a.Q;
-                if (ok) chunk_coefs<T>(a, o, r, k_lo, k_hi, Sb, Rb, sA, sB, cf_buf, tid, bd);
+                if (ok) chunk_coefs<T, LPT == 4>(a, o, r, k_lo, k_hi, Sb, Rb, sA, sB, cf_buf, tid, bd);
                 // one barrier per chunk: this chunk's coefficients are complete, and
                 // everyone is done with the previous chunk (its staging buffer is
                 // refilled next, its coefficient buffer on the following chunk);
@@ -759,16 +796,32 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                                        rows_s + ((ci + 1) & 1) * NPT * rowB, &bar[(ci + 1) & 1], rowB, lane);
                 }
                 if (active) {
+                    // step k reads rows jf = k - k_lo + 1 and jn = jf - 1; the
+                    // near row's chi is the next step's far chi, so two steps
+                    // per trip swap the two chi arrays instead of reloading
+                    const T *row = Rb + (k_hi - k_lo + 1) * a.RS + line0;
+                    const V2 *cfp = cf_buf + (k_hi - k_lo) * a.Q + q;
+                    T chiA[LPT], chiB[LPT], S_f[LPT];
+                    load_vec<LPT>(row, chiA);
+                    int k = k_hi;
 #pragma unroll 1
-                    for (int k = k_hi; k >= k_lo; --k) {
-                        const int jf = k - k_lo + 1, jn = jf - 1;
-                        const V2 cc = cf_buf[(k - k_lo) * a.Q + q];
-                        const T *rowf = Rb + jf * a.RS, *rown = Rb + jn * a.RS;
-                        T chi_f[LPT], S_f[LPT], chi_n[LPT];
-                        load_vec<LPT>(rowf + line0, chi_f);
-                        load_vec<LPT>(rowf + a.Mpad + line0, S_f);
-                        load_vec<LPT>(rown + line0, chi_n);
-                        eliminate_row<T, LPT>(cc.x, cc.y, chi_f, S_f, chi_n, P, Y, aa);
+                    for (; k - 1 >= k_lo; k -= 2) {
+                        V2 cc = *cfp;
+                        load_vec<LPT>(row + a.Mpad, S_f);
+                        load_vec<LPT>(row - a.RS, chiB);
+                        eliminate_row<T, LPT>(cc.x, cc.y, chiA, S_f, chiB, P, Y, aa);
+                        cc = *(cfp - a.Q);
+                        load_vec<LPT>(row - a.RS + a.Mpad, S_f);
+                        load_vec<LPT>(row - 2 * a.RS, chiA);
+                        eliminate_row<T, LPT>(cc.x, cc.y, chiB, S_f, chiA, P, Y, aa);
+                        row -= 2 * a.RS;
+                        cfp -= 2 * a.Q;
+                    }
+                    if (k == k_lo) {
+                        const V2 cc = *cfp;
+                        load_vec<LPT>(row + a.Mpad, S_f);
+                        load_vec<LPT>(row - a.RS, chiB);
+                        eliminate_row<T, LPT>(cc.x, cc.y, chiA, S_f, chiB, P, Y, aa);
                     }
                 }
                 ++ci;
