@@ -531,23 +531,34 @@ struct Chunk {
     int k_lo, k_hi;    // steps covered by the chunk
 };
 
-__device__ __forceinline__ void half_extent(const FSArgs &a, int64_t o, int p, int h, int64_t &s0, int &n)
+// The origin's half-rays as {first step record, length}, ext[2 p + h], read
+// from the ray offsets once per item into shared memory.
+__device__ __forceinline__ void fill_extents(const FSArgs &a, int64_t o, longlong2 *ext, int tid, int bd)
 {
-    const int2 pr = a.pairs[p];
-    const int r = h == 0 ? pr.y : pr.x;
-    const int64_t t = (int64_t)r * a.N + o;
-    s0 = a.ray_off[t];
-    n = (int)(a.ray_off[t + 1] - s0);
+    for (int t = tid; t < 2 * a.P; t += bd) {
+        const int2 pr = a.pairs[t >> 1];
+        const int r = (t & 1) == 0 ? pr.y : pr.x;
+        const int64_t i = (int64_t)r * a.N + o;
+        const int64_t s0 = a.ray_off[i];
+        ext[t] = make_longlong2(s0, a.ray_off[i + 1] - s0);
+    }
+}
+
+__device__ __forceinline__ void half_extent(const longlong2 *ext, int p, int h, int64_t &s0, int &n)
+{
+    const longlong2 e = ext[2 * p + h];
+    s0 = e.x;
+    n = (int)e.y;
 }
 
 // First chunk at or after half (p, h); false if none.
-__device__ __forceinline__ bool first_chunk_from(const FSArgs &a, int64_t o, int p, int h, int CH, Chunk &c)
+__device__ __forceinline__ bool first_chunk_from(const longlong2 *ext, int P, int p, int h, int CH, Chunk &c)
 {
-    for (; p < a.P; ++p, h = 0) {
+    for (; p < P; ++p, h = 0) {
         for (; h < 2; ++h) {
             int64_t s0;
             int n;
-            half_extent(a, o, p, h, s0, n);
+            half_extent(ext, p, h, s0, n);
             if (n > 0) {
                 c = {p, h, s0, n, max(1, n - CH + 1), n};
                 return true;
@@ -557,7 +568,7 @@ __device__ __forceinline__ bool first_chunk_from(const FSArgs &a, int64_t o, int
     return false;
 }
 
-__device__ __forceinline__ bool next_chunk(const FSArgs &a, int64_t o, const Chunk &cur, int CH, Chunk &nx)
+__device__ __forceinline__ bool next_chunk(const longlong2 *ext, int P, const Chunk &cur, int CH, Chunk &nx)
 {
     if (cur.k_lo > 1) {
         nx = cur;
@@ -565,7 +576,7 @@ __device__ __forceinline__ bool next_chunk(const FSArgs &a, int64_t o, const Chu
         nx.k_lo = max(1, nx.k_hi - CH + 1);
         return true;
     }
-    return cur.h == 0 ? first_chunk_from(a, o, cur.p, 1, CH, nx) : first_chunk_from(a, o, cur.p + 1, 0, CH, nx);
+    return cur.h == 0 ? first_chunk_from(ext, P, cur.p, 1, CH, nx) : first_chunk_from(ext, P, cur.p + 1, 0, CH, nx);
 }
 
 // Issue the copies of chunk c into one buffer (warp 0).  Point slot j holds
@@ -598,13 +609,13 @@ __device__ __forceinline__ void issue_chunk(const FSArgs &a, int64_t o, const Ch
 // Shared-memory carve-out of the staged kernel (bytes from the dynamic base),
 // computed identically on the host (launch size) and the device.
 struct StagedLayout {
-    int stage, coef, ibg, sab, acc, half0, total;
+    int stage, coef, ibg, sab, acc, half0, ext, total;
 };
 
 // Staging buffers [2] and coefficient buffers [2] are contiguous; the final
 // FP64 reduction area aliases them once the last chunk is done.
 template <typename T, int LPT, int CH>
-__host__ __device__ inline StagedLayout staged_layout(int Q, int Mb, int RS, int bd)
+__host__ __device__ inline StagedLayout staged_layout(int Q, int Mb, int RS, int bd, int P)
 {
     constexpr int SB = sizeof(T) == 4 ? 16 : 32;
     constexpr int NPT = CH + 1;
@@ -621,7 +632,8 @@ __host__ __device__ inline StagedLayout staged_layout(int Q, int Mb, int RS, int
     L.sab = L.ibg + up(Mb * Q * (int)sizeof(T));
     L.acc = L.sab + up(2 * Q * (int)sizeof(T));
     L.half0 = L.acc + up(3 * LPT * bd * (int)sizeof(T));
-    L.total = L.half0 + up(3 * LPT * bd * (int)sizeof(T));
+    L.ext = L.half0 + up(3 * LPT * bd * (int)sizeof(T));
+    L.total = L.ext + 2 * P * 16;
     return L;
 }
 
@@ -716,7 +728,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rowB = a.RS * (int)sizeof(T);
     const int Mb = a.Gb * LPT;
-    const StagedLayout lay = staged_layout<T, LPT, CH>(a.Q, Mb, a.RS, bd);
+    const StagedLayout lay = staged_layout<T, LPT, CH>(a.Q, Mb, a.RS, bd, a.P);
 
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);                   // [2]
     int *abort_flag = reinterpret_cast<int *>(smem + 16);
@@ -727,6 +739,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
     T *sA = reinterpret_cast<T *>(smem + lay.sab), *sB = sA + a.Q;        // [Q] each
     T *acc = reinterpret_cast<T *>(smem + lay.acc);                       // [3][LPT][bd]
     T *half0 = reinterpret_cast<T *>(smem + lay.half0);                   // [3][LPT][bd] first half's P, Y, a
+    longlong2 *ext = reinterpret_cast<longlong2 *>(smem + lay.ext);       // [2 P] half-ray extents
     double *red = reinterpret_cast<double *>(smem + lay.stage);           // reuses staging + coefficients at the end
 
     const int64_t o = a.order[oi];
@@ -736,6 +749,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
     const bool active = tid < a.Q * a.Gb && gg < a.Gtot;
 
     const double wo64 = a.w64[o];
+    fill_extents(a, o, ext, tid, bd);
     if (tid < a.Q) {
         const T Aq = T(a.xq[tid]) * T(wo64);
         sA[tid] = Aq;
@@ -753,7 +767,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
     __syncthreads();
 
     Chunk cur;
-    const bool any = first_chunk_from(a, o, 0, 0, CH, cur);
+    const bool any = first_chunk_from(ext, a.P, 0, 0, CH, cur);
     if (any && warp == 0) issue_chunk<T>(a, o, cur, steps_s + (ci & 1) * NPT * SB, rows_s + (ci & 1) * NPT * rowB,
                                          &bar[ci & 1], rowB, lane);
 
@@ -766,7 +780,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
             const int r = h == 0 ? pr.y : pr.x;
             int64_t s0;
             int n;
-            half_extent(a, o, p, h, s0, n);
+            half_extent(ext, p, h, s0, n);
 #pragma unroll
             for (int l = 0; l < LPT; ++l) {
                 P[l] = T(2);
@@ -791,7 +805,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                 if (warp == 0) {
                     Chunk nx;
                     const Chunk c{p, h, s0, n, k_lo, k_hi};
-                    if (next_chunk(a, o, c, CH, nx))
+                    if (next_chunk(ext, a.P, c, CH, nx))
                         issue_chunk<T>(a, o, nx, steps_s + ((ci + 1) & 1) * NPT * SB,
                                        rows_s + ((ci + 1) & 1) * NPT * rowB, &bar[(ci + 1) & 1], rowB, lane);
                 }
@@ -1012,7 +1026,7 @@ template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_
         const int threads = a.Q * a.Gb;
         const int bd = ((threads + 31) / 32) * 32;
         if (bd > 256) return set_error(MGT_ERR_ARG, "formal solve: more than 256 bins per origin");
-        const size_t smem = (size_t)staged_layout<T, LPT, kChunk>(a.Q, Mb, a.RS, bd).total;
+        const size_t smem = (size_t)staged_layout<T, LPT, kChunk>(a.Q, Mb, a.RS, bd, a.P).total;
         dim3 grid((unsigned)m->N, (unsigned)ceil_div(a.Gtot, a.Gb));
         if (schedule == 3) {
             MGT_CUDA(cudaFuncSetAttribute(k_fs_staged<T, LPT, kChunk, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1081,8 +1095,8 @@ size_t fs_batch_smem(const void *args, int bd)
     FSArgs a;
     std::memcpy(&a, args, sizeof a);
     const int Mb = a.Gb * a.lpt;
-    return a.lpt == 4 ? (size_t)staged_layout<float, 4, kChunk>(a.Q, Mb, a.RS, bd).total
-                      : (size_t)staged_layout<float, 8, kChunk>(a.Q, Mb, a.RS, bd).total;
+    return a.lpt == 4 ? (size_t)staged_layout<float, 4, kChunk>(a.Q, Mb, a.RS, bd, a.P).total
+                      : (size_t)staged_layout<float, 8, kChunk>(a.Q, Mb, a.RS, bd, a.P).total;
 }
 
 mgt_status fs_batch_grid(int bd, size_t smem, int *grid)
