@@ -574,6 +574,15 @@ def run_batch(args):
             c.record(stream)
             torch.cuda.synchronize()
             fs_times.append(a.elapsed_time(c))
+        # the same formal solutions as one launch per model (schedule 2, the
+        # tuned lines per thread), for comparison with the persistent launch
+        a, c = ev(), ev()
+        a.record(stream)
+        for h in hs:
+            mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED, want=False, stream=stream)
+        c.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = a.elapsed_time(c)
     ms = float(np.mean(times))
     fs_ms = float(np.mean(fs_times))
     units = sum(m.n_points * (m.dirs.shape[0] // 2) * m.lines.n_lines * m.n_quad for m in models)
@@ -601,6 +610,9 @@ def run_batch(args):
                      "line_steps_per_launch": line_steps, "launch_ms": fs_ms,
                      "launch_ms_source": "CUDA events around mgt_batch_formal_solve (line data + formal solution)",
                      "share_of_step": fs_ms / ms},
+        "one_launch_per_model": {"formal_solve_ms": seq_ms, "batch_speedup": seq_ms / fs_ms,
+                                 "note": "mgt_formal_solve per model in turn (line data where stale + staged "
+                                         "kernel), same schedules"},
         "gpu_launches": launches, "clocks": clk,
         "host_setup_s": {"generate": gen_s, "create_and_trace": setup_s}}), flush=True)
 

@@ -426,8 +426,10 @@ mgt_status mgt_autotune(mgt_model *m, mgt_precision p, int32_t staged_only, int3
  * mgt_batch_formal_solve: line data of every model from its current
  * populations, then J-bar and Lambda* of every model (the values of
  * mgt_formal_solve in FP32-mixed with schedule 2 and the model's lines per
- * thread) in one persistent launch: CTAs take (model, origin, line block)
- * items from a counter; models with the most work per item come first.
+ * thread) in one persistent launch per CTA width (bins x line groups of one
+ * origin, rounded to warps; models of one width share a launch): CTAs take
+ * (model, origin, line block) items from a counter, models with the most work
+ * per item first.
  * mgt_batch_stat_equilibrium: the statistical equilibrium of every point of
  * every model in one launch (the values of mgt_stat_equilibrium).
  * mgt_batch_iterate: n_iter ALI iterations of every model.  The first call
@@ -445,12 +447,13 @@ typedef struct mgt_batch mgt_batch;
 typedef struct {
     int32_t n_models;
     int64_t fs_items;          /* (model, origin, line block) items of the formal solution */
-    int32_t fs_grid;           /* CTAs of the persistent formal-solution launch */
-    int32_t fs_threads;        /* threads per CTA (largest over the models) */
-    int64_t fs_smem_bytes;     /* dynamic shared memory per CTA */
+    int32_t fs_grid;           /* CTAs of the persistent formal-solution launches, summed */
+    int32_t fs_threads;        /* threads per CTA of the widest launch */
+    int64_t fs_smem_bytes;     /* largest dynamic shared memory per CTA */
     int64_t se_blocks;         /* CTAs of the statistical-equilibrium launch */
     int32_t graph_kernels;     /* kernels per replay of the captured iteration (0 before the
                                   first mgt_batch_iterate) */
+    int32_t fs_launches;       /* persistent formal-solution launches (one per CTA width) */
 } mgt_batch_layout;
 mgt_status mgt_batch_create(mgt_batch **out, mgt_model *const *models, int32_t n_models, void *stream);
 mgt_status mgt_batch_destroy(mgt_batch *b);

@@ -1,12 +1,14 @@
 // Batches of models (mgt_batch_*) and the schedule autotuner (mgt_autotune).
 //
-// A batch runs the per-iteration work of many models as three launches:
-// line data of every point of every model, the formal solution of every
-// (model, origin, line block) item in one persistent kernel (items taken from
+// A batch runs the per-iteration work of many models in a few launches:
+// line data of every point of every model; the formal solution of every
+// (model, origin, line block) item in one persistent kernel per CTA width
+// (bins x line groups of one origin, in warps: a model runs at its own width,
+// so narrow models keep many CTAs per SM; within a width, items are taken from
 // a global counter, models ordered from the most to the least work per item
-// so that the short items fill the tail), and the statistical equilibrium of
+// so that the short items fill the tail); and the statistical equilibrium of
 // every point with per-model level counts.  mgt_batch_iterate captures the
-// three launches once in a CUDA graph and replays it per iteration.
+// launches once in a CUDA graph and replays it per iteration.
 //
 // Each launch reads its per-model arguments from a device table.  The tables
 // are rebuilt from the models before every batch call; when a model changed
@@ -25,13 +27,23 @@ struct mgt_batch {
     std::vector<int32_t> order;            // table slot -> caller index (most work per item first)
     // host copies of the argument tables, in table order
     std::vector<unsigned char> fs_args, se_args, ld_args;
-    std::vector<int64_t> fs_end, se_end, ld_end;
-    int fs_threads = 0, fs_grid = 0;
-    size_t fs_smem = 0, se_smem = 0;
+    std::vector<int64_t> fs_end, se_end, ld_end;   // fs_end restarts at each width class
+    struct FsClass {
+        int threads = 0, grid = 0, first = 0, count = 0;
+        size_t smem = 0;
+        int64_t items = 0;
+        bool operator==(const FsClass &o) const
+        {
+            return threads == o.threads && grid == o.grid && first == o.first && count == o.count &&
+                   smem == o.smem && items == o.items;
+        }
+    };
+    std::vector<FsClass> fs_classes;               // in launch order, widest first
+    size_t se_smem = 0;
     // device copies
     unsigned char *d_fs_args = nullptr, *d_se_args = nullptr, *d_ld_args = nullptr;
     int64_t *d_fs_end = nullptr, *d_se_end = nullptr, *d_ld_end = nullptr;
-    unsigned long long *d_next = nullptr;
+    unsigned long long *d_next = nullptr;          // one item counter per width class
     // the captured iteration
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -81,43 +93,67 @@ mgt_status refresh(mgt_batch *b, cudaStream_t s)
 {
     const int n = (int)b->models.size();
     for (mgt_model *m : b->models) MGT_TRY_STATUS(ensure_rays(m, MGT_FP32_MIXED, s));
-    // order: most work per item first, ties by caller index
+    const size_t fsz = fs_args_bytes(), ssz = se_args_bytes(), lsz = ld_args_bytes();
+    // each model's formal-solution arguments, CTA width and items (caller's order)
+    std::vector<unsigned char> fa_c(fsz * n);
+    std::vector<int> width(n);
+    std::vector<int64_t> items(n);
     std::vector<double> cost(n);
-    for (int i = 0; i < n; ++i) cost[i] = item_cost(b->models[i]);
+    for (int i = 0; i < n; ++i) {
+        MGT_TRY_STATUS(fs_batch_args(b->models[i], fa_c.data() + i * fsz, &width[i], &items[i]));
+        cost[i] = item_cost(b->models[i]);
+    }
+    // order: widest CTAs first, then most work per item, ties by caller index
     std::vector<int32_t> order(n);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return width[x] != width[y] ? width[x] > width[y] : cost[x] > cost[y];
+    });
 
-    const size_t fsz = fs_args_bytes(), ssz = se_args_bytes(), lsz = ld_args_bytes();
     std::vector<unsigned char> fa(fsz * n), sa(ssz * n), la(lsz * n);
     std::vector<int64_t> fe(n), se(n), le(n);
-    int threads = 32;
+    std::vector<mgt_batch::FsClass> classes;
     size_t se_smem = 0;
-    int64_t fi = 0, si = 0, li = 0;
+    int64_t si = 0, li = 0, fi = 0;
     for (int k = 0; k < n; ++k) {
-        const mgt_model *m = b->models[order[k]];
-        int bd = 0;
-        int64_t items = 0, sblocks = 0, lblocks = 0;
+        const int i = order[k];
+        const mgt_model *m = b->models[i];
+        std::memcpy(fa.data() + k * fsz, fa_c.data() + i * fsz, fsz);
+        if (classes.empty() || classes.back().threads != width[i]) {
+            classes.emplace_back();
+            classes.back().threads = width[i];
+            classes.back().first = k;
+            fi = 0;
+        }
+        mgt_batch::FsClass &c = classes.back();
+        ++c.count;
+        c.items = (fi += items[i]);
+        c.smem = std::max(c.smem, fs_batch_smem(fa.data() + k * fsz, c.threads));
+        fe[k] = fi;
+        int64_t sblocks = 0, lblocks = 0;
         size_t ssm = 0;
-        MGT_TRY_STATUS(fs_batch_args(m, fa.data() + k * fsz, &bd, &items));
         MGT_TRY_STATUS(se_batch_args(m, sa.data() + k * ssz, &sblocks, &ssm));
         MGT_TRY_STATUS(ld_batch_args(m, la.data() + k * lsz, &lblocks));
-        threads = std::max(threads, bd);
         se_smem = std::max(se_smem, ssm);
-        fe[k] = (fi += items);
         se[k] = (si += sblocks);
         le[k] = (li += lblocks);
     }
     if (li > 0x7fffffffLL || si > 0x7fffffffLL)
         return set_error(MGT_ERR_ARG, "batch: too many points for one launch");
-    size_t fs_smem = 0;
-    for (int k = 0; k < n; ++k) fs_smem = std::max(fs_smem, fs_batch_smem(fa.data() + k * fsz, threads));
-    if (fs_smem > 227 * 1024) return set_error(MGT_ERR_ARG, "batch: formal-solution shared memory above 227 KB");
+    size_t max_smem = 0;
+    for (const mgt_batch::FsClass &c : classes) max_smem = std::max(max_smem, c.smem);
+    if (max_smem > 227 * 1024) return set_error(MGT_ERR_ARG, "batch: formal-solution shared memory above 227 KB");
+    for (mgt_batch::FsClass &c : classes) MGT_TRY_STATUS(fs_batch_grid(c.threads, c.smem, max_smem, &c.grid));
 
     const bool same = order == b->order && fa == b->fs_args && sa == b->se_args && la == b->ld_args &&
-                      threads == b->fs_threads && fs_smem == b->fs_smem && se_smem == b->se_smem;
+                      classes == b->fs_classes && se_smem == b->se_smem;
     if (same && b->d_next) return MGT_OK;
     drop_graph(b);
+    if (b->d_next && classes.size() != b->fs_classes.size()) {
+        MGT_CUDA(cudaStreamSynchronize(s));
+        MGT_CUDA(cudaFree(b->d_next));
+        b->d_next = nullptr;
+    }
     b->order = order;
     b->fs_args = fa;
     b->se_args = sa;
@@ -125,10 +161,8 @@ mgt_status refresh(mgt_batch *b, cudaStream_t s)
     b->fs_end = fe;
     b->se_end = se;
     b->ld_end = le;
-    b->fs_threads = threads;
-    b->fs_smem = fs_smem;
+    b->fs_classes = classes;
     b->se_smem = se_smem;
-    MGT_TRY_STATUS(fs_batch_grid(threads, fs_smem, &b->fs_grid));
     MGT_TRY_STATUS(se_batch_prepare(se_smem));
     MGT_TRY_STATUS(upload(&b->d_fs_args, fa, fa.size(), s));
     MGT_TRY_STATUS(upload(&b->d_se_args, sa, sa.size(), s));
@@ -136,7 +170,7 @@ mgt_status refresh(mgt_batch *b, cudaStream_t s)
     MGT_TRY_STATUS(upload(&b->d_fs_end, fe, n, s));
     MGT_TRY_STATUS(upload(&b->d_se_end, se, n, s));
     MGT_TRY_STATUS(upload(&b->d_ld_end, le, n, s));
-    if (!b->d_next) MGT_CUDA(cudaMalloc(&b->d_next, sizeof(unsigned long long)));
+    if (!b->d_next) MGT_CUDA(cudaMalloc(&b->d_next, sizeof(unsigned long long) * classes.size()));
     // the host vectors must outlive the copies
     MGT_CUDA(cudaStreamSynchronize(s));
     return MGT_OK;
@@ -146,8 +180,13 @@ mgt_status launch_fs(mgt_batch *b, cudaStream_t s)
 {
     const int n = (int)b->models.size();
     MGT_TRY_STATUS(ld_batch_launch(b->d_ld_args, b->d_ld_end, n, b->ld_end.back(), s));
-    return fs_batch_launch(b->d_fs_args, b->d_fs_end, n, b->fs_end.back(), b->d_next, b->fs_threads, b->fs_smem,
-                           b->fs_grid, s);
+    const size_t fsz = fs_args_bytes();
+    for (size_t c = 0; c < b->fs_classes.size(); ++c) {
+        const mgt_batch::FsClass &k = b->fs_classes[c];
+        MGT_TRY_STATUS(fs_batch_launch(b->d_fs_args + k.first * fsz, b->d_fs_end + k.first, k.count, k.items,
+                                       b->d_next + c, k.threads, k.smem, k.grid, s));
+    }
+    return MGT_OK;
 }
 
 mgt_status launch_se(mgt_batch *b, cudaStream_t s)
@@ -314,10 +353,17 @@ mgt_status mgt_batch_get_layout(const mgt_batch *b, mgt_batch_layout *layout, in
     if (!b) return set_error(MGT_ERR_ARG, "batch is NULL");
     if (layout) {
         layout->n_models = (int32_t)b->models.size();
-        layout->fs_items = b->fs_end.empty() ? 0 : b->fs_end.back();
-        layout->fs_grid = b->fs_grid;
-        layout->fs_threads = b->fs_threads;
-        layout->fs_smem_bytes = (int64_t)b->fs_smem;
+        layout->fs_items = 0;
+        layout->fs_grid = 0;
+        layout->fs_threads = 0;
+        layout->fs_smem_bytes = 0;
+        for (const mgt_batch::FsClass &c : b->fs_classes) {
+            layout->fs_items += c.items;
+            layout->fs_grid += c.grid;
+            layout->fs_threads = std::max(layout->fs_threads, c.threads);
+            layout->fs_smem_bytes = std::max<int64_t>(layout->fs_smem_bytes, (int64_t)c.smem);
+        }
+        layout->fs_launches = (int32_t)b->fs_classes.size();
         layout->se_blocks = b->se_end.empty() ? 0 : b->se_end.back();
         layout->graph_kernels = b->graph_kernels;
     }

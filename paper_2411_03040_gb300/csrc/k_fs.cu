@@ -1099,10 +1099,10 @@ size_t fs_batch_smem(const void *args, int bd)
                       : (size_t)staged_layout<float, 8, kChunk>(a.Q, Mb, a.RS, bd, a.P).total;
 }
 
-mgt_status fs_batch_grid(int bd, size_t smem, int *grid)
+mgt_status fs_batch_grid(int bd, size_t smem, size_t max_smem, int *grid)
 {
     auto kern = k_fs_batch<float, kChunk>;
-    MGT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MGT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
     int dev = 0, sms = 0, per_sm = 0;
     MGT_CUDA(cudaGetDevice(&dev));
     MGT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

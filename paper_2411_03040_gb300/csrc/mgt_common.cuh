@@ -182,7 +182,7 @@ int fs_lines_per_thread(const mgt_model *m, mgt_precision p);
 size_t fs_args_bytes();
 mgt_status fs_batch_args(const mgt_model *m, void *args, int *threads, int64_t *items);
 size_t fs_batch_smem(const void *args, int threads);
-mgt_status fs_batch_grid(int threads, size_t smem, int *grid);
+mgt_status fs_batch_grid(int threads, size_t smem, size_t max_smem, int *grid);
 mgt_status fs_batch_launch(const void *d_args, const int64_t *d_item_end, int n_models, int64_t n_items,
                            unsigned long long *d_next, int threads, size_t smem, int grid, cudaStream_t s);
 size_t se_args_bytes();

@@ -66,7 +66,7 @@ class mgt_autotune_result(ctypes.Structure):
 
 class mgt_batch_layout(ctypes.Structure):
     _fields_ = [("n_models", _i32), ("fs_items", _i64), ("fs_grid", _i32), ("fs_threads", _i32),
-                ("fs_smem_bytes", _i64), ("se_blocks", _i64), ("graph_kernels", _i32)]
+                ("fs_smem_bytes", _i64), ("se_blocks", _i64), ("graph_kernels", _i32), ("fs_launches", _i32)]
 
 
 # name -> argtypes (every function returns an int status, except mgt_last_error)

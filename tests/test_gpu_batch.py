@@ -60,6 +60,7 @@ def test_batch_formal_solve_and_se_match_single_model_calls(mgt, batch_models):
     assert lay["n_models"] == len(hs)
     assert lay["graph_kernels"] == 0
     assert lay["fs_threads"] == 160                       # 31 bins x 5 groups of 8 lines, in warps
+    assert lay["fs_launches"] == 2                        # CTA widths 160 and 32
     # launch order: most work per item first
     assert sorted(lay["order"].tolist()) == list(range(len(hs)))
     mgt.mgt_batch_formal_solve(b)
@@ -101,7 +102,7 @@ def test_batch_iterate_graph_matches_ali_per_model(mgt, batch_models, ng_mode):
     n0 = mgt.mgt_launch_count()
     stats = mgt.mgt_batch_iterate(b, n_iter=n_iter, ng_mode=ng_mode, n_steps=3, want_stats=True)
     lay = mgt.mgt_batch_get_layout(b)
-    assert lay["graph_kernels"] == 3                      # line data, formal solution, SE
+    assert lay["graph_kernels"] == 2 + lay["fs_launches"]  # line data, formal solution per width, SE
     assert mgt.mgt_launch_count() - n0 >= 3 * n_iter
     for h, (P, st), bs in zip(hs, ref, stats):
         np.testing.assert_array_equal(mgt.mgt_get_populations(h), P)
@@ -110,7 +111,7 @@ def test_batch_iterate_graph_matches_ali_per_model(mgt, batch_models, ng_mode):
         assert bs["last_maxrel"] == st["last_maxrel"]
     # a second call replays the same graph
     mgt.mgt_batch_iterate(b, n_iter=1)
-    assert mgt.mgt_batch_get_layout(b)["graph_kernels"] == 3
+    assert mgt.mgt_batch_get_layout(b)["graph_kernels"] == 2 + lay["fs_launches"]
 
 
 def test_batch_follows_model_changes(mgt, batch_models):
