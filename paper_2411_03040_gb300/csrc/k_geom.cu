@@ -386,8 +386,11 @@ struct ImgWalkArgs {
     double n[3];              // unit direction toward the observer
 };
 
+// Four blocks of 256 per SM (registers capped at 64): the walk is bound by
+// dependent latency (L2 row loads, shuffle chains), and 32 resident warps per
+// SM beat the spill-free 93-register build at 16 (workload 2 trace: 91 -> 73 ms).
 template <int MODE>
-__global__ void __launch_bounds__(256) k_walk(WalkArgs a, int64_t *__restrict__ lens, const int64_t *__restrict__ ray_off,
+__global__ void __launch_bounds__(256, 4) k_walk(WalkArgs a, int64_t *__restrict__ lens, const int64_t *__restrict__ ray_off,
                                               const int64_t *__restrict__ list, int64_t n_list, int32_t K,
                                               unsigned long long *__restrict__ n_stall,
                                               const float *__restrict__ vel_hl, const float2 *__restrict__ w32,
