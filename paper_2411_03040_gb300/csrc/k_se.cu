@@ -81,8 +81,15 @@ __device__ __forceinline__ void se_point(const SEArgs &a, int64_t p, double *sm,
     const double *E = a.level_tab, *g = a.level_tab + L;
     const double ikT = 1.0 / (kKB * Tp);
     // one exponential per level instead of one per collisional pair: the
-    // upward rate C_lu = C_ul (g_u/g_l) exp(-(E_u - E_l)/kT) = C_ul bz_u / bz_l
-    for (int i = lane; i < L; i += 32) bz[i] = g[i] * exp(-(E[i] - E[0]) * ikT);
+    // upward rate C_lu = C_ul (g_u/g_l) exp(-(E_u - E_l)/kT) = C_ul bz_u / bz_l,
+    // formed with 1/bz_l from one division per level (kept in xx until the
+    // populations need it; FP64 division is a long sequence on this GPU's
+    // narrow FP64 pipe, and there are L^2/2 upward pairs)
+    for (int i = lane; i < L; i += 32) {
+        const double b = g[i] * exp(-(E[i] - E[0]) * ikT);
+        bz[i] = b;
+        xx[i] = b > 1e-290 ? 1.0 / b : 0.0;
+    }
     __syncwarp();
     for (int e = lane; e < LL; e += 32) {
         const int i = e / L, j = e - i * L;
@@ -97,7 +104,7 @@ __device__ __forceinline__ void se_point(const SEArgs &a, int64_t p, double *sm,
                 if (i == cu)
                     v += Cul;
                 else if (bz[cl] > 1e-290 && bz[cu] > 1e-290)
-                    v += Cul * bz[cu] / bz[cl];
+                    v += Cul * bz[cu] * xx[cl];
                 else   // a factor near the bottom of the FP64 range: the pair's own exponential
                     v += Cul * g[cu] / g[cl] * exp(-(E[cu] - E[cl]) * ikT);
             }
