@@ -397,8 +397,7 @@ def run_mine(args, model, cfg):
                 he = mgt.mgt_model_create(pm, stream=stream)
                 mgt.mgt_trace_rays(he, stream=stream)
                 mgt.mgt_formal_solve(he, mgt.MGT_FP32_MIXED, want=False, stream=stream)
-                res = mgt.mgt_stat_equilibrium(he, want=True, stream=stream)
-                pops_host[...] = res
+                mgt.mgt_stat_equilibrium(he, want=True, out=pops_host, stream=stream)
                 mgt.mgt_ng_accelerate(he, mgt.MGT_NG_ADAPTIVE, n_max=8, stream=stream)
                 he.close()
             torch.cuda.synchronize()

@@ -246,40 +246,6 @@ template <typename T> static mgt_status upload(T *dst, const T *src, size_t n, c
         if (st_ != MGT_OK) return st_;     \
     } while (0)
 
-// Points sorted along a Morton (Z-order) curve of their positions: walks and
-// origins visited in this order keep neighbouring work close in memory.
-static std::vector<int32_t> morton_order(const double *pos, int64_t N)
-{
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int64_t i = 0; i < N; ++i)
-        for (int d = 0; d < 3; ++d) {
-            lo[d] = std::min(lo[d], pos[3 * i + d]);
-            hi[d] = std::max(hi[d], pos[3 * i + d]);
-        }
-    auto spread = [](uint64_t v) {
-        v &= 0x1fffff;
-        v = (v | v << 32) & 0x1f00000000ffffULL;
-        v = (v | v << 16) & 0x1f0000ff0000ffULL;
-        v = (v | v << 8) & 0x100f00f00f00f00fULL;
-        v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
-        v = (v | v << 2) & 0x1249249249249249ULL;
-        return v;
-    };
-    std::vector<std::pair<uint64_t, int32_t>> key(N);
-    for (int64_t i = 0; i < N; ++i) {
-        uint64_t k = 0;
-        for (int d = 0; d < 3; ++d) {
-            const double span = hi[d] > lo[d] ? hi[d] - lo[d] : 1.0;
-            const uint64_t q = (uint64_t)std::min(2097151.0, std::max(0.0, (pos[3 * i + d] - lo[d]) / span * 2097151.0));
-            k |= spread(q) << d;
-        }
-        key[i] = {k, (int32_t)i};
-    }
-    std::sort(key.begin(), key.end());
-    std::vector<int32_t> out(N);
-    for (int64_t i = 0; i < N; ++i) out[i] = key[i].second;
-    return out;
-}
 
 static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_t s)
 {
@@ -405,32 +371,24 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
     MGT_TRY(upload(m->d_nspec, d->n_spec, N, s));
     MGT_TRY(upload(m->d_nbr_off, off32.data(), N + 1, s));
     MGT_TRY(upload(m->d_nbrs, d->nbrs, m->nnz, s));
+    MGT_TRY(upload(m->d_bnd, bnd.data(), N, s));
     {
-        std::vector<double> np(3 * (size_t)m->nnz);
-        double xmax = 0.0;
-        for (int64_t i = 0; i < 3 * N; ++i) xmax = std::max(xmax, std::fabs(d->pos[i]));
         // exact power-of-two scaling that brings coordinates to order one, so
-        // FP32 squared distances cannot overflow
+        // FP32 squared distances cannot overflow; the bounding box for the
+        // visiting order
+        double xmax = 0.0, lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int64_t i = 0; i < N; ++i)
+            for (int c = 0; c < 3; ++c) {
+                const double x = d->pos[3 * i + c];
+                xmax = std::max(xmax, std::fabs(x));
+                lo[c] = std::min(lo[c], x);
+                hi[c] = std::max(hi[c], x);
+            }
         int ex = 0;
         std::frexp(xmax > 0.0 ? xmax : 1.0, &ex);
         m->pos_scale = std::ldexp(1.0, -ex);
-        for (int64_t k = 0; k < m->nnz; ++k)
-            for (int c = 0; c < 3; ++c) np[3 * k + c] = d->pos[3 * (int64_t)d->nbrs[k] + c];
         // |xs - (hi + lo)| <= 2^-24 |lo| <= 2^-48 |xs| <= 2^-48; four times that, for both endpoints
         m->pos_slack = (float)std::ldexp(1.0, -46);
-        // per point: the scaled position and v/c, each split into float hi + lo
-        std::vector<float> phl(6 * (size_t)N), vhl(6 * (size_t)N);
-        for (int64_t i = 0; i < N; ++i)
-            for (int c = 0; c < 3; ++c) {
-                const double xs = d->pos[3 * i + c] * m->pos_scale;
-                const float hi = (float)xs;
-                phl[6 * i + c] = hi;
-                phl[6 * i + 3 + c] = (float)(xs - (double)hi);
-                const double vb = d->vel[3 * i + c] / kC;
-                const float vh = (float)vb;
-                vhl[6 * i + c] = vh;
-                vhl[6 * i + 3 + c] = (float)(vb - (double)vh);
-            }
         // packed walk rows: every point's neighbours in CSR order, the last one
         // flagged; an empty row holds one kEntEmpty entry; 16 pad entries
         std::vector<int32_t> eoff(N);
@@ -440,56 +398,19 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
             const int64_t deg = d->nbr_offsets[i + 1] - d->nbr_offsets[i];
             ne += deg > 0 ? deg : 1;
         }
-        std::vector<float4> ent(2 * (size_t)(ne + 16));
-        auto put = [&](int64_t e, int64_t mpt, uint32_t word) {
-            float v[6] = {0, 0, 0, 0, 0, 0};
-            if (mpt >= 0)
-                for (int c = 0; c < 3; ++c) {
-                    v[c] = phl[6 * mpt + c];
-                    v[3 + c] = phl[6 * mpt + 3 + c];
-                }
-            const int32_t noff = mpt >= 0 ? eoff[mpt] : 0;
-            ent[2 * e] = make_float4(v[0], v[1], v[2], v[3]);
-            float4 b;
-            b.x = v[4];
-            b.y = v[5];
-            std::memcpy(&b.z, &word, 4);
-            std::memcpy(&b.w, &noff, 4);
-            ent[2 * e + 1] = b;
-        };
-        for (int64_t i = 0; i < N; ++i) {
-            const int64_t k0 = d->nbr_offsets[i], k1 = d->nbr_offsets[i + 1];
-            if (k1 == k0) {
-                put(eoff[i], -1, kEntEmpty | kEntLast);
-                continue;
-            }
-            for (int64_t k = k0; k < k1; ++k) {
-                const int64_t mpt = d->nbrs[k];
-                uint32_t word = (uint32_t)mpt;
-                if (k == k1 - 1) word |= kEntLast;
-                if (bnd[mpt]) word |= kEntBnd;
-                put(eoff[i] + (k - k0), mpt, word);
-            }
-        }
-        for (int64_t e = ne; e < ne + 16; ++e) put(e, -1, kEntEmpty | kEntLast);
         m->n_ent = ne + 16;
-        MGT_TRY(dalloc(&m->d_ent, ent.size()));
+        MGT_TRY(dalloc(&m->d_ent, 2 * (size_t)m->n_ent));
         MGT_TRY(dalloc(&m->d_ent_off, (size_t)N));
-        MGT_TRY(upload(m->d_ent, ent.data(), ent.size(), s));
         MGT_TRY(upload(m->d_ent_off, eoff.data(), (size_t)N, s));
         std::vector<float4> d32(m->R);
         for (int r = 0; r < m->R; ++r)
             d32[r] = make_float4((float)d->dirs[3 * r], (float)d->dirs[3 * r + 1], (float)d->dirs[3 * r + 2], 0.0f);
-        MGT_TRY(upload(m->d_nbr_pos, np.data(), np.size(), s));
-        MGT_TRY(upload(m->d_pos_hl, phl.data(), phl.size(), s));
-        MGT_TRY(upload(m->d_vel_hl, vhl.data(), vhl.size(), s));
         MGT_TRY(upload(m->d_dirs32, d32.data(), d32.size(), s));
+        // hi + lo splits, neighbour positions, packed rows and the visiting order
+        MGT_TRY(build_walk_tables(m, lo, hi, s));
         MGT_CUDA(cudaStreamSynchronize(s));   // the host staging vectors go out of scope
-        const std::vector<int32_t> ord = morton_order(d->pos, N);
-        MGT_TRY(upload(m->d_order, ord.data(), (size_t)N, s));
-        MGT_CUDA(cudaStreamSynchronize(s));
     }
-    MGT_TRY(upload(m->d_bnd, bnd.data(), N, s));
+
     MGT_TRY(upload(m->d_dirs, d->dirs, 3 * (size_t)m->R, s));
     std::vector<int2> pr(m->P);
     for (int p = 0; p < m->P; ++p) pr[p] = make_int2(m->pairs[2 * p], m->pairs[2 * p + 1]);

@@ -35,6 +35,157 @@ mgt_status launch_widths(mgt_model *m, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------------------
+// Walk tables built on the device at model set-up (from the uploaded
+// positions, velocities, neighbour lists and boundary mask):
+//  * positions times pos_scale and v/c, each split into float hi + lo;
+//  * the FP64 position of every neighbour entry;
+//  * the packed neighbour rows (see WalkEntry in mgt_common.cuh);
+//  * the Morton (Z-curve) visiting order of the points: 21 bits per axis of
+//    the point's place in the bounding box, sorted with ties to the lower
+//    index.
+// The arithmetic is the host definition's (IEEE operations, no contraction),
+// so the tables do not depend on where they are built.
+// ---------------------------------------------------------------------------
+__global__ void k_split_hl(int64_t N, const double *__restrict__ pos, const double *__restrict__ vel, double scale,
+                           double inv_c, float *__restrict__ pos_hl, float *__restrict__ vel_hl)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= 3 * N) return;
+    const int64_t i = t / 3;
+    const int c = (int)(t - 3 * i);
+    const double xs = __dmul_rn(pos[t], scale);
+    const float hi = __double2float_rn(xs);
+    pos_hl[6 * i + c] = hi;
+    pos_hl[6 * i + 3 + c] = __double2float_rn(__dsub_rn(xs, (double)hi));
+    const double vb = __dmul_rn(vel[t], inv_c);
+    const float vh = __double2float_rn(vb);
+    vel_hl[6 * i + c] = vh;
+    vel_hl[6 * i + 3 + c] = __double2float_rn(__dsub_rn(vb, (double)vh));
+}
+
+__global__ void k_nbr_pos(int64_t nnz, const int32_t *__restrict__ nb, const double *__restrict__ pos,
+                          double *__restrict__ nb_pos)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= 3 * nnz) return;
+    const int64_t k = t / 3;
+    nb_pos[t] = pos[3 * (int64_t)nb[k] + (t - 3 * k)];
+}
+
+__device__ __forceinline__ void put_entry(float4 *ent, int64_t e, const float *phl, int64_t mpt, uint32_t word,
+                                          int32_t noff)
+{
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (mpt >= 0)
+        for (int c = 0; c < 6; ++c) v[c] = phl[6 * mpt + c];
+    ent[2 * e] = make_float4(v[0], v[1], v[2], v[3]);
+    ent[2 * e + 1] = make_float4(v[4], v[5], __uint_as_float(word), __int_as_float(noff));
+}
+
+// One thread per point (rows of ~15 entries), then the 16 pad entries.
+__global__ void k_pack_rows(int64_t N, int64_t ne, const int32_t *__restrict__ off, const int32_t *__restrict__ nb,
+                            const uint8_t *__restrict__ bnd, const float *__restrict__ phl,
+                            const int32_t *__restrict__ eoff, float4 *__restrict__ ent)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N + 16) return;
+    if (i >= N) {
+        put_entry(ent, ne + (i - N), phl, -1, kEntEmpty | kEntLast, 0);
+        return;
+    }
+    const int32_t k0 = off[i], k1 = off[i + 1];
+    const int64_t e0 = eoff[i];
+    if (k1 == k0) {
+        put_entry(ent, e0, phl, -1, kEntEmpty | kEntLast, 0);
+        return;
+    }
+    for (int32_t k = k0; k < k1; ++k) {
+        const int32_t mpt = nb[k];
+        uint32_t word = (uint32_t)mpt;
+        if (k == k1 - 1) word |= kEntLast;
+        if (bnd[mpt]) word |= kEntBnd;
+        put_entry(ent, e0 + (k - k0), phl, mpt, word, eoff[mpt]);
+    }
+}
+
+__device__ __forceinline__ uint64_t morton_spread(uint64_t v)
+{
+    v &= 0x1fffff;
+    v = (v | v << 32) & 0x1f00000000ffffULL;
+    v = (v | v << 16) & 0x1f0000ff0000ffULL;
+    v = (v | v << 8) & 0x100f00f00f00f00fULL;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+    v = (v | v << 2) & 0x1249249249249249ULL;
+    return v;
+}
+
+__global__ void k_morton_keys(int64_t N, const double *__restrict__ pos, double lo0, double lo1, double lo2,
+                              double sp0, double sp1, double sp2, uint64_t *__restrict__ key,
+                              int32_t *__restrict__ idx)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double lo[3] = {lo0, lo1, lo2}, sp[3] = {sp0, sp1, sp2};
+    uint64_t k = 0;
+    for (int d = 0; d < 3; ++d) {
+        const double x = __dmul_rn(__ddiv_rn(__dsub_rn(pos[3 * i + d], lo[d]), sp[d]), 2097151.0);
+        const uint64_t q = (uint64_t)fmin(2097151.0, fmax(0.0, x));
+        k |= morton_spread(q) << d;
+    }
+    key[i] = k;
+    idx[i] = (int32_t)i;
+}
+
+mgt_status build_walk_tables(mgt_model *m, const double lo[3], const double hi[3], cudaStream_t s)
+{
+    const int64_t N = m->N;
+    k_split_hl<<<ceil_div(3 * N, 256), 256, 0, s>>>(N, m->d_pos, m->d_vel, m->pos_scale, 1.0 / kC, m->d_pos_hl,
+                                                    m->d_vel_hl);
+    MGT_LAUNCH_CHECK("k_split_hl");
+    if (m->nnz > 0) {
+        k_nbr_pos<<<ceil_div(3 * m->nnz, 256), 256, 0, s>>>(m->nnz, m->d_nbrs, m->d_pos, m->d_nbr_pos);
+        MGT_LAUNCH_CHECK("k_nbr_pos");
+    }
+    k_pack_rows<<<ceil_div(N + 16, 128), 128, 0, s>>>(N, m->n_ent - 16, m->d_nbr_off, m->d_nbrs, m->d_bnd,
+                                                      m->d_pos_hl, m->d_ent_off, m->d_ent);
+    MGT_LAUNCH_CHECK("k_pack_rows");
+    // Morton order: keys, then a stable radix sort of (key, index)
+    uint64_t *keys = nullptr;
+    int32_t *idx = nullptr;
+    void *tmp = nullptr;
+    size_t tmp_bytes = 0;
+    mgt_status st = MGT_OK;
+    auto fail = [&](cudaError_t e, const char *what) {
+        if (st == MGT_OK) st = cuda_status(e, what);
+    };
+    cudaError_t e = cudaMallocAsync(&keys, sizeof(uint64_t) * 2 * N, s);
+    if (e != cudaSuccess) fail(e, "cudaMallocAsync");
+    if (st == MGT_OK && (e = cudaMallocAsync(&idx, sizeof(int32_t) * N, s)) != cudaSuccess) fail(e, "cudaMallocAsync");
+    double sp[3];
+    for (int d = 0; d < 3; ++d) sp[d] = hi[d] > lo[d] ? hi[d] - lo[d] : 1.0;
+    if (st == MGT_OK) {
+        k_morton_keys<<<ceil_div(N, 256), 256, 0, s>>>(N, m->d_pos, lo[0], lo[1], lo[2], sp[0], sp[1], sp[2], keys,
+                                                      idx);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) fail(e, "k_morton_keys");
+        else note_launch();
+    }
+    if (st == MGT_OK &&
+        (e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys + N, idx, m->d_order, (int)N, 0, 64,
+                                             s)) != cudaSuccess)
+        fail(e, "cub::DeviceRadixSort::SortPairs");
+    if (st == MGT_OK && (e = cudaMallocAsync(&tmp, tmp_bytes, s)) != cudaSuccess) fail(e, "cudaMallocAsync");
+    if (st == MGT_OK &&
+        (e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys + N, idx, m->d_order, (int)N, 0, 64, s)) !=
+            cudaSuccess)
+        fail(e, "cub::DeviceRadixSort::SortPairs");
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (idx) cudaFreeAsync(idx, s);
+    if (keys) cudaFreeAsync(keys, s);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
 // LTE: n_i = n_spec g_i exp(-(E_i - E_0)/kT) / sum_j g_j exp(-(E_j - E_0)/kT).
 // ---------------------------------------------------------------------------
 __global__ void k_lte(int64_t N, int L, const double *__restrict__ T, const double *__restrict__ nspec,

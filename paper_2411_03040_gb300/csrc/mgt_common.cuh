@@ -160,6 +160,7 @@ mgt_status check_device_error(mgt_model *m, cudaStream_t s);
 mgt_status launch_widths(mgt_model *m, cudaStream_t s);
 mgt_status launch_lte(mgt_model *m, cudaStream_t s);
 mgt_status launch_line_data(mgt_model *m, cudaStream_t s);
+mgt_status build_walk_tables(mgt_model *m, const double lo[3], const double hi[3], cudaStream_t s);
 mgt_status trace_all(mgt_model *m, cudaStream_t s);
 mgt_status trace_range(mgt_model *m, cudaStream_t s, int32_t p0, int32_t np);
 mgt_status build_steps64(mgt_model *m, cudaStream_t s);

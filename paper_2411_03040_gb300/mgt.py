@@ -273,11 +273,13 @@ def mgt_get_jbar(m: Model, Jbar=None, Lstar=None, stream=None):
     return Jbar, Lstar
 
 
-def mgt_stat_equilibrium(m: Model, want=True, stream=None):
-    out = None
-    if want:
+def mgt_stat_equilibrium(m: Model, want=True, stream=None, out=None):
+    """New populations [N][L]; into ``out`` (host array, e.g. pinned) if given."""
+    if want and out is None:
         s = mgt_model_sizes(m)
         out = np.zeros((s["n_points"], s["n_levels"]), np.float64)
+    if not want:
+        out = None
     _check(load().mgt_stat_equilibrium(m.handle, _ptr(out), _stream(stream)), "mgt_stat_equilibrium")
     return out
 
