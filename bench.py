@@ -285,19 +285,25 @@ def run_mine(args, model, cfg):
         tst = mgt.mgt_trace_rays(h, stream=stream)
 
         fs_ev = []
+        part_ev = []           # per timed step: events after trace, formal solution, SE
 
         def step(record):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+            if record:
+                evs[0].record(stream)
             # with pair batches the formal solution traces each batch itself
             if not batch:
                 mgt.mgt_trace_rays(h, stream=stream)
             if record:
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
+                evs[1].record(stream)
             mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED, want=False, stream=stream)
             if record:
-                b.record(stream)
-                fs_ev.append((a, b))
+                evs[2].record(stream)
+                fs_ev.append((evs[1], evs[2]))
             mgt.mgt_stat_equilibrium(h, want=False, stream=stream)
+            if record:
+                evs[3].record(stream)
+                part_ev.append(evs)
             mgt.mgt_ng_accelerate(h, mgt.MGT_NG_ADAPTIVE, n_max=8, stream=stream)
 
         for _ in range(max(3, args.warmup)):
@@ -323,6 +329,8 @@ def run_mine(args, model, cfg):
         clk = clocks.stop()
         ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
         fs_ms = sum(a.elapsed_time(b) for a, b in fs_ev) / args.steps
+        trace_ms = sum(e[0].elapsed_time(e[1]) for e in part_ev) / args.steps
+        se_ms = sum(e[2].elapsed_time(e[3]) for e in part_ev) / args.steps
         fs_source = "CUDA events around mgt_formal_solve"
         if batch:
             # the batched formal solution includes the trace of each batch:
@@ -333,6 +341,7 @@ def run_mine(args, model, cfg):
             b.record(stream)
             torch.cuda.synchronize()
             fs_ms -= a.elapsed_time(b)
+            trace_ms = a.elapsed_time(b)
             fs_source = "mgt_formal_solve (pair batches, traces included) minus a separately timed trace of all batches"
         ms = allreduce_max(world, ms)
         value = world * units / (ms * 1e-3)
@@ -377,6 +386,15 @@ def run_mine(args, model, cfg):
         "launch_ms": fs_ms, "launch_ms_source": fs_source, "step_ms": ms, "share_of_step": fs_ms / ms}
     if batch:
         out["config"]["pairs_per_batch"] = batch
+    # where the step goes, and the secondary unit: ray steps (points on a full
+    # ray through the origin, both halves and the origin) per second over all
+    # formal solutions
+    pairs = model.dirs.shape[0] // 2
+    out["step_breakdown_ms"] = {"trace": trace_ms, "formal_solve": fs_ms, "stat_equilibrium": se_ms,
+                                "ng_and_gaps": ms - trace_ms - fs_ms - se_ms,
+                                "source": "CUDA events on the library's stream inside the timed steps"}
+    out["ray_steps_per_s"] = {"value": model.n_quad * (tst["total_steps"] + model.n_points * pairs) / (fs_ms * 1e-3),
+                              "unit": "ray steps/s (formal solve)"}
     out["gpu_launches"] = launches
     out["clocks"] = clk
     out["trace"] = tst
