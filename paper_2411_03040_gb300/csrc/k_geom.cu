@@ -633,8 +633,9 @@ __global__ void __launch_bounds__(256, 4) k_walk(WalkArgs a, int64_t *__restrict
     // the site and returns
     const uint64_t t_start = walk_clock_ns();
     bool gave_up = false;
+    uint32_t iter = 0;                          // the same in every lane (the loop test is a warp vote)
     while (!__all_sync(full, done)) {
-        if (__any_sync(full, walk_clock_ns() - t_start > 2000000000ull)) {
+        if ((++iter & 15u) == 0u && __any_sync(full, walk_clock_ns() - t_start > 2000000000ull)) {
             if (sl == 0 && !done) walk_give_up(err, 1, wg, n);
             gave_up = true;
             break;
