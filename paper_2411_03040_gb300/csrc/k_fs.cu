@@ -253,7 +253,7 @@ __device__ __forceinline__ void eliminate_row_scalar(T cf, T cn, const T (&chi_f
 }
 
 // The same row in FP32 on line pairs with Blackwell's packed FP32 operations
-// (two lanes of arithmetic per issue slot): four packed operations and two
+// (two lanes of arithmetic per issue slot): eight packed operations and two
 // reciprocals per pair of lines, so 5 issue slots per line and step instead of 9.
 template <int LPT>
 __device__ __forceinline__ void eliminate_row_packed(float cf, float cn, const float (&chi_f)[LPT],
