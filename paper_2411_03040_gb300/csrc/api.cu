@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <set>
 #include <string>
 #include <utility>
@@ -18,6 +19,51 @@ static std::atomic<long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Scratch pools, one per device, and the number of live models per device.
+constexpr int kMaxPoolDevices = 64;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[kMaxPoolDevices];
+static int g_live_models[kMaxPoolDevices];
+
+mgt_status scratch_pool(cudaMemPool_t *pool)
+{
+    int dev = 0;
+    MGT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxPoolDevices) return set_error(MGT_ERR_ARG, "device id too large for the scratch pool");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        MGT_CUDA(cudaMemPoolCreate(&p, &props));
+        uint64_t keep = ~0ull;
+        cudaError_t e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return cuda_status(e, "cudaMemPoolSetAttribute");
+        }
+        g_pools[dev] = p;
+    }
+    *pool = g_pools[dev];
+    return MGT_OK;
+}
+
+static void model_born(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev >= 0 && dev < kMaxPoolDevices) ++g_live_models[dev];
+}
+
+// The last model of a device gone: give the pool's reserve back to the driver.
+static void model_gone(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= kMaxPoolDevices) return;
+    if (g_live_models[dev] > 0 && --g_live_models[dev] == 0 && g_pools[dev]) cudaMemPoolTrimTo(g_pools[dev], 0);
+}
 
 mgt_status set_error(mgt_status s, const std::string &msg)
 {
@@ -511,6 +557,7 @@ mgt_status mgt_model_create(mgt_model **out, const mgt_model_desc *desc, void *s
         g_last_error = keep;
         return st;
     }
+    model_born(m->device);
     *out = m;
     return MGT_OK;
 }
@@ -519,7 +566,9 @@ mgt_status mgt_model_destroy(mgt_model *m)
 {
     if (!m) return MGT_OK;
     cudaDeviceSynchronize();
+    const int dev = m->device;
     free_model(m);
+    model_gone(dev);
     return MGT_OK;
 }
 

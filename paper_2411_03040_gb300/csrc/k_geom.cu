@@ -926,11 +926,18 @@ mgt_status trace_range(mgt_model *m, cudaStream_t s, int32_t p0, int32_t np)
     if (!m->d_ray_off) MGT_CUDA(cudaMalloc(&m->d_ray_off, sizeof(int64_t) * ((int64_t)m->R * m->N + 1)));
     // Scratch slot per walk: K records, a multiple of 16; the longest half-ray
     // of this model's previous trace when there was one (64 otherwise), kept
-    // within a third of the free device memory.  Longer walks are redone.
+    // within a third of the free device memory (counting what the scratch
+    // pool holds unused).  Longer walks are redone.
     int64_t K = m->max_half > 0 ? (m->max_half + 15) / 16 * 16 : 64;
+    cudaMemPool_t pool = nullptr;
+    MGT_TRY_STATUS(scratch_pool(&pool));
     {
         size_t freeb = 0, totalb = 0;
         MGT_CUDA(cudaMemGetInfo(&freeb, &totalb));
+        uint64_t reserved = 0, used = 0;
+        MGT_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+        MGT_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+        freeb += reserved > used ? (size_t)(reserved - used) : 0;
         while (K > 16 && (size_t)(W * K) * sizeof(Step32) > freeb / 3) K -= 16;
     }
     int64_t *d_len = nullptr, *d_list = nullptr, *d_max = nullptr;
@@ -950,10 +957,11 @@ mgt_status trace_range(mgt_model *m, cudaStream_t s, int32_t p0, int32_t np)
         decltype(release) &f;
         ~Guard() { f(); }
     } guard{release};
-    MGT_CUDA(cudaMallocAsync(&d_len, sizeof(int64_t) * (W + 1), s));
-    MGT_CUDA(cudaMallocAsync(&d_list, sizeof(int64_t) * W, s));
-    MGT_CUDA(cudaMallocAsync(&d_nover, sizeof(unsigned long long), s));
-    if (cudaMallocAsync(&d_scratch, sizeof(Step32) * W * K, s) != cudaSuccess) {
+    MGT_CUDA(cudaMallocFromPoolAsync(&d_len, sizeof(int64_t) * (W + 1), pool, s));
+    MGT_CUDA(cudaMallocFromPoolAsync(&d_list, sizeof(int64_t) * W, pool, s));
+    MGT_CUDA(cudaMallocFromPoolAsync(&d_nover, sizeof(unsigned long long), pool, s));
+    if (cudaMallocFromPoolAsync(&d_scratch, sizeof(Step32) * W * K, pool, s) != cudaSuccess) {
+        cudaGetLastError();
         d_scratch = nullptr;
         return set_error(MGT_ERR_OOM, "cannot allocate the walk scratch");
     }
@@ -967,13 +975,13 @@ mgt_status trace_range(mgt_model *m, cudaStream_t s, int32_t p0, int32_t np)
     MGT_CUDA(cudaMemsetAsync(d_len + W, 0, sizeof(int64_t), s));
     size_t tmp_bytes = 0;
     MGT_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, d_len, m->d_ray_off, W + 1, s));
-    MGT_CUDA(cudaMallocAsync(&tmp, tmp_bytes, s));
+    MGT_CUDA(cudaMallocFromPoolAsync(&tmp, tmp_bytes, pool, s));
     MGT_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, d_len, m->d_ray_off, W + 1, s));
     // longest half-ray
-    MGT_CUDA(cudaMallocAsync(&d_max, sizeof(int64_t), s));
+    MGT_CUDA(cudaMallocFromPoolAsync(&d_max, sizeof(int64_t), pool, s));
     size_t tmp2 = 0;
     MGT_CUDA(cub::DeviceReduce::Max(nullptr, tmp2, d_len, d_max, W, s));
-    MGT_CUDA(cudaMallocAsync(&tmpb, tmp2, s));
+    MGT_CUDA(cudaMallocFromPoolAsync(&tmpb, tmp2, pool, s));
     MGT_CUDA(cub::DeviceReduce::Max(tmpb, tmp2, d_len, d_max, W, s));
     k_walk_overflow<<<ceil_div(W, 256), 256, 0, s>>>(W, d_len, (int32_t)K, d_list, d_nover);
     MGT_LAUNCH_CHECK("k_walk_overflow");

@@ -150,6 +150,13 @@ struct mgt_model {
 
 namespace mgt {
 
+// The library's stream-ordered pool for large temporaries (the walk scratch),
+// one per device, created on first use.  Freed blocks stay reserved in the
+// pool for the next trace instead of going back to the driver (mapping tens of
+// GB again on every trace costs more than the walk itself); the reserve is
+// released when the last model of the process is destroyed (api.cu).
+mgt_status scratch_pool(cudaMemPool_t *pool);
+
 // error helpers (api.cu)
 void note_launch();
 mgt_status set_error(mgt_status s, const std::string &msg);
