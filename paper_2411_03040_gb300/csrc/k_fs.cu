@@ -696,9 +696,13 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
             g_n = g_f;
         }
     } else {
+        // warp 0 issues the bulk copies after the barrier: in a wide CTA it
+        // takes no items, and the last threads take the extra items of an
+        // uneven split
         const int items = a.Q * nst;
+        const int pw = bd >= 128 ? 32 : 0;
 #pragma unroll 1
-        for (int it = tid; it < items; it += bd) {
+        for (int it = tid >= pw ? bd - 1 - tid : items; it < items; it += bd - pw) {
             const int kk = it / a.Q, q = it - kk * a.Q;
             const int k = k_lo + kk;
             const StepG<T> sf = step_from<T>(Sb + (kk + 1) * SB);
