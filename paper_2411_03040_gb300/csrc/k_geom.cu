@@ -925,10 +925,12 @@ mgt_status trace_range(mgt_model *m, cudaStream_t s, int32_t p0, int32_t np)
                (int32_t)((m->n_ent + 15) / 16 + 2), m->n_ent, all ? nullptr : m->d_dir_map};
     if (!m->d_ray_off) MGT_CUDA(cudaMalloc(&m->d_ray_off, sizeof(int64_t) * ((int64_t)m->R * m->N + 1)));
     // Scratch slot per walk: K records, a multiple of 16; the longest half-ray
-    // of this model's previous trace when there was one (64 otherwise), kept
-    // within a third of the free device memory (counting what the scratch
-    // pool holds unused).  Longer walks are redone.
-    int64_t K = m->max_half > 0 ? (m->max_half + 15) / 16 * 16 : 64;
+    // of this model's previous trace when there was one, else 4 N^(1/3) + 16
+    // (a few times the mean half-ray of a cloud of N points), kept within a
+    // third of the free device memory (counting what the scratch pool holds
+    // unused).  Longer walks are redone.
+    int64_t K = m->max_half > 0 ? (m->max_half + 15) / 16 * 16
+                                : ((int64_t)(4.0 * std::cbrt((double)m->N)) + 16 + 15) / 16 * 16;
     cudaMemPool_t pool = nullptr;
     MGT_TRY_STATUS(scratch_pool(&pool));
     {
