@@ -377,7 +377,17 @@ __device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, 
     }
     if (n == 0) return;
     const T thr = (T)a.thr;
-    int64_t c_f = a.s32[s0 + n - 1].x;
+    // a point index from the ray records out of range: record it, use point 0
+    auto checked = [&](int64_t c) -> int64_t {
+        if (c >= 0 && c < a.N) return c;
+        if (atomicCAS(a.err, 0, (int)kDevBounds) == 0) {
+            a.err[1] = 21;
+            a.err[2] = (int)o;
+            a.err[3] = (int)c;
+        }
+        return 0;
+    };
+    int64_t c_f = checked(a.s32[s0 + n - 1].x);
     StepG<T> sf = step_global<T>(a, s0 + n - 1);
     T chi_f[LPT], S_f[LPT];
     load_vec<LPT>(line + c_f * a.RS + line0, chi_f);
@@ -389,7 +399,7 @@ __device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, 
         int64_t c_n = o;
         StepG<T> sn{T(0), T(0), T(0)};
         if (k > 1) {
-            c_n = a.s32[s0 + k - 2].x;
+            c_n = checked(a.s32[s0 + k - 2].x);
             sn = step_global<T>(a, s0 + k - 2);
         }
         const T *row = line + c_n * a.RS;
@@ -597,7 +607,15 @@ __device__ __forceinline__ void issue_chunk(const FSArgs &a, int64_t o, const Ch
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (lane < npts) {
         const int k = c.k_lo - 1 + lane;
-        const int64_t pt = k == 0 ? o : (int64_t)__ldg(&a.s32[c.s0 + k - 1].x);
+        int64_t pt = k == 0 ? o : (int64_t)__ldg(&a.s32[c.s0 + k - 1].x);
+        if (pt < 0 || pt >= a.N) {   // a point index from the ray records out of range: record, copy row 0
+            if (atomicCAS(a.err, 0, (int)kDevBounds) == 0) {
+                a.err[1] = 20;
+                a.err[2] = (int)o;
+                a.err[3] = (int)pt;
+            }
+            pt = 0;
+        }
         bulk_g2s(rows_buf + lane * rowB, lines + pt * (int64_t)rowB, (uint32_t)rowB, bar);
     }
     if (lane == 0) {

@@ -274,6 +274,35 @@ def test_ng_step_by_step_matches_oracle_controller(mgt, ali_ref, mode):
     assert accepted >= 1
 
 
+@pytest.mark.parametrize("scale,faster", [(1e-4, True), (1e-2, False)], ids=["low-density", "mid-density"])
+def test_ng_reaches_the_plain_fixed_point_in_fewer_iterations(mgt, scale, faster):
+    # Sec. 4.2's Ng experiment on the synthetic stand-in: the sphere with the
+    # collider density lowered 1e4 times (strongly non-LTE, slow plain ALI)
+    # and 1e2 times (plain ALI converges in a few iterations).  Plain ALI,
+    # classical and adaptive Ng (FP64) iterate until the regular iterate
+    # changes by less than 1e-9; all three land on the same populations; Ng
+    # needs fewer iterations where plain ALI is slow and never more.
+    m = synth.config_model(1, n_points=400)
+    m.n_coll = m.n_coll * scale
+    result = {}
+    for mode in (mgt.MGT_NG_NONE, mgt.MGT_NG_CLASSICAL, mgt.MGT_NG_ADAPTIVE):
+        h = mgt.mgt_model_create(m)
+        mgt.mgt_trace_rays(h)
+        it = 0
+        while True:
+            it += 1
+            st = mgt.mgt_ali_solve(h, n_iter=1, precision=mgt.MGT_FP64, ng_mode=mode, n_steps=4, n_max=8)
+            if st["last_maxrel"] < 1e-9 or it >= 400:
+                break
+        assert it < 400, (mode, it)
+        result[mode] = (it, mgt.mgt_get_populations(h))
+    it_plain, p_plain = result[mgt.MGT_NG_NONE]
+    for mode in (mgt.MGT_NG_CLASSICAL, mgt.MGT_NG_ADAPTIVE):
+        it_ng, p_ng = result[mode]
+        assert rel_err(p_ng, p_plain) < 1e-7, mode
+        assert it_ng < it_plain if faster else it_ng <= it_plain, (mode, it_ng, it_plain)
+
+
 # ------------------------------------------------ full size, sampled outputs
 @pytest.mark.slow
 def test_full_size_shell_100k_sampled(mgt):
