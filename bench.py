@@ -61,6 +61,8 @@ def parse():
                     help="time ALI iterations of a batch of uneven models (256 spheres, 5k-200k points, 5/11/21/41 "
                          "levels, 12 or 48 rays, 31 bins) replayed as one CUDA graph per iteration")
     ap.add_argument("--batch-models", type=int, default=256, help="models in the --batch workload")
+    ap.add_argument("--batch-min-points", type=int, default=None,
+                    help="smallest model of the --batch workload (default 5000; --points sets the largest)")
     ap.add_argument("--image", action="store_true",
                     help="time mgt_image and mgt_image_adjoint instead (differentiation workload: 200k-point "
                          "outflow, 256 x 256 pixels x 100 channels, populations held fixed)")
@@ -516,8 +518,9 @@ def run_batch(args):
     import multiprocessing as mp
 
     from paper_2411_03040_gb300 import synth
-    specs = synth.batch_specs(args.batch_models, n_max=args.points or 200_000,
-                              n_min=min(5_000, args.points or 5_000))
+    n_max = args.points or 200_000
+    n_min = args.batch_min_points or min(5_000, n_max)
+    specs = synth.batch_specs(args.batch_models, n_max=n_max, n_min=min(n_min, n_max))
     # the models are generated on the host cores before any CUDA call
     # (spawned workers), largest first
     t0 = time.perf_counter()

@@ -178,7 +178,11 @@ mgt_status mgt_set_solve_opts(mgt_model *m, const mgt_solve_opts *opts);
  * Most steps are settled by FP32 arithmetic with rigorous error bounds that
  * prove the FP64 predicates agree; the others are evaluated in FP64.
  * Stores the ray geometry on the device.  `stats` (host, may be NULL) is
- * filled after a stream synchronisation.
+ * filled after a stream synchronisation.  The walk's working memory (one
+ * record slot per walk and step, a few GB for 10^5 points and 48 rays) comes
+ * from a memory pool of this library, one per device, that keeps it reserved
+ * for the next trace of any model; the reserve is returned to the driver when
+ * the last model on that device is destroyed.
  */
 mgt_status mgt_trace_rays(mgt_model *m, mgt_trace_stats *stats, void *stream);
 
