@@ -47,6 +47,17 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Sum over the warp when only lanes below n hold nonzero values: the xor
+// butterfly stops at the smallest power of two >= n, and every lane below n
+// ends with the total (fewer FP64 additions on GB300's narrow FP64 pipe).
+__device__ __forceinline__ double warp_sum_first(double v, int n)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        if (o < n) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 constexpr int kMaxWarpsPerBlock = 4;
 
 // Point p, solved by one warp in its shared-memory slice sm (LL + 3L + 2 Mpad doubles).
@@ -54,7 +65,7 @@ __device__ __forceinline__ void se_point(const SEArgs &a, int64_t p, double *sm,
 {
     const int L = a.L, LL = L * L;
     double *R = sm;                       // R[i*L + j]: rate i -> j
-    double *Sn = R + LL;                  // [L] pivots
+    double *Sn = R + LL;                  // [L] reciprocals of the pivots
     double *xx = Sn + L;                  // [L] unnormalised populations
     double *bz = xx + L;                  // [L] Boltzmann factors g_i exp(-(E_i - E_0)/kT)
     double *rdown = bz + L;               // [Mpad] radiative u -> l rate per line
@@ -116,11 +127,11 @@ __device__ __forceinline__ void se_point(const SEArgs &a, int64_t p, double *sm,
     for (int n = L - 1; n >= 1; --n) {
         double part = 0.0;
         for (int j = lane; j < n; j += 32) part += R[n * L + j];
-        double s = warp_sum(part);
+        double s = warp_sum_first(part, n);
         s = s > 0.0 ? s : 1e-300;
-        if (lane == 0) Sn[n] = s;
-        __syncwarp();
         const double rs = 1.0 / s;
+        if (lane == 0) Sn[n] = rs;
+        __syncwarp();
         for (int j = lane; j < n; j += 32) R[n * L + j] *= rs;
         __syncwarp();
         const int nn = n * n;
@@ -135,8 +146,8 @@ __device__ __forceinline__ void se_point(const SEArgs &a, int64_t p, double *sm,
     for (int n = 1; n < L; ++n) {
         double part = 0.0;
         for (int i = lane; i < n; i += 32) part += xx[i] * R[i * L + n];
-        const double v = warp_sum(part);
-        if (lane == 0) xx[n] = v / Sn[n];
+        const double v = warp_sum_first(part, n);
+        if (lane == 0) xx[n] = v * Sn[n];
         __syncwarp();
     }
     double part = 0.0;
