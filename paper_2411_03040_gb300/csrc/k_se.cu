@@ -129,9 +129,13 @@ __device__ __forceinline__ void se_point(const SEArgs &a, int64_t p, double *sm,
         for (int j = lane; j < n; j += 32) part += R[n * L + j];
         double s = warp_sum_first(part, n);
         s = s > 0.0 ? s : 1e-300;
-        const double rs = 1.0 / s;
-        if (lane == 0) Sn[n] = rs;
-        __syncwarp();
+        // one lane divides (the division is a long FP64 sequence), all read it
+        double rs = 0.0;
+        if (lane == 0) {
+            rs = 1.0 / s;
+            Sn[n] = rs;
+        }
+        rs = __shfl_sync(0xffffffffu, rs, 0);
         for (int j = lane; j < n; j += 32) R[n * L + j] *= rs;
         __syncwarp();
         const int nn = n * n;
