@@ -439,8 +439,9 @@ mgt_status mgt_autotune(mgt_model *m, mgt_precision p, int32_t staged_only, int3
  * mgt_batch_iterate: n_iter ALI iterations of every model.  The first call
  * captures {line data, formal solution, statistical equilibrium} in a CUDA
  * graph, and each iteration replays it; then, when ng->mode != MGT_NG_NONE or
- * stats is not NULL, each model takes its Ng step as mgt_ng_accelerate would
- * (synchronising the stream once per model).  ng (host) may be NULL (no Ng);
+ * stats is not NULL, each model takes its Ng step as mgt_ng_accelerate would,
+ * all models phase by phase (two stream synchronisations per iteration for
+ * the whole batch).  ng (host) may be NULL (no Ng);
  * stats (host, [n_models] in the caller's order) may be NULL.  The results
  * equal those of mgt_ali_solve per model with FP32-mixed precision and
  * schedule 2.  Returns

@@ -44,6 +44,7 @@ struct mgt_batch {
     unsigned char *d_fs_args = nullptr, *d_se_args = nullptr, *d_ld_args = nullptr;
     int64_t *d_fs_end = nullptr, *d_se_end = nullptr, *d_ld_end = nullptr;
     unsigned long long *d_next = nullptr;          // one item counter per width class
+    int *h_err = nullptr;                          // pinned [n_models][4]: the models' device error words
     // the captured iteration
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -67,6 +68,7 @@ void free_batch(mgt_batch *b)
 {
     drop_graph(b);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->h_err) cudaFreeHost(b->h_err);
     for (void *p : {(void *)b->d_fs_args, (void *)b->d_se_args, (void *)b->d_ld_args, (void *)b->d_fs_end,
                     (void *)b->d_se_end, (void *)b->d_ld_end, (void *)b->d_next})
         if (p) cudaFree(p);
@@ -217,6 +219,20 @@ mgt_status capture(mgt_batch *b)
     return MGT_OK;
 }
 
+// The models' device error words with one synchronisation; the first model
+// with an error reports it (and clears it) as its own calls would.
+mgt_status check_errors(mgt_batch *b, cudaStream_t s)
+{
+    const int n = (int)b->models.size();
+    if (!b->h_err) MGT_CUDA(cudaMallocHost(&b->h_err, sizeof(int) * 4 * n));
+    for (int i = 0; i < n; ++i)
+        MGT_CUDA(cudaMemcpyAsync(b->h_err + 4 * i, b->models[i]->d_err, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    MGT_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i)
+        if (b->h_err[4 * i] != 0) return check_device_error(b->models[i], s);
+    return MGT_OK;
+}
+
 void mark_solved(mgt_batch *b)
 {
     for (mgt_model *m : b->models) {
@@ -332,10 +348,20 @@ mgt_status mgt_batch_iterate(mgt_batch *b, int32_t n_iter, const mgt_ng_opts *ng
         mark_solved(b);
         mark_se(b);
         if (o.mode == MGT_NG_NONE && !stats) continue;
+        // every model's Ng step, phase by phase, one host synchronisation per
+        // phase for the whole batch
+        for (int i = 0; i < n; ++i) MGT_TRY_STATUS(ng_begin(b->models[i], &o, s));
+        MGT_CUDA(cudaStreamSynchronize(s));
+        bool predicting = false;
         for (int i = 0; i < n; ++i) {
-            int acc = 0;
-            double mr = 0.0;
-            MGT_TRY_STATUS(ng_step(b->models[i], &o, &acc, &mr, s));
+            MGT_TRY_STATUS(ng_after_push(b->models[i], s));
+            predicting = predicting || b->models[i]->ng.pend.phase == 2;
+        }
+        if (predicting) MGT_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < n; ++i) {
+            MGT_TRY_STATUS(ng_after_predict(b->models[i], s));
+            const int acc = b->models[i]->ng.pend.accepted;
+            const double mr = b->models[i]->ng.pend.maxrel;
             if (stats) {
                 stats[i].iterations = it + 1;
                 stats[i].ng_accepted += acc;
@@ -344,8 +370,7 @@ mgt_status mgt_batch_iterate(mgt_batch *b, int32_t n_iter, const mgt_ng_opts *ng
             if (!std::isfinite(mr)) return set_error(MGT_ERR_NOT_CONVERGED, "populations became non-finite");
         }
     }
-    for (mgt_model *m : b->models) MGT_TRY_STATUS(check_device_error(m, s));
-    return MGT_OK;
+    return check_errors(b, s);
 }
 
 mgt_status mgt_batch_get_layout(const mgt_batch *b, mgt_batch_layout *layout, int32_t *order)

@@ -230,12 +230,30 @@ static mgt_status ng_alloc(mgt_model *m, const mgt_ng_opts &o)
 }
 
 // One Ng step after a statistical-equilibrium solve: pops = new regular
-// iterate, pops_prev = the populations it was computed from.
-mgt_status ng_step(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *maxrel, cudaStream_t s)
+// iterate, pops_prev = the populations it was computed from.  It runs in three
+// phases so that a batch of models can share each host synchronisation:
+//   ng_begin        push the new iterate (Gram row, maximum change), copy the
+//                   reductions to the host asynchronously;
+//   ng_after_push   (reductions on the host) update the Gram matrix and, when
+//                   a prediction is due, launch it and copy its checks back;
+//   ng_after_predict (checks on the host) use the prediction or not.
+// ng_step runs the three with a stream synchronisation between them.
+namespace {
+
+Slots hist_slots(const NgState &ng, double *slot, int64_t n, int count)
+{
+    Slots h{};
+    for (int k = 0; k < count; ++k) h.h[k] = slot + (size_t)ng.hist[k] * n;
+    return h;
+}
+
+}  // namespace
+
+mgt_status ng_begin(mgt_model *m, const mgt_ng_opts *o, cudaStream_t s)
 {
     NgState &ng = m->ng;
     const int64_t n = m->N * m->L;
-    if (accepted) *accepted = 0;
+    ng.pend = NgPending{};
     const mgt_ng_opts opts = o ? *o : mgt_ng_opts{MGT_NG_NONE, 4, 8};
     if (opts.mode != ng.opts.mode || opts.n_steps != ng.opts.n_steps || opts.n_max != ng.opts.n_max) {
         ng.opts = opts;
@@ -245,7 +263,6 @@ mgt_status ng_step(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *ma
     if (st != MGT_OK) return st;
     const int grid = grid_for(n);
     double *slot = ng.d_slots;
-    auto slot_ptr = [&](int id) { return slot + (size_t)id * n; };
 
     if (opts.mode == MGT_NG_NONE) {
         MGT_CUDA(cudaMemsetAsync(ng.d_red + kMaxNgHist, 0, sizeof(double), s));
@@ -254,17 +271,18 @@ mgt_status ng_step(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *ma
                                               ng.d_partials, ng.d_red + kMaxNgHist);
         MGT_LAUNCH_CHECK("k_ng_push");
         MGT_CUDA(cudaMemcpyAsync(ng.h_red, ng.d_red + kMaxNgHist, sizeof(double), cudaMemcpyDeviceToHost, s));
-        MGT_CUDA(cudaStreamSynchronize(s));
-        if (maxrel) *maxrel = ng.h_red[0];
-        return check_device_error(m, s);
+        ng.pend.phase = 1;
+        ng.pend.none = true;
+        return MGT_OK;
     }
 
     // first call after a reset: the populations the iterate came from start the history
     if (ng.hist.empty()) {
         const int s0 = free_slot(ng);
         Slots hs{};
-        k_ng_push<<<grid, kNgThreads, 0, s>>>(n, m->L, m->d_pops_prev, m->d_pops_prev, m->d_nspec, slot_ptr(s0), hs,
-                                              0, ng.d_partials, ng.d_red + kMaxNgHist + 1);
+        k_ng_push<<<grid, kNgThreads, 0, s>>>(n, m->L, m->d_pops_prev, m->d_pops_prev, m->d_nspec,
+                                              slot + (size_t)s0 * n, hs, 0, ng.d_partials,
+                                              ng.d_red + kMaxNgHist + 1);
         MGT_LAUNCH_CHECK("k_ng_push");
         ng.hist.push_back(s0);
         ng.G.assign(kMaxNgHist * kMaxNgHist, 0.0);
@@ -274,54 +292,94 @@ mgt_status ng_step(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *ma
     const int mh = (int)ng.hist.size();
     const int snew = free_slot(ng);
     if (snew < 0 || mh > kMaxNgHist) return set_error(MGT_ERR_STATE, "Ng history overflow");
-    Slots hs{};
-    for (int k = 0; k < mh; ++k) hs.h[k] = slot_ptr(ng.hist[k]);
+    const Slots hs = hist_slots(ng, slot, n, mh);
     MGT_CUDA(cudaMemsetAsync(ng.d_red + kMaxNgHist, 0, sizeof(double), s));
-    k_ng_push<<<grid, kNgThreads, 0, s>>>(n, m->L, m->d_pops, m->d_pops_prev, m->d_nspec, slot_ptr(snew), hs, mh,
-                                          ng.d_partials, ng.d_red + kMaxNgHist);
+    k_ng_push<<<grid, kNgThreads, 0, s>>>(n, m->L, m->d_pops, m->d_pops_prev, m->d_nspec, slot + (size_t)snew * n,
+                                          hs, mh, ng.d_partials, ng.d_red + kMaxNgHist);
     MGT_LAUNCH_CHECK("k_ng_push");
     k_ng_finish<<<1, 32, 0, s>>>(grid, mh, ng.d_partials, ng.d_red);
     MGT_LAUNCH_CHECK("k_ng_finish");
     MGT_CUDA(cudaMemcpyAsync(ng.h_red, ng.d_red, sizeof(double) * (kMaxNgHist + 1), cudaMemcpyDeviceToHost, s));
-    MGT_CUDA(cudaStreamSynchronize(s));
-    const double mr_regular = ng.h_red[kMaxNgHist];
-    if (maxrel) *maxrel = mr_regular;
+    ng.pend.phase = 1;
+    ng.pend.mh = mh;
+    ng.pend.snew = snew;
+    return MGT_OK;
+}
+
+mgt_status ng_after_push(mgt_model *m, cudaStream_t s)
+{
+    NgState &ng = m->ng;
+    NgPending &pd = ng.pend;
+    if (pd.phase != 1) return set_error(MGT_ERR_STATE, "Ng: no push in flight");
+    pd.phase = 0;
+    if (pd.none) {
+        pd.maxrel = ng.h_red[0];
+        return MGT_OK;
+    }
+    const int64_t n = m->N * m->L;
+    const int grid = grid_for(n);
+    double *slot = ng.d_slots;
+    pd.maxrel = ng.h_red[kMaxNgHist];
     // new residual index mh-1 (residual between hist[mh-1] and the new iterate)
-    const int rn = mh - 1;
+    const int rn = pd.mh - 1;
     for (int k = 0; k <= rn; ++k) {
         ng.G[rn * kMaxNgHist + k] = ng.h_red[k];
         ng.G[k * kMaxNgHist + rn] = ng.h_red[k];
     }
-    ng.hist.push_back(snew);
+    ng.hist.push_back(pd.snew);
     const int mcount = (int)ng.hist.size();
-
-    auto predict = [&](const double *prev, double *mr_pred, bool *negative) -> mgt_status {
-        const int nres = mcount - 1;
-        Coef cf{};
-        if (!ng_coefficients(ng.G, nres, cf.c)) {   // exactly singular: no prediction
-            *negative = true;
-            *mr_pred = INFINITY;
+    pd.mcount = mcount;
+    const double *prev = nullptr;
+    if (ng.opts.mode == MGT_NG_CLASSICAL) {
+        if (mcount < ng.opts.n_steps + 1) return MGT_OK;
+    } else {
+        if (mcount == 2) {
+            ng.prev_pred_slot = ng.hist[1];   // P_2 := x_2
+            ng.have_prev_pred = true;
             return MGT_OK;
         }
-        if (ng.pred_slot < 0 || ng.pred_slot == ng.prev_pred_slot) {
-            ng.pred_slot = -1;
-            ng.pred_slot = free_slot(ng);
-        }
-        Slots h2{};
-        for (int k = 0; k < mcount; ++k) h2.h[k] = slot_ptr(ng.hist[k]);
-        MGT_CUDA(cudaMemsetAsync(ng.d_red + kMaxNgHist + 1, 0, sizeof(double) * 2, s));
-        k_ng_predict<<<grid, kNgThreads, 0, s>>>(n, h2, nres, cf, slot_ptr(ng.pred_slot), prev,
-                                                 ng.d_red + kMaxNgHist + 1);
-        MGT_LAUNCH_CHECK("k_ng_predict");
-        MGT_CUDA(cudaMemcpyAsync(ng.h_red + kMaxNgHist + 1, ng.d_red + kMaxNgHist + 1, sizeof(double) * 2,
-                                 cudaMemcpyDeviceToHost, s));
-        MGT_CUDA(cudaStreamSynchronize(s));
-        *mr_pred = ng.h_red[kMaxNgHist + 1];
-        *negative = ng.h_red[kMaxNgHist + 2] != 0.0;
+        if (mcount < 3) return MGT_OK;
+        if (ng.have_prev_pred) prev = slot + (size_t)ng.prev_pred_slot * n;
+    }
+    // a prediction from the residuals' Gram matrix
+    const int nres = mcount - 1;
+    Coef cf{};
+    if (!ng_coefficients(ng.G, nres, cf.c)) {   // exactly singular: no prediction
+        pd.negative = true;
+        pd.mr_pred = INFINITY;
+        pd.phase = 3;
         return MGT_OK;
-    };
+    }
+    if (ng.pred_slot < 0 || ng.pred_slot == ng.prev_pred_slot) {
+        ng.pred_slot = -1;
+        ng.pred_slot = free_slot(ng);
+    }
+    const Slots h2 = hist_slots(ng, slot, n, mcount);
+    MGT_CUDA(cudaMemsetAsync(ng.d_red + kMaxNgHist + 1, 0, sizeof(double) * 2, s));
+    k_ng_predict<<<grid, kNgThreads, 0, s>>>(n, h2, nres, cf, slot + (size_t)ng.pred_slot * n, prev,
+                                             ng.d_red + kMaxNgHist + 1);
+    MGT_LAUNCH_CHECK("k_ng_predict");
+    MGT_CUDA(cudaMemcpyAsync(ng.h_red + kMaxNgHist + 1, ng.d_red + kMaxNgHist + 1, sizeof(double) * 2,
+                             cudaMemcpyDeviceToHost, s));
+    pd.phase = 2;
+    return MGT_OK;
+}
+
+mgt_status ng_after_predict(mgt_model *m, cudaStream_t s)
+{
+    NgState &ng = m->ng;
+    NgPending &pd = ng.pend;
+    if (pd.phase != 2 && pd.phase != 3) return MGT_OK;   // no prediction this step
+    if (pd.phase == 2) {
+        pd.mr_pred = ng.h_red[kMaxNgHist + 1];
+        pd.negative = ng.h_red[kMaxNgHist + 2] != 0.0;
+    }
+    pd.phase = 0;
+    const int64_t n = m->N * m->L;
+    const int grid = grid_for(n);
     auto use_prediction = [&]() -> mgt_status {
-        k_ng_apply<<<grid, kNgThreads, 0, s>>>(n, m->L, slot_ptr(ng.pred_slot), m->d_nspec, m->d_pops);
+        k_ng_apply<<<grid, kNgThreads, 0, s>>>(n, m->L, ng.d_slots + (size_t)ng.pred_slot * n, m->d_nspec,
+                                               m->d_pops);
         MGT_LAUNCH_CHECK("k_ng_apply");
         const int keep = ng.pred_slot;
         ng.hist.assign(1, keep);
@@ -329,7 +387,7 @@ mgt_status ng_step(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *ma
         ng.have_prev_pred = false;
         ng.G.assign(kMaxNgHist * kMaxNgHist, 0.0);
         m->line_dirty = true;
-        if (accepted) *accepted = 1;
+        pd.accepted = 1;
         return MGT_OK;
     };
     auto restart_from_newest = [&]() {
@@ -338,49 +396,45 @@ mgt_status ng_step(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *ma
         ng.have_prev_pred = false;
         ng.G.assign(kMaxNgHist * kMaxNgHist, 0.0);
     };
-
-    if (opts.mode == MGT_NG_CLASSICAL) {
-        if (mcount < opts.n_steps + 1) return check_device_error(m, s);
-        double mrp;
-        bool neg;
-        st = predict(nullptr, &mrp, &neg);
-        if (st != MGT_OK) return st;
-        if (neg) {
+    if (ng.opts.mode == MGT_NG_CLASSICAL) {
+        if (pd.negative) {
             restart_from_newest();
-            return check_device_error(m, s);
+            return MGT_OK;
         }
-        st = use_prediction();
-        if (st != MGT_OK) return st;
-        return check_device_error(m, s);
+        return use_prediction();
     }
     // adaptive
-    if (mcount == 2) {
-        ng.prev_pred_slot = ng.hist[1];   // P_2 := x_2
-        ng.have_prev_pred = true;
-        return check_device_error(m, s);
-    }
-    if (mcount < 3) return check_device_error(m, s);
-    double mrp;
-    bool neg;
-    st = predict(ng.have_prev_pred ? slot_ptr(ng.prev_pred_slot) : nullptr, &mrp, &neg);
-    if (st != MGT_OK) return st;
-    if (std::isinf(mrp)) {          // singular Gram matrix
+    if (std::isinf(pd.mr_pred)) {          // singular Gram matrix
         restart_from_newest();
-        return check_device_error(m, s);
+        return MGT_OK;
     }
-    if (mrp < mr_regular || mcount >= opts.n_max) {
-        if (neg) {
+    if (pd.mr_pred < pd.maxrel || pd.mcount >= ng.opts.n_max) {
+        if (pd.negative) {
             restart_from_newest();
-            return check_device_error(m, s);
+            return MGT_OK;
         }
-        st = use_prediction();
-        if (st != MGT_OK) return st;
-        return check_device_error(m, s);
+        return use_prediction();
     }
     // keep the running prediction for the next comparison
     ng.prev_pred_slot = ng.pred_slot;
     ng.have_prev_pred = true;
     ng.pred_slot = -1;
+    return MGT_OK;
+}
+
+mgt_status ng_step(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *maxrel, cudaStream_t s)
+{
+    if (accepted) *accepted = 0;
+    mgt_status st = ng_begin(m, o, s);
+    if (st != MGT_OK) return st;
+    MGT_CUDA(cudaStreamSynchronize(s));
+    st = ng_after_push(m, s);
+    if (st != MGT_OK) return st;
+    if (m->ng.pend.phase == 2) MGT_CUDA(cudaStreamSynchronize(s));
+    st = ng_after_predict(m, s);
+    if (st != MGT_OK) return st;
+    if (accepted) *accepted = m->ng.pend.accepted;
+    if (maxrel) *maxrel = m->ng.pend.maxrel;
     return check_device_error(m, s);
 }
 

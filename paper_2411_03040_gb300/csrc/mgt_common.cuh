@@ -64,6 +64,17 @@ struct ImageGeom {
     int32_t *d_pts = nullptr;           // [total] far end first
 };
 
+// What a started Ng step still has to do (see ng_step).
+struct NgPending {
+    int phase = 0;          // 0 idle, 1 push in flight, 2 prediction in flight, 3 prediction singular
+    bool none = false;      // mode NONE: only the maximum change
+    int mh = 0, snew = -1;  // history length before the push, slot of the new iterate
+    int mcount = 0;         // history length after the push
+    double maxrel = 0.0, mr_pred = 0.0;
+    bool negative = false;
+    int accepted = 0;
+};
+
 struct NgState {
     mgt_ng_opts opts{MGT_NG_NONE, 4, 8};
     int n_slots = 0;
@@ -76,6 +87,7 @@ struct NgState {
     double *d_red = nullptr;            // reduced values (dots, maxrel, negatives)
     double *h_red = nullptr;            // pinned host copy
     size_t partial_cap = 0;
+    NgPending pend;
 };
 
 }  // namespace mgt
@@ -209,6 +221,9 @@ mgt_status launch_stat_eq(mgt_model *m, cudaStream_t s);
 // Ng (k_ng.cu)
 mgt_status ng_reset(mgt_model *m, cudaStream_t s);
 mgt_status ng_step(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *maxrel, cudaStream_t s);
+mgt_status ng_begin(mgt_model *m, const mgt_ng_opts *o, cudaStream_t s);
+mgt_status ng_after_push(mgt_model *m, cudaStream_t s);
+mgt_status ng_after_predict(mgt_model *m, cudaStream_t s);
 void ng_free(mgt_model *m);
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
