@@ -7,7 +7,7 @@
 // work (comoving frequency, Gaussian, the trapezoid/erf switch, erf) is done
 // once per (q, step) and shared by the thread's LPT lines.
 //
-// Two kernels:
+// Three kernels:
 //  * k_fs_staged: one CTA per origin.  Each half-ray is cut into chunks of CH
 //    steps; warp 0 moves the next chunk's step records and point rows (line
 //    data + width) into shared memory with bulk asynchronous copies
@@ -35,12 +35,13 @@
 // q = 1/(1 + beta G), Pi <- G q, Y <- (S h + Y) q -- eight FP32 operations
 // and one reciprocal per line and step, from Pi = 2, alpha = 0 at the far end.
 //
-// Staged kernel, per chunk of a half-ray: first every thread of the CTA
-// computes line-independent segment coefficients for a share of the chunk's
-// (bin, step) pairs (Gaussian at both ends, trapezoid/erf switch, erf
-// difference) into shared memory, then each thread eliminates its lines
-// reading one coefficient pair per step.  The line groups of a bin no longer
-// repeat that work.
+// Staged kernel, per chunk of a half-ray: first the CTA's threads (in a CTA of
+// 128 threads or more all but warp 0, which issues the copies) compute
+// line-independent segment coefficients for a share of the chunk's (bin,
+// step) pairs (Gaussian at both ends, trapezoid/erf switch, erf difference)
+// into shared memory, then each thread eliminates its lines reading one
+// coefficient pair per step, two steps per trip.  The line groups of a bin
+// do not repeat the coefficient work.
 #include <algorithm>
 #include <cstring>
 
