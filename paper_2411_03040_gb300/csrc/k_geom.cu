@@ -537,11 +537,14 @@ struct ImgWalkArgs {
     double n[3];              // unit direction toward the observer
 };
 
-// Four blocks of 256 per SM (registers capped at 64): the walk is bound by
-// dependent latency (L2 row loads, shuffle chains), and 32 resident warps per
-// SM beat the spill-free 93-register build at 16 (workload 2 trace: 91 -> 73 ms).
+// Blocks of 128 threads, eight per SM (registers capped at 64): the walk is
+// bound by dependent latency (L2 row loads, shuffle chains), and 32 resident
+// warps per SM beat the spill-free 93-register build at 16 (workload 2 trace:
+// 91 -> 73 ms; 128-thread blocks instead of 256 a further 3 %).  Every launch
+// uses kWalkThreads.
+constexpr int kWalkThreads = 128;
 template <int MODE>
-__global__ void __launch_bounds__(256, 4) k_walk(WalkArgs a, int64_t *__restrict__ lens, const int64_t *__restrict__ ray_off,
+__global__ void __launch_bounds__(kWalkThreads, 8) k_walk(WalkArgs a, int64_t *__restrict__ lens, const int64_t *__restrict__ ray_off,
                                               const int64_t *__restrict__ list, int64_t n_list, int32_t K,
                                               unsigned long long *__restrict__ n_stall,
                                               const float *__restrict__ vel_hl, const float2 *__restrict__ w32,
@@ -970,7 +973,7 @@ mgt_status trace_range(mgt_model *m, cudaStream_t s, int32_t p0, int32_t np)
     MGT_CUDA(cudaMemsetAsync(m->d_count + 1, 0, 2 * sizeof(unsigned long long), s));
     MGT_CUDA(cudaMemsetAsync(d_nover, 0, sizeof(unsigned long long), s));
     const float inv_Lunit = (float)(1.0 / (m->pos_scale * m->L_unit));
-    k_walk<kWalkFused><<<ceil_div(W * 16, 256), 256, 0, s>>>(a, d_len, nullptr, nullptr, 0, (int32_t)K,
+    k_walk<kWalkFused><<<ceil_div(W * 16, kWalkThreads), kWalkThreads, 0, s>>>(a, d_len, nullptr, nullptr, 0, (int32_t)K,
                                                              m->d_count + 1, m->d_vel_hl, m->d_w32, inv_Lunit,
                                                              m->opts.width_mode, d_scratch, m->d_err, ImgWalkArgs{});
     MGT_LAUNCH_CHECK("k_walk<fused>");
@@ -1014,7 +1017,7 @@ mgt_status trace_range(mgt_model *m, cudaStream_t s, int32_t p0, int32_t np)
         k_walk_compact<<<ceil_div(W * 32, 256), 256, 0, s>>>(W, m->d_ray_off, (int32_t)K, d_scratch, m->d_steps32);
         MGT_LAUNCH_CHECK("k_walk_compact");
         if (n_over > 0) {
-            k_walk<kWalkList><<<ceil_div((int64_t)n_over * 16, 256), 256, 0, s>>>(
+            k_walk<kWalkList><<<ceil_div((int64_t)n_over * 16, kWalkThreads), kWalkThreads, 0, s>>>(
                 a, nullptr, m->d_ray_off, d_list, (int64_t)n_over, 0, nullptr, m->d_vel_hl, m->d_w32, inv_Lunit,
                 m->opts.width_mode, m->d_steps32, m->d_err, ImgWalkArgs{});
             MGT_LAUNCH_CHECK("k_walk<list>");
@@ -1240,7 +1243,7 @@ mgt_status trace_image(mgt_model *m, const double n[3], int32_t npx, int32_t npy
     MGT_CUDA(cudaMallocAsync(&d_lens, sizeof(int64_t) * 2 * npix, s));
     MGT_CUDA(cudaMallocAsync(&d_sizes, sizeof(int64_t) * (npix + 1), s));
     ImgWalkArgs im{g.d_ref, g.d_anchor, g.d_off, nullptr, npix, {n[0], n[1], n[2]}};
-    k_walk<kWalkImgCount><<<ceil_div(2 * npix * 16, 256), 256, 0, s>>>(a, d_lens, nullptr, nullptr, 0, 0, nullptr,
+    k_walk<kWalkImgCount><<<ceil_div(2 * npix * 16, kWalkThreads), kWalkThreads, 0, s>>>(a, d_lens, nullptr, nullptr, 0, 0, nullptr,
                                                                        nullptr, nullptr, 0.0f, 0, nullptr, m->d_err,
                                                                        im);
     MGT_LAUNCH_CHECK("k_walk<image count>");
@@ -1265,7 +1268,7 @@ mgt_status trace_image(mgt_model *m, const double n[3], int32_t npx, int32_t npy
     }
     MGT_CUDA(cudaMalloc(&g.d_pts, sizeof(int32_t) * (total > 0 ? total : 1)));
     im.pts = g.d_pts;
-    k_walk<kWalkImgFill><<<ceil_div(2 * npix * 16, 256), 256, 0, s>>>(a, d_lens, nullptr, nullptr, 0, 0, nullptr,
+    k_walk<kWalkImgFill><<<ceil_div(2 * npix * 16, kWalkThreads), kWalkThreads, 0, s>>>(a, d_lens, nullptr, nullptr, 0, 0, nullptr,
                                                                       nullptr, nullptr, 0.0f, 0, nullptr, m->d_err, im);
     MGT_LAUNCH_CHECK("k_walk<image fill>");
     k_img_place_anchor<<<ceil_div(npix, 256), 256, 0, s>>>(npix, d_lens, g.d_off, g.d_anchor, g.d_pts);
