@@ -545,6 +545,7 @@ const char *mgt_last_error(void) { return g_last_error.c_str(); }
 
 mgt_status mgt_model_create(mgt_model **out, const mgt_model_desc *desc, void *stream)
 {
+    MGT_RANGE("mgt_model_create");
     if (!out) return set_error(MGT_ERR_ARG, "out is NULL");
     *out = nullptr;
     MGT_TRY(validate(desc));
@@ -593,6 +594,7 @@ mgt_status mgt_set_solve_opts(mgt_model *m, const mgt_solve_opts *o)
 
 mgt_status mgt_trace_rays(mgt_model *m, mgt_trace_stats *stats, void *stream)
 {
+    MGT_RANGE("mgt_trace_rays");
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     mgt_trace_stats st{};
@@ -631,6 +633,7 @@ mgt_status mgt_get_rays(mgt_model *m, int64_t *ray_off, int32_t *idx, void *stre
 
 mgt_status mgt_set_populations(mgt_model *m, const double *pops, void *stream)
 {
+    MGT_RANGE("mgt_set_populations");
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (pops) {
@@ -684,6 +687,7 @@ static mgt_status copy_out_jbar(mgt_model *m, double *Jbar, double *Lstar, int o
 
 mgt_status mgt_formal_solve(mgt_model *m, mgt_precision p, double *Jbar, double *Lstar, int on_device, void *stream)
 {
+    MGT_RANGE("mgt_formal_solve");
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     MGT_TRY(formal_solve_device(m, p, s));
@@ -699,6 +703,7 @@ mgt_status mgt_get_jbar(mgt_model *m, double *Jbar, double *Lstar, int on_device
 
 mgt_status mgt_stat_equilibrium(mgt_model *m, double *pops_out, void *stream)
 {
+    MGT_RANGE("mgt_stat_equilibrium");
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     MGT_TRY(stat_eq_device(m, s));
@@ -711,6 +716,7 @@ mgt_status mgt_stat_equilibrium(mgt_model *m, double *pops_out, void *stream)
 
 mgt_status mgt_ng_accelerate(mgt_model *m, const mgt_ng_opts *o, int *accepted, double *maxrel, void *stream)
 {
+    MGT_RANGE("mgt_ng_accelerate");
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
     if (o) {
         if (o->mode < MGT_NG_NONE || o->mode > MGT_NG_ADAPTIVE) return set_error(MGT_ERR_ARG, "unknown Ng mode");
@@ -724,6 +730,7 @@ mgt_status mgt_ng_accelerate(mgt_model *m, const mgt_ng_opts *o, int *accepted, 
 
 mgt_status mgt_ali_solve(mgt_model *m, const mgt_ali_opts *o, mgt_ali_stats *stats, void *stream)
 {
+    MGT_RANGE("mgt_ali_solve");
     if (!m || !o) return set_error(MGT_ERR_ARG, "model or options NULL");
     if (o->n_iter < 0) return set_error(MGT_ERR_ARG, "n_iter must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;

@@ -256,6 +256,7 @@ extern "C" {
 
 mgt_status mgt_batch_create(mgt_batch **out, mgt_model *const *models, int32_t n_models, void *stream)
 {
+    MGT_RANGE("mgt_batch_create");
     if (!out) return set_error(MGT_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!models || n_models < 1 || n_models > 65536) return set_error(MGT_ERR_ARG, "n_models must be 1..65536");
@@ -304,6 +305,7 @@ mgt_status mgt_batch_destroy(mgt_batch *b)
 
 mgt_status mgt_batch_formal_solve(mgt_batch *b, void *stream)
 {
+    MGT_RANGE("mgt_batch_formal_solve");
     if (!b) return set_error(MGT_ERR_ARG, "batch is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MGT_TRY_STATUS(refresh(b, s));
@@ -314,6 +316,7 @@ mgt_status mgt_batch_formal_solve(mgt_batch *b, void *stream)
 
 mgt_status mgt_batch_stat_equilibrium(mgt_batch *b, void *stream)
 {
+    MGT_RANGE("mgt_batch_stat_equilibrium");
     if (!b) return set_error(MGT_ERR_ARG, "batch is NULL");
     for (mgt_model *m : b->models)
         if (!m->have_J) return set_error(MGT_ERR_STATE, "mgt_batch_formal_solve must be called first");
@@ -327,6 +330,7 @@ mgt_status mgt_batch_stat_equilibrium(mgt_batch *b, void *stream)
 mgt_status mgt_batch_iterate(mgt_batch *b, int32_t n_iter, const mgt_ng_opts *ng, mgt_ali_stats *stats,
                              void *stream)
 {
+    MGT_RANGE("mgt_batch_iterate");
     if (!b) return set_error(MGT_ERR_ARG, "batch is NULL");
     if (n_iter < 0) return set_error(MGT_ERR_ARG, "n_iter must be >= 0");
     const int n = (int)b->models.size();
@@ -399,6 +403,7 @@ mgt_status mgt_batch_get_layout(const mgt_batch *b, mgt_batch_layout *layout, in
 mgt_status mgt_autotune(mgt_model *m, mgt_precision p, int32_t staged_only, int32_t reps, mgt_autotune_result *res,
                         void *stream)
 {
+    MGT_RANGE("mgt_autotune");
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
     if (p != MGT_FP64 && p != MGT_FP32_MIXED) return set_error(MGT_ERR_ARG, "unknown precision");
     if (reps < 1 || reps > 100) return set_error(MGT_ERR_ARG, "reps must be 1..100");

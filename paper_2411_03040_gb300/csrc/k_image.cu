@@ -396,6 +396,7 @@ extern "C" {
 mgt_status mgt_image_rays(mgt_model *m, const double dir[3], int32_t npx, int32_t npy, int32_t *anchor,
                           int64_t *ray_off, int32_t *pts, void *stream)
 {
+    MGT_RANGE("mgt_image_rays");
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
     MGT_TRY_STATUS(check_image_args(dir, npx, npy, 1, 1.0, 1.0));
     cudaStream_t s = (cudaStream_t)stream;
@@ -411,6 +412,7 @@ mgt_status mgt_image_rays(mgt_model *m, const double dir[3], int32_t npx, int32_
 mgt_status mgt_image(mgt_model *m, const double dir[3], int32_t npx, int32_t npy, int32_t nfreq, double fmin,
                      double fmax, float *out, int on_device, void *stream)
 {
+    MGT_RANGE("mgt_image");
     if (!m || !out) return set_error(MGT_ERR_ARG, "model or output is NULL");
     MGT_TRY_STATUS(check_image_args(dir, npx, npy, nfreq, fmin, fmax));
     cudaStream_t s = (cudaStream_t)stream;
@@ -435,6 +437,7 @@ mgt_status mgt_image_adjoint(mgt_model *m, const double dir[3], int32_t npx, int
                              double fmax, const float *grad_out, double *g_logT, double *g_logn, double *g_vel,
                              int on_device, void *stream)
 {
+    MGT_RANGE("mgt_image_adjoint");
     if (!m || !grad_out) return set_error(MGT_ERR_ARG, "model or grad_out is NULL");
     MGT_TRY_STATUS(check_image_args(dir, npx, npy, nfreq, fmin, fmax));
     cudaStream_t s = (cudaStream_t)stream;

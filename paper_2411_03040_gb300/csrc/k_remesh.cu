@@ -206,6 +206,7 @@ extern "C" mgt_status mgt_remesh(int64_t n_points, const double *pos, const doub
                                  int32_t max_level, int32_t n_side, double *out_pos, uint8_t *out_boundary,
                                  int64_t capacity, int64_t *n_out, void *stream)
 {
+    MGT_RANGE("mgt_remesh");
     if (n_points < 1 || n_points >= ((int64_t)1 << 31)) return set_error(MGT_ERR_ARG, "n_points must be 1..2^31-1");
     if (!pos || !rho || !n_out) return set_error(MGT_ERR_ARG, "pos, rho and n_out are required");
     if (!(r_max >= 0.0) || !std::isfinite(r_max)) return set_error(MGT_ERR_ARG, "r_max must be finite and >= 0");

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -227,6 +228,16 @@ mgt_status ng_after_predict(mgt_model *m, cudaStream_t s);
 void ng_free(mgt_model *m);
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// NVTX range over one C-ABI call (visible to profilers that record NVTX, such
+// as ncu's --nvtx filters; a few nanoseconds when none is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define MGT_RANGE(name) ::mgt::NvtxRange mgt_nvtx_range_(name)
 
 // Per-point line-data rows, in scalars of the row's precision:
 //   [0, Mpad)        chi~'  per line (zero for padding lines)
