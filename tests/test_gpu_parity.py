@@ -303,6 +303,28 @@ def test_ng_reaches_the_plain_fixed_point_in_fewer_iterations(mgt, scale, faster
         assert it_ng < it_plain if faster else it_ng <= it_plain, (mode, it_ng, it_plain)
 
 
+def test_ali_resumes_from_saved_populations(mgt):
+    # checkpoint and resume: three plain ALI iterations, the populations saved
+    # to the host, restored into a fresh model of the same inputs, three more
+    # iterations; the result is bit-identical to six uninterrupted iterations
+    m = nonlte_sphere()
+    for prec in (mgt.MGT_FP64, mgt.MGT_FP32_MIXED):
+        h = mgt.mgt_model_create(m)
+        mgt.mgt_trace_rays(h)
+        mgt.mgt_ali_solve(h, n_iter=6, precision=prec)
+        straight = mgt.mgt_get_populations(h)
+        a = mgt.mgt_model_create(m)
+        mgt.mgt_trace_rays(a)
+        mgt.mgt_ali_solve(a, n_iter=3, precision=prec)
+        saved = mgt.mgt_get_populations(a)
+        a.close()
+        b = mgt.mgt_model_create(m)
+        mgt.mgt_trace_rays(b)
+        mgt.mgt_set_populations(b, saved)
+        mgt.mgt_ali_solve(b, n_iter=3, precision=prec)
+        np.testing.assert_array_equal(mgt.mgt_get_populations(b), straight)
+
+
 # ------------------------------------------------ full size, sampled outputs
 @pytest.mark.slow
 def test_full_size_shell_100k_sampled(mgt):
