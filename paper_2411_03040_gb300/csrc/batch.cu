@@ -142,10 +142,17 @@ mgt_status refresh(mgt_batch *b, cudaStream_t s)
     }
     if (li > 0x7fffffffLL || si > 0x7fffffffLL)
         return set_error(MGT_ERR_ARG, "batch: too many points for one launch");
-    size_t max_smem = 0;
-    for (const mgt_batch::FsClass &c : classes) max_smem = std::max(max_smem, c.smem);
-    if (max_smem > 227 * 1024) return set_error(MGT_ERR_ARG, "batch: formal-solution shared memory above 227 KB");
-    for (mgt_batch::FsClass &c : classes) MGT_TRY_STATUS(fs_batch_grid(c.threads, c.smem, max_smem, &c.grid));
+    // one-warp CTAs run another instance of the kernel (shorter chunks): the
+    // shared-memory limit is set per instance, to its largest class
+    size_t max_narrow = 0, max_wide = 0;
+    for (const mgt_batch::FsClass &c : classes) {
+        size_t &mx = c.threads == 32 ? max_narrow : max_wide;
+        mx = std::max(mx, c.smem);
+    }
+    if (std::max(max_narrow, max_wide) > 227 * 1024)
+        return set_error(MGT_ERR_ARG, "batch: formal-solution shared memory above 227 KB");
+    for (mgt_batch::FsClass &c : classes)
+        MGT_TRY_STATUS(fs_batch_grid(c.threads, c.smem, c.threads == 32 ? max_narrow : max_wide, &c.grid));
 
     const bool same = order == b->order && fa == b->fs_args && sa == b->se_args && la == b->ld_args &&
                       classes == b->fs_classes && se_smem == b->se_smem;

@@ -1113,18 +1113,27 @@ mgt_status fs_batch_args(const mgt_model *m, void *args, int *threads, int64_t *
     return MGT_OK;
 }
 
+// One-warp CTAs (models with few lines) take chunks of 15 steps: half the
+// staging and coefficient buffers, so twice as many CTAs fit on an SM, and a
+// barrier of one warp costs little.  The arithmetic does not depend on the
+// chunk length.
+constexpr int kChunkNarrow = 15;
+
 size_t fs_batch_smem(const void *args, int bd)
 {
     FSArgs a;
     std::memcpy(&a, args, sizeof a);
     const int Mb = a.Gb * a.lpt;
+    if (bd == 32)
+        return a.lpt == 4 ? (size_t)staged_layout<float, 4, kChunkNarrow>(a.Q, Mb, a.RS, bd, a.P).total
+                          : (size_t)staged_layout<float, 8, kChunkNarrow>(a.Q, Mb, a.RS, bd, a.P).total;
     return a.lpt == 4 ? (size_t)staged_layout<float, 4, kChunk>(a.Q, Mb, a.RS, bd, a.P).total
                       : (size_t)staged_layout<float, 8, kChunk>(a.Q, Mb, a.RS, bd, a.P).total;
 }
 
 mgt_status fs_batch_grid(int bd, size_t smem, size_t max_smem, int *grid)
 {
-    auto kern = k_fs_batch<float, kChunk>;
+    auto kern = bd == 32 ? k_fs_batch<float, kChunkNarrow> : k_fs_batch<float, kChunk>;
     MGT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
     int dev = 0, sms = 0, per_sm = 0;
     MGT_CUDA(cudaGetDevice(&dev));
@@ -1141,7 +1150,10 @@ mgt_status fs_batch_launch(const void *d_args, const int64_t *d_item_end, int n_
     FSBatchArgs b{static_cast<const FSArgs *>(d_args), d_item_end, n_models, n_items, d_next};
     MGT_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), s));
     const int64_t g = std::min<int64_t>(grid, n_items);
-    k_fs_batch<float, kChunk><<<(unsigned)g, bd, smem, s>>>(b);
+    if (bd == 32)
+        k_fs_batch<float, kChunkNarrow><<<(unsigned)g, bd, smem, s>>>(b);
+    else
+        k_fs_batch<float, kChunk><<<(unsigned)g, bd, smem, s>>>(b);
     MGT_LAUNCH_CHECK("k_fs_batch");
     return MGT_OK;
 }
