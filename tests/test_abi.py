@@ -53,6 +53,8 @@ def test_struct_layout_matches_header(tmp_path):
         "mgt_ng_opts": mgt.mgt_ng_opts,
         "mgt_ali_opts": mgt.mgt_ali_opts,
         "mgt_ali_stats": mgt.mgt_ali_stats,
+        "mgt_autotune_result": mgt.mgt_autotune_result,
+        "mgt_batch_layout": mgt.mgt_batch_layout,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for name, cls in structs.items():
@@ -116,6 +118,18 @@ def test_null_arguments(lib):
     assert lib.mgt_formal_solve(None, 0, None, None, 0, None) == 1
     assert lib.mgt_model_destroy(None) == 0
     assert b"NULL" in lib.mgt_last_error()
+    # batches and the autotuner reject their arguments before any device call
+    out = ctypes.c_void_p()
+    assert lib.mgt_batch_create(ctypes.byref(out), None, 0, None) == 1
+    assert out.value is None
+    assert lib.mgt_batch_create(None, None, 1, None) == 1
+    assert lib.mgt_batch_formal_solve(None, None) == 1
+    assert lib.mgt_batch_stat_equilibrium(None, None) == 1
+    assert lib.mgt_batch_iterate(None, 1, None, None, None) == 1
+    assert lib.mgt_batch_get_layout(None, None, None) == 1
+    assert lib.mgt_batch_destroy(None) == 0
+    assert lib.mgt_autotune(None, 1, 0, 3, None, None) == 1
+    assert lib.mgt_get_jbar(None, None, None, 0, None) == 1
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
@@ -124,3 +138,18 @@ def test_binding_fails_loudly_without_library(tmp_path):
             "try:\n    g.load()\nexcept RuntimeError as e:\n    print('RAISED', 'no CPU fallback' in str(e))\n")
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT).stdout
     assert "RAISED True" in out
+
+
+def test_batch_workload_specs_are_seeded_and_in_range():
+    # the batch workload's sizes: log-uniform points in [5k, 200k], levels from
+    # {5, 11, 21, 41}, HEALPix nside 1 or 2, the same on every call
+    from paper_2411_03040_gb300 import synth
+    a = synth.batch_specs(256)
+    assert a == synth.batch_specs(256)
+    n = np.array([x[0] for x in a])
+    assert n.min() >= 5_000 and n.max() <= 200_000
+    assert {x[1] for x in a} == {5, 11, 21, 41}
+    assert {x[2] for x in a} == {1, 2}
+    # log-uniform: about half the models below the geometric mean of the range
+    assert 0.35 < np.mean(n < np.sqrt(5_000 * 200_000)) < 0.65
+    assert len({x[4] for x in a}) == 256            # one seed per model
