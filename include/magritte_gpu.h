@@ -102,8 +102,7 @@ typedef struct {
     int32_t width_mode;       /* dnu_bar of a segment: 0 = from the averaged temperature
                                  and turbulence (default), 1 = mean of the endpoint widths */
     int32_t lines_per_thread; /* FP32 kernel schedule: 0 = auto, else 4 or 8 */
-    int32_t schedule;         /* formal-solve kernel: 0 = auto (2 when one origin's bins x
-                                 line groups fill at least 96 threads, else 1), 1 = per-thread
+    int32_t schedule;         /* formal-solve kernel: 0 = auto (currently 2), 1 = per-thread
                                  gathers from global memory, 2 = bulk-copy staging of ray chunks
                                  in shared memory (registers capped for two blocks per SM),
                                  3 = staging with one block per SM */
