@@ -181,7 +181,9 @@ mgt_status mgt_set_solve_opts(mgt_model *m, const mgt_solve_opts *opts);
  * record slot per walk and step, a few GB for 10^5 points and 48 rays) comes
  * from a memory pool of this library, one per device, that keeps it reserved
  * for the next trace of any model; the reserve is returned to the driver when
- * the last model on that device is destroyed.
+ * the last model on that device is destroyed.  The model's ray buffer (16 B
+ * per step) comes from the same pool and is returned to it by
+ * mgt_model_destroy.
  */
 mgt_status mgt_trace_rays(mgt_model *m, mgt_trace_stats *stats, void *stream);
 

@@ -264,9 +264,13 @@ static void free_model(mgt_model *m)
                     m->d_nbr_off, m->d_nbrs, m->d_bnd, m->d_dirs, m->d_pairs, m->d_xq, m->d_wq, m->d_line_tab,
                     m->d_line_ul, m->d_level_tab, m->d_coll_tab, m->d_coll_ul, m->d_entry, m->d_pops,
                     m->d_pops_prev, m->d_line32, m->d_line64, m->d_J, m->d_Lst, m->d_err, m->d_count,
-                    m->d_ray_off, m->d_steps32, m->d_steps64};
+                    m->d_ray_off, m->d_steps64};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (m->d_steps32) {   // from the library's pool: back to its reserve
+        cudaFreeAsync(m->d_steps32, nullptr);
+        cudaStreamSynchronize(nullptr);
+    }
     ng_free(m);
     image_free(m);
     delete m;

@@ -999,13 +999,17 @@ mgt_status trace_range(mgt_model *m, cudaStream_t s, int32_t p0, int32_t np)
     MGT_CUDA(cudaMemcpyAsync(&n_over, d_nover, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     MGT_CUDA(cudaStreamSynchronize(s));
     MGT_TRY_STATUS(check_device_error(m, s));     // a walk that gave up leaves the lengths unusable
+    // the ray buffer comes from the same pool: a model created after another
+    // one was destroyed reuses its mapping.  A formal solution on another
+    // stream may still read the old buffer, hence the device-wide wait.
     if (m->d_steps32 && total > m->steps32_cap) {
-        MGT_CUDA(cudaFree(m->d_steps32));
+        MGT_CUDA(cudaDeviceSynchronize());
+        MGT_CUDA(cudaFreeAsync(m->d_steps32, s));
         m->d_steps32 = nullptr;
     }
     m->steps64_width_mode = -1;                // the FP64 geometry describes the previous rays
     if (!m->d_steps32 && total > 0) {
-        cudaError_t e = cudaMalloc(&m->d_steps32, sizeof(Step32) * total);
+        cudaError_t e = cudaMallocFromPoolAsync(&m->d_steps32, sizeof(Step32) * total, pool, s);
         if (e != cudaSuccess) return set_error(MGT_ERR_OOM, "cannot allocate the ray buffer");
         m->steps32_cap = total;
     }

@@ -1,8 +1,9 @@
 """Device memory of the trace's working pool, through the C-ABI.
 
-The walk's record slots come from a memory pool of the library that keeps them
-reserved between traces (of the same or another model) and returns them to the
-driver when the last model on the device is destroyed.  The test traces two
+The walk's record slots and each model's ray buffer come from a memory pool of
+the library that keeps them reserved between traces (of the same or another
+model) and returns them to the driver when the last model on the device is
+destroyed.  The test traces two
 models in turn, checks that the second trace reuses the reserve instead of
 taking more memory, that the rays are unchanged by the reuse, and that
 destroying both models gives the memory back.  It runs in a fresh process, so
