@@ -347,6 +347,42 @@ def test_full_size_shell_100k_sampled(mgt):
     Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP64)
     assert rel_err(Jg[orig], J) < TOL64
     assert rel_err(Lg[orig], L) < TOL64
+    # statistical equilibrium at every point, fed by the FP64 J-bar; the
+    # oracle's at the sampled points, fed by its own
+    pg = mgt.mgt_stat_equilibrium(h)
+    p0 = O.lte_populations(m.temp, m.n_spec, m.lines.energy_J, m.lines.g)
+    po = O.stat_equilibrium(p0[orig], J, L, m.temp[orig], m.n_coll[orig], m.n_spec[orig], m.lines)
+    assert rel_err(pg[orig], po) < 1e-8
+    np.testing.assert_allclose(pg.sum(1), m.n_spec, rtol=1e-12)
+    h.close()
+
+
+@pytest.mark.slow
+def test_full_size_shells_grf_1m_sampled(mgt):
+    # the 1M-point workload (192 rays, 40 lines x 40 bins, random velocity
+    # field) in the launch configuration the benchmark times for it: pair
+    # batches of 8, each traced inside the formal solution.  FP32-mixed only:
+    # an FP64 solution of this size takes minutes.
+    m = synth.config_model(3)
+    h = mgt.mgt_model_create(m)
+    mgt.mgt_set_solve_opts(h, pairs_per_batch=8)
+    st = mgt.mgt_trace_rays(h)
+    assert st["n_stalls"] == 0
+    rng = np.random.default_rng(3)
+    orig = np.sort(rng.choice(m.n_points, 12, replace=False))
+    rays = O.trace(m, origins=orig)
+    assert rays.stalls == 0
+    assert int(np.diff(rays.off).max()) <= st["max_half_ray"]
+    J, L = oracle_fields(m, rays, orig)
+    Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP32_MIXED)
+    assert rel_err(Jg[orig], J) < TOL32
+    assert rel_err(Lg[orig], L) < TOL32
+    assert np.all(np.isfinite(Jg)) and np.all(Lg >= 0) and np.all(Lg < 1)
+    # populations at every point: finite and conserving the species density
+    pg = mgt.mgt_stat_equilibrium(h)
+    assert np.all(np.isfinite(pg))
+    np.testing.assert_allclose(pg.sum(1), m.n_spec, rtol=1e-12)
+    h.close()
 
 
 # ------------------------------------------- subdivision reference (Sec. 4.3 study)
