@@ -542,6 +542,57 @@ def test_formal_solve_uniform_static_lattice_closed_form():
     assert errs[1] < errs[0] / 3 and errs[2] < errs[1] / 3, errs
 
 
+@pytest.mark.parametrize("widths", [2.4, 20.0], ids=["trapezoid", "semi-analytic"])
+def test_formal_solve_linear_velocity_lattice_closed_form(widths):
+    # the static lattice above with v_x = g x: along the x axis the comoving
+    # offset of bin q grows linearly with the distance s from the origin, in
+    # both directions, nu_q g s / c (Sec. 4.3, the Doppler-shifted profile),
+    # so tau(l) = chi [erf(x_q + k l / dnu) - erf(x_q)] / (2 k), k = nu_q g / c,
+    # and u_o tends to S + (I - S)(e^-tau+ + e^-tau-)/2 at second order.  The
+    # origin is off centre, so its own velocity is not zero.  A shift of 2.4
+    # line widths across the cube keeps every segment below the 0.35 switch
+    # (trapezoid); 20 widths keep every segment above it (semi-analytic).
+    errs = []
+    for n_side in (9, 17, 33):
+        size = 8e11
+        spacing = size / (n_side - 1)
+        m = synth.lattice_model(n_side=n_side, spacing_m=spacing, n_levels=2, n_quad=5,
+                                temp=40.0, n_coll=1e30)
+        m.n_spec[:] = 5e7
+        nu0 = m.lines.freq_Hz[0]
+        dnu = O.line_width(nu0, 40.0, 0.0, m.lines.mol_mass_kg)
+        g = widths * (dnu / nu0) * O.C / size
+        m.vel = np.zeros_like(m.pos)
+        m.vel[:, 0] = g * m.pos[:, 0]
+        ii = (n_side - 1) // 4
+        o = int(np.ravel_multi_index((ii, (n_side - 1) // 2, (n_side - 1) // 2), (n_side,) * 3))
+        rays = O.trace(m, origins=[o])
+        pops = O.lte_populations(m.temp, m.n_spec, m.lines.energy_J, m.lines.g)
+        chi, S, _ = O.line_chi_S(pops, m.lines)
+        J, _ = O.formal_solve(m, rays, chi, S, origins=[o])
+        x, w = O.gauss_hermite(m.n_quad)
+        Sv, ch = S[0, 0], chi[0, 0]
+        lx = [ii * spacing, (n_side - 1 - ii) * spacing]
+        ly = (n_side - 1) / 2 * spacing
+        moving = static = 0.0
+        for q in range(m.n_quad):
+            nuq = nu0 + x[q] * dnu
+            I = O.planck(nuq, m.T_bg)
+            k = nuq * g / O.C
+            tau = [ch / (2 * k) * (special.erf(x[q] + k * l / dnu) - special.erf(x[q])) for l in lx]
+            kap = ch * math.exp(-x[q] ** 2) / (dnu * math.sqrt(math.pi))
+            uy = Sv + (I - Sv) * math.exp(-kap * ly)
+            ux = Sv + (I - Sv) * (math.exp(-tau[0]) + math.exp(-tau[1])) / 2
+            ux0 = Sv + (I - Sv) * (math.exp(-kap * lx[0]) + math.exp(-kap * lx[1])) / 2
+            moving += w[q] * (ux + 2 * uy) / 3
+            static += w[q] * (ux0 + 2 * uy) / 3
+        errs.append(abs(J[0, 0] / moving - 1))
+    assert errs[0] < 1e-3
+    assert errs[1] < errs[0] / 3 and errs[2] < errs[1] / 3, errs
+    # the velocity field matters far more than the remaining error
+    assert abs(moving / static - 1) > 1000 * errs[2]
+
+
 # ------------------------------------------------------------- ALI end to end
 @pytest.mark.slow
 def test_ali_plain_and_ng_same_fixed_point():
