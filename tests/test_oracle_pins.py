@@ -93,6 +93,21 @@ def test_profile_normalisation_through_static_segment():
     assert abs(tot / 3.0 - 1) < 1e-10
 
 
+@pytest.mark.parametrize("T,vturb", [(40.0, 0.0), (2000.0, 0.0), (300.0, 1.0e3)])
+def test_line_width_is_the_maxwellian_velocity_spread(T, vturb):
+    # a thermal line of sight velocity has variance kT/m (one component of a
+    # Maxwell-Boltzmann distribution), so the profile's variance in frequency
+    # is (nu/c)^2 kT/m; the turbulent term enters as v_turb^2 next to 2kT/m
+    # (Sec. 4.3, eq. line width), i.e. adds (nu/c)^2 v_turb^2 / 2.  The profile
+    # is read back through a static segment of unit length and opacity.
+    nu, mass = 230.5e9, 28 * 1.66053906660e-27
+    dnu = O.line_width(nu, T, vturb ** 2, mass)
+    f = lambda off: off * off * O.segment_dtau(1.0, 1.0, 1.0, dnu, dnu, dnu, off, off)
+    var, _ = integrate.quad(f, -12 * dnu, 12 * dnu, limit=200)
+    expect = (nu / 299792458.0) ** 2 * (1.380649e-23 * T / mass + vturb ** 2 / 2)
+    assert abs(var / expect - 1) < 1e-9
+
+
 @pytest.mark.parametrize("off0,shift", [(0.0, 0.5), (-1.3, 2.0), (0.4, -3.0), (2.5, 1.2),
                                         (-6.0, -0.8), (3.0, 0.35), (5.0, 8.0)])
 def test_semi_analytic_exact_for_constant_opacity(off0, shift):
