@@ -77,6 +77,10 @@ def test_line_data_lte_closed_forms():
         expect = O.H * lines.freq_Hz[k] / (4 * math.pi) * pops[:, lines.lo[k]] * Blu * \
             -np.expm1(-O.H * lines.freq_Hz[k] / (O.KB * T))
         np.testing.assert_allclose(chi[k], expect, rtol=1e-10)
+        # Kirchhoff: in LTE the opacity is the spontaneous emissivity
+        # (h nu / 4 pi) n_u A_ul over the Planck function, with no B coefficient
+        emis = O.H * lines.freq_Hz[k] / (4 * math.pi) * pops[:, lines.up[k]] * lines.A[k]
+        np.testing.assert_allclose(chi[k], emis / O.planck(lines.freq_Hz[k], T), rtol=1e-10)
 
 
 # ------------------------------------------------------ segment optical depth
