@@ -36,6 +36,9 @@ constexpr int kCk = 64;            // intensity checkpoints per ray (adjoint)
 constexpr int kBlk = 64;           // segments per checkpoint block, so rays up to kCk * kBlk segments
 constexpr float kImgBand = 2e-4f;  // |du| this close (relative) to the switch is re-decided in FP64
 constexpr float kSqrtPiF = 1.77245385090551602730f;
+constexpr int kImgStage = 128;     // pixel-ray points staged in shared memory at a time (forward)
+
+struct Chan;
 
 struct ImgArgs {
     int64_t N, npix;
@@ -52,6 +55,7 @@ struct ImgArgs {
     float inv_Lunit;
     double thr;
     float theta_k;            // k_B / (m c^2): theta = theta_k T = d w / d log T * w
+    const Chan *chan;         // [nfreq] per-channel constants (k_image_chan)
     float *out;               // [nfreq][npix] intensity (SI)
     const float *gout;        // [nfreq][npix] dL/dI (SI)
     double *g_logT, *g_logn, *g_beta;
@@ -192,26 +196,68 @@ __device__ __forceinline__ void weights(float t, float &E, float &w0, float &w1,
     }
 }
 
-// One block per pixel, threads over channels.
+// The channel constants depend only on the channel: computed once per call.
+__global__ void k_image_chan(ImgArgs a, Chan *__restrict__ out)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < a.nfreq) out[f] = channel(a, f);
+}
+
+// One block per pixel, threads over channels.  The ray's point geometry (the
+// velocity projection, the width and the length of the segment ending at each
+// point) is the same for every channel: the block stages it in shared memory,
+// kImgStage points at a time, and each thread reads only its line's opacity
+// and source function per point.
 __global__ void __launch_bounds__(256) k_image_fwd(ImgArgs a)
 {
+    __shared__ float4 geo[kImgStage];     // beta, w, 1/w, length of the segment ending here
+    __shared__ int32_t pid[kImgStage];
     const int64_t q = blockIdx.x;
     const int64_t base = a.off[q];
-    const int64_t D = a.off[q + 1] - base - 1;
+    const int64_t np = a.off[q + 1] - base;  // points on the ray (segments + 1)
     float dd[6];
-    for (int f = threadIdx.x; f < a.nfreq; f += blockDim.x) {
-        const Chan ch = channel(a, f);
+    for (int f0 = 0; f0 < a.nfreq; f0 += blockDim.x) {   // the same trip count for the whole block
+        const int f = f0 + threadIdx.x;
+        const bool active = f < a.nfreq;
+        const Chan ch = a.chan[active ? f : 0];
         float I = ch.I0;
-        Pt A = load_pt(a, a.pts[base], ch.l, false);
-        for (int64_t d = 0; d < D; ++d) {
-            const Pt B = load_pt(a, a.pts[base + d + 1], ch.l, false);
-            const float t = seg_dtau(a, ch, A, B, seg_length(a, A.c, B.c), false, dd);
-            float E, w0, w1, gp;
-            weights(t, E, w0, w1, gp);
-            I = fmaf(E, I, fmaf(w0, A.S, w1 * B.S));
-            A = B;
+        Pt A{};
+        for (int64_t c0 = 0; c0 < np; c0 += kImgStage) {
+            const int n = (int)min((int64_t)kImgStage, np - c0);
+            __syncthreads();                 // the previous chunk is consumed
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int64_t d = c0 + i;
+                const int32_t c = a.pts[base + d];
+                const float *row = a.line + (int64_t)c * a.RS;
+                const float *v = a.vel_hl + 6 * (int64_t)c;
+                const float beta = fmaf(a.n2, v[2] + v[5], fmaf(a.n1, v[1] + v[4], a.n0 * (v[0] + v[3])));
+                const float dx = d > 0 ? seg_length(a, a.pts[base + d - 1], c) : 0.0f;
+                geo[i] = make_float4(beta, row[2 * a.Mpad], row[2 * a.Mpad + 1], dx);
+                pid[i] = c;
+            }
+            __syncthreads();
+            if (!active) continue;
+            for (int i = 0; i < n; ++i) {
+                const float4 g = geo[i];
+                Pt B;
+                B.c = pid[i];
+                const float *row = a.line + B.c * a.RS;
+                B.chi = row[ch.l];
+                B.S = row[a.Mpad + ch.l];
+                B.w = g.y;
+                B.winv = g.z;
+                B.beta = g.x;
+                B.theta = 0.0f;
+                if (c0 + i > 0) {
+                    const float t = seg_dtau(a, ch, A, B, g.w, false, dd);
+                    float E, w0, w1, gp;
+                    weights(t, E, w0, w1, gp);
+                    I = fmaf(E, I, fmaf(w0, A.S, w1 * B.S));
+                }
+                A = B;
+            }
         }
-        a.out[(int64_t)f * a.npix + q] = I * ch.U;
+        if (active) a.out[(int64_t)f * a.npix + q] = I * ch.U;
     }
 }
 
@@ -249,7 +295,7 @@ __global__ void __launch_bounds__(128) k_image_adj(ImgArgs a)
     for (int f0 = 0; f0 < a.nfreq; f0 += blockDim.x) {
         const int f = f0 + threadIdx.x;
         const bool active = f < a.nfreq;
-        const Chan ch = channel(a, active ? f : 0);
+        const Chan ch = a.chan[active ? f : 0];
         // forward, keeping checkpoints
         float I = ch.I0;
         {
@@ -378,6 +424,17 @@ ImgArgs image_args(mgt_model *m, const double *dir, int32_t nfreq, double fmin, 
     return a;
 }
 
+// The per-channel constants of one call, stream-ordered; the caller frees a.chan.
+mgt_status image_channels(ImgArgs &a, cudaStream_t s)
+{
+    Chan *c = nullptr;
+    MGT_CUDA(cudaMallocAsync(&c, sizeof(Chan) * a.nfreq, s));
+    k_image_chan<<<ceil_div(a.nfreq, 128), 128, 0, s>>>(a, c);
+    MGT_LAUNCH_CHECK("k_image_chan");
+    a.chan = c;
+    return MGT_OK;
+}
+
 mgt_status image_prepare(mgt_model *m, const double *dir, int32_t npx, int32_t npy, cudaStream_t s)
 {
     MGT_TRY_STATUS(trace_image(m, dir, npx, npy, s));
@@ -422,9 +479,11 @@ mgt_status mgt_image(mgt_model *m, const double dir[3], int32_t npx, int32_t npy
     float *dev = out;
     if (!on_device) MGT_CUDA(cudaMallocAsync(&dev, sizeof(float) * n, s));
     a.out = dev;
+    MGT_TRY_STATUS(image_channels(a, s));
     const int bd = nfreq >= 256 ? 256 : (nfreq + 31) / 32 * 32;
     k_image_fwd<<<(unsigned)a.npix, bd, 0, s>>>(a);
     MGT_LAUNCH_CHECK("k_image_fwd");
+    MGT_CUDA(cudaFreeAsync((void *)a.chan, s));
     if (!on_device) {
         MGT_CUDA(cudaMemcpyAsync(out, dev, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
         MGT_CUDA(cudaFreeAsync(dev, s));
@@ -459,9 +518,11 @@ mgt_status mgt_image_adjoint(mgt_model *m, const double dir[3], int32_t npx, int
     a.g_logT = acc;
     a.g_logn = acc + N;
     a.g_beta = acc + 2 * N;
+    MGT_TRY_STATUS(image_channels(a, s));
     const int bd = nfreq >= 128 ? 128 : (nfreq + 31) / 32 * 32;
     k_image_adj<<<(unsigned)a.npix, bd, 0, s>>>(a);
     MGT_LAUNCH_CHECK("k_image_adj");
+    MGT_CUDA(cudaFreeAsync((void *)a.chan, s));
     k_beta_to_vel<<<ceil_div(N, 256), 256, 0, s>>>(N, a.g_beta, dir[0], dir[1], dir[2], gv);
     MGT_LAUNCH_CHECK("k_beta_to_vel");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
