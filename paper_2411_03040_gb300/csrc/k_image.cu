@@ -36,7 +36,8 @@ constexpr int kCk = 64;            // intensity checkpoints per ray (adjoint)
 constexpr int kBlk = 64;           // segments per checkpoint block, so rays up to kCk * kBlk segments
 constexpr float kImgBand = 2e-4f;  // |du| this close (relative) to the switch is re-decided in FP64
 constexpr float kSqrtPiF = 1.77245385090551602730f;
-constexpr int kImgStage = 128;     // pixel-ray points staged in shared memory at a time (forward)
+constexpr int kImgStage = 128;     // pixel-ray points staged in shared memory at a time
+static_assert(kBlk + 1 <= kImgStage, "one adjoint checkpoint block must fit one stage");
 
 struct Chan;
 
@@ -89,21 +90,6 @@ struct Pt {
     int64_t c;
     float chi, S, w, winv, beta, theta;
 };
-
-__device__ __forceinline__ Pt load_pt(const ImgArgs &a, int64_t c, int l, bool want_theta)
-{
-    Pt p;
-    p.c = c;
-    const float *row = a.line + c * a.RS;
-    p.chi = row[l];
-    p.S = row[a.Mpad + l];
-    p.w = row[2 * a.Mpad];
-    p.winv = row[2 * a.Mpad + 1];
-    const float *v = a.vel_hl + 6 * c;
-    p.beta = fmaf(a.n2, v[2] + v[5], fmaf(a.n1, v[1] + v[4], a.n0 * (v[0] + v[3])));
-    p.theta = want_theta ? a.theta_k * (float)a.temp[c] : 0.0f;
-    return p;
-}
 
 __device__ __forceinline__ float seg_length(const ImgArgs &a, int64_t ca, int64_t cb)
 {
@@ -281,10 +267,56 @@ __device__ __forceinline__ void flush_point(const ImgArgs &a, int64_t c, float g
     }
 }
 
+// Stage ray points c0 .. c0+n-1 of pixel ray `base` (n <= kImgStage): the
+// velocity projection, width, 1/width, the length of the segment ending at the
+// point and, with `theta`, the width's temperature factor.  Every thread of the
+// block calls it.
+__device__ __forceinline__ void stage_points(const ImgArgs &a, int64_t base, int64_t c0, int n, bool theta,
+                                             float4 *geo, float *sth, int32_t *pid)
+{
+    __syncthreads();                 // the previous stage is consumed
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t d = c0 + i;
+        const int32_t c = a.pts[base + d];
+        const float *row = a.line + (int64_t)c * a.RS;
+        const float *v = a.vel_hl + 6 * (int64_t)c;
+        const float beta = fmaf(a.n2, v[2] + v[5], fmaf(a.n1, v[1] + v[4], a.n0 * (v[0] + v[3])));
+        const float dx = d > 0 ? seg_length(a, a.pts[base + d - 1], c) : 0.0f;
+        geo[i] = make_float4(beta, row[2 * a.Mpad], row[2 * a.Mpad + 1], dx);
+        pid[i] = c;
+        if (theta) sth[i] = a.theta_k * (float)a.temp[c];
+    }
+    __syncthreads();
+}
+
+// Staged point i with line l's scaled opacity and source function.
+__device__ __forceinline__ Pt staged_pt(const ImgArgs &a, const float4 *geo, const float *sth, const int32_t *pid,
+                                        int i, int l, bool theta)
+{
+    const float4 g = geo[i];
+    Pt p;
+    p.c = pid[i];
+    const float *row = a.line + p.c * a.RS;
+    p.chi = row[l];
+    p.S = row[a.Mpad + l];
+    p.w = g.y;
+    p.winv = g.z;
+    p.beta = g.x;
+    p.theta = theta ? sth[i] : 0.0f;
+    return p;
+}
+
 // Adjoint: one block per pixel, threads over channels (the whole block runs
-// the same number of channel rounds, so every warp intrinsic is uniform).
+// the same number of channel rounds, so every warp intrinsic and barrier is
+// uniform; threads past the last channel run channel 0 with zero weight).  The
+// ray's points are staged in shared memory: 128 at a time for the forward pass
+// that keeps the checkpoints, then one checkpoint block (at most kBlk + 1
+// points) at a time for its recomputation and reverse sweep.
 __global__ void __launch_bounds__(128) k_image_adj(ImgArgs a)
 {
+    __shared__ float4 geo[kImgStage];
+    __shared__ float sth[kImgStage];
+    __shared__ int32_t pid[kImgStage];
     const int64_t q = blockIdx.x;
     const int64_t base = a.off[q];
     const int64_t D = a.off[q + 1] - base - 1;
@@ -299,39 +331,49 @@ __global__ void __launch_bounds__(128) k_image_adj(ImgArgs a)
         // forward, keeping checkpoints
         float I = ch.I0;
         {
-            Pt A = load_pt(a, a.pts[base], ch.l, false);
-            for (int64_t d = 0; d < D; ++d) {
-                if (d % s == 0) ck[d / s] = I;
-                const Pt B = load_pt(a, a.pts[base + d + 1], ch.l, false);
-                const float t = seg_dtau(a, ch, A, B, seg_length(a, A.c, B.c), false, dd);
-                float E, w0, w1, gp;
-                weights(t, E, w0, w1, gp);
-                I = fmaf(E, I, fmaf(w0, A.S, w1 * B.S));
-                A = B;
+            Pt A{};
+            for (int64_t c0 = 0; c0 <= D; c0 += kImgStage) {
+                const int n = (int)min((int64_t)kImgStage, D + 1 - c0);
+                stage_points(a, base, c0, n, false, geo, sth, pid);
+                for (int i = 0; i < n; ++i) {
+                    const Pt B = staged_pt(a, geo, sth, pid, i, ch.l, false);
+                    const int64_t d = c0 + i - 1;              // the segment ending at this point
+                    if (d >= 0) {
+                        if (d % s == 0) ck[d / s] = I;
+                        const float t = seg_dtau(a, ch, A, B, geo[i].w, false, dd);
+                        float E, w0, w1, gp;
+                        weights(t, E, w0, w1, gp);
+                        I = fmaf(E, I, fmaf(w0, A.S, w1 * B.S));
+                    }
+                    A = B;
+                }
             }
         }
         float lam = active ? a.gout[(int64_t)f * a.npix + q] * ch.U : 0.0f;
         float pT = 0.0f, pn = 0.0f, pb = 0.0f;      // pending gradient of point P_{d+1}
         for (int64_t blk = nblk - 1; blk >= 0; --blk) {
             const int64_t d0 = blk * s, d1 = min(D, d0 + s);
+            stage_points(a, base, d0, (int)(d1 - d0 + 1), true, geo, sth, pid);
             float Ir = ck[blk];
-            Pt A = load_pt(a, a.pts[base + d0], ch.l, false);
+            Pt A = staged_pt(a, geo, sth, pid, 0, ch.l, false);
             for (int64_t d = d0; d < d1; ++d) {
-                loc[d - d0] = Ir;
-                const Pt B = load_pt(a, a.pts[base + d + 1], ch.l, false);
-                const float t = seg_dtau(a, ch, A, B, seg_length(a, A.c, B.c), false, dd);
+                const int i = (int)(d - d0) + 1;
+                loc[i - 1] = Ir;
+                const Pt B = staged_pt(a, geo, sth, pid, i, ch.l, false);
+                const float t = seg_dtau(a, ch, A, B, geo[i].w, false, dd);
                 float E, w0, w1, gp;
                 weights(t, E, w0, w1, gp);
                 Ir = fmaf(E, Ir, fmaf(w0, A.S, w1 * B.S));
                 A = B;
             }
             for (int64_t d = d1 - 1; d >= d0; --d) {
-                const Pt Pa = load_pt(a, a.pts[base + d], ch.l, true);
-                const Pt Pb = load_pt(a, a.pts[base + d + 1], ch.l, true);
-                const float t = seg_dtau(a, ch, Pa, Pb, seg_length(a, Pa.c, Pb.c), true, dd);
+                const int i = (int)(d - d0);
+                const Pt Pa = staged_pt(a, geo, sth, pid, i, ch.l, true);
+                const Pt Pb = staged_pt(a, geo, sth, pid, i + 1, ch.l, true);
+                const float t = seg_dtau(a, ch, Pa, Pb, geo[i + 1].w, true, dd);
                 float E, w0, w1, gp;
                 weights(t, E, w0, w1, gp);
-                const float dIdt = -E * loc[d - d0] + (gp + E) * Pa.S - gp * Pb.S;
+                const float dIdt = -E * loc[i] + (gp + E) * Pa.S - gp * Pb.S;
                 const float G = active ? lam * dIdt : 0.0f;
                 flush_point(a, Pb.c, pT + G * dd[3], pn + G * dd[4], pb + G * dd[5]);
                 pT = G * dd[0];
