@@ -12,6 +12,9 @@
  *  - All arrays are plain C pointers.  Host arrays passed to mgt_model_create
  *    are borrowed for the duration of the call and copied; the library owns all
  *    device memory of a model until mgt_model_destroy.
+ *  - A model lives on the device that is current when mgt_model_create is
+ *    called; every later call on it, mgt_model_destroy included, must be made
+ *    with that device current (the library never switches devices).
  *  - Output pointers are caller-owned.  Where an `on_device` flag is taken,
  *    nonzero means the pointer is a device address on the model's device,
  *    zero means host memory.
