@@ -115,12 +115,10 @@ __device__ __noinline__ bool img_trapezoid_fp64(const ImgArgs &a, double rf, int
 // Optical depth of segment (A -> B) for channel ch; with `want` also its
 // partial derivatives d[0..2] = d/d(log T_A, log n_A, beta_A) and
 // d[3..5] = the same for B.
-__device__ float seg_dtau(const ImgArgs &a, const Chan &ch, const Pt &A, const Pt &B, float dx, bool want,
+__device__ float seg_dtau(const ImgArgs &a, const Chan &ch, const Pt &A, const Pt &B, float dx, float iwbar, bool want,
                           float (&d)[6])
 {
     const float za = fmaf(-ch.rf, A.beta, ch.rf1), zb = fmaf(-ch.rf, B.beta, ch.rf1);
-    const float wbar = a.width_mode == 0 ? sqrtf(0.5f * (A.w * A.w + B.w * B.w)) : 0.5f * (A.w + B.w);
-    const float iwbar = 1.0f / wbar;
     const float du = (zb - za) * iwbar;
     const float thr = (float)a.thr;
     bool trap = fabsf(du) < thr;
@@ -175,11 +173,59 @@ __device__ __forceinline__ void weights(float t, float &E, float &w0, float &w1,
         w0 = t * (0.5f - t * (1.0f / 3.0f - t * (1.0f / 8.0f - t * (1.0f / 30.0f - t * (1.0f / 144.0f)))));
         gp = -0.5f + t * (1.0f / 3.0f - t * (1.0f / 8.0f - t * (1.0f / 30.0f - t * (1.0f / 144.0f))));
     } else {
-        const float g = (1.0f - E) / t;
+        const float rt = 1.0f / t;
+        const float g = (1.0f - E) * rt;
         w0 = g - E;
         w1 = 1.0f - g;
-        gp = (E - g) / t;
+        gp = (E - g) * rt;
     }
+}
+
+// Stage ray points c0 .. c0+n-1 of pixel ray `base` (n <= kImgStage): the
+// velocity projection, width, 1/width and length of the segment ending at the
+// point, that segment's inverse mean width, and, with `theta`, the width's
+// temperature factor.  Every thread of the block calls it.
+__device__ __forceinline__ void stage_points(const ImgArgs &a, int64_t base, int64_t c0, int n, bool theta,
+                                             float4 *geo, float *siw, float *sth, int32_t *pid)
+{
+    __syncthreads();                 // the previous stage is consumed
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t d = c0 + i;
+        const int32_t c = a.pts[base + d];
+        const float *row = a.line + (int64_t)c * a.RS;
+        const float *v = a.vel_hl + 6 * (int64_t)c;
+        const float beta = fmaf(a.n2, v[2] + v[5], fmaf(a.n1, v[1] + v[4], a.n0 * (v[0] + v[3])));
+        const float wb = row[2 * a.Mpad];
+        float dx = 0.0f, iw = 0.0f;
+        if (d > 0) {
+            const int32_t cp = a.pts[base + d - 1];
+            dx = seg_length(a, cp, c);
+            const float wa = a.line[(int64_t)cp * a.RS + 2 * a.Mpad];
+            iw = 1.0f / (a.width_mode == 0 ? sqrtf(0.5f * (wa * wa + wb * wb)) : 0.5f * (wa + wb));
+        }
+        geo[i] = make_float4(beta, wb, row[2 * a.Mpad + 1], dx);
+        siw[i] = iw;
+        pid[i] = c;
+        if (theta) sth[i] = a.theta_k * (float)a.temp[c];
+    }
+    __syncthreads();
+}
+
+// Staged point i with line l's scaled opacity and source function.
+__device__ __forceinline__ Pt staged_pt(const ImgArgs &a, const float4 *geo, const float *sth, const int32_t *pid,
+                                        int i, int l, bool theta)
+{
+    const float4 g = geo[i];
+    Pt p;
+    p.c = pid[i];
+    const float *row = a.line + p.c * a.RS;
+    p.chi = row[l];
+    p.S = row[a.Mpad + l];
+    p.w = g.y;
+    p.winv = g.z;
+    p.beta = g.x;
+    p.theta = theta ? sth[i] : 0.0f;
+    return p;
 }
 
 // The channel constants depend only on the channel: computed once per call.
@@ -190,13 +236,14 @@ __global__ void k_image_chan(ImgArgs a, Chan *__restrict__ out)
 }
 
 // One block per pixel, threads over channels.  The ray's point geometry (the
-// velocity projection, the width and the length of the segment ending at each
-// point) is the same for every channel: the block stages it in shared memory,
-// kImgStage points at a time, and each thread reads only its line's opacity
-// and source function per point.
+// velocity projection, the widths and the segment lengths) is the same for
+// every channel: the block stages it in shared memory, kImgStage points at a
+// time, and each thread reads only its line's opacity and source function per
+// point.
 __global__ void __launch_bounds__(256) k_image_fwd(ImgArgs a)
 {
-    __shared__ float4 geo[kImgStage];     // beta, w, 1/w, length of the segment ending here
+    __shared__ float4 geo[kImgStage];
+    __shared__ float siw[kImgStage];
     __shared__ int32_t pid[kImgStage];
     const int64_t q = blockIdx.x;
     const int64_t base = a.off[q];
@@ -210,32 +257,12 @@ __global__ void __launch_bounds__(256) k_image_fwd(ImgArgs a)
         Pt A{};
         for (int64_t c0 = 0; c0 < np; c0 += kImgStage) {
             const int n = (int)min((int64_t)kImgStage, np - c0);
-            __syncthreads();                 // the previous chunk is consumed
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const int64_t d = c0 + i;
-                const int32_t c = a.pts[base + d];
-                const float *row = a.line + (int64_t)c * a.RS;
-                const float *v = a.vel_hl + 6 * (int64_t)c;
-                const float beta = fmaf(a.n2, v[2] + v[5], fmaf(a.n1, v[1] + v[4], a.n0 * (v[0] + v[3])));
-                const float dx = d > 0 ? seg_length(a, a.pts[base + d - 1], c) : 0.0f;
-                geo[i] = make_float4(beta, row[2 * a.Mpad], row[2 * a.Mpad + 1], dx);
-                pid[i] = c;
-            }
-            __syncthreads();
+            stage_points(a, base, c0, n, false, geo, siw, nullptr, pid);
             if (!active) continue;
             for (int i = 0; i < n; ++i) {
-                const float4 g = geo[i];
-                Pt B;
-                B.c = pid[i];
-                const float *row = a.line + B.c * a.RS;
-                B.chi = row[ch.l];
-                B.S = row[a.Mpad + ch.l];
-                B.w = g.y;
-                B.winv = g.z;
-                B.beta = g.x;
-                B.theta = 0.0f;
+                const Pt B = staged_pt(a, geo, nullptr, pid, i, ch.l, false);
                 if (c0 + i > 0) {
-                    const float t = seg_dtau(a, ch, A, B, g.w, false, dd);
+                    const float t = seg_dtau(a, ch, A, B, geo[i].w, siw[i], false, dd);
                     float E, w0, w1, gp;
                     weights(t, E, w0, w1, gp);
                     I = fmaf(E, I, fmaf(w0, A.S, w1 * B.S));
@@ -267,45 +294,6 @@ __device__ __forceinline__ void flush_point(const ImgArgs &a, int64_t c, float g
     }
 }
 
-// Stage ray points c0 .. c0+n-1 of pixel ray `base` (n <= kImgStage): the
-// velocity projection, width, 1/width, the length of the segment ending at the
-// point and, with `theta`, the width's temperature factor.  Every thread of the
-// block calls it.
-__device__ __forceinline__ void stage_points(const ImgArgs &a, int64_t base, int64_t c0, int n, bool theta,
-                                             float4 *geo, float *sth, int32_t *pid)
-{
-    __syncthreads();                 // the previous stage is consumed
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int64_t d = c0 + i;
-        const int32_t c = a.pts[base + d];
-        const float *row = a.line + (int64_t)c * a.RS;
-        const float *v = a.vel_hl + 6 * (int64_t)c;
-        const float beta = fmaf(a.n2, v[2] + v[5], fmaf(a.n1, v[1] + v[4], a.n0 * (v[0] + v[3])));
-        const float dx = d > 0 ? seg_length(a, a.pts[base + d - 1], c) : 0.0f;
-        geo[i] = make_float4(beta, row[2 * a.Mpad], row[2 * a.Mpad + 1], dx);
-        pid[i] = c;
-        if (theta) sth[i] = a.theta_k * (float)a.temp[c];
-    }
-    __syncthreads();
-}
-
-// Staged point i with line l's scaled opacity and source function.
-__device__ __forceinline__ Pt staged_pt(const ImgArgs &a, const float4 *geo, const float *sth, const int32_t *pid,
-                                        int i, int l, bool theta)
-{
-    const float4 g = geo[i];
-    Pt p;
-    p.c = pid[i];
-    const float *row = a.line + p.c * a.RS;
-    p.chi = row[l];
-    p.S = row[a.Mpad + l];
-    p.w = g.y;
-    p.winv = g.z;
-    p.beta = g.x;
-    p.theta = theta ? sth[i] : 0.0f;
-    return p;
-}
-
 // Adjoint: one block per pixel, threads over channels (the whole block runs
 // the same number of channel rounds, so every warp intrinsic and barrier is
 // uniform; threads past the last channel run channel 0 with zero weight).  The
@@ -315,6 +303,7 @@ __device__ __forceinline__ Pt staged_pt(const ImgArgs &a, const float4 *geo, con
 __global__ void __launch_bounds__(128) k_image_adj(ImgArgs a)
 {
     __shared__ float4 geo[kImgStage];
+    __shared__ float siw[kImgStage];
     __shared__ float sth[kImgStage];
     __shared__ int32_t pid[kImgStage];
     const int64_t q = blockIdx.x;
@@ -334,13 +323,13 @@ __global__ void __launch_bounds__(128) k_image_adj(ImgArgs a)
             Pt A{};
             for (int64_t c0 = 0; c0 <= D; c0 += kImgStage) {
                 const int n = (int)min((int64_t)kImgStage, D + 1 - c0);
-                stage_points(a, base, c0, n, false, geo, sth, pid);
+                stage_points(a, base, c0, n, false, geo, siw, sth, pid);
                 for (int i = 0; i < n; ++i) {
                     const Pt B = staged_pt(a, geo, sth, pid, i, ch.l, false);
                     const int64_t d = c0 + i - 1;              // the segment ending at this point
                     if (d >= 0) {
                         if (d % s == 0) ck[d / s] = I;
-                        const float t = seg_dtau(a, ch, A, B, geo[i].w, false, dd);
+                        const float t = seg_dtau(a, ch, A, B, geo[i].w, siw[i], false, dd);
                         float E, w0, w1, gp;
                         weights(t, E, w0, w1, gp);
                         I = fmaf(E, I, fmaf(w0, A.S, w1 * B.S));
@@ -353,14 +342,14 @@ __global__ void __launch_bounds__(128) k_image_adj(ImgArgs a)
         float pT = 0.0f, pn = 0.0f, pb = 0.0f;      // pending gradient of point P_{d+1}
         for (int64_t blk = nblk - 1; blk >= 0; --blk) {
             const int64_t d0 = blk * s, d1 = min(D, d0 + s);
-            stage_points(a, base, d0, (int)(d1 - d0 + 1), true, geo, sth, pid);
+            stage_points(a, base, d0, (int)(d1 - d0 + 1), true, geo, siw, sth, pid);
             float Ir = ck[blk];
             Pt A = staged_pt(a, geo, sth, pid, 0, ch.l, false);
             for (int64_t d = d0; d < d1; ++d) {
                 const int i = (int)(d - d0) + 1;
                 loc[i - 1] = Ir;
                 const Pt B = staged_pt(a, geo, sth, pid, i, ch.l, false);
-                const float t = seg_dtau(a, ch, A, B, geo[i].w, false, dd);
+                const float t = seg_dtau(a, ch, A, B, geo[i].w, siw[i], false, dd);
                 float E, w0, w1, gp;
                 weights(t, E, w0, w1, gp);
                 Ir = fmaf(E, Ir, fmaf(w0, A.S, w1 * B.S));
@@ -370,7 +359,7 @@ __global__ void __launch_bounds__(128) k_image_adj(ImgArgs a)
                 const int i = (int)(d - d0);
                 const Pt Pa = staged_pt(a, geo, sth, pid, i, ch.l, true);
                 const Pt Pb = staged_pt(a, geo, sth, pid, i + 1, ch.l, true);
-                const float t = seg_dtau(a, ch, Pa, Pb, geo[i + 1].w, true, dd);
+                const float t = seg_dtau(a, ch, Pa, Pb, geo[i + 1].w, siw[i + 1], true, dd);
                 float E, w0, w1, gp;
                 weights(t, E, w0, w1, gp);
                 const float dIdt = -E * loc[i] + (gp + E) * Pa.S - gp * Pb.S;
