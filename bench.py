@@ -732,6 +732,8 @@ def main():
     if args.batch:
         run_batch(args)
         return
+    if args.impl == "reference" and int(os.environ.get("RANK", "0")) != 0:
+        return                 # the reference arm runs on rank 0 alone; the others exit without work
     from paper_2411_03040_gb300 import synth
     model = synth.config_model(args.workload, n_points=args.points)
     cfg = workload_config(model, args.workload)
