@@ -3,7 +3,8 @@
 With N ranks the bench runs N independent replicas of the workload: no data
 crosses ranks, the timed region is bracketed by barriers, the step time is the
 maximum over ranks and only rank 0 prints.  This checks those pieces without a
-GPU.
+GPU, and the summary of the nvidia-smi clock samples the bench takes during the
+timed region (median SM clock, throttle reasons seen active).
 """
 import os
 import socket
@@ -55,3 +56,20 @@ def test_single_rank_helpers_are_identity():
     import bench
     bench.barrier(1)
     assert bench.allreduce_max(1, 3.25) == 3.25
+
+
+def test_clock_summary_from_nvidia_smi_lines():
+    sys.path.insert(0, ROOT)
+    import bench
+    text = "\n".join([
+        "0, 2070, 2070, 812.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1398.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 905.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",     # unreadable sample: skipped
+        "garbage line",
+    ])
+    c = bench.summarize_clocks(text)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "samples": 3, "reasons": ["sw_power_cap"]}
+    hot = "0, 1500, 2070, 1400, 0x48, Active, Not Active, Active, Not Active"
+    assert bench.summarize_clocks(hot)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.summarize_clocks("") is None
