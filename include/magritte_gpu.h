@@ -161,7 +161,10 @@ typedef struct {
  */
 mgt_status mgt_model_create(mgt_model **out, const mgt_model_desc *desc, void *stream);
 
-/* Free all device and host memory of a model (NULL is a no-op). */
+/* Free all device and host memory of a model (NULL is a no-op); waits for the
+ * device first.  Its ray buffer goes back to the library's memory pool, which
+ * returns its reserve to the driver when the last model on the device is
+ * destroyed.  Always MGT_OK. */
 mgt_status mgt_model_destroy(mgt_model *m);
 
 /* Set the numerical options of mgt_formal_solve; NULL restores the defaults. */
@@ -192,11 +195,15 @@ mgt_status mgt_trace_rays(mgt_model *m, mgt_trace_stats *stats, void *stream);
 
 /* Copy the traced rays to host memory: ray_off [R*N+1] (exclusive prefix of
  * half-ray lengths, direction-major: entry r*N+o) and idx [total_steps] point
- * indices in outward order.  Either pointer may be NULL. */
+ * indices in outward order.  Either pointer may be NULL.  The stream is
+ * synchronised before returning.  MGT_ERR_STATE before mgt_trace_rays, and
+ * while pairs_per_batch > 0 (rays are then held one pair batch at a time). */
 mgt_status mgt_get_rays(mgt_model *m, int64_t *ray_off, int32_t *idx, void *stream);
 
-/* Set level populations [N][L] (m^-3; host pointer), or LTE when pops is NULL.
- * Resets the Ng history. */
+/* Set level populations [N][L] (m^-3; host pointer), or LTE when pops is
+ * NULL.  Resets the Ng history.  The stream is synchronised before returning,
+ * so `pops` may be reused at once.  MGT_ERR_ARG for a non-finite or negative
+ * entry, with the model unchanged. */
 mgt_status mgt_set_populations(mgt_model *m, const double *pops, void *stream);
 
 /* Copy the current level populations [N][L] to `pops` (host or device). */
