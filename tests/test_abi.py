@@ -74,6 +74,18 @@ def test_struct_layout_matches_header(tmp_path):
             assert int(out[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
 
 
+def _with(a, i, v):
+    a = np.array(a, copy=True)
+    a[i] = v
+    return a
+
+
+def _swap_line_levels(lines, k):
+    up, lo = lines.up[k], lines.lo[k]
+    lines.up = _with(lines.up, k, lo)
+    lines.lo = _with(lines.lo, k, up)
+
+
 def _small_model():
     from paper_2411_03040_gb300 import synth
     return synth.config_model(1, n_points=60)
@@ -89,6 +101,18 @@ def _small_model():
     (lambda m: setattr(m, "boundary", np.append(m.boundary, -2)), "boundary"),
     (lambda m: setattr(m.lines, "A", -m.lines.A), "line A"),
     (lambda m: setattr(m, "n_spec", np.zeros_like(m.n_spec)), "n_spec"),
+    (lambda m: setattr(m, "vturb2", -np.ones_like(m.vturb2)), "vturb2"),
+    (lambda m: setattr(m, "nbr_offsets", _with(m.nbr_offsets, 5, m.nbr_offsets[4] - 1)), "decrease"),
+    (lambda m: setattr(m.lines, "up", _with(m.lines.up, 0, m.lines.n_levels)), "line level"),
+    (lambda m: _swap_line_levels(m.lines, 0), "above lower"),
+    (lambda m: (setattr(m.lines, "up", _with(m.lines.up, 1, m.lines.up[0])),
+                setattr(m.lines, "lo", _with(m.lines.lo, 1, m.lines.lo[0]))), "duplicate radiative"),
+    (lambda m: setattr(m.lines, "freq_Hz", _with(m.lines.freq_Hz, 1, m.lines.freq_Hz[0] * (1 + 1e-7))),
+     "overlapping"),
+    (lambda m: setattr(m.lines, "cup", _with(m.lines.cup, 0, m.lines.n_levels)), "collision level"),
+    (lambda m: setattr(m.lines, "K_ul", _with(m.lines.K_ul, 0, -1e-17)), "K_ul"),
+    (lambda m: setattr(m.lines, "g", _with(m.lines.g, 0, 0.0)), "weights"),
+    (lambda m: setattr(m.lines, "mol_mass_kg", 0.0), "mol_mass"),
 ])
 def test_invalid_inputs_rejected_before_any_device_work(lib, breaker, fragment):
     from paper_2411_03040_gb300 import mgt
