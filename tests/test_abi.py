@@ -177,3 +177,32 @@ def test_batch_workload_specs_are_seeded_and_in_range():
     # log-uniform: about half the models below the geometric mean of the range
     assert 0.35 < np.mean(n < np.sqrt(5_000 * 200_000)) < 0.65
     assert len({x[4] for x in a}) == 256            # one seed per model
+
+
+@pytest.mark.parametrize("kw,fragment", [
+    (dict(rho=np.array([1.0, 2.0, -1.0, 1.0])), "rho"),
+    (dict(pos=np.where(np.arange(12).reshape(4, 3) == 5, np.inf, 0.0)), "positions"),
+    (dict(r_max=-0.1), "r_max"),
+    (dict(max_level=31), "max_level"),
+    (dict(n_side=1), "n_side"),
+    (dict(pos=np.zeros((0, 3)), rho=np.zeros(0)), "n_points"),
+])
+def test_remesh_rejects_bad_input_before_any_device_work(lib, kw, fragment):
+    from paper_2411_03040_gb300 import mgt
+    args = dict(pos=np.zeros((4, 3)), rho=np.ones(4), r_max=0.4, max_level=5, n_side=3)
+    args.update(kw)
+    with pytest.raises(mgt.MgtError) as e:
+        mgt.mgt_remesh(args["pos"], args["rho"], args["r_max"], args["max_level"], args["n_side"])
+    assert e.value.status == mgt.MGT_ERR_ARG
+    assert fragment in str(e.value)
+
+
+def test_noalloc_ng_rejects_sizes_and_null_pointers_before_any_device_work(lib):
+    import ctypes as C
+    buf = (C.c_double * 4)()
+    neg = C.c_int64()
+    # n_iterates outside 2..17, an empty vector, null device pointers
+    for n, ln, it, pr in [(1, 4, buf, buf), (18, 4, buf, buf), (3, 0, buf, buf), (3, 4, None, buf), (3, 4, buf, None)]:
+        st = lib.mgt_ng_extrapolate_noalloc(n, it, ln, pr, buf, C.byref(neg), None)
+        assert st == 1, (n, ln)
+        assert b"mgt_ng_extrapolate_noalloc" in lib.mgt_last_error()
