@@ -6,8 +6,10 @@
  *
  * Deliberately slow and literal: every (origin, ray pair, frequency bin, line)
  * rebuilds its full ray, evaluates the opacity at every point in the paper's
- * own frequency variables, and solves the second-order (Feautrier) system with
- * the textbook Rybicki-Hummer elimination.  OpenMP runs over origin points only.
+ * own frequency variables, assembles the second-order (Feautrier) system of
+ * the whole ray and solves it by the Thomas algorithm (forward elimination and
+ * back substitution), twice: once for u, once for the diagonal of the inverse.
+ * OpenMP runs over origin points only.
  * Built with -ffp-contract=off so that no multiply-add is fused: the ray-walk
  * predicates must round exactly as written.
  */
@@ -174,20 +176,80 @@ double oracle_segment_dtau_subdiv(double dx, double chi0, double chi1, double dn
 /* ------------------------------------------------------------------------ */
 /* Second-order (Feautrier) two-point system on one ray, solved at point io. */
 /*                                                                           */
-/* Points d = 0..D-1, dtau[d] = optical depth of segment (d, d+1).  Interior */
-/* rows: -A_d u_{d-1} + B_d u_d - C_d u_{d+1} = S_d with                     */
-/*   A_d = 2/(a(a+b)), C_d = 2/(b(a+b)), B_d = 1 + A_d + C_d,                */
-/* a = dtau[d-1], b = dtau[d].  End rows (Auer 1967 second-order boundary):  */
-/*   (1 + 2/t + 2/t^2) u_0 - (2/t^2) u_1 = S_0 + (2/t) I_left,               */
-/* mirrored at D-1 with I_right, t the optical depth of the end segment.     */
-/* Elimination: Rybicki & Hummer (1991) F-form from both ends,               */
-/*   F_d = (1 + A_d F_{d-1}/(1+F_{d-1})) / C_d,                              */
-/*   z_d = (S_d + A_d z_{d-1}) / (C_d (1 + F_d)),                            */
-/* and the mirrored G, w from the right.  At io:                             */
-/*   u = (S + A z_{io-1} + C w_{io+1}) / den,  L = 1/den (the diagonal of    */
-/*   the inverse matrix), den = B - A/(1+F) - C/(1+G).                       */
+/* Points d = 0..D-1, dtau[d] = optical depth of segment (d, d+1).  The      */
+/* tridiagonal system  -A_d u_{d-1} + B_d u_d - C_d u_{d+1} = r_d  is first  */
+/* assembled row by row:                                                     */
+/*   interior rows (a = dtau[d-1], b = dtau[d]):                             */
+/*     A_d = 2/(a(a+b)),  C_d = 2/(b(a+b)),  B_d = 1 + A_d + C_d,  r_d = S_d;*/
+/*   end rows (second-order boundary condition of Auer 1967, t the optical   */
+/*   depth of the end segment):                                              */
+/*     row 0:   B_0 = 1 + 2/t + 2/t^2,  C_0 = 2/t^2,  r_0 = S_0 + (2/t) I_left*/
+/*     row D-1: A = 2/t^2,  B = 1 + 2/t + 2/t^2,  r = S_{D-1} + (2/t) I_right.*/
+/* It is then solved by the Thomas algorithm over the whole ray: forward     */
+/* elimination from row 0 to row D-1 (pivots m_d, reduced right-hand sides   */
+/* r'_d), and back substitution from row D-1 down to row io, u_io = x_io.    */
+/* Lambda*_oo, the io-th diagonal entry of the inverse matrix, is x_io of a  */
+/* second Thomas solve with right-hand side e_io.                            */
+/*                                                                           */
+/* Pivots.  The textbook pivot m_d = B_d - A_d C_{d-1} / m_{d-1} subtracts   */
+/* numbers of size 1/dtau^2 whose difference is of order 1 + 2/dtau: for    */
+/* optically thin segments (dtau^2 below the rounding unit, common in the    */
+/* line wings) it loses every digit of the row's excess.  Each row's excess  */
+/* B_d - A_d - C_d is known exactly (1 inside, 1 + 2/t at the ends), so the  */
+/* same pivot is evaluated as                                                */
+/*   m_d = x_d + C_d,  x_d = (B_d - A_d - C_d) + A_d x_{d-1} / m_{d-1},      */
+/* with x_d the excess of the reduced row (x_0 = 1 + 2/t): algebraically the  */
+/* textbook value, formed from positive terms only.  The forward and back    */
+/* substitutions add positive terms too (all A, C, S, I >= 0).               */
 /* D == 1: no system; u = background, L = 0.                                 */
 /* ------------------------------------------------------------------------ */
+static void thomas_at(int64_t D, const double *dtau, const double *S, double I_left, double I_right, int64_t io,
+                      double *w, double *u_out, double *L_out)
+{
+    double *A = w, *C = w + D, *X = w + 2 * D, *R = w + 3 * D, *m = w + 4 * D, *rp = w + 5 * D;
+    /* assemble: sub-diagonal A, super-diagonal C, row excess X = B - A - C, right-hand side R */
+    for (int64_t d = 0; d < D; ++d) {
+        if (d == 0) {
+            double t = dtau[0];
+            A[d] = 0.0;
+            C[d] = 2.0 / (t * t);
+            X[d] = 1.0 + 2.0 / t;
+            R[d] = S[0] + 2.0 * I_left / t;
+        } else if (d == D - 1) {
+            double t = dtau[D - 2];
+            A[d] = 2.0 / (t * t);
+            C[d] = 0.0;
+            X[d] = 1.0 + 2.0 / t;
+            R[d] = S[D - 1] + 2.0 * I_right / t;
+        } else {
+            double a = dtau[d - 1], b = dtau[d];
+            A[d] = 2.0 / (a * (a + b));
+            C[d] = 2.0 / (b * (a + b));
+            X[d] = 1.0;
+            R[d] = S[d];
+        }
+    }
+    /* forward elimination: m[d] pivot, X[d] reduced excess, rp[d] reduced rhs */
+    for (int64_t d = 0; d < D; ++d) {
+        if (d > 0) X[d] = X[d] + A[d] * (X[d - 1] / m[d - 1]);
+        m[d] = X[d] + C[d];
+        rp[d] = d > 0 ? (R[d] + A[d] * rp[d - 1]) / m[d] : R[d] / m[d];
+    }
+    /* back substitution x_d = r'_d + (C_d / m_d) x_{d+1}, from D-1 to io */
+    double x = rp[D - 1];
+    for (int64_t d = D - 2; d >= io; --d) x = rp[d] + C[d] / m[d] * x;
+    *u_out = x;
+    /* second solve, right-hand side e_io: r'_d = 0 below io */
+    double q = 0.0;
+    for (int64_t d = io; d < D; ++d) {
+        q = d == io ? 1.0 / m[d] : A[d] * q / m[d];
+        rp[d] = q;
+    }
+    x = rp[D - 1];
+    for (int64_t d = D - 2; d >= io; --d) x = rp[d] + C[d] / m[d] * x;
+    *L_out = x;
+}
+
 void oracle_feautrier_at(int64_t D, const double *dtau, const double *S,
                          double I_left, double I_right, int64_t io,
                          double *u_out, double *L_out)
@@ -197,56 +259,9 @@ void oracle_feautrier_at(int64_t D, const double *dtau, const double *S,
         *L_out = 0.0;
         return;
     }
-    double F = 0.0, z = 0.0, G = 0.0, w = 0.0;
-    /* forward sweep over rows 0 .. io-1 */
-    for (int64_t d = 0; d < io; ++d) {
-        if (d == 0) {
-            double t = dtau[0];
-            double B0 = 1.0 + 2.0 / t + 2.0 / (t * t);
-            F = (1.0 + 2.0 / t) * t * t / 2.0;
-            z = (S[0] + 2.0 * I_left / t) / B0;
-        } else {
-            double a = dtau[d - 1], b = dtau[d];
-            double A = 2.0 / (a * (a + b)), C = 2.0 / (b * (a + b));
-            double Fn = (1.0 + A * F / (1.0 + F)) / C;
-            z = (S[d] + A * z) / (C * (1.0 + Fn));
-            F = Fn;
-        }
-    }
-    /* backward sweep over rows D-1 .. io+1 */
-    for (int64_t d = D - 1; d > io; --d) {
-        if (d == D - 1) {
-            double t = dtau[D - 2];
-            double B1 = 1.0 + 2.0 / t + 2.0 / (t * t);
-            G = (1.0 + 2.0 / t) * t * t / 2.0;
-            w = (S[D - 1] + 2.0 * I_right / t) / B1;
-        } else {
-            double a = dtau[d - 1], b = dtau[d];
-            double A = 2.0 / (a * (a + b)), C = 2.0 / (b * (a + b));
-            double Gn = (1.0 + C * G / (1.0 + G)) / A;
-            w = (S[d] + C * w) / (A * (1.0 + Gn));
-            G = Gn;
-        }
-    }
-    double den, num;
-    if (io == 0) {
-        double t = dtau[0];
-        double C = 2.0 / (t * t);
-        den = 1.0 + 2.0 / t + C * G / (1.0 + G);
-        num = S[0] + 2.0 * I_left / t + C * w;
-    } else if (io == D - 1) {
-        double t = dtau[D - 2];
-        double A = 2.0 / (t * t);
-        den = 1.0 + 2.0 / t + A * F / (1.0 + F);
-        num = S[D - 1] + 2.0 * I_right / t + A * z;
-    } else {
-        double a = dtau[io - 1], b = dtau[io];
-        double A = 2.0 / (a * (a + b)), C = 2.0 / (b * (a + b));
-        den = 1.0 + A * F / (1.0 + F) + C * G / (1.0 + G);
-        num = S[io] + A * z + C * w;
-    }
-    *u_out = num / den;
-    *L_out = 1.0 / den;
+    double *w = malloc(sizeof(double) * 6 * (size_t)D);
+    thomas_at(D, dtau, S, I_left, I_right, io, w, u_out, L_out);
+    free(w);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -294,6 +309,7 @@ void oracle_formal_solve(int64_t N, const double *pos, const double *vel, const 
         double *off = malloc(sizeof(double) * Dmax);
         double *dtau = malloc(sizeof(double) * Dmax);
         double *Sd = malloc(sizeof(double) * Dmax);
+        double *work = malloc(sizeof(double) * 6 * Dmax);
         for (int32_t m = 0; m < M; ++m) {
             Jbar[io_ * M + m] = 0.0;
             Lstar[io_ * M + m] = 0.0;
@@ -355,13 +371,18 @@ void oracle_formal_solve(int64_t N, const double *pos, const double *vel, const 
                         dtau[d] = t > tau_min ? t : tau_min;
                     }
                     double u, L;
-                    oracle_feautrier_at(D, dtau, Sd, Ibg, Ibg, d_o, &u, &L);
+                    if (D <= 1) {
+                        u = Ibg;
+                        L = 0.0;
+                    } else {
+                        thomas_at(D, dtau, Sd, Ibg, Ibg, d_o, work, &u, &L);
+                    }
                     Jbar[io_ * M + m] += (2.0 / R) * wq[q] * u;
                     Lstar[io_ * M + m] += (2.0 / R) * wq[q] * L;
                 }
             }
         }
-        free(pt); free(beta); free(dx); free(dnu); free(off); free(dtau); free(Sd);
+        free(pt); free(beta); free(dx); free(dnu); free(off); free(dtau); free(Sd); free(work);
     }
 }
 

@@ -223,6 +223,111 @@ def test_feautrier_matches_dense_lu():
                 assert 0 < L < 1
 
 
+def _exact_solve(dtau, S, Il, Ir, io):
+    """u_io and (T^-1)_{io,io} of the assembled system in exact rational
+    arithmetic (the float inputs converted exactly; Gauss-Jordan elimination)."""
+    from fractions import Fraction as Fr
+    D = len(S)
+    dt = [Fr(float(x)) for x in dtau]
+    T = [[Fr(0)] * D for _ in range(D)]
+    rhs = [Fr(float(x)) for x in S]
+    t = dt[0]
+    T[0][0], T[0][1] = 1 + 2 / t + 2 / t ** 2, -2 / t ** 2
+    rhs[0] += 2 * Fr(float(Il)) / t
+    t = dt[-1]
+    T[D - 1][D - 1], T[D - 1][D - 2] = 1 + 2 / t + 2 / t ** 2, -2 / t ** 2
+    rhs[D - 1] += 2 * Fr(float(Ir)) / t
+    for d in range(1, D - 1):
+        a, b = dt[d - 1], dt[d]
+        A, Cc = 2 / (a * (a + b)), 2 / (b * (a + b))
+        T[d][d - 1], T[d][d], T[d][d + 1] = -A, 1 + A + Cc, -Cc
+    e = [Fr(int(k == io)) for k in range(D)]
+    M = [T[k][:] + [rhs[k], e[k]] for k in range(D)]
+    for c in range(D):
+        p = next(r for r in range(c, D) if M[r][c] != 0)
+        M[c], M[p] = M[p], M[c]
+        for r in range(D):
+            if r != c and M[r][c] != 0:
+                f = M[r][c] / M[c][c]
+                M[r] = [x - f * y for x, y in zip(M[r], M[c])]
+    return float(M[io][D] / M[io][io]), float(M[io][D + 1] / M[io][io])
+
+
+def test_feautrier_exact_rational_at_extreme_depths():
+    # optically thin segments (down to the 1e-150 floor), thick ones and mixed
+    # rays: the oracle's solve against exact rational arithmetic
+    rng = np.random.default_rng(13)
+    cases = []
+    for D in range(2, 7):
+        for lo, hi in [(-150, -140), (-12, -6), (-3, 3), (2, 6), (-150, 6)]:
+            cases.append((D, np.exp(rng.uniform(lo, hi, D - 1) * np.log(10.0))))
+    for D, dtau in cases:
+        S = rng.uniform(0.1, 3.0, D)
+        Il, Ir = rng.uniform(0.0, 2.0, 2)
+        for io in range(D):
+            u_ex, L_ex = _exact_solve(dtau, S, Il, Ir, io)
+            u, L = O.feautrier_at(dtau, S, Il, Ir, io)
+            assert abs(u / u_ex - 1) < 1e-13, (D, dtau, io, u, u_ex)
+            assert L_ex == 0.0 or abs(L / L_ex - 1) < 1e-13, (D, dtau, io, L, L_ex)
+
+
+def _rh_two_sweep(dtau, S, Il, Ir, io):
+    """Cross-check: Rybicki-Hummer elimination from both ends toward io,
+    F_d = (1 + A_d F_{d-1}/(1 + F_{d-1})) / C_d with its source sweep, and the
+    mirrored sweep from the far end, combined at io (a formulation the oracle
+    does not use)."""
+    D = len(S)
+    F = z = G = w = 0.0
+    for d in range(io):
+        if d == 0:
+            t = dtau[0]
+            F = (1 + 2 / t) * t * t / 2
+            z = (S[0] + 2 * Il / t) / (1 + 2 / t + 2 / t ** 2)
+        else:
+            a, b = dtau[d - 1], dtau[d]
+            A, Cc = 2 / (a * (a + b)), 2 / (b * (a + b))
+            Fn = (1 + A * F / (1 + F)) / Cc
+            z = (S[d] + A * z) / (Cc * (1 + Fn))
+            F = Fn
+    for d in range(D - 1, io, -1):
+        if d == D - 1:
+            t = dtau[D - 2]
+            G = (1 + 2 / t) * t * t / 2
+            w = (S[D - 1] + 2 * Ir / t) / (1 + 2 / t + 2 / t ** 2)
+        else:
+            a, b = dtau[d - 1], dtau[d]
+            A, Cc = 2 / (a * (a + b)), 2 / (b * (a + b))
+            Gn = (1 + Cc * G / (1 + G)) / A
+            w = (S[d] + Cc * w) / (A * (1 + Gn))
+            G = Gn
+    if io == 0:
+        t = dtau[0]
+        Cc = 2 / (t * t)
+        den, num = 1 + 2 / t + Cc * G / (1 + G), S[0] + 2 * Il / t + Cc * w
+    elif io == D - 1:
+        t = dtau[D - 2]
+        A = 2 / (t * t)
+        den, num = 1 + 2 / t + A * F / (1 + F), S[D - 1] + 2 * Ir / t + A * z
+    else:
+        a, b = dtau[io - 1], dtau[io]
+        A, Cc = 2 / (a * (a + b)), 2 / (b * (a + b))
+        den, num = 1 + A * F / (1 + F) + Cc * G / (1 + G), S[io] + A * z + Cc * w
+    return num / den, 1 / den
+
+
+def test_feautrier_matches_two_sided_elimination_on_long_rays():
+    rng = np.random.default_rng(14)
+    for D in (17, 60, 301):
+        for lo, hi in [(-30, -8), (-4, 1), (-1, 4), (-30, 4)]:
+            dtau = np.exp(rng.uniform(lo, hi, D - 1) * np.log(10.0))
+            S = rng.uniform(0.1, 3.0, D)
+            Il, Ir = rng.uniform(0.0, 2.0, 2)
+            for io in (0, D // 3, D - 1):
+                u, L = O.feautrier_at(dtau, S, Il, Ir, io)
+                u2, L2 = _rh_two_sweep(dtau, S, Il, Ir, io)
+                assert abs(u / u2 - 1) < 1e-12 and abs(L / L2 - 1) < 1e-11, (D, lo, io, u, u2, L, L2)
+
+
 def test_feautrier_uniform_slab_second_order():
     # uniform static medium: u(o) -> S + (I - S)(e^-tau+ + e^-tau-)/2
     S, I = 2.0, 0.5
@@ -376,6 +481,62 @@ def test_se_matches_dense_lu_where_populations_are_not_tiny_and_balances_every_l
     assert np.max(np.abs(inflow - outflow) / outflow) < 1e-12
 
 
+def _tree_theorem_stationary(R):
+    """Steady state of the rate matrix R[i, j] (i -> j) by the Markov chain tree
+    theorem: the population of level i is proportional to the sum, over all
+    spanning trees directed toward i, of the product of their rates.  Trees
+    are enumerated by brute force (each other level picks a successor; keep
+    the choices whose paths all reach i).  Only products and sums of positive
+    numbers: exact to rounding however small the populations are."""
+    import itertools
+    L = R.shape[0]
+    w = np.zeros(L)
+    for root in range(L):
+        others = [j for j in range(L) if j != root]
+        total = 0.0
+        for succ in itertools.product(range(L), repeat=len(others)):
+            f = dict(zip(others, succ))
+            if any(f[j] == j for j in others):
+                continue
+            ok = True
+            for j in others:
+                seen, k = set(), j
+                while k != root:
+                    if k in seen:
+                        ok = False
+                        break
+                    seen.add(k)
+                    k = f[k]
+                if not ok:
+                    break
+            if ok:
+                total += float(np.prod([R[j, f[j]] for j in others]))
+        w[root] = total
+    return w / w.sum()
+
+
+def test_se_matches_markov_chain_tree_theorem_down_to_tiny_populations():
+    # cold gas and a weak field: the top level sits ~1e-41 below the ground
+    rng = np.random.default_rng(16)
+    lines = synth.linear_rotor(5, rng)
+    N = 4
+    T = np.array([0.6, 1.5, 8.0, 60.0])
+    nspec = rng.uniform(1, 10, N)
+    ncoll = 10 ** rng.uniform(3, 9, N)
+    M = lines.n_lines
+    J = np.stack([O.planck(lines.freq_Hz[k], 0.5) * rng.uniform(0.5, 2.0, N) for k in range(M)], axis=1)
+    Lst = rng.uniform(0.0, 0.6, (N, M))
+    p0 = O.lte_populations(T, nspec, lines.energy_J, lines.g)
+    new = O.stat_equilibrium(p0, J, Lst, T, ncoll, nspec, lines)
+    R = O.rate_matrix(p0, J, Lst, T, ncoll, nspec, lines)
+    for p in range(N):
+        Rp = R[p].copy()
+        np.fill_diagonal(Rp, 0.0)
+        ref = _tree_theorem_stationary(Rp) * nspec[p]
+        np.testing.assert_allclose(new[p], ref, rtol=1e-12)
+    assert (new / nspec[:, None]).min() < 1e-40
+
+
 def test_se_two_level_closed_form_and_high_density():
     rng = np.random.default_rng(6)
     lines = synth.linear_rotor(2, rng)
@@ -490,6 +651,110 @@ def test_ng_controllers_reach_fixed_point_faster():
     plain, cl, ad = run(None), run(O.NgClassical(4)), run(O.NgAdaptive(8))
     assert cl < plain and ad < plain
     assert ad < 1e-6
+
+
+# Hand-worked controller sequences (Sec. 4.2).  The iterates are small dyadic
+# vectors, so every coefficient and prediction below is a short fraction,
+# derived by hand from the closed form of the two-residual solve:
+#   G = [[r1.r1, r1.r2], [r1.r2, r2.r2]],  c proportional to
+#   (G22 - G12, G11 - G12), normalised to sum 1,
+# and for orthogonal residuals c_k proportional to 1/|r_k|^2.
+def _x(*v):
+    return np.array(v, dtype=np.float64)
+
+
+def test_ng_adaptive_first_running_prediction_is_the_newest_iterate():
+    # x1 = (1, 1), x2 = (1/2, 1), x3 = (1/2, 3/4): orthogonal residuals
+    # r1 = (-1/2, 0), r2 = (0, -1/4); c = (1/16, 1/4) / (5/16) = (1/5, 4/5);
+    # P3 = x2/5 + 4 x3/5 = (1/2, 4/5).  With P2 = x2 (the prediction of two
+    # iterates is the newer one): maxrel(P3, x2) = 1/5 < maxrel(x3, x2) = 1/4,
+    # so P3 is used.  (Reading P2 as x1 would give maxrel(P3, x1) = 1/2 > 1/4.)
+    ng = O.NgAdaptive(n_max=8)
+    ng.reset(_x(1, 1))
+    out, acc = ng.push(_x(0.5, 1))
+    assert not acc and np.array_equal(out, _x(0.5, 1))
+    out, acc = ng.push(_x(0.5, 0.75))
+    assert acc
+    np.testing.assert_allclose(out, _x(0.5, 0.8), rtol=1e-14)
+
+
+def test_ng_adaptive_compares_with_the_previous_running_prediction():
+    # x1 = (1, 1, 1), x2 = (3/2, 3/2, 19/16), x3 = (15/8, 15/8, 11/8),
+    # x4 = (9/4, 37/16, 21/16).
+    # m = 3: r1 = (1/2, 1/2, 3/16), r2 = (3/8, 3/8, 3/16), G = [[137, 105],
+    #   [105, 81]] / 256, c = (-24, 32) / 8 = (-3, 4), P3 = -3 x2 + 4 x3
+    #   = (3, 3, 31/16); maxrel(P3, x2) = 1 >= maxrel(x3, x2) = 1/4: not used,
+    #   P3 becomes the running prediction.
+    # m = 4: c = (-35, 38, 8) / 11, P4 = (147/44, 149/44, 339/176);
+    #   maxrel(P4, P3) = 17/132 < maxrel(x4, x3) = 7/30: used.  (Comparing with
+    #   a running prediction left at P2 = x2 would give 83/66 > 7/30.)
+    ng = O.NgAdaptive(n_max=8)
+    ng.reset(_x(1, 1, 1))
+    for x in (_x(1.5, 1.5, 19 / 16), _x(15 / 8, 15 / 8, 11 / 8)):
+        out, acc = ng.push(x)
+        assert not acc and np.array_equal(out, x)
+    out, acc = ng.push(_x(9 / 4, 37 / 16, 21 / 16))
+    assert acc
+    np.testing.assert_allclose(out, _x(147 / 44, 149 / 44, 339 / 176), rtol=1e-13)
+
+
+def test_ng_adaptive_forced_at_exactly_n_max_iterates():
+    # N_max = 4.  x1 = (1, 1, 1), x2 = (3/4, 1/2, 1/2), x3 = (5/8, 3/8, 1/4),
+    # x4 = (3/8, 3/8, 3/8).
+    # m = 3: r1 = (-1/4, -1/2, -1/2), r2 = (-1/8, -1/8, -1/4), G = [[18, 7],
+    #   [7, 3]] / 32, c = (-4, 11) / 7, P3 = (31/56, 17/56, 3/28);
+    #   maxrel(P3, x2) = 11/14 >= 1/2: not used.
+    # m = 4: c = (-4, 11, 2) / 9, P4 = (37/72, 23/72, 1/6);
+    #   maxrel(P4, P3) = 5/9 >= maxrel(x4, x3) = 1/2, but m = N_max: used anyway.
+    ng = O.NgAdaptive(n_max=4)
+    ng.reset(_x(1, 1, 1))
+    for x in (_x(0.75, 0.5, 0.5), _x(5 / 8, 3 / 8, 0.25)):
+        out, acc = ng.push(x)
+        assert not acc
+    out, acc = ng.push(_x(3 / 8, 3 / 8, 3 / 8))
+    assert acc
+    np.testing.assert_allclose(out, _x(37 / 72, 23 / 72, 1 / 6), rtol=1e-13)
+    # with N_max = 5 the same sequence is not accelerated at m = 4
+    ng = O.NgAdaptive(n_max=5)
+    ng.reset(_x(1, 1, 1))
+    accs = [ng.push(x)[1] for x in (_x(0.75, 0.5, 0.5), _x(5 / 8, 3 / 8, 0.25), _x(3 / 8, 3 / 8, 3 / 8))]
+    assert accs == [False, False, False]
+
+
+def test_ng_adaptive_negative_prediction_restarts_from_the_regular_iterate():
+    # N_max = 3.  x1 = (1, 1), x2 = (1/2, 1), x3 = (1/8, 17/16):
+    # r1 = (-1/2, 0), r2 = (-3/8, 1/16), G = [[64, 48], [48, 37]] / 256,
+    # c = (-11, 16) / 5, P3 = (-7/10, 6/5): forced at m = N_max but negative, so
+    # x3 is kept and the history restarts from it.  Then x4 = (1/8, 21/16),
+    # x5 = (3/16, 21/16): residuals (0, 1/4), (1/16, 0) from x3, c = (1, 16) / 17,
+    # P = (25/136, 21/16), used at m = 3 of the new history.
+    ng = O.NgAdaptive(n_max=3)
+    ng.reset(_x(1, 1))
+    assert not ng.push(_x(0.5, 1))[1]
+    out, acc = ng.push(_x(1 / 8, 17 / 16))
+    assert not acc and np.array_equal(out, _x(1 / 8, 17 / 16))
+    assert not ng.push(_x(1 / 8, 21 / 16))[1]
+    out, acc = ng.push(_x(3 / 16, 21 / 16))
+    assert acc
+    np.testing.assert_allclose(out, _x(25 / 136, 21 / 16), rtol=1e-14)
+
+
+def test_ng_classical_restarts_from_its_prediction():
+    # N_steps = 2.  y0 = (1, 1, 1), y1 = (1/2, 1, 1), y2 = (1/2, 3/4, 1):
+    # orthogonal residuals of sizes 1/2, 1/4, c = (1/5, 4/5), Q1 = (1/2, 4/5, 1)
+    # replaces y2 and is the first iterate of the next history.  y3 = (1/2, 4/5,
+    # 1/2), y4 = (3/4, 4/5, 1/2): residuals from Q1 of sizes 1/2, 1/4 again,
+    # Q2 = y3/5 + 4 y4/5 = (7/10, 4/5, 1/2).
+    ng = O.NgClassical(n_steps=2)
+    ng.reset(_x(1, 1, 1))
+    assert not ng.push(_x(0.5, 1, 1))[1]
+    out, acc = ng.push(_x(0.5, 0.75, 1))
+    assert acc
+    np.testing.assert_allclose(out, _x(0.5, 0.8, 1), rtol=1e-14)
+    assert not ng.push(_x(0.5, 0.8, 0.5))[1]
+    out, acc = ng.push(_x(0.75, 0.8, 0.5))
+    assert acc
+    np.testing.assert_allclose(out, _x(0.7, 0.8, 0.5), rtol=1e-14)
 
 
 # -------------------------------------------------- whole-model closed forms
