@@ -19,6 +19,9 @@ What is here, each step in the paper's notation:
     Appendix A), classical and adaptive variants.
   * The accelerated-Lambda-iteration driver (Listing 3,
     compute_level_populations_sparse).
+  * The synthetic image (Listing 3, compute_image_new) and its gradient with
+    respect to per-point log T, log n_spec and velocity by a plain reverse
+    sweep (in ``oracle_c.c``).
 
 Pins: every function here is checked in ``tests/test_oracle_*.py`` against
 closed forms, limits, invariants, brute force or an independent library route.
@@ -83,6 +86,9 @@ def _load():
             lib.oracle_image_rays.argtypes = [i64, P, P, P, P, P, i64, P, P, P, P, P, P]
             lib.oracle_image_solve.argtypes = [i64, P, P, P, P, f64, P, i32, P, P, P, f64, f64, i64, P, P,
                                                i32, P, P]
+            lib.oracle_image_adjoint.argtypes = [i64, P, P, P, P, f64, P, i32, P, P, P, f64, f64, i64, P, P,
+                                                 i32, P, P, P, P, P]
+            lib.oracle_image_branches.argtypes = [i64, P, P, P, P, f64, P, i32, P, f64, i64, P, P, i32, P, P]
             _lib = lib
     return _lib
 
@@ -621,3 +627,42 @@ def remesh(pos, rho, r_max, max_level, n_side):
     pts = np.concatenate([inner, bnd], axis=0)
     flags = np.concatenate([np.zeros(inner.shape[0], np.uint8), np.ones(bnd.shape[0], np.uint8)])
     return pts, flags, leaves
+
+
+def image_adjoint(model, pops, direction, npx, npy, nfreq, fmin, fmax, gimg, thr=0.35, rays=None):
+    """Gradient of L = sum(gimg * image) with respect to every point's log T,
+    log n_spec and velocity, from a plain FP64 reverse sweep of the image solve
+    (each segment's branch held; populations held as fractions of n_spec).
+    Returns (g_logT [N], g_logn [N], g_v [N][3]); g_v is along the line of sight,
+    the only velocity component the image depends on."""
+    lib = _load()
+    if rays is None:
+        rays = image_rays(model, direction, npx, npy)
+    chi, S, _ = line_chi_S(pops, model.lines)
+    nu_f = image_frequencies(nfreq, fmin, fmax)
+    arr = lambda a, t=np.float64: np.ascontiguousarray(a, t)
+    N = model.n_points
+    g = arr(np.asarray(gimg, np.float64).reshape(nfreq, npx * npy))
+    gT, gn, gl = np.zeros(N), np.zeros(N), np.zeros(N)
+    d = arr(direction)
+    lib.oracle_image_adjoint(N, _p(arr(model.pos)), _p(arr(model.vel)), _p(arr(model.temp)), _p(arr(model.vturb2)),
+                             float(model.lines.mol_mass_kg), _p(d), model.lines.n_lines, _p(arr(model.lines.freq_Hz)),
+                             _p(arr(chi)), _p(arr(S)), float(model.T_bg), thr, npx * npy, _p(rays.off), _p(rays.pts),
+                             nfreq, _p(nu_f), _p(g), _p(gT), _p(gn), _p(gl))
+    return gT, gn, gl[:, None] * d[None, :]
+
+
+def image_branches(model, direction, nfreq, fmin, fmax, rays, thr=0.35):
+    """Branch of every segment of every (channel, pixel ray) of the image solve,
+    [nfreq][segments], 1 = trapezoid, 0 = semi-analytic."""
+    lib = _load()
+    nu_f = image_frequencies(nfreq, fmin, fmax)
+    arr = lambda a, t=np.float64: np.ascontiguousarray(a, t)
+    npix = rays.off.shape[0] - 1
+    n_seg = int(rays.off[-1]) - npix
+    out = np.zeros((nfreq, n_seg), np.uint8)
+    lib.oracle_image_branches(model.n_points, _p(arr(model.pos)), _p(arr(model.vel)), _p(arr(model.temp)),
+                              _p(arr(model.vturb2)), float(model.lines.mol_mass_kg), _p(arr(direction)),
+                              model.lines.n_lines, _p(arr(model.lines.freq_Hz)), thr, npix, _p(rays.off),
+                              _p(rays.pts), nfreq, _p(nu_f), _p(out))
+    return out

@@ -581,3 +581,183 @@ void oracle_image_solve(int64_t N, const double *pos, const double *vel, const d
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the image (reverse sweep of oracle_image_solve).              */
+/*                                                                           */
+/* For a loss L = sum over channels and pixels of gimg * image, returns       */
+/* dL/d log T_p, dL/d log n_spec,p and dL/d (n . v_p) for every point p.      */
+/* Readings (the paper does not differentiate the image): populations are    */
+/* held as fractions of n_spec, so chi^{ij} scales with n_spec and S does not */
+/* change; T enters only through the Doppler widths (of the end points and    */
+/* of the segment's averaged width); each segment keeps the branch           */
+/* (trapezoid or semi-analytic) that the forward solve takes.                */
+/* Plain reverse mode, FP64: every (pixel, channel) reruns its forward solve, */
+/* keeping the intensity at every point, then walks back from the near end,  */
+/* lambda = dL/dI, lambda_d = e^-t lambda_{d+1}, and adds                     */
+/* lambda_{d+1} dI_{d+1}/dt dt/d(field) to the segment's two end points.      */
+/* ------------------------------------------------------------------------ */
+
+/* Partial derivatives of oracle_segment_dtau with its branch held:
+ * g[0..6] = dt / d(chi0, chi1, dnu0, dnu1, dnubar, off0, off1). */
+static void segment_dtau_grad(double dx, double chi0, double chi1, double dnu0, double dnu1, double dnubar,
+                              double off0, double off1, double thr, double *g)
+{
+    double shift = off1 - off0;
+    for (int k = 0; k < 7; ++k) g[k] = 0.0;
+    if (fabs(shift) < thr * dnubar) {
+        /* t = dx/2 (chi0 phi(off0, dnu0) + chi1 phi(off1, dnu1)),
+         * phi(o, d) = exp(-(o/d)^2) / (d sqrt(pi)):
+         * dphi/do = phi (-2 o / d^2),  dphi/dd = phi (2 o^2 / d^3 - 1/d) */
+        double p0 = profile(off0, dnu0), p1 = profile(off1, dnu1);
+        g[0] = 0.5 * dx * p0;
+        g[1] = 0.5 * dx * p1;
+        g[2] = 0.5 * dx * chi0 * p0 * (2.0 * off0 * off0 / (dnu0 * dnu0 * dnu0) - 1.0 / dnu0);
+        g[3] = 0.5 * dx * chi1 * p1 * (2.0 * off1 * off1 / (dnu1 * dnu1 * dnu1) - 1.0 / dnu1);
+        g[5] = 0.5 * dx * chi0 * p0 * (-2.0 * off0 / (dnu0 * dnu0));
+        g[6] = 0.5 * dx * chi1 * p1 * (-2.0 * off1 / (dnu1 * dnu1));
+        return;
+    }
+    /* t = dx/2 (chi0 + chi1) E / (2 shift),  E = erf(u1) - erf(u0),  u = off / dnubar;
+     * dE/du = +-(2/sqrt(pi)) exp(-u^2) */
+    double u0 = off0 / dnubar, u1 = off1 / dnubar, E;
+    if (u0 > 0.0 && u1 > 0.0)
+        E = erfc(u0) - erfc(u1);
+    else if (u0 < 0.0 && u1 < 0.0)
+        E = erfc(-u1) - erfc(-u0);
+    else
+        E = erf(u1) - erf(u0);
+    double c = 0.5 * dx * (chi0 + chi1);
+    double dE_du0 = -2.0 / OR_SQRTPI * exp(-u0 * u0), dE_du1 = 2.0 / OR_SQRTPI * exp(-u1 * u1);
+    g[0] = g[1] = 0.5 * dx * E / (2.0 * shift);
+    g[4] = c / (2.0 * shift) * (dE_du0 * (-u0 / dnubar) + dE_du1 * (-u1 / dnubar));
+    g[5] = c / (2.0 * shift) * dE_du0 / dnubar + c * E / (2.0 * shift * shift);
+    g[6] = c / (2.0 * shift) * dE_du1 / dnubar - c * E / (2.0 * shift * shift);
+}
+
+/* d/dt of the update I' = e^-t I + w0 S0 + w1 S1 (oracle_image_weights):
+ * with g(t) = (1 - e^-t)/t, w0 = g - e^-t, w1 = 1 - g,
+ * dI'/dt = -e^-t I + (g' + e^-t) S0 - g' S1,  g' = (t e^-t - 1 + e^-t)/t^2,
+ * by its Taylor series -1/2 + t/3 - t^2/8 + t^3/30 for t < 1e-3. */
+static double image_update_dt(double t, double I, double S0, double S1)
+{
+    double E = exp(-t), gp;
+    if (t < 1e-3)
+        gp = -0.5 + t / 3.0 - t * t / 8.0 + t * t * t / 30.0;
+    else
+        gp = (t * E - 1.0 + E) / (t * t);
+    return -E * I + (gp + E) * S0 - gp * S1;
+}
+
+void oracle_image_adjoint(int64_t N, const double *pos, const double *vel, const double *temp, const double *vturb2,
+                          double mol_mass, const double *n, int32_t M, const double *nu_line, const double *chi,
+                          const double *S, double T_bg, double thr, int64_t npix, const int64_t *ray_off,
+                          const int32_t *pts, int32_t nfreq, const double *nu_f, const double *gimg,
+                          double *g_logT, double *g_logn, double *g_vlos)
+{
+    for (int64_t p = 0; p < N; ++p) g_logT[p] = g_logn[p] = g_vlos[p] = 0.0;
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < npix; ++q) {
+        const int32_t *r = pts + ray_off[q];
+        int64_t D = ray_off[q + 1] - ray_off[q] - 1;   /* segments */
+        double *Iv = malloc(sizeof(double) * (size_t)(D + 1));
+        for (int32_t f = 0; f < nfreq; ++f) {
+            double lam = gimg[(int64_t)f * npix + q];
+            if (lam == 0.0) continue;
+            double nu = nu_f[f];
+            int32_t l = 0;
+            for (int32_t k = 1; k < M; ++k)
+                if (fabs(nu - nu_line[k]) < fabs(nu - nu_line[l])) l = k;
+            double nl = nu_line[l];
+            /* forward, keeping I at every point */
+            Iv[0] = oracle_planck(nu, T_bg);
+            for (int64_t d = 0; d < D; ++d) {
+                int64_t a = r[d], b = r[d + 1];
+                double ex = pos[3 * b] - pos[3 * a], ey = pos[3 * b + 1] - pos[3 * a + 1],
+                       ez = pos[3 * b + 2] - pos[3 * a + 2];
+                double dx = sqrt(ex * ex + ey * ey + ez * ez);
+                double va = (n[0] * vel[3 * a] + n[1] * vel[3 * a + 1] + n[2] * vel[3 * a + 2]) / OR_C;
+                double vb = (n[0] * vel[3 * b] + n[1] * vel[3 * b + 1] + n[2] * vel[3 * b + 2]) / OR_C;
+                double dna = nl / OR_C * sqrt(2.0 * OR_KB * temp[a] / mol_mass + vturb2[a]);
+                double dnb = nl / OR_C * sqrt(2.0 * OR_KB * temp[b] / mol_mass + vturb2[b]);
+                double Tb = 0.5 * (temp[a] + temp[b]), vb2 = 0.5 * (vturb2[a] + vturb2[b]);
+                double dnbar = nl / OR_C * sqrt(2.0 * OR_KB * Tb / mol_mass + vb2);
+                double t = oracle_segment_dtau(dx, chi[(int64_t)l * N + a], chi[(int64_t)l * N + b], dna, dnb, dnbar,
+                                               nu * (1.0 - va) - nl, nu * (1.0 - vb) - nl, thr);
+                double E, w0, w1;
+                oracle_image_weights(t, &E, &w0, &w1);
+                Iv[d + 1] = E * Iv[d] + w0 * S[(int64_t)l * N + a] + w1 * S[(int64_t)l * N + b];
+            }
+            /* reverse */
+            for (int64_t d = D - 1; d >= 0; --d) {
+                int64_t a = r[d], b = r[d + 1];
+                double ex = pos[3 * b] - pos[3 * a], ey = pos[3 * b + 1] - pos[3 * a + 1],
+                       ez = pos[3 * b + 2] - pos[3 * a + 2];
+                double dx = sqrt(ex * ex + ey * ey + ez * ez);
+                double va = (n[0] * vel[3 * a] + n[1] * vel[3 * a + 1] + n[2] * vel[3 * a + 2]) / OR_C;
+                double vb = (n[0] * vel[3 * b] + n[1] * vel[3 * b + 1] + n[2] * vel[3 * b + 2]) / OR_C;
+                double Aa = 2.0 * OR_KB * temp[a] / mol_mass + vturb2[a];
+                double Ab = 2.0 * OR_KB * temp[b] / mol_mass + vturb2[b];
+                double Abar = 2.0 * OR_KB * (0.5 * (temp[a] + temp[b])) / mol_mass + 0.5 * (vturb2[a] + vturb2[b]);
+                double dna = nl / OR_C * sqrt(Aa), dnb = nl / OR_C * sqrt(Ab), dnbar = nl / OR_C * sqrt(Abar);
+                double ca = chi[(int64_t)l * N + a], cb = chi[(int64_t)l * N + b];
+                double oa = nu * (1.0 - va) - nl, ob = nu * (1.0 - vb) - nl;
+                double t = oracle_segment_dtau(dx, ca, cb, dna, dnb, dnbar, oa, ob, thr);
+                double tb = lam * image_update_dt(t, Iv[d], S[(int64_t)l * N + a], S[(int64_t)l * N + b]);
+                double g[7];
+                segment_dtau_grad(dx, ca, cb, dna, dnb, dnbar, oa, ob, thr, g);
+                /* chain to the point fields */
+                double kTa = OR_KB * temp[a] / mol_mass, kTb = OR_KB * temp[b] / mol_mass;
+                double dlogTa = g[2] * dna * kTa / Aa + g[4] * dnbar * kTa / (2.0 * Abar);
+                double dlogTb = g[3] * dnb * kTb / Ab + g[4] * dnbar * kTb / (2.0 * Abar);
+                #pragma omp atomic
+                g_logT[a] += tb * dlogTa;
+                #pragma omp atomic
+                g_logT[b] += tb * dlogTb;
+                #pragma omp atomic
+                g_logn[a] += tb * g[0] * ca;
+                #pragma omp atomic
+                g_logn[b] += tb * g[1] * cb;
+                #pragma omp atomic
+                g_vlos[a] += tb * g[5] * (-nu / OR_C);
+                #pragma omp atomic
+                g_vlos[b] += tb * g[6] * (-nu / OR_C);
+                lam *= exp(-t);
+            }
+        }
+        free(Iv);
+    }
+}
+
+/* Branch of every segment of every (channel, pixel ray) in the forward solve:
+ * out[f * n_seg + s] = 1 for the trapezoid, 0 for the semi-analytic form, with
+ * s the segment's index over all rays (ray q's segments start at
+ * ray_off[q] - q). */
+void oracle_image_branches(int64_t N, const double *pos, const double *vel, const double *temp, const double *vturb2,
+                           double mol_mass, const double *n, int32_t M, const double *nu_line, double thr,
+                           int64_t npix, const int64_t *ray_off, const int32_t *pts, int32_t nfreq,
+                           const double *nu_f, uint8_t *out)
+{
+    int64_t n_seg = ray_off[npix] - npix;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < npix; ++q) {
+        const int32_t *r = pts + ray_off[q];
+        int64_t D = ray_off[q + 1] - ray_off[q] - 1, s0 = ray_off[q] - q;
+        for (int32_t f = 0; f < nfreq; ++f) {
+            double nu = nu_f[f];
+            int32_t l = 0;
+            for (int32_t k = 1; k < M; ++k)
+                if (fabs(nu - nu_line[k]) < fabs(nu - nu_line[l])) l = k;
+            double nl = nu_line[l];
+            for (int64_t d = 0; d < D; ++d) {
+                int64_t a = r[d], b = r[d + 1];
+                double va = (n[0] * vel[3 * a] + n[1] * vel[3 * a + 1] + n[2] * vel[3 * a + 2]) / OR_C;
+                double vb = (n[0] * vel[3 * b] + n[1] * vel[3 * b + 1] + n[2] * vel[3 * b + 2]) / OR_C;
+                double Tb = 0.5 * (temp[a] + temp[b]), vb2 = 0.5 * (vturb2[a] + vturb2[b]);
+                double dnbar = nl / OR_C * sqrt(2.0 * OR_KB * Tb / mol_mass + vb2);
+                double shift = (nu * (1.0 - vb) - nl) - (nu * (1.0 - va) - nl);
+                out[(int64_t)f * n_seg + s0 + d] = fabs(shift) < thr * dnbar ? 1 : 0;
+            }
+        }
+    }
+}

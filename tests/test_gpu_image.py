@@ -1,11 +1,14 @@
 """Synthetic image (mgt_image) and its adjoint against the CPU oracle, through the C-ABI.
 
 Tolerances: pixel rays bit-exact (anchors and point lists); image 1e-4
-relative per pixel and channel (FP32 path); adjoint gradients against FP64
-central differences of the oracle image within 2e-3 of the largest sampled
+relative per pixel and channel (FP32 path); adjoint gradients against the
+oracle's FP64 gradient (a reverse sweep of its image solve) element by element
+on 64 points, within 2e-3 relative plus 2e-4 of the field's largest sampled
 gradient; against central differences of the GPU image on 64 points (h = 1e-4
 in log T and log n_spec, 1 m/s in velocity; FP32 images differenced pixel by
-pixel, unaffected pixels cancel exactly) within 2e-2 for at least 60 of them.
+pixel, unaffected pixels cancel exactly) within 2e-2 of the largest, leaving
+out only (point, field) pairs whose step moves a segment across the
+trapezoid / erf switch (found from the oracle's branch map).
 """
 import numpy as np
 import pytest
@@ -16,6 +19,10 @@ from paper_2411_03040_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 DIR = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+# adjoint (FP32) against the oracle's FP64 gradient: relative, with an absolute
+# floor of the field's largest sampled gradient for entries that are sums of
+# contributions of both signs
+RTOL_ADJ, ATOL_ADJ = 2e-3, 2e-4
 
 
 @pytest.fixture(scope="module")
@@ -72,46 +79,27 @@ def test_image_matches_oracle(mgt, case):
     assert np.max(np.abs(out.cpu().numpy() - ref2) / np.abs(ref2)) < 1e-4
 
 
-def _oracle_loss(m, pops, w, lo, hi, npx, npy, nfreq, rays):
-    img, _ = O.image(m, pops, DIR, npx, npy, nfreq, lo, hi, rays=rays)
-    return float(np.sum(w * img))
-
-
-def test_adjoint_matches_oracle_finite_differences(mgt):
+def test_adjoint_matches_oracle_gradient(mgt):
+    # element by element against the oracle's FP64 reverse sweep, on 64 random
+    # points of the pixel rays, all three fields (the velocity gradient lies
+    # along the line of sight on both sides)
     m = synth.config_model(1, n_points=600)
-    npx, npy, nfreq = 10, 10, 15
+    npx, npy, nfreq = 12, 12, 15
     lo, hi = _band(m)
     rng = np.random.default_rng(3)
     w = rng.uniform(0.0, 1.0, size=(nfreq, npy, npx))
     h = mgt.mgt_model_create(m)
     gT, gn, gv = mgt.mgt_image_adjoint(h, DIR, npx, npy, nfreq, lo, hi, w.astype(np.float32))
-    pops = _pops(m)
     rays = O.image_rays(m, DIR, npx, npy)
-    on_rays = np.unique(rays.pts)
-    pick = rng.choice(on_rays, size=16, replace=False)
-    eps = 1e-6
-    fd = {"T": [], "n": [], "v": []}
-    for c in pick:
-        for key in ("T", "n", "v"):
-            vals = []
-            for sgn in (1, -1):
-                mm = synth.Model(m.name, m.pos, m.vel.copy(), m.temp.copy(), m.vturb2, m.n_coll, m.n_spec.copy(),
-                                 m.nbr_offsets, m.nbrs, m.boundary, m.dirs, m.n_quad, m.lines, m.T_bg)
-                pp = pops.copy()
-                if key == "T":
-                    mm.temp[c] *= np.exp(sgn * eps)
-                elif key == "n":
-                    mm.n_spec[c] *= np.exp(sgn * eps)
-                    pp[c] *= np.exp(sgn * eps)
-                else:
-                    mm.vel[c] = mm.vel[c] + sgn * 1e-3 * DIR        # 1 mm/s along the line of sight
-                vals.append(_oracle_loss(mm, pp, w, lo, hi, npx, npy, nfreq, rays))
-            fd[key].append((vals[0] - vals[1]) / (2 * (eps if key != "v" else 1e-3)))
-    for key, g in (("T", gT[pick]), ("n", gn[pick]), ("v", gv[pick] @ DIR)):
-        ref = np.asarray(fd[key])
+    rT, rn, rv = O.image_adjoint(m, _pops(m), DIR, npx, npy, nfreq, lo, hi, w.astype(np.float32).astype(np.float64),
+                                 rays=rays)
+    pick = rng.choice(np.unique(rays.pts), size=64, replace=False)
+    for key, g, ref in (("T", gT, rT), ("n", gn, rn), ("v", gv, rv)):
+        g, ref = g[pick], ref[pick]
         scale = np.max(np.abs(ref))
         assert scale > 0
-        assert np.max(np.abs(g - ref)) < 2e-3 * scale, (key, g, ref)
+        err = np.abs(g - ref)
+        assert np.all(err <= RTOL_ADJ * np.abs(ref) + ATOL_ADJ * scale), (key, np.max(err / (np.abs(ref) + scale)))
 
 
 def test_adjoint_matches_gpu_finite_differences_and_autograd(mgt):
@@ -133,10 +121,13 @@ def test_adjoint_matches_gpu_finite_differences_and_autograd(mgt):
         return img.astype(np.float64)
 
     T0, n0, v0 = m.temp.copy(), m.n_spec.copy(), m.vel.copy()
-    bad = []
+    rays = O.image_rays(m, DIR, npx, npy)
+    base_br = O.image_branches(m, DIR, nfreq, lo, hi, rays)
+    res = []
+    flips = 0
     for c in pick:
         for key, g in (("T", gT[c]), ("n", gn[c]), ("v", gv[c] @ DIR)):
-            imgs = []
+            imgs, same = [], True
             for sgn in (1, -1):
                 T, n, v = T0.copy(), n0.copy(), v0.copy()
                 if key == "T":
@@ -146,18 +137,26 @@ def test_adjoint_matches_gpu_finite_differences_and_autograd(mgt):
                 else:
                     v[c] = v[c] + sgn * 1.0 * DIR                  # 1 m/s
                 imgs.append(loss(T, n, v))
+                mm = synth.Model(m.name, m.pos, v, T, m.vturb2, m.n_coll, n, m.nbr_offsets, m.nbrs, m.boundary,
+                                 m.dirs, m.n_quad, m.lines, m.T_bg)
+                same = same and np.array_equal(O.image_branches(mm, DIR, nfreq, lo, hi, rays), base_br)
             step = hstep if key != "v" else 1.0
             fdv = float(np.sum(w * (imgs[0] - imgs[1]))) / (2 * step)
-            bad.append((key, g, fdv))
+            if same:
+                res.append((key, g, fdv))
+            else:
+                flips += 1
     mgt.mgt_set_point_fields(h, T0, n0, v0)
-    # A finite step can move a segment across the trapezoid / erf switch, where
-    # the image jumps (the two forms differ slightly at the threshold) and the
-    # difference quotient means nothing; such points are allowed to miss.
+    # A finite step that moves a segment across the trapezoid / erf switch
+    # makes the image jump (the two forms differ slightly at the threshold), so
+    # the difference quotient means nothing there: such (point, field) pairs,
+    # found from the oracle's branch map of the perturbed fields, are left out.
+    assert flips <= 8, flips
     for key in ("T", "n", "v"):
-        g = np.array([b[1] for b in bad if b[0] == key])
-        f = np.array([b[2] for b in bad if b[0] == key])
-        ok = np.abs(g - f) < 2e-2 * np.max(np.abs(f))
-        assert ok.sum() >= 60, (key, int(ok.sum()))
+        g = np.array([b[1] for b in res if b[0] == key])
+        f = np.array([b[2] for b in res if b[0] == key])
+        assert g.size >= 56
+        assert np.all(np.abs(g - f) < 2e-2 * np.max(np.abs(f))), (key, np.max(np.abs(g - f)) / np.max(np.abs(f)))
     # the autograd.Function gives the same gradients as the direct adjoint call
     from paper_2411_03040_gb300.autograd import ImageFunction
     lt = torch.tensor(np.log(T0), device="cuda", requires_grad=True)

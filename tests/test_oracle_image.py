@@ -120,3 +120,92 @@ def test_uniform_velocity_shifts_the_spectrum(v):
     iv0, _ = O.image(mv, pops, n, 6, 6, 11, lo, hi)
     is0, _ = O.image(ms, pops, n, 6, 6, 11, lo * b, hi * b)
     assert np.max(np.abs(iv0 - is0) / np.max(np.abs(is0))) < 1e-9
+
+
+# ------------------------------------------------------------- image gradient
+def test_image_gradient_uniform_column_closed_form():
+    # uniform static lattice, line of sight along a lattice axis: every full
+    # column gives I = S + (I_bg - S) exp(-tau), tau proportional to n_spec and
+    # to phi(nu - nu0; dnu) = exp(-u^2) / (dnu sqrt(pi)), u = (nu - nu0)/dnu,
+    # dnu proportional to sqrt(2kT/m) (no turbulence here).  Changing every
+    # point of a column together:
+    #   d I / d log n  = (S - I_bg) e^-tau tau
+    #   d I / d log T  = (S - I_bg) e^-tau tau (2 u^2 - 1) / 2
+    #   d I / d (n.v)  = (S - I_bg) e^-tau tau (-2 u / dnu) (-nu / c)
+    # so the oracle's per-point gradients summed over a column must give these.
+    m = _lattice()
+    n = np.array([0.0, 0.0, 1.0])
+    pops = O.lte_populations(m.temp, m.n_spec, m.lines.energy_J, m.lines.g)
+    chi, S, _ = O.line_chi_S(pops, m.lines)
+    nu0 = m.lines.freq_Hz[0]
+    w = math.sqrt(2 * O.KB * 80.0 / m.lines.mol_mass_kg) / O.C
+    nf = 7
+    lo, hi = nu0 * (1 - 2 * w), nu0 * (1 + 2 * w)
+    rays = O.image_rays(m, n, 7, 7)
+    full = np.nonzero(np.diff(rays.off) == 7)[0]
+    assert full.size == 25
+    h = 1e11
+    dnu = nu0 * w
+    for f, nu in enumerate(O.image_frequencies(nf, lo, hi)):
+        gimg = np.zeros((nf, 7, 7))
+        gimg[f] = 1.0
+        gT, gn, gv = O.image_adjoint(m, pops, n, 7, 7, nf, lo, hi, gimg, rays=rays)
+        u = (nu - nu0) / dnu
+        tau = chi[0, 0] * math.exp(-u * u) / (dnu * math.sqrt(math.pi)) * 6 * h
+        base = (S[0, 0] - O.planck(nu, m.T_bg)) * math.exp(-tau) * tau
+        for q in full:
+            col = rays.pts[rays.off[q]:rays.off[q + 1]]
+            for got, want in ((gn[col].sum(), base), (gT[col].sum(), base * (2 * u * u - 1) / 2),
+                              ((gv[col] @ n).sum(), base * (-2 * u / dnu) * (-nu / O.C))):
+                assert abs(got - want) <= 1e-10 * abs(base) + 1e-10 * abs(want), (f, q, got, want)
+
+
+def test_image_gradient_matches_finite_differences_of_the_oracle_image():
+    # per point and field, against central differences of the oracle's own FP64
+    # image; a (point, field) whose perturbation moves any segment across the
+    # trapezoid / erf switch (a jump of the image) is left out and counted
+    m = synth.config_model(1, n_points=500)
+    d = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+    npx = npy = 8
+    nf = 9
+    nu0 = m.lines.freq_Hz[0]
+    lo, hi = nu0 * (1 - 4e-5), nu0 * (1 + 4e-5)
+    rng = np.random.default_rng(31)
+    gimg = rng.uniform(0.0, 1.0, size=(nf, npy, npx))
+    pops = O.lte_populations(m.temp, m.n_spec, m.lines.energy_J, m.lines.g)
+    rays = O.image_rays(m, d, npx, npy)
+    gT, gn, gv = O.image_adjoint(m, pops, d, npx, npy, nf, lo, hi, gimg, rays=rays)
+    base_br = O.image_branches(m, d, nf, lo, hi, rays)
+    pick = rng.choice(np.unique(rays.pts), size=24, replace=False)
+    skipped = 0
+    # the velocity step is 0.1 m/s: a shift of ~40 Hz in offsets formed as differences of
+    # frequencies of ~1e11 Hz (rounding ~1e-5 Hz), far below a line width (~5e5 Hz)
+    for key, g, step in (("T", gT, 1e-6), ("n", gn, 1e-6), ("v", gv @ d, 0.1)):
+        fd, got = [], []
+        for c in pick:
+            vals, same = [], True
+            for sgn in (1, -1):
+                mm = synth.Model(m.name, m.pos, m.vel.copy(), m.temp.copy(), m.vturb2, m.n_coll, m.n_spec.copy(),
+                                 m.nbr_offsets, m.nbrs, m.boundary, m.dirs, m.n_quad, m.lines, m.T_bg)
+                pp = pops.copy()
+                if key == "T":
+                    mm.temp[c] *= math.exp(sgn * step)
+                elif key == "n":
+                    mm.n_spec[c] *= math.exp(sgn * step)
+                    pp[c] *= math.exp(sgn * step)
+                else:
+                    mm.vel[c] = mm.vel[c] + sgn * step * d
+                same = same and np.array_equal(O.image_branches(mm, d, nf, lo, hi, rays), base_br)
+                img, _ = O.image(mm, pp, d, npx, npy, nf, lo, hi, rays=rays)
+                vals.append(float(np.sum(gimg * img)))
+            if not same:
+                skipped += 1
+                continue
+            fd.append((vals[0] - vals[1]) / (2 * step))
+            got.append(g[c])
+        fd, got = np.asarray(fd), np.asarray(got)
+        scale = np.max(np.abs(fd))
+        assert scale > 0
+        err = np.abs(got - fd)
+        assert np.all(err <= 1e-6 * scale + 1e-5 * np.abs(fd)), (key, np.max(err / scale))
+    assert skipped <= 3
