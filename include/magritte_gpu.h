@@ -377,7 +377,8 @@ mgt_status mgt_remesh(int64_t n_points, const double *pos, const double *rho, do
  *               with MGT_ERR_ARG (the scratch holds at most 16 residuals)
  *   iterates    device, [n_iterates][len] f64 row-major, oldest first
  *   len         elements per iterate, >= 1
- *   prediction  device, [len] f64 (caller-owned; may not alias iterates)
+ *   prediction  device, [len] f64 (caller-owned; a prediction overlapping the
+ *               iterates is rejected with MGT_ERR_ARG)
  *   coef        host, [n_iterates-1] coefficients c_k, may be NULL
  *   n_negative  host, number of negative prediction entries, may be NULL
  * Both device buffers must be on the current device.  MGT_ERR_SINGULAR (the
@@ -386,11 +387,13 @@ mgt_status mgt_remesh(int64_t n_points, const double *pos, const double *rho, do
  *
  * Working memory is one static device array of MGT_NG_NOALLOC_SCRATCH_BYTES
  * that every GPU loading this library holds until the process exits; the call
- * itself allocates nothing on the device.  The first call on a device looks
- * up that device's address of the array (cudaGetSymbolAddress), so make it
- * before any stream capture.  All calls share the one array: calls that can
- * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.
+ * itself allocates nothing on the device.  The first call on a device does a
+ * one-time set-up, looking up that device's address of the array
+ * (cudaGetSymbolAddress, retried by the next call if it fails), so make that
+ * first call before any stream capture.  All calls share the one array, which
+ * keeps the last call's contents (each call clears what it accumulates):
+ * calls that can overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller.
  */
 #define MGT_NG_NOALLOC_MAX_ITERATES 17
 #define MGT_NG_NOALLOC_SCRATCH_BYTES 157952
@@ -491,6 +494,28 @@ mgt_status mgt_model_sizes(const mgt_model *m, int64_t *n_points, int32_t *n_ray
 /* Number of kernels this library has launched in the process so far (all
  * models, all threads); library kernels such as CUB scans are not counted. */
 mgt_status mgt_launch_count(int64_t *count);
+
+/*
+ * Per-kernel timing, for measurement (the paper has no counterpart: it times
+ * whole runs).  mgt_kernel_timing(1) clears the totals and starts recording a
+ * CUDA event before and after each instrumented kernel launch of this library
+ * (line data, ray walk and compaction, formal solution, statistical
+ * equilibrium, Ng), on the launch's own stream; launches on a capturing stream
+ * are not recorded.  mgt_kernel_timing(0) stops recording.
+ * mgt_kernel_times waits for the recorded events, adds their durations to the
+ * per-kernel totals and returns up to `capacity` of them in `out` (host,
+ * caller-owned) with their number in *n_out (the number of kernels timed so
+ * far, which may exceed `capacity`).  Timing adds two event records per launch.
+ */
+typedef struct {
+    char name[48];          /* kernel name, NUL-terminated */
+    int64_t launches;       /* launches recorded */
+    double total_ms;        /* summed event-to-event durations */
+    double bytes;           /* summed algorithmic bytes (least the kernel must read
+                               and write) of the launches, 0 where not stated */
+} mgt_kernel_time;
+mgt_status mgt_kernel_timing(int32_t enable);
+mgt_status mgt_kernel_times(int32_t capacity, mgt_kernel_time *out, int32_t *n_out);
 
 /* Thread-local description of the last non-OK status of this thread. */
 const char *mgt_last_error(void);

@@ -20,6 +20,65 @@ static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Per-kernel event timing (measurement only).  Event pairs are recorded while
+// timing is on and resolved into per-name totals by mgt_kernel_times.
+namespace {
+struct KtRecord {
+    const char *name;
+    cudaEvent_t a, b;
+    double bytes;
+};
+struct KtTotal {
+    std::string name;
+    long long launches;
+    double ms, bytes;
+};
+std::mutex g_kt_mu;
+std::atomic<bool> g_kt_on{false};
+std::vector<KtRecord> g_kt_pending;
+std::vector<cudaEvent_t> g_kt_spare;
+std::vector<KtTotal> g_kt_totals;
+
+cudaEvent_t kt_event()
+{
+    if (!g_kt_spare.empty()) {
+        cudaEvent_t e = g_kt_spare.back();
+        g_kt_spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+}  // namespace
+
+KernelTimer::KernelTimer(const char *name, cudaStream_t s, double bytes) : name_(name), s_(s), bytes_(bytes)
+{
+    if (!g_kt_on.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    a_ = kt_event();
+    b_ = kt_event();
+    if (!a_ || !b_ || cudaEventRecord(a_, s) != cudaSuccess) {
+        if (a_) g_kt_spare.push_back(a_);
+        if (b_) g_kt_spare.push_back(b_);
+        a_ = b_ = nullptr;
+    }
+}
+
+KernelTimer::~KernelTimer()
+{
+    if (!a_) return;
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    if (cudaEventRecord(b_, s_) == cudaSuccess) {
+        g_kt_pending.push_back({name_, a_, b_, bytes_});
+    } else {
+        g_kt_spare.push_back(a_);
+        g_kt_spare.push_back(b_);
+    }
+}
+
 // Scratch pools, one per device, and the number of live models per device.
 constexpr int kMaxPoolDevices = 64;
 static std::mutex g_pool_mu;
@@ -260,10 +319,10 @@ static mgt_status validate(const mgt_model_desc *d)
 
 static void free_model(mgt_model *m)
 {
-    void *ptrs[] = {m->d_dir_map, m->d_batch_pairs, m->d_nbr_pos, m->d_ent, m->d_ent_off, m->d_pos_hl, m->d_vel_hl, m->d_dirs32, m->d_order, m->d_pos, m->d_vel, m->d_temp, m->d_vturb2, m->d_ncoll, m->d_nspec, m->d_w64, m->d_w32,
+    void *ptrs[] = {m->d_dir_map, m->d_batch_pairs, m->d_nbr_pos, m->d_ent, m->d_ent_off, m->d_pos_hl, m->d_vel_hl, m->d_dirs32, m->d_order, m->d_pos, m->d_vel, m->d_temp, m->d_vturb2, m->d_ncoll, m->d_nspec, m->d_w64, m->d_w32, m->d_dxmax,
                     m->d_nbr_off, m->d_nbrs, m->d_bnd, m->d_dirs, m->d_pairs, m->d_xq, m->d_wq, m->d_line_tab,
                     m->d_line_ul, m->d_level_tab, m->d_coll_tab, m->d_coll_ul, m->d_entry, m->d_pops,
-                    m->d_pops_prev, m->d_line32, m->d_line64, m->d_J, m->d_Lst, m->d_err, m->d_count,
+                    m->d_pops_prev, m->d_line32, m->d_line64, m->d_J, m->d_Lst, m->d_err, m->d_range_bad, m->d_count,
                     m->d_ray_off, m->d_steps64};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -342,7 +401,7 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
         const double Blu = Bul * m->g[m->up[k]] / m->g[m->lo[k]];
         const double hk = m->T_bg > 0.0 ? kH * nu / (kKB * m->T_bg) : 0.0;
         const double nbg = hk > 0.0 ? 1.0 / std::expm1(hk) : 0.0;
-        const double nbgmax = std::max(nbg, 1e-30);
+        const double nbgmax = std::max(nbg, 1e-15);
         tab[0 * Mp + k] = nu;
         tab[1 * Mp + k] = m->A[k];
         tab[2 * Mp + k] = Bul;
@@ -384,6 +443,7 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
     MGT_TRY(dalloc(&m->d_nspec, N));
     MGT_TRY(dalloc(&m->d_w64, N));
     MGT_TRY(dalloc(&m->d_w32, N));
+    MGT_TRY(dalloc(&m->d_dxmax, N));
     MGT_TRY(dalloc(&m->d_nbr_off, N + 1));
     MGT_TRY(dalloc(&m->d_nbrs, m->nnz));
     MGT_TRY(dalloc(&m->d_nbr_pos, 3 * m->nnz));
@@ -411,6 +471,7 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
     MGT_TRY(dalloc(&m->d_J, N * m->M));
     MGT_TRY(dalloc(&m->d_Lst, N * m->M));
     MGT_TRY(dalloc(&m->d_err, 4));
+    MGT_TRY(dalloc(&m->d_range_bad, 1));
     MGT_TRY(dalloc(&m->d_count, 4));
 
     MGT_TRY(upload(m->d_pos, d->pos, 3 * N, s));
@@ -765,6 +826,58 @@ mgt_status mgt_launch_count(int64_t *count)
 {
     if (!count) return set_error(MGT_ERR_ARG, "count is NULL");
     *count = g_launches.load(std::memory_order_relaxed);
+    return MGT_OK;
+}
+
+mgt_status mgt_kernel_timing(int32_t enable)
+{
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    if (enable) {
+        for (const KtRecord &r : g_kt_pending) {
+            cudaEventSynchronize(r.b);
+            g_kt_spare.push_back(r.a);
+            g_kt_spare.push_back(r.b);
+        }
+        g_kt_pending.clear();
+        g_kt_totals.clear();
+    }
+    g_kt_on.store(enable != 0, std::memory_order_relaxed);
+    return MGT_OK;
+}
+
+mgt_status mgt_kernel_times(int32_t capacity, mgt_kernel_time *out, int32_t *n_out)
+{
+    if (capacity < 0 || (capacity > 0 && !out) || !n_out) return set_error(MGT_ERR_ARG, "mgt_kernel_times: bad output");
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    cudaError_t err = cudaSuccess;
+    for (const KtRecord &r : g_kt_pending) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+        auto it = std::find_if(g_kt_totals.begin(), g_kt_totals.end(),
+                               [&](const KtTotal &t) { return t.name == r.name; });
+        if (it == g_kt_totals.end()) {
+            g_kt_totals.push_back({r.name, 0, 0.0, 0.0});
+            it = g_kt_totals.end() - 1;
+        }
+        it->launches += 1;
+        it->ms += ms;
+        it->bytes += r.bytes;
+        g_kt_spare.push_back(r.a);
+        g_kt_spare.push_back(r.b);
+    }
+    g_kt_pending.clear();
+    if (err != cudaSuccess) return cuda_status(err, "mgt_kernel_times");
+    const int n = (int)g_kt_totals.size();
+    for (int i = 0; i < n && i < capacity; ++i) {
+        std::memset(out[i].name, 0, sizeof out[i].name);
+        std::strncpy(out[i].name, g_kt_totals[i].name.c_str(), sizeof out[i].name - 1);
+        out[i].launches = g_kt_totals[i].launches;
+        out[i].total_ms = g_kt_totals[i].ms;
+        out[i].bytes = g_kt_totals[i].bytes;
+    }
+    *n_out = n;
     return MGT_OK;
 }
 

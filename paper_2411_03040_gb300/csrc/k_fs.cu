@@ -98,6 +98,7 @@ struct FSArgs {
     int nblk;                  // line blocks per origin (ceil(Gtot / Gb))
     double *J, *Lst;           // [N][M]
     int *err;
+    const int *range_bad;      // nonzero: a point's range figure exceeds 1 (set by the line data)
 };
 
 // Geometry of one traced step in the solver's precision.
@@ -282,6 +283,118 @@ __device__ __forceinline__ void eliminate_row_packed(float cf, float cn, const f
         aa[l + 1] = b.y;
     }
 }
+
+// Two rows per reciprocal (FP32, line pairs packed).  The row map
+//     (Pi, Y) -> (G q, (S h + Y) q),  G = 2h + Pi,  q = 1/(1 + beta G)
+// is linear-fractional, so in homogeneous coordinates Pi = p/d, Y = y/d it is
+// the linear map
+//     p' = p + 2 h d,  y' = y + S h d,  d' = d + beta p'
+// with no division.  Two rows are taken from d = 1 and the state is brought
+// back to Pi, Y with one reciprocal of the final d: 15 packed operations and
+// two reciprocals per line pair and two steps, against 16 and four for two
+// eliminate_row calls, and a dependent chain without the reciprocal's
+// latency in every row.  d grows by 1 + beta G per row; the caller takes this
+// path only while that growth and the source terms provably stay inside the
+// FP32 range (the range guard below), so the two forms differ by rounding alone.
+template <int LPT>
+__device__ __forceinline__ void homog_row1_packed(float cf, float cn, const float (&chi_f)[LPT],
+                                                  const float (&S_f)[LPT], const float (&chi_n)[LPT],
+                                                  float (&P)[LPT], float (&Y)[LPT], float (&aa)[LPT],
+                                                  float (&D)[LPT])
+{
+    static_assert(LPT % 2 == 0, "line pairs");
+    const float2 cf2 = make_float2(cf, cf), cn2 = make_float2(cn, cn);
+    const float2 two = make_float2(2.0f, 2.0f), one = make_float2(1.0f, 1.0f);
+#pragma unroll
+    for (int l = 0; l < LPT; l += 2) {
+        const float2 cx = make_float2(chi_f[l], chi_f[l + 1]), nx = make_float2(chi_n[l], chi_n[l + 1]);
+        const float2 b = __ffma2_rn(cf2, cx, __fmul2_rn(cn2, nx));
+        const float2 h = __fadd2_rn(make_float2(aa[l], aa[l + 1]), b);
+        const float2 p = __ffma2_rn(two, h, make_float2(P[l], P[l + 1]));
+        const float2 y = __ffma2_rn(make_float2(S_f[l], S_f[l + 1]), h, make_float2(Y[l], Y[l + 1]));
+        const float2 d = __ffma2_rn(b, p, one);
+        P[l] = p.x;
+        P[l + 1] = p.y;
+        Y[l] = y.x;
+        Y[l + 1] = y.y;
+        D[l] = d.x;
+        D[l + 1] = d.y;
+        aa[l] = b.x;
+        aa[l + 1] = b.y;
+    }
+}
+
+template <int LPT>
+__device__ __forceinline__ void homog_row2_packed(float cf, float cn, const float (&chi_f)[LPT],
+                                                  const float (&S_f)[LPT], const float (&chi_n)[LPT],
+                                                  float (&P)[LPT], float (&Y)[LPT], float (&aa)[LPT],
+                                                  const float (&D)[LPT])
+{
+    const float2 cf2 = make_float2(cf, cf), cn2 = make_float2(cn, cn);
+    const float2 two = make_float2(2.0f, 2.0f);
+#pragma unroll
+    for (int l = 0; l < LPT; l += 2) {
+        const float2 cx = make_float2(chi_f[l], chi_f[l + 1]), nx = make_float2(chi_n[l], chi_n[l + 1]);
+        const float2 b = __ffma2_rn(cf2, cx, __fmul2_rn(cn2, nx));
+        const float2 h = __fadd2_rn(make_float2(aa[l], aa[l + 1]), b);
+        const float2 d1 = make_float2(D[l], D[l + 1]);
+        const float2 hd = __fmul2_rn(h, d1);
+        const float2 p = __ffma2_rn(two, hd, make_float2(P[l], P[l + 1]));
+        const float2 y = __ffma2_rn(make_float2(S_f[l], S_f[l + 1]), hd, make_float2(Y[l], Y[l + 1]));
+        const float2 d = __ffma2_rn(b, p, d1);
+        const float2 r = make_float2(Prec<float>::rcp(d.x), Prec<float>::rcp(d.y));
+        const float2 Pn = __fmul2_rn(p, r), Yn = __fmul2_rn(y, r);
+        P[l] = Pn.x;
+        P[l + 1] = Pn.y;
+        Y[l] = Yn.x;
+        Y[l + 1] = Yn.y;
+        aa[l] = b.x;
+        aa[l + 1] = b.y;
+    }
+}
+
+// Back to Pi = p/d, Y = y/d and d = 1 after the first of two rows (both lines
+// of each pair); followed by homog_row2_packed this is eliminate_row twice,
+// operation for operation.
+template <int LPT>
+__device__ __forceinline__ void renormalize_packed(float (&P)[LPT], float (&Y)[LPT], float (&D)[LPT])
+{
+#pragma unroll
+    for (int l = 0; l < LPT; l += 2) {
+        const float2 r = make_float2(Prec<float>::rcp(D[l]), Prec<float>::rcp(D[l + 1]));
+        const float2 Pn = __fmul2_rn(make_float2(P[l], P[l + 1]), r), Yn = __fmul2_rn(make_float2(Y[l], Y[l + 1]), r);
+        P[l] = Pn.x;
+        P[l + 1] = Pn.y;
+        Y[l] = Yn.x;
+        Y[l + 1] = Yn.y;
+        D[l] = 1.0f;
+        D[l + 1] = 1.0f;
+    }
+}
+
+// Range guard of the two-row form.  A row's half depth is at most
+// 0.5 dx (chi~max_far + chi~max_near), with chi~max the largest chi~' of a
+// point over the lines: the trapezoid has cf <= dx/4, the semi-analytic form
+// |erf difference| <= (2/sqrt(pi)) |du|, so cf <= dx w_far/(4 wbar) <= dx/2
+// for either averaged width.  A point's row stores
+//   G = max(chi~max dxmax / kFastB, S'max / kFastS)
+// with dxmax its longest graph edge (every walk step is a graph edge), so a
+// row between two points with G <= 1 has a half depth <= kFastB and sources
+// <= kFastS.  The elimination of a half-ray takes two rows at a time as long
+// as every row so far was such a row, the half-ray is shorter than
+// kFastSteps, its background is <= kFastY and the optical depths are the
+// switch rule's (not the subdivided reference's).  Then alpha, beta <= 2^8 (h <= 2^9), Pi <= 2^16 at
+// every row (Pi' <= 1/beta after a row, and it grows by less than 2^-13 per
+// row while beta < 2^-15, so rising past 2^16 takes more than 2^27 rows),
+// Y < 2^117 (Y grows by at most S' h <= 2^89 per row), and within a two-row
+// step d < 2^26 after the first row, then p < 2^37, y < 2^117, d < 2^46: all
+// finite and normal in FP32.  From the first row past the bounds on, the
+// half-ray is eliminated one row at a time.
+constexpr float kFastB = kTwoRowDepth;           // 2^8
+constexpr float kFastY = 1.2676506002282294e30f;  // 2^100
+constexpr float kFastS = kTwoRowSource;           // 2^80
+static_assert(kFastB == 256.0f && kFastS == 1.2089258196146292e24f, "range of the two-row elimination");
+constexpr int kFastSteps = 1 << 27;
 
 template <typename T, int LPT>
 __device__ __forceinline__ void eliminate_row(T cf, T cn, const T (&chi_f)[LPT], const T (&S_f)[LPT],
@@ -741,7 +854,7 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
 // consumed so far, so their phases carry over from one item to the next.
 // Returns false if a wait gave up: the error word is set and no copy of this
 // CTA is left in flight.
-template <typename T, int LPT, int CH>
+template <typename T, int LPT, int CH, bool FAST>
 __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int blk, unsigned char *smem, int &ci)
 {
     using V2 = typename Prec<T>::V2;
@@ -825,6 +938,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                     if (tid == 0) *abort_flag = 1;
                     goto done;
                 }
+
                 if (warp == 0) {
                     Chunk nx;
                     const Chunk c{p, h, s0, n, k_lo, k_hi};
@@ -841,18 +955,36 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                     T chiA[LPT], chiB[LPT], S_f[LPT];
                     load_vec<LPT>(row, chiA);
                     int k = k_hi;
+                    if constexpr (FAST) {
+                        // two rows per reciprocal (the launch checked the range)
+                        T D[LPT];
 #pragma unroll 1
-                    for (; k - 1 >= k_lo; k -= 2) {
-                        V2 cc = *cfp;
-                        load_vec<LPT>(row + a.Mpad, S_f);
-                        load_vec<LPT>(row - a.RS, chiB);
-                        eliminate_row<T, LPT>(cc.x, cc.y, chiA, S_f, chiB, P, Y, aa);
-                        cc = *(cfp - a.Q);
-                        load_vec<LPT>(row - a.RS + a.Mpad, S_f);
-                        load_vec<LPT>(row - 2 * a.RS, chiA);
-                        eliminate_row<T, LPT>(cc.x, cc.y, chiB, S_f, chiA, P, Y, aa);
-                        row -= 2 * a.RS;
-                        cfp -= 2 * a.Q;
+                        for (; k - 1 >= k_lo; k -= 2) {
+                            V2 cc = *cfp;
+                            load_vec<LPT>(row + a.Mpad, S_f);
+                            load_vec<LPT>(row - a.RS, chiB);
+                            homog_row1_packed<LPT>(cc.x, cc.y, chiA, S_f, chiB, P, Y, aa, D);
+                            cc = *(cfp - a.Q);
+                            load_vec<LPT>(row - a.RS + a.Mpad, S_f);
+                            load_vec<LPT>(row - 2 * a.RS, chiA);
+                            homog_row2_packed<LPT>(cc.x, cc.y, chiB, S_f, chiA, P, Y, aa, D);
+                            row -= 2 * a.RS;
+                            cfp -= 2 * a.Q;
+                        }
+                    } else {
+#pragma unroll 1
+                        for (; k - 1 >= k_lo; k -= 2) {
+                            V2 cc = *cfp;
+                            load_vec<LPT>(row + a.Mpad, S_f);
+                            load_vec<LPT>(row - a.RS, chiB);
+                            eliminate_row<T, LPT>(cc.x, cc.y, chiA, S_f, chiB, P, Y, aa);
+                            cc = *(cfp - a.Q);
+                            load_vec<LPT>(row - a.RS + a.Mpad, S_f);
+                            load_vec<LPT>(row - 2 * a.RS, chiA);
+                            eliminate_row<T, LPT>(cc.x, cc.y, chiB, S_f, chiA, P, Y, aa);
+                            row -= 2 * a.RS;
+                            cfp -= 2 * a.Q;
+                        }
                     }
                     if (k == k_lo) {
                         const V2 cc = *cfp;
@@ -933,13 +1065,36 @@ __device__ __forceinline__ void staged_init(unsigned char *smem)
 }
 
 // One CTA per (origin, line block): blockIdx.x is the origin's place in the
-// visiting order, blockIdx.y the line block.
-template <typename T, int LPT, int CH, int MINB> __global__ void __launch_bounds__(256, MINB) k_fs_staged(FSArgs a)
+// visiting order, blockIdx.y the line block.  FAST: the two-row elimination,
+// which only runs when no point of the model is outside its range (the line
+// data set *range_bad otherwise; every CTA then returns at once and
+// k_fs_exact does the work).
+template <typename T, int LPT, int CH, int MINB, bool FAST>
+__global__ void __launch_bounds__(256, MINB) k_fs_staged(FSArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    if constexpr (FAST) {
+        if (*a.range_bad) return;
+    }
     staged_init(smem);
     int ci = 0;
-    fs_staged_item<T, LPT, CH>(a, (int64_t)blockIdx.x, (int)blockIdx.y, smem, ci);
+    fs_staged_item<T, LPT, CH, FAST>(a, (int64_t)blockIdx.x, (int)blockIdx.y, smem, ci);
+}
+
+// The one-row elimination of every item of a model whose range figures
+// exclude the two-row form (*range_bad set), in a persistent grid; launched
+// after the two-row kernel, it returns at once for every other model.
+template <typename T, int LPT, int CH> __global__ void __launch_bounds__(256, 2) k_fs_exact(FSArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (!*a.range_bad) return;
+    staged_init(smem);
+    int ci = 0;
+    const int64_t items = a.N * a.nblk;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int64_t oi = it / a.nblk;
+        if (!fs_staged_item<T, LPT, CH, false>(a, oi, (int)(it - oi * a.nblk), smem, ci)) return;
+    }
 }
 
 // Many models in one persistent launch.  Items (model, origin, line block)
@@ -954,6 +1109,13 @@ struct FSBatchArgs {
     int64_t n_items;
     unsigned long long *next;  // item counter, zero at launch
 };
+
+// A model's items take the two-row elimination: no point outside its range,
+// half-rays shorter than kFastSteps, and the switch rule's optical depths.
+__device__ __forceinline__ bool two_row_ok(const FSArgs &a)
+{
+    return !*a.range_bad && a.subdiv == 0 && a.N < kFastSteps;
+}
 
 template <typename T, int CH> __global__ void __launch_bounds__(256, 2) k_fs_batch(FSBatchArgs b)
 {
@@ -984,16 +1146,43 @@ template <typename T, int CH> __global__ void __launch_bounds__(256, 2) k_fs_bat
         const int model = s_model;
         if (model < 0) return;
         cur = model;
+        if (!two_row_ok(sa)) continue;            // the model's items are k_fs_batch_exact's
         const int64_t local = s_item - s_first;
         const int64_t oi = local / sa.nblk;
         const int blk = (int)(local - oi * sa.nblk);
-        const bool ok = sa.lpt == 8 ? fs_staged_item<T, 8, CH>(sa, oi, blk, smem, ci)
-                                    : fs_staged_item<T, 4, CH>(sa, oi, blk, smem, ci);
+        const bool ok = sa.lpt == 8 ? fs_staged_item<T, 8, CH, true>(sa, oi, blk, smem, ci)
+                                    : fs_staged_item<T, 4, CH, true>(sa, oi, blk, smem, ci);
         if (!ok) return;
     }
 }
 
-constexpr int kChunk = 31;
+// The items of the batch's models whose range figures exclude the two-row
+// form, with the one-row elimination: every CTA walks the models and takes
+// every gridDim.x-th item of each such model (returns at once when there is
+// none).
+template <typename T, int CH> __global__ void __launch_bounds__(256, 2) k_fs_batch_exact(FSBatchArgs b)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ FSArgs sa;
+    staged_init(smem);
+    int ci = 0;
+    for (int mdl = 0; mdl < b.n_models; ++mdl) {
+        if (two_row_ok(b.args[mdl])) continue;    // the same for every thread
+        __syncthreads();                          // the previous model's items are done with sa
+        if (threadIdx.x == 0) sa = b.args[mdl];
+        __syncthreads();
+        const int64_t first = mdl > 0 ? b.item_end[mdl - 1] : 0, n = b.item_end[mdl] - first;
+        for (int64_t it = blockIdx.x; it < n; it += gridDim.x) {
+            const int64_t oi = it / sa.nblk;
+            const int blk = (int)(it - oi * sa.nblk);
+            const bool ok = sa.lpt == 8 ? fs_staged_item<T, 8, CH, false>(sa, oi, blk, smem, ci)
+                                        : fs_staged_item<T, 4, CH, false>(sa, oi, blk, smem, ci);
+            if (!ok) return;
+        }
+    }
+}
+
+constexpr int kChunk = 30;
 
 template <typename T, int LPT> FSArgs fill_fs_args(const mgt_model *m, bool accumulate)
 {
@@ -1031,14 +1220,49 @@ template <typename T, int LPT> FSArgs fill_fs_args(const mgt_model *m, bool accu
     a.J = m->d_J;
     a.Lst = m->d_Lst;
     a.err = m->d_err;
+    a.range_bad = m->d_range_bad;
     a.lpt = LPT;
     a.nblk = ceil_div(a.Gtot, a.Gb);
     return a;
 }
 
+template <typename T, int LPT, int MINB, bool FAST>
+mgt_status launch_staged(const FSArgs &a, dim3 grid, int bd, size_t smem, double fs_bytes, cudaStream_t s)
+{
+    MGT_CUDA(cudaFuncSetAttribute(k_fs_staged<T, LPT, kChunk, MINB, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    {
+        MGT_KTIMER_BYTES(sizeof(T) == 4 ? "k_fs_staged<f32>" : "k_fs_staged<f64>", s, fs_bytes);
+        k_fs_staged<T, LPT, kChunk, MINB, FAST><<<grid, bd, smem, s>>>(a);
+    }
+    MGT_LAUNCH_CHECK("k_fs_staged");
+    if constexpr (FAST) {
+        // the same items with the one-row elimination if the model is outside
+        // the two-row range (a persistent grid; it returns at once otherwise)
+        auto kern = k_fs_exact<T, LPT, kChunk>;
+        MGT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int dev = 0, sms = 0, per_sm = 0;
+        MGT_CUDA(cudaGetDevice(&dev));
+        MGT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        MGT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bd, smem));
+        const int64_t items = (int64_t)grid.x * grid.y;
+        const int g = (int)std::min<int64_t>(items, (int64_t)sms * std::max(per_sm, 1));
+        {
+            MGT_KTIMER("k_fs_exact", s);
+            kern<<<g, bd, smem, s>>>(a);
+        }
+        MGT_LAUNCH_CHECK("k_fs_exact");
+    }
+    return MGT_OK;
+}
+
 template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_t s, int schedule, bool accumulate)
 {
     FSArgs a = fill_fs_args<T, LPT>(m, accumulate);
+    // least traffic of a launch: every step record of the held rays once, every
+    // point's row once, J-bar and Lambda* written
+    const double fs_bytes = (double)m->total_steps * (sizeof(T) == 4 ? 16.0 : 32.0) +
+                            (double)m->N * (double)a.RS * sizeof(T) + 16.0 * (double)m->N * m->M;
     const int Mb = a.Gb * LPT;
     // one origin per CTA: the staged kernel (schedule 2, also the automatic
     // choice: register-capped for two blocks per SM; 3: one block per SM).
@@ -1052,17 +1276,15 @@ template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_
         if (bd > 256) return set_error(MGT_ERR_ARG, "formal solve: more than 256 bins per origin");
         const size_t smem = (size_t)staged_layout<T, LPT, kChunk>(a.Q, Mb, a.RS, bd, a.P).total;
         dim3 grid((unsigned)m->N, (unsigned)ceil_div(a.Gtot, a.Gb));
-        if (schedule == 3) {
-            MGT_CUDA(cudaFuncSetAttribute(k_fs_staged<T, LPT, kChunk, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            k_fs_staged<T, LPT, kChunk, 1><<<grid, bd, smem, s>>>(a);
-        } else {
-            MGT_CUDA(cudaFuncSetAttribute(k_fs_staged<T, LPT, kChunk, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            k_fs_staged<T, LPT, kChunk, 2><<<grid, bd, smem, s>>>(a);
+        // the two-row elimination in FP32 (the subdivided reference keeps the
+        // one-row form; the range argument needs half-rays below kFastSteps)
+        if constexpr (sizeof(T) == 4) {
+            if (a.subdiv == 0 && m->N < kFastSteps)
+                return schedule == 3 ? launch_staged<T, LPT, 1, true>(a, grid, bd, smem, fs_bytes, s)
+                                     : launch_staged<T, LPT, 2, true>(a, grid, bd, smem, fs_bytes, s);
         }
-        MGT_LAUNCH_CHECK("k_fs_staged");
-        return MGT_OK;
+        return schedule == 3 ? launch_staged<T, LPT, 1, false>(a, grid, bd, smem, fs_bytes, s)
+                             : launch_staged<T, LPT, 2, false>(a, grid, bd, smem, fs_bytes, s);
     }
     const int threads = a.OPB * a.Q * a.Gb;
     const int bd = ((threads + 31) / 32) * 32;
@@ -1070,7 +1292,10 @@ template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_
     const size_t smem = sizeof(T) * 4 * LPT * bd + sizeof(double) * 2 * a.OPB * Mb * a.Q;
     MGT_CUDA(cudaFuncSetAttribute(k_fs_gather<T, LPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)ceil_div(m->N, a.OPB), (unsigned)ceil_div(a.Gtot, a.Gb));
-    k_fs_gather<T, LPT><<<grid, bd, smem, s>>>(a);
+    {
+        MGT_KTIMER_BYTES(sizeof(T) == 4 ? "k_fs_gather<f32>" : "k_fs_gather<f64>", s, fs_bytes);
+        k_fs_gather<T, LPT><<<grid, bd, smem, s>>>(a);
+    }
     MGT_LAUNCH_CHECK("k_fs_gather");
     return MGT_OK;
 }
@@ -1118,7 +1343,7 @@ mgt_status fs_batch_args(const mgt_model *m, void *args, int *threads, int64_t *
 // staging and coefficient buffers, so twice as many CTAs fit on an SM, and a
 // barrier of one warp costs little.  The arithmetic does not depend on the
 // chunk length.
-constexpr int kChunkNarrow = 15;
+constexpr int kChunkNarrow = 14;
 
 size_t fs_batch_smem(const void *args, int bd)
 {
@@ -1135,7 +1360,9 @@ size_t fs_batch_smem(const void *args, int bd)
 mgt_status fs_batch_grid(int bd, size_t smem, size_t max_smem, int *grid)
 {
     auto kern = bd == 32 ? k_fs_batch<float, kChunkNarrow> : k_fs_batch<float, kChunk>;
+    auto kex = bd == 32 ? k_fs_batch_exact<float, kChunkNarrow> : k_fs_batch_exact<float, kChunk>;
     MGT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
+    MGT_CUDA(cudaFuncSetAttribute(kex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
     int dev = 0, sms = 0, per_sm = 0;
     MGT_CUDA(cudaGetDevice(&dev));
     MGT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1156,6 +1383,12 @@ mgt_status fs_batch_launch(const void *d_args, const int64_t *d_item_end, int n_
     else
         k_fs_batch<float, kChunk><<<(unsigned)g, bd, smem, s>>>(b);
     MGT_LAUNCH_CHECK("k_fs_batch");
+    // the items of models outside the two-row range (returns at once without)
+    if (bd == 32)
+        k_fs_batch_exact<float, kChunkNarrow><<<(unsigned)g, bd, smem, s>>>(b);
+    else
+        k_fs_batch_exact<float, kChunk><<<(unsigned)g, bd, smem, s>>>(b);
+    MGT_LAUNCH_CHECK("k_fs_batch_exact");
     return MGT_OK;
 }
 

@@ -136,9 +136,35 @@ __global__ void k_morton_keys(int64_t N, const double *__restrict__ pos, double 
     idx[i] = (int32_t)i;
 }
 
+// Longest graph edge at each point, over the edges of its own neighbour list
+// and those that name it (so that every step of a walk, from a point to one of
+// its neighbours, is no longer than dxmax at either end): FP64 distance in
+// length units, rounded up to FP32 with a margin over the walk's own FP32 step
+// lengths.  Non-negative floats order like their bit patterns.
+__global__ void k_edge_max(int64_t N, const int32_t *__restrict__ off, const int32_t *__restrict__ nbrs,
+                           const double *__restrict__ pos, double inv_Lunit, float *__restrict__ dxmax)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    int *dm = reinterpret_cast<int *>(dxmax);
+    float best = 0.0f;
+    for (int32_t k = off[p]; k < off[p + 1]; ++k) {
+        const int64_t q = nbrs[k];
+        const double dx = pos[3 * q] - pos[3 * p], dy = pos[3 * q + 1] - pos[3 * p + 1],
+                     dz = pos[3 * q + 2] - pos[3 * p + 2];
+        const float d = __double2float_ru(sqrt(dx * dx + dy * dy + dz * dz) * inv_Lunit * (1.0 + 1e-5));
+        best = fmaxf(best, d);
+        atomicMax(dm + q, __float_as_int(d));
+    }
+    atomicMax(dm + p, __float_as_int(best));
+}
+
 mgt_status build_walk_tables(mgt_model *m, const double lo[3], const double hi[3], cudaStream_t s)
 {
     const int64_t N = m->N;
+    MGT_CUDA(cudaMemsetAsync(m->d_dxmax, 0, sizeof(float) * N, s));
+    k_edge_max<<<ceil_div(N, 256), 256, 0, s>>>(N, m->d_nbr_off, m->d_nbrs, m->d_pos, 1.0 / m->L_unit, m->d_dxmax);
+    MGT_LAUNCH_CHECK("k_edge_max");
     k_split_hl<<<ceil_div(3 * N, 256), 256, 0, s>>>(N, m->d_pos, m->d_vel, m->pos_scale, 1.0 / kC, m->d_pos_hl,
                                                     m->d_vel_hl);
     MGT_LAUNCH_CHECK("k_split_hl");
@@ -216,78 +242,105 @@ mgt_status launch_lte(mgt_model *m, cudaStream_t s)
 // Stored scaled for the solver:
 //   chi~' = chi^{ij} / (nu w sqrt(pi)) * L_unit  -- opacity per length unit at
 //           line centre, so that chi(nu) = chi~ exp(-u^2);
-//   S'    = S^{ij} / U_line, U_line = (2 h nu^3/c^2) max(n_bg(nu), 1e-30)
+//   S'    = S^{ij} / U_line, U_line = (2 h nu^3/c^2) max(n_bg(nu), 1e-15)
 //         = n_u B_ul / (net * nbgmax).
 // Row layout (see row_stride32): chi~' of every line, then S' of every line,
-// then w and 1/w of the point.  One thread per (point, line slot).
+// then w and 1/w of the point, then (FP32 rows only) the range figure
+// G = max(chi~max dxmax / 2^8, S'max / 2^80) of the formal solution's two-row
+// elimination (chi~max, S'max the largest over the point's lines, dxmax its
+// longest graph edge) and a zero.
+// One warp per point; lane j takes line slots j, j + 32, ...
 // ---------------------------------------------------------------------------
 struct LDArgs {
     int64_t N;
     int L, M, Mpad;
     const double *pops, *w64, *line_tab;
     const int32_t *line_ul;
+    const float *dxmax;
     double Lunit;
     float *out32;
     double *out64;
     unsigned long long *n_floor;
+    int *range_bad;           // set when a point's range figure exceeds 1 (zeroed before the launch)
 };
 
-__device__ __forceinline__ void line_data_slot(const LDArgs &d, int64_t t)
+__device__ __forceinline__ void line_data_point(const LDArgs &d, int64_t p, int lane)
 {
+    if (p >= d.N) return;                            // whole warp: p is warp-uniform
     const int Mpad = d.Mpad, RS = row_stride32(Mpad), RS64 = row_stride64(Mpad);
-    const int slots = Mpad + 2;                      // Mpad lines + {w, 1/w} + {0, 0}
-    if (t >= d.N * slots) return;
     const double *__restrict__ line_tab = d.line_tab;
     const int32_t *__restrict__ line_ul = d.line_ul;
-    float *__restrict__ out32 = d.out32;
-    double *__restrict__ out64 = d.out64;
-    int64_t p = t / slots;
-    int k = (int)(t - p * slots);
-    double a0 = 0.0, a1 = 0.0;
-    if (k < d.M) {
-        int u = line_ul[k], l = line_ul[Mpad + k];
-        double Bul = line_tab[2 * Mpad + k], Blu = line_tab[3 * Mpad + k];
-        double nbgmax = line_tab[4 * Mpad + k];
-        double nu_ = d.pops[p * d.L + u], nl_ = d.pops[p * d.L + l];
-        double a = nl_ * Blu, b = nu_ * Bul;
-        double net = a - b, floor_ = 1e-30 * (a + b);
-        if (net < floor_) {
-            net = floor_;
-            atomicAdd(d.n_floor, 1ULL);
+    float *__restrict__ r32 = d.out32 + p * RS;
+    double *__restrict__ r64 = d.out64 ? d.out64 + p * RS64 : nullptr;
+    float chi_max = 0.0f, S_max = 0.0f;
+    for (int k = lane; k < Mpad; k += 32) {
+        double a0 = 0.0, a1 = 0.0;
+        if (k < d.M) {
+            const int u = line_ul[k], l = line_ul[Mpad + k];
+            const double Bul = line_tab[2 * Mpad + k], Blu = line_tab[3 * Mpad + k];
+            const double nbgmax = line_tab[4 * Mpad + k];
+            const double nu_ = d.pops[p * d.L + u], nl_ = d.pops[p * d.L + l];
+            const double a = nl_ * Blu, b = nu_ * Bul;
+            double net = a - b;
+            const double floor_ = 1e-30 * (a + b);
+            if (net < floor_) {
+                net = floor_;
+                atomicAdd(d.n_floor, 1ULL);
+            }
+            if (net > 0.0) {
+                a0 = kH * net * d.Lunit / (4.0 * kPi * kSqrtPi * d.w64[p]);
+                a1 = b / (net * nbgmax);
+            }
         }
-        if (net > 0.0) {
-            a0 = kH * net * d.Lunit / (4.0 * kPi * kSqrtPi * d.w64[p]);
-            a1 = b / (net * nbgmax);
+        const float f0 = (float)a0, f1 = (float)a1;
+        r32[k] = f0;
+        r32[Mpad + k] = f1;
+        // !(x <= m) also carries a NaN into the bound, which then disables the
+        // fast elimination for every step through this point
+        chi_max = !(f0 <= chi_max) ? f0 : chi_max;
+        S_max = !(f1 <= S_max) ? f1 : S_max;
+        if (r64) {
+            r64[k] = a0;
+            r64[Mpad + k] = a1;
         }
-    } else if (k == Mpad) {
-        a0 = d.w64[p];
-        a1 = 1.0 / a0;
     }
-    float *r32 = out32 + p * RS;
-    if (k < Mpad) {
-        r32[k] = (float)a0;
-        r32[Mpad + k] = (float)a1;
-        if (out64) {
-            out64[p * RS64 + k] = a0;
-            out64[p * RS64 + Mpad + k] = a1;
-        }
-    } else if (k == Mpad) {
-        r32[2 * Mpad] = (float)a0;
-        r32[2 * Mpad + 1] = (float)a1;
-        if (out64) {
-            out64[p * RS64 + 2 * Mpad] = a0;
-            out64[p * RS64 + 2 * Mpad + 1] = a1;
-        }
-    } else {
-        r32[2 * Mpad + 2] = 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float c = __shfl_xor_sync(0xffffffffu, chi_max, o), t = __shfl_xor_sync(0xffffffffu, S_max, o);
+        chi_max = !(c <= chi_max) ? c : chi_max;
+        S_max = !(t <= S_max) ? t : S_max;
+    }
+    if (lane == 0) {
+        const double w = d.w64[p];
+        r32[2 * Mpad] = (float)w;
+        r32[2 * Mpad + 1] = (float)(1.0 / w);
+        // range figure of the formal solution's two-row elimination: at most 1
+        // when every step through the point has half depths <= kTwoRowDepth and
+        // sources <= kTwoRowSource; NaN and infinity give a figure above 1
+        // (a width above 1% of c, where no real line is, would also let the
+        // background of the far bins outgrow the range: it sets the flag too)
+        const float G = fmaxf(chi_max * d.dxmax[p] / kTwoRowDepth, S_max / kTwoRowSource);
+        const bool inside = chi_max == chi_max && S_max == S_max && G <= 1.0f && w < 0.01;
+        r32[2 * Mpad + 2] = inside ? G : 2.0f;
         r32[2 * Mpad + 3] = 0.0f;
+        if (!inside) atomicOr(d.range_bad, 1);
+        if (r64) {
+            r64[2 * Mpad] = w;
+            r64[2 * Mpad + 1] = 1.0 / w;
+        }
     }
 }
 
-__global__ void k_line_data(LDArgs d) { line_data_slot(d, blockIdx.x * (int64_t)blockDim.x + threadIdx.x); }
+constexpr int kLDThreads = 256, kLDPointsPerBlock = kLDThreads / 32;
+
+__global__ void __launch_bounds__(kLDThreads) k_line_data(LDArgs d)
+{
+    line_data_point(d, (int64_t)blockIdx.x * kLDPointsPerBlock + (threadIdx.x >> 5), threadIdx.x & 31);
+}
 
 // Many models in one launch: blk_end[i] is one past the last CTA of model i.
-__global__ void k_line_data_batch(const LDArgs *__restrict__ args, const int64_t *__restrict__ blk_end, int n_models)
+__global__ void __launch_bounds__(kLDThreads) k_line_data_batch(const LDArgs *__restrict__ args,
+                                                                const int64_t *__restrict__ blk_end, int n_models)
 {
     __shared__ LDArgs sd;
     __shared__ int64_t s_first;
@@ -302,19 +355,25 @@ __global__ void k_line_data_batch(const LDArgs *__restrict__ args, const int64_t
         s_first = lo > 0 ? blk_end[lo - 1] : 0;
     }
     __syncthreads();
-    line_data_slot(sd, ((int64_t)blockIdx.x - s_first) * blockDim.x + threadIdx.x);
+    line_data_point(sd, ((int64_t)blockIdx.x - s_first) * kLDPointsPerBlock + (threadIdx.x >> 5), threadIdx.x & 31);
 }
 
 static LDArgs fill_ld_args(const mgt_model *m)
 {
-    return LDArgs{m->N, m->L, m->M, m->Mpad, m->d_pops, m->d_w64, m->d_line_tab, m->d_line_ul, m->L_unit,
-                  m->d_line32, m->d_line64, m->d_count + 0};
+    return LDArgs{m->N, m->L, m->M, m->Mpad, m->d_pops, m->d_w64, m->d_line_tab, m->d_line_ul, m->d_dxmax,
+                  m->L_unit, m->d_line32, m->d_line64, m->d_count + 0, m->d_range_bad};
 }
 
 mgt_status launch_line_data(mgt_model *m, cudaStream_t s)
 {
-    int64_t n = m->N * (m->Mpad + 2);
-    k_line_data<<<ceil_div(n, 256), 256, 0, s>>>(fill_ld_args(m));
+    MGT_CUDA(cudaMemsetAsync(m->d_range_bad, 0, sizeof(int), s));
+    {
+        // populations and w in; the FP32 row (and the FP64 row if kept) out
+        const double ld_bytes = (double)m->N * (8.0 * m->L + 8.0 + 4.0 * row_stride32(m->Mpad) +
+                                                 (m->d_line64 ? 8.0 * row_stride64(m->Mpad) : 0.0));
+        MGT_KTIMER_BYTES("k_line_data", s, ld_bytes);
+        k_line_data<<<ceil_div(m->N, (int64_t)kLDPointsPerBlock), kLDThreads, 0, s>>>(fill_ld_args(m));
+    }
     MGT_LAUNCH_CHECK("k_line_data");
     m->line_dirty = false;
     return MGT_OK;
@@ -326,14 +385,23 @@ mgt_status ld_batch_args(const mgt_model *m, void *args, int64_t *blocks)
 {
     const LDArgs a = fill_ld_args(m);
     std::memcpy(args, &a, sizeof a);
-    *blocks = (m->N * (m->Mpad + 2) + 255) / 256;
+    *blocks = ceil_div(m->N, (int64_t)kLDPointsPerBlock);
     return MGT_OK;
+}
+
+// Zero every model's range flag before the batched line data set them.
+__global__ void k_reset_range(const LDArgs *__restrict__ args, int n_models)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_models) *args[i].range_bad = 0;
 }
 
 mgt_status ld_batch_launch(const void *d_args, const int64_t *d_blk_end, int n_models, int64_t n_blocks,
                            cudaStream_t s)
 {
-    k_line_data_batch<<<(unsigned)n_blocks, 256, 0, s>>>(static_cast<const LDArgs *>(d_args), d_blk_end, n_models);
+    k_reset_range<<<ceil_div(n_models, 256), 256, 0, s>>>(static_cast<const LDArgs *>(d_args), n_models);
+    MGT_LAUNCH_CHECK("k_reset_range");
+    k_line_data_batch<<<(unsigned)n_blocks, kLDThreads, 0, s>>>(static_cast<const LDArgs *>(d_args), d_blk_end, n_models);
     MGT_LAUNCH_CHECK("k_line_data_batch");
     return MGT_OK;
 }
@@ -973,9 +1041,12 @@ mgt_status trace_range(mgt_model *m, cudaStream_t s, int32_t p0, int32_t np)
     MGT_CUDA(cudaMemsetAsync(m->d_count + 1, 0, 2 * sizeof(unsigned long long), s));
     MGT_CUDA(cudaMemsetAsync(d_nover, 0, sizeof(unsigned long long), s));
     const float inv_Lunit = (float)(1.0 / (m->pos_scale * m->L_unit));
-    k_walk<kWalkFused><<<ceil_div(W * 16, kWalkThreads), kWalkThreads, 0, s>>>(a, d_len, nullptr, nullptr, 0, (int32_t)K,
-                                                             m->d_count + 1, m->d_vel_hl, m->d_w32, inv_Lunit,
-                                                             m->opts.width_mode, d_scratch, m->d_err, ImgWalkArgs{});
+    {
+        MGT_KTIMER("k_walk<fused>", s);
+        k_walk<kWalkFused><<<ceil_div(W * 16, kWalkThreads), kWalkThreads, 0, s>>>(a, d_len, nullptr, nullptr, 0, (int32_t)K,
+                                                                 m->d_count + 1, m->d_vel_hl, m->d_w32, inv_Lunit,
+                                                                 m->opts.width_mode, d_scratch, m->d_err, ImgWalkArgs{});
+    }
     MGT_LAUNCH_CHECK("k_walk<fused>");
     MGT_CUDA(cudaMemsetAsync(d_len + W, 0, sizeof(int64_t), s));
     size_t tmp_bytes = 0;
@@ -1018,12 +1089,19 @@ mgt_status trace_range(mgt_model *m, cudaStream_t s, int32_t p0, int32_t np)
     m->n_stalls = (int64_t)stalls;
     m->n_exact_steps = (int64_t)exact_steps;   // the walks of the fused pass
     if (total > 0) {
-        k_walk_compact<<<ceil_div(W * 32, 256), 256, 0, s>>>(W, m->d_ray_off, (int32_t)K, d_scratch, m->d_steps32);
+        {
+            // each record read once from its slot and written once, plus the offsets
+            MGT_KTIMER_BYTES("k_walk_compact", s, 32.0 * (double)total + 8.0 * (double)W);
+            k_walk_compact<<<ceil_div(W * 32, 256), 256, 0, s>>>(W, m->d_ray_off, (int32_t)K, d_scratch, m->d_steps32);
+        }
         MGT_LAUNCH_CHECK("k_walk_compact");
         if (n_over > 0) {
-            k_walk<kWalkList><<<ceil_div((int64_t)n_over * 16, kWalkThreads), kWalkThreads, 0, s>>>(
-                a, nullptr, m->d_ray_off, d_list, (int64_t)n_over, 0, nullptr, m->d_vel_hl, m->d_w32, inv_Lunit,
-                m->opts.width_mode, m->d_steps32, m->d_err, ImgWalkArgs{});
+            {
+                MGT_KTIMER("k_walk<list>", s);
+                k_walk<kWalkList><<<ceil_div((int64_t)n_over * 16, kWalkThreads), kWalkThreads, 0, s>>>(
+                    a, nullptr, m->d_ray_off, d_list, (int64_t)n_over, 0, nullptr, m->d_vel_hl, m->d_w32, inv_Lunit,
+                    m->opts.width_mode, m->d_steps32, m->d_err, ImgWalkArgs{});
+            }
             MGT_LAUNCH_CHECK("k_walk<list>");
         }
     }

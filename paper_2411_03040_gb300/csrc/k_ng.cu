@@ -126,47 +126,6 @@ int grid_for(int64_t n)
     return (int)(b < kNgMaxBlocks ? (b < 1 ? 1 : b) : kNgMaxBlocks);
 }
 
-// Solve (G / tr G) y = 1 by LU with partial pivoting; c = y / sum(y).
-bool ng_coefficients(const std::vector<double> &G, int n, double *c)
-{
-    double a[kMaxNgHist][kMaxNgHist], y[kMaxNgHist];
-    double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += G[i * kMaxNgHist + i];
-    if (!(tr > 0.0) || !std::isfinite(tr)) return false;
-    for (int i = 0; i < n; ++i) {
-        for (int j = 0; j < n; ++j) a[i][j] = G[i * kMaxNgHist + j] / tr;
-        y[i] = 1.0;
-    }
-    for (int k = 0; k < n; ++k) {
-        int piv = k;
-        for (int i = k + 1; i < n; ++i)
-            if (std::fabs(a[i][k]) > std::fabs(a[piv][k])) piv = i;
-        if (a[piv][k] == 0.0) return false;
-        if (piv != k) {
-            for (int j = 0; j < n; ++j) std::swap(a[k][j], a[piv][j]);
-            std::swap(y[k], y[piv]);
-        }
-        for (int i = k + 1; i < n; ++i) {
-            const double f = a[i][k] / a[k][k];
-            for (int j = k; j < n; ++j) a[i][j] -= f * a[k][j];
-            y[i] -= f * y[k];
-        }
-    }
-    for (int i = n - 1; i >= 0; --i) {
-        double s = y[i];
-        for (int j = i + 1; j < n; ++j) s -= a[i][j] * y[j];
-        y[i] = s / a[i][i];
-    }
-    double sum = 0.0;
-    for (int i = 0; i < n; ++i) sum += y[i];
-    if (!std::isfinite(sum) || sum == 0.0) return false;
-    for (int i = 0; i < n; ++i) {
-        c[i] = y[i] / sum;
-        if (!std::isfinite(c[i])) return false;
-    }
-    return true;
-}
-
 int slots_needed(const mgt_ng_opts &o)
 {
     if (o.mode == MGT_NG_CLASSICAL) return o.n_steps + 2;
@@ -267,8 +226,11 @@ mgt_status ng_begin(mgt_model *m, const mgt_ng_opts *o, cudaStream_t s)
     if (opts.mode == MGT_NG_NONE) {
         MGT_CUDA(cudaMemsetAsync(ng.d_red + kMaxNgHist, 0, sizeof(double), s));
         Slots hs{};
-        k_ng_push<<<grid, kNgThreads, 0, s>>>(n, m->L, m->d_pops, m->d_pops_prev, m->d_nspec, nullptr, hs, 0,
-                                              ng.d_partials, ng.d_red + kMaxNgHist);
+        {
+            MGT_KTIMER_BYTES("k_ng_push", s, 16.0 * n);
+            k_ng_push<<<grid, kNgThreads, 0, s>>>(n, m->L, m->d_pops, m->d_pops_prev, m->d_nspec, nullptr, hs, 0,
+                                                  ng.d_partials, ng.d_red + kMaxNgHist);
+        }
         MGT_LAUNCH_CHECK("k_ng_push");
         MGT_CUDA(cudaMemcpyAsync(ng.h_red, ng.d_red + kMaxNgHist, sizeof(double), cudaMemcpyDeviceToHost, s));
         ng.pend.phase = 1;
@@ -280,9 +242,12 @@ mgt_status ng_begin(mgt_model *m, const mgt_ng_opts *o, cudaStream_t s)
     if (ng.hist.empty()) {
         const int s0 = free_slot(ng);
         Slots hs{};
-        k_ng_push<<<grid, kNgThreads, 0, s>>>(n, m->L, m->d_pops_prev, m->d_pops_prev, m->d_nspec,
-                                              slot + (size_t)s0 * n, hs, 0, ng.d_partials,
-                                              ng.d_red + kMaxNgHist + 1);
+        {
+            MGT_KTIMER_BYTES("k_ng_push", s, 16.0 * n + 8.0 * m->N);
+            k_ng_push<<<grid, kNgThreads, 0, s>>>(n, m->L, m->d_pops_prev, m->d_pops_prev, m->d_nspec,
+                                                  slot + (size_t)s0 * n, hs, 0, ng.d_partials,
+                                                  ng.d_red + kMaxNgHist + 1);
+        }
         MGT_LAUNCH_CHECK("k_ng_push");
         ng.hist.push_back(s0);
         ng.G.assign(kMaxNgHist * kMaxNgHist, 0.0);
@@ -294,8 +259,12 @@ mgt_status ng_begin(mgt_model *m, const mgt_ng_opts *o, cudaStream_t s)
     if (snew < 0 || mh > kMaxNgHist) return set_error(MGT_ERR_STATE, "Ng history overflow");
     const Slots hs = hist_slots(ng, slot, n, mh);
     MGT_CUDA(cudaMemsetAsync(ng.d_red + kMaxNgHist, 0, sizeof(double), s));
-    k_ng_push<<<grid, kNgThreads, 0, s>>>(n, m->L, m->d_pops, m->d_pops_prev, m->d_nspec, slot + (size_t)snew * n,
-                                          hs, mh, ng.d_partials, ng.d_red + kMaxNgHist);
+    {
+        // populations, previous populations and every history slot in, the new slot out
+        MGT_KTIMER_BYTES("k_ng_push", s, (3.0 + mh) * 8.0 * n + 8.0 * m->N);
+        k_ng_push<<<grid, kNgThreads, 0, s>>>(n, m->L, m->d_pops, m->d_pops_prev, m->d_nspec, slot + (size_t)snew * n,
+                                              hs, mh, ng.d_partials, ng.d_red + kMaxNgHist);
+    }
     MGT_LAUNCH_CHECK("k_ng_push");
     k_ng_finish<<<1, 32, 0, s>>>(grid, mh, ng.d_partials, ng.d_red);
     MGT_LAUNCH_CHECK("k_ng_finish");
@@ -344,7 +313,7 @@ mgt_status ng_after_push(mgt_model *m, cudaStream_t s)
     // a prediction from the residuals' Gram matrix
     const int nres = mcount - 1;
     Coef cf{};
-    if (!ng_coefficients(ng.G, nres, cf.c)) {   // exactly singular: no prediction
+    if (!ng_solve_coefficients(ng.G.data(), kMaxNgHist, nres, cf.c)) {   // exactly singular: no prediction
         pd.negative = true;
         pd.mr_pred = INFINITY;
         pd.phase = 3;
@@ -356,8 +325,11 @@ mgt_status ng_after_push(mgt_model *m, cudaStream_t s)
     }
     const Slots h2 = hist_slots(ng, slot, n, mcount);
     MGT_CUDA(cudaMemsetAsync(ng.d_red + kMaxNgHist + 1, 0, sizeof(double) * 2, s));
-    k_ng_predict<<<grid, kNgThreads, 0, s>>>(n, h2, nres, cf, slot + (size_t)ng.pred_slot * n, prev,
-                                             ng.d_red + kMaxNgHist + 1);
+    {
+        MGT_KTIMER_BYTES("k_ng_predict", s, (nres + 1.0 + (prev ? 1.0 : 0.0)) * 8.0 * n);
+        k_ng_predict<<<grid, kNgThreads, 0, s>>>(n, h2, nres, cf, slot + (size_t)ng.pred_slot * n, prev,
+                                                 ng.d_red + kMaxNgHist + 1);
+    }
     MGT_LAUNCH_CHECK("k_ng_predict");
     MGT_CUDA(cudaMemcpyAsync(ng.h_red + kMaxNgHist + 1, ng.d_red + kMaxNgHist + 1, sizeof(double) * 2,
                              cudaMemcpyDeviceToHost, s));
@@ -378,8 +350,11 @@ mgt_status ng_after_predict(mgt_model *m, cudaStream_t s)
     const int64_t n = m->N * m->L;
     const int grid = grid_for(n);
     auto use_prediction = [&]() -> mgt_status {
-        k_ng_apply<<<grid, kNgThreads, 0, s>>>(n, m->L, ng.d_slots + (size_t)ng.pred_slot * n, m->d_nspec,
-                                               m->d_pops);
+        {
+            MGT_KTIMER_BYTES("k_ng_apply", s, 16.0 * n + 8.0 * m->N);
+            k_ng_apply<<<grid, kNgThreads, 0, s>>>(n, m->L, ng.d_slots + (size_t)ng.pred_slot * n, m->d_nspec,
+                                                   m->d_pops);
+        }
         MGT_LAUNCH_CHECK("k_ng_apply");
         const int keep = ng.pred_slot;
         ng.hist.assign(1, keep);

@@ -9,8 +9,10 @@
 // Working memory lives in one file-scope static device array instead of
 // cudaMalloc'd buffers.  In host code the array's name is only a host-side
 // stand-in, so each device's address of it is looked up once with
-// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+// cudaGetSymbolAddress (with that device current; the first call on the device
+// does this) and passed to the kernels.
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "mgt_common.cuh"
@@ -100,52 +102,25 @@ __global__ void __launch_bounds__(kNaThreads) k_ng_na_predict(int64_t len, const
     if (neg) atomicAdd(n_neg, neg);
 }
 
-// c = y / sum(y) with (G / tr G) y = 1, LU with partial pivoting on a copy.
-bool na_coefficients(const double *G, int n, double *c)
-{
-    double a[kNaMaxRes][kNaMaxRes], y[kNaMaxRes];
-    double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += G[i * kNaMaxRes + i];
-    if (!(tr > 0.0) || !std::isfinite(tr)) return false;
-    for (int i = 0; i < n; ++i) {
-        for (int j = 0; j < n; ++j) a[i][j] = G[i * kNaMaxRes + j] / tr;
-        y[i] = 1.0;
-    }
-    for (int k = 0; k < n; ++k) {
-        int piv = k;
-        for (int i = k + 1; i < n; ++i)
-            if (std::fabs(a[i][k]) > std::fabs(a[piv][k])) piv = i;
-        if (a[piv][k] == 0.0) return false;
-        if (piv != k) {
-            for (int j = 0; j < n; ++j) std::swap(a[k][j], a[piv][j]);
-            std::swap(y[k], y[piv]);
-        }
-        for (int i = k + 1; i < n; ++i) {
-            const double f = a[i][k] / a[k][k];
-            for (int j = k; j < n; ++j) a[i][j] -= f * a[k][j];
-            y[i] -= f * y[k];
-        }
-    }
-    for (int i = n - 1; i >= 0; --i) {
-        double s = y[i];
-        for (int j = i + 1; j < n; ++j) s -= a[i][j] * y[j];
-        y[i] = s / a[i][i];
-    }
-    double sum = 0.0;
-    for (int i = 0; i < n; ++i) sum += y[i];
-    if (!std::isfinite(sum) || sum == 0.0) return false;
-    for (int i = 0; i < n; ++i) {
-        c[i] = y[i] / sum;
-        if (!std::isfinite(c[i])) return false;
-    }
-    return true;
-}
-
-// Per-device address of the scratch array, looked up once per device.
+// Per-device address of the scratch array.  The lookup runs with the device
+// current and is cached only once it has succeeded: a failed lookup (a
+// transient error) is retried by the next call on that device.
 constexpr int kNaMaxDevices = 64;
-std::once_flag g_na_once[kNaMaxDevices];
+std::mutex g_na_mutex;
 double *g_na_ptr[kNaMaxDevices];
-cudaError_t g_na_err[kNaMaxDevices];
+
+mgt_status scratch_address(int dev, double **out)
+{
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+        double *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress((void **)&p, g_ng_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_ng_noalloc_scratch)");
+        g_na_ptr[dev] = p;
+    }
+    *out = g_na_ptr[dev];
+    return MGT_OK;
+}
 
 }  // namespace
 
@@ -174,11 +149,15 @@ extern "C" mgt_status mgt_ng_extrapolate_noalloc(int32_t n_iterates, const doubl
         if (at.device != dev)
             return set_error(MGT_ERR_ARG, "mgt_ng_extrapolate_noalloc: buffers are not on the current device");
     }
-    std::call_once(g_na_once[dev], [dev] {
-        g_na_err[dev] = cudaGetSymbolAddress((void **)&g_na_ptr[dev], g_ng_noalloc_scratch);
-    });
-    if (g_na_err[dev] != cudaSuccess) return cuda_status(g_na_err[dev], "cudaGetSymbolAddress(g_ng_noalloc_scratch)");
-    double *scratch = g_na_ptr[dev];
+    {
+        // the prediction may not overlap any iterate (it is written while they are read)
+        const char *pb = reinterpret_cast<const char *>(prediction), *ib = reinterpret_cast<const char *>(iterates);
+        const uint64_t pn = (uint64_t)len * sizeof(double), in = (uint64_t)n_iterates * pn;
+        if ((uint64_t)(uintptr_t)pb < (uint64_t)(uintptr_t)ib + in && (uint64_t)(uintptr_t)ib < (uint64_t)(uintptr_t)pb + pn)
+            return set_error(MGT_ERR_ARG, "mgt_ng_extrapolate_noalloc: prediction overlaps the iterates");
+    }
+    double *scratch = nullptr;
+    MGT_TRY_STATUS(scratch_address(dev, &scratch));
     double *partials = scratch, *G = scratch + kGramOff;
     unsigned long long *count = reinterpret_cast<unsigned long long *>(scratch + kCountOff);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -196,7 +175,7 @@ extern "C" mgt_status mgt_ng_extrapolate_noalloc(int32_t n_iterates, const doubl
     MGT_CUDA(cudaMemcpyAsync(Gh, G, sizeof(double) * nres * kNaMaxRes, cudaMemcpyDeviceToHost, s));
     MGT_CUDA(cudaStreamSynchronize(s));
     NaCoef cf{};
-    if (!na_coefficients(Gh, nres, cf.c))
+    if (!ng_solve_coefficients(Gh, kNaMaxRes, nres, cf.c))
         return set_error(MGT_ERR_SINGULAR, "mgt_ng_extrapolate_noalloc: the residual Gram matrix is singular");
     MGT_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
     k_ng_na_predict<<<grid, kNaThreads, 0, s>>>(len, iterates, nres, cf, prediction, count);

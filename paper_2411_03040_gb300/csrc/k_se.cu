@@ -235,7 +235,10 @@ mgt_status launch_stat_eq(mgt_model *m, cudaStream_t s)
     a.wpb = wpb;
     const size_t smem = per_warp * wpb;
     MGT_CUDA(cudaFuncSetAttribute(k_se, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_se<<<ceil_div(m->N, wpb), 32 * wpb, smem, s>>>(a);
+    {
+        MGT_KTIMER("k_se", s);
+        k_se<<<ceil_div(m->N, wpb), 32 * wpb, smem, s>>>(a);
+    }
     MGT_LAUNCH_CHECK("k_se");
     return MGT_OK;
 }

@@ -5,7 +5,9 @@
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/magritte_gpu.h"
@@ -112,6 +114,7 @@ struct mgt_model {
     double *d_pos = nullptr, *d_vel = nullptr, *d_temp = nullptr, *d_vturb2 = nullptr;
     double *d_ncoll = nullptr, *d_nspec = nullptr, *d_w64 = nullptr;
     float2 *d_w32 = nullptr;                   // {w, 1/w}
+    float *d_dxmax = nullptr;                  // [N] longest graph edge at each point, in length units (rounded up)
     int32_t *d_nbr_off = nullptr, *d_nbrs = nullptr;
     double *d_nbr_pos = nullptr;               // [nnz][3] position of each neighbour entry
     float4 *d_ent = nullptr;                   // packed neighbour rows for the walk (see WalkEntry)
@@ -140,6 +143,7 @@ struct mgt_model {
     double *d_line64 = nullptr;                // [N][row_stride64] chi~', S', w, 1/w
     double *d_J = nullptr, *d_Lst = nullptr;   // [N][M]
     int *d_err = nullptr;                      // [4]
+    int *d_range_bad = nullptr;                // set by the line data when a point is outside the two-row range
     unsigned long long *d_count = nullptr;     // [4] counters (opacity floors, stalls)
     // rays
     int64_t *d_ray_off = nullptr;              // [R*N+1]
@@ -169,6 +173,28 @@ namespace mgt {
 // GB again on every trace costs more than the walk itself); the reserve is
 // released when the last model of the process is destroyed (api.cu).
 mgt_status scratch_pool(cudaMemPool_t *pool);
+
+// Per-kernel CUDA-event timing for measurement (mgt_kernel_timing): while it
+// is on, a KernelTimer records an event before the launch that follows it in
+// the same scope and one when the scope ends, on the launch's stream, with the
+// launch's algorithmic bytes (what the kernel must read and write at least;
+// 0 where the site states none).  Off by default, and skipped on a capturing
+// stream.
+class KernelTimer {
+public:
+    KernelTimer(const char *name, cudaStream_t s, double bytes = 0.0);
+    ~KernelTimer();
+    KernelTimer(const KernelTimer &) = delete;
+    KernelTimer &operator=(const KernelTimer &) = delete;
+
+private:
+    const char *name_;
+    cudaStream_t s_;
+    double bytes_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+#define MGT_KTIMER(name, s) ::mgt::KernelTimer mgt_ktimer_(name, s)
+#define MGT_KTIMER_BYTES(name, s, bytes) ::mgt::KernelTimer mgt_ktimer_(name, s, bytes)
 
 // error helpers (api.cu)
 void note_launch();
@@ -229,6 +255,52 @@ void ng_free(mgt_model *m);
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Ng coefficients from a Gram matrix G (n x n, row stride ld, n <= kMaxNgHist):
+// (G / tr G) y = 1 by LU with partial pivoting on a copy, c = y / sum(y).
+// False when the trace is not positive and finite, a pivot is exactly zero or
+// the result is not finite.  Used by the model's Ng step and by the
+// no-allocation entry point, so both give the same coefficients.
+inline bool ng_solve_coefficients(const double *G, int ld, int n, double *c)
+{
+    double a[kMaxNgHist][kMaxNgHist], y[kMaxNgHist];
+    if (n < 1 || n > kMaxNgHist) return false;
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += G[i * ld + i];
+    if (!(tr > 0.0) || !std::isfinite(tr)) return false;
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) a[i][j] = G[i * ld + j] / tr;
+        y[i] = 1.0;
+    }
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < n; ++i)
+            if (std::fabs(a[i][k]) > std::fabs(a[piv][k])) piv = i;
+        if (a[piv][k] == 0.0) return false;
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) std::swap(a[k][j], a[piv][j]);
+            std::swap(y[k], y[piv]);
+        }
+        for (int i = k + 1; i < n; ++i) {
+            const double f = a[i][k] / a[k][k];
+            for (int j = k; j < n; ++j) a[i][j] -= f * a[k][j];
+            y[i] -= f * y[k];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int j = i + 1; j < n; ++j) s -= a[i][j] * y[j];
+        y[i] = s / a[i][i];
+    }
+    double sum = 0.0;
+    for (int i = 0; i < n; ++i) sum += y[i];
+    if (!std::isfinite(sum) || sum == 0.0) return false;
+    for (int i = 0; i < n; ++i) {
+        c[i] = y[i] / sum;
+        if (!std::isfinite(c[i])) return false;
+    }
+    return true;
+}
+
 // NVTX range over one C-ABI call (visible to profilers that record NVTX, such
 // as ncu's --nvtx filters; a few nanoseconds when none is attached).
 struct NvtxRange {
@@ -242,10 +314,18 @@ struct NvtxRange {
 // Per-point line-data rows, in scalars of the row's precision:
 //   [0, Mpad)        chi~'  per line (zero for padding lines)
 //   [Mpad, 2 Mpad)   S'     per line
-//   2 Mpad, 2 Mpad+1 the point's w and 1/w; FP32 rows end with two zeros
+//   2 Mpad, 2 Mpad+1 the point's w and 1/w; FP32 rows end with the range
+//                    figure of the two-row elimination (k_fs.cu) and a zero
 // Mpad is a multiple of 8, so a row is a multiple of 16 bytes (one bulk copy)
 // and every group of 4 (FP32) or 2 (FP64) lines starts 16-byte aligned.
 __host__ __device__ inline int row_stride32(int Mpad) { return 2 * Mpad + 4; }   // floats
+
+// Range of the formal solution's two-row elimination (k_fs.cu): per-row half
+// depths up to kTwoRowDepth and sources S' up to kTwoRowSource.  The line data
+// store each point's figure G = max(chi~max dxmax / kTwoRowDepth,
+// S'max / kTwoRowSource) in its FP32 row (k_geom.cu).
+constexpr float kTwoRowDepth = 256.0f;                     // 2^8
+constexpr float kTwoRowSource = 1.2089258196146292e24f;    // 2^80
 __host__ __device__ inline int row_stride64(int Mpad) { return 2 * Mpad + 2; }   // doubles
 
 }  // namespace mgt

@@ -64,6 +64,10 @@ class mgt_autotune_result(ctypes.Structure):
                 ("schedules", _i32 * 8), ("lines", _i32 * 8), ("ms", ctypes.c_float * 8)]
 
 
+class mgt_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", _i64), ("total_ms", _f64), ("bytes", _f64)]
+
+
 class mgt_batch_layout(ctypes.Structure):
     _fields_ = [("n_models", _i32), ("fs_items", _i64), ("fs_grid", _i32), ("fs_threads", _i32),
                 ("fs_smem_bytes", _i64), ("se_blocks", _i64), ("graph_kernels", _i32), ("fs_launches", _i32)]
@@ -101,6 +105,8 @@ SIGNATURES = {
     "mgt_model_sizes": [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                         ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
     "mgt_launch_count": [ctypes.POINTER(_i64)],
+    "mgt_kernel_timing": [_i32],
+    "mgt_kernel_times": [_i32, ctypes.POINTER(mgt_kernel_time), ctypes.POINTER(_i32)],
     "mgt_last_error": [],
 }
 
@@ -373,10 +379,35 @@ def mgt_remesh(pos, rho, r_max, max_level, n_side, stream=None):
     return out, flags
 
 
+def _check_noalloc_tensors(iterates, prediction):
+    """The C side sees only pointers and sizes, so the tensors' dtype, shape,
+    layout, device and disjointness are checked here, before the library is
+    touched; ValueError otherwise."""
+    for name, t in (("iterates", iterates), ("prediction", prediction)):
+        if str(getattr(t, "dtype", None)) != "torch.float64":
+            raise ValueError(f"mgt_ng_extrapolate_noalloc: {name} must be a float64 torch tensor")
+    if iterates.dim() != 2:
+        raise ValueError("mgt_ng_extrapolate_noalloc: iterates must be 2-D [n_iterates][len]")
+    if int(iterates.shape[1]) != int(prediction.numel()):
+        raise ValueError(f"mgt_ng_extrapolate_noalloc: iterates have {int(iterates.shape[1])} entries per iterate, "
+                         f"prediction has {int(prediction.numel())}")
+    for name, t in (("iterates", iterates), ("prediction", prediction)):
+        if not t.is_contiguous():
+            raise ValueError(f"mgt_ng_extrapolate_noalloc: {name} must be contiguous")
+    import torch
+    for name, t in (("iterates", iterates), ("prediction", prediction)):
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise ValueError(f"mgt_ng_extrapolate_noalloc: {name} must be on the current CUDA device")
+    p0, i0 = prediction.data_ptr(), iterates.data_ptr()
+    if p0 < i0 + iterates.numel() * 8 and i0 < p0 + prediction.numel() * 8:
+        raise ValueError("mgt_ng_extrapolate_noalloc: prediction overlaps the iterates")
+
+
 def mgt_ng_extrapolate_noalloc(iterates, prediction, stream=None):
     """Ng prediction from ``iterates`` (device tensor [n][len] f64, oldest
     first) into ``prediction`` (device tensor [len] f64) without any device
     allocation; returns (coefficients, number of negative entries)."""
+    _check_noalloc_tensors(iterates, prediction)
     n = int(iterates.shape[0])
     ln = int(prediction.numel())
     coef = np.zeros(max(n - 1, 1), np.float64)
@@ -460,6 +491,21 @@ def mgt_launch_count() -> int:
     c = _i64(0)
     _check(load().mgt_launch_count(ctypes.byref(c)), "mgt_launch_count")
     return c.value
+
+
+def mgt_kernel_timing(enable: bool):
+    """Start (clearing the totals) or stop per-kernel event timing."""
+    _check(load().mgt_kernel_timing(int(bool(enable))), "mgt_kernel_timing")
+
+
+def mgt_kernel_times() -> dict:
+    """{kernel name: {"launches", "total_ms", "bytes"}} of the timed launches so far."""
+    n = _i32(0)
+    _check(load().mgt_kernel_times(0, None, ctypes.byref(n)), "mgt_kernel_times")
+    arr = (mgt_kernel_time * max(n.value, 1))()
+    _check(load().mgt_kernel_times(n.value, arr, ctypes.byref(n)), "mgt_kernel_times")
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms),
+                                   "bytes": float(arr[i].bytes)} for i in range(n.value)}
 
 
 def mgt_last_error() -> str:

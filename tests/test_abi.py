@@ -55,6 +55,7 @@ def test_struct_layout_matches_header(tmp_path):
         "mgt_ali_stats": mgt.mgt_ali_stats,
         "mgt_autotune_result": mgt.mgt_autotune_result,
         "mgt_batch_layout": mgt.mgt_batch_layout,
+        "mgt_kernel_time": mgt.mgt_kernel_time,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for name, cls in structs.items():
@@ -206,3 +207,23 @@ def test_noalloc_ng_rejects_sizes_and_null_pointers_before_any_device_work(lib):
         st = lib.mgt_ng_extrapolate_noalloc(n, it, ln, pr, buf, C.byref(neg), None)
         assert st == 1, (n, ln)
         assert b"mgt_ng_extrapolate_noalloc" in lib.mgt_last_error()
+
+
+def test_noalloc_wrapper_rejects_bad_tensors_before_the_library():
+    # the C entry point sees only pointers and a length: the binding checks
+    # dtype, shape, layout and device first (these CPU tensors never reach it)
+    torch = pytest.importorskip("torch")
+    from paper_2411_03040_gb300 import mgt
+    X = torch.zeros((3, 8), dtype=torch.float64)
+    out = torch.zeros(8, dtype=torch.float64)
+    cases = [
+        (X.float(), out, "float64"),
+        (X, out.float(), "float64"),
+        (X.reshape(-1), out, "2-D"),
+        (X, torch.zeros(7, dtype=torch.float64), "entries per iterate"),
+        (torch.zeros((8, 3), dtype=torch.float64).t(), out, "contiguous"),
+        (X, out, "CUDA device"),
+    ]
+    for it, pr, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            mgt.mgt_ng_extrapolate_noalloc(it, pr)

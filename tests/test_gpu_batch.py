@@ -102,7 +102,9 @@ def test_batch_iterate_graph_matches_ali_per_model(mgt, batch_models, ng_mode):
     n0 = mgt.mgt_launch_count()
     stats = mgt.mgt_batch_iterate(b, n_iter=n_iter, ng_mode=ng_mode, n_steps=3, want_stats=True)
     lay = mgt.mgt_batch_get_layout(b)
-    assert lay["graph_kernels"] == 2 + lay["fs_launches"]  # line data, formal solution per width, SE
+    # range-flag reset and line data; per CTA width the two-row formal solution
+    # and its one-row fallback; SE
+    assert lay["graph_kernels"] == 3 + 2 * lay["fs_launches"]
     assert mgt.mgt_launch_count() - n0 >= 3 * n_iter
     for h, (P, st), bs in zip(hs, ref, stats):
         np.testing.assert_array_equal(mgt.mgt_get_populations(h), P)
@@ -111,7 +113,7 @@ def test_batch_iterate_graph_matches_ali_per_model(mgt, batch_models, ng_mode):
         assert bs["last_maxrel"] == st["last_maxrel"]
     # a second call replays the same graph
     mgt.mgt_batch_iterate(b, n_iter=1)
-    assert mgt.mgt_batch_get_layout(b)["graph_kernels"] == 2 + lay["fs_launches"]
+    assert mgt.mgt_batch_get_layout(b)["graph_kernels"] == 3 + 2 * lay["fs_launches"]
 
 
 def test_batch_follows_model_changes(mgt, batch_models):

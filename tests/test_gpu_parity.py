@@ -162,6 +162,28 @@ def test_shell_41_levels_sampled(mgt, grf, schedule):
     assert rel_err(Lg[orig], L) < TOL32
 
 
+@pytest.mark.parametrize("lpt", [4, 8])
+def test_items_outside_the_two_row_range_are_redone_exactly(mgt, lpt):
+    # points in the inner half of the sphere get a species density 1e12 times
+    # higher: their segments reach optical depths of ~1e12, far outside the
+    # range of the two-row elimination (whose state would overflow FP32 there);
+    # those items are redone with the one-row form, the others keep the
+    # two-row form, and every point must still match the oracle
+    m = synth.config_model(1, n_points=800)
+    r = np.linalg.norm(m.pos, axis=1)
+    m.n_spec = np.where(r < 0.5 * r.max(), m.n_spec * 1e12, m.n_spec)
+    h = mgt.mgt_model_create(m)
+    mgt.mgt_set_solve_opts(h, lines_per_thread=lpt)
+    mgt.mgt_trace_rays(h)
+    rays = O.trace(m)
+    J, L = oracle_fields(m, rays)
+    Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP32_MIXED)
+    assert np.all(np.isfinite(Jg)) and np.all(np.isfinite(Lg))
+    assert rel_err(Jg, J) < TOL32 and rel_err(Lg, L) < TOL32
+    J64, L64 = gpu_fields(mgt, h, mgt.MGT_FP64)
+    assert rel_err(J64, J) < TOL64 and rel_err(L64, L) < TOL64
+
+
 def test_single_point_model_is_background(mgt):
     # no neighbours: every half-ray is empty, u = I_bg, Lambda* = 0
     lines = synth.linear_rotor(3, np.random.default_rng(0))

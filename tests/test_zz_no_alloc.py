@@ -6,7 +6,9 @@ loop that must stay free of cudaMalloc/cudaFree because they can synchronise
 the device.  It keeps its working memory in one static device array shared by
 every call, so this test makes two calls in a row with different iterate
 counts and checks each against the prediction mgt_ng_accelerate applied to the
-model's populations, within the FP64 tolerance of the parity tests.
+model's populations and against the CPU oracle's Ng prediction from the same
+iterates, within the FP64 tolerance of the parity tests.  A further call must
+leave the device's free memory unchanged: it allocates nothing.
 
 This file is named to be collected last, so that a run stopping at the first
 failure has run every other test before it.
@@ -64,13 +66,29 @@ def test_noalloc_ng_matches_model_ng_on_two_calls_in_a_row():
     c2, neg2 = mgt.mgt_ng_extrapolate_noalloc(X2, out2)
     torch.cuda.synchronize()
 
-    for c, neg, out, pred, nres in ((c1, neg1, out1, pred1, 4), (c2, neg2, out2, pred2, 3)):
+    import oracle as O
+    for c, neg, out, pred, nres, hist in ((c1, neg1, out1, pred1, 4, hist1), (c2, neg2, out2, pred2, 3, hist2)):
         assert c.shape == (nres,)
         assert abs(c.sum() - 1.0) < 1e-12
         assert neg == 0
-        got = out.cpu().numpy().reshape(pred.shape) * m.n_spec[:, None]
+        frac = out.cpu().numpy()
+        got = frac.reshape(pred.shape) * m.n_spec[:, None]
         assert np.all(np.isfinite(got))
         assert _rel(got, pred) < TOL64
+        ref = O.ng_predict(hist.reshape(hist.shape[0], -1))
+        np.testing.assert_allclose(c, O.ng_coefficients(hist.reshape(hist.shape[0], -1)), rtol=1e-8)
+        assert _rel(frac, ref) < TOL64
+
+    # a further call allocates no device memory (the free memory the driver
+    # reports does not move), and still gives the same prediction
+    out3 = torch.full_like(out1, float("nan"))
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    mgt.mgt_ng_extrapolate_noalloc(X1, out3)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.equal(out3, out1)
 
 
 def test_noalloc_ng_rejects_sizes_beyond_its_scratch():
@@ -86,3 +104,10 @@ def test_noalloc_ng_rejects_sizes_beyond_its_scratch():
         mgt.mgt_ng_extrapolate_noalloc(X, out)
     assert e.value.status == mgt.MGT_ERR_ARG
     assert "n_iterates" in str(e.value)
+    # the C entry point itself refuses a prediction that overlaps the iterates
+    import ctypes
+    Y = torch.zeros((3, 64), dtype=torch.float64, device="cuda")
+    st = mgt.load().mgt_ng_extrapolate_noalloc(3, ctypes.c_void_p(Y.data_ptr()), 64,
+                                               ctypes.c_void_p(Y[1].data_ptr()), None, None, None)
+    assert st == mgt.MGT_ERR_ARG
+    assert "overlaps" in mgt.mgt_last_error()
