@@ -39,6 +39,12 @@ UNIT = "formal solutions/s"
 # time, 15 FP32 operations and 1 reciprocal (MUFU) per two rows, so 8 lane-ops
 # per line-step; each takes one issue slot per lane.
 OPS_PER_LINE_STEP = 8
+# The line-independent work of one bin-step (one bin, one ray step, shared by
+# the M lines): the comoving offset, the Gaussian at the far point (the near
+# point's is the step before's), the Doppler shift and switch test, and the
+# two trapezoid coefficients, about 8 FP32 operations and 1 exponential
+# (MUFU); semi-analytic segments cost more and are not counted.
+OPS_PER_BIN_STEP = 9
 
 
 def parse():
@@ -410,17 +416,19 @@ def run_mine(args, model, cfg, emit=True, n_error_origins=None, min_warmup=3):
 
     # roofline of the dominant kernel (formal solution)
     line_steps = tst["total_steps"] * model.lines.n_lines * model.n_quad
-    achieved = OPS_PER_LINE_STEP * line_steps / (fs_ms * 1e-3) / 1e12
+    bin_steps = tst["total_steps"] * model.n_quad
+    ops = OPS_PER_LINE_STEP * line_steps + OPS_PER_BIN_STEP * bin_steps
+    achieved = ops / (fs_ms * 1e-3) / 1e12
     tr = traffic_record()
     out["roofline"] = {
-        "bound": "alu", "kernel": "k_fs_staged<float,8,31,2> (formal solution + J-bar/Lambda* reduction)",
+        "bound": "alu", "kernel": "k_fs_staged<float,8,30,2,true> (formal solution + J-bar/Lambda* reduction, two-row elimination)",
         "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak,
         "traffic": (tr["dram_bytes_per_traced_step"] * tst["total_steps"] if tr else None),
         "traffic_source": (tr["source"] if tr else None),
         "peak_source": f"{src} SM clock: issue roof {n_sms} SMs (read from the device) x 4 schedulers x 32 lanes x "
                        f"{sm_max:.0f} MHz (one FP32 or MUFU lane-op per issue slot)",
-        "ops_per_line_step": OPS_PER_LINE_STEP,
-        "ops_per_launch": OPS_PER_LINE_STEP * line_steps, "line_steps_per_launch": line_steps,
+        "ops_per_line_step": OPS_PER_LINE_STEP, "ops_per_bin_step": OPS_PER_BIN_STEP,
+        "ops_per_launch": ops, "line_steps_per_launch": line_steps, "bin_steps_per_launch": bin_steps,
         "launch_ms": fs_ms, "launch_ms_source": "CUDA events around each k_fs_staged launch (library kernel "
                                                 "timer, on the launch's stream) in the timed steps",
         "step_ms": ms, "share_of_step": fs_ms / ms}
@@ -437,6 +445,13 @@ def run_mine(args, model, cfg, emit=True, n_error_origins=None, min_warmup=3):
                            f"lengths written; its L2 gather of rows is {wg / 1e9:.1f} GB per step)")
     out["ray_steps_per_s"] = {"value": model.n_quad * (tst["total_steps"] + model.n_points * pairs) / (fs_ms * 1e-3),
                               "unit": "ray steps/s (formal solve)"}
+    # the formal-solution rate over the narrower timed region of the scope
+    # table (line data + formal solution + J-bar/Lambda* on traced rays), beside
+    # the whole ALI step of the headline value
+    ld_ms = per("k_line_data")
+    out["formal_solution_rate"] = {
+        "value": units / ((fs_ms + ld_ms) * 1e-3), "unit": UNIT, "ms": fs_ms + ld_ms,
+        "region": "line data + formal solution with J-bar/Lambda* per step (rays traced), kernel event times"}
     out["gpu_launches"] = launches
     out["clocks"] = clk
     out["trace"] = tst
@@ -640,13 +655,18 @@ def run_batch(args):
         clk = clocks.stop()
         # the formal solution alone (line data + persistent kernel), for the roofline
         fs_times = []
-        for _ in range(max(2, args.steps)):
+        reps = max(2, args.steps)
+        mgt.mgt_kernel_timing(True)
+        for _ in range(reps):
             a, c = ev(), ev()
             a.record(stream)
             mgt.mgt_batch_formal_solve(b, stream=stream)
             c.record(stream)
             torch.cuda.synchronize()
             fs_times.append(a.elapsed_time(c))
+        bkt = mgt.mgt_kernel_times()
+        mgt.mgt_kernel_timing(False)
+        fs_kernel_ms = sum(bkt[k]["total_ms"] for k in ("k_fs_batch", "k_fs_batch_exact") if k in bkt) / reps
         # the same formal solutions as one launch per model (schedule 2, the
         # tuned lines per thread), for comparison with the persistent launch
         a, c = ev(), ev()
@@ -657,12 +677,14 @@ def run_batch(args):
         torch.cuda.synchronize()
         seq_ms = a.elapsed_time(c)
     ms = float(np.mean(times))
-    fs_ms = float(np.mean(fs_times))
+    fs_call_ms = float(np.mean(fs_times))
+    fs_ms = fs_kernel_ms
     units = sum(m.n_points * (m.dirs.shape[0] // 2) * m.lines.n_lines * m.n_quad for m in models)
     line_steps = sum(st * m.lines.n_lines * m.n_quad for st, m in zip(steps, models))
+    bin_steps = sum(st * m.n_quad for st, m in zip(steps, models))
     pk, src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    achieved = OPS_PER_LINE_STEP * line_steps / (fs_ms * 1e-3) / 1e12
+    achieved = (OPS_PER_LINE_STEP * line_steps + OPS_PER_BIN_STEP * bin_steps) / (fs_ms * 1e-3) / 1e12
     n_sms, peak = issue_roof(sm_max)
     npts = np.array([m.n_points for m in models])
     print(json.dumps({
@@ -677,13 +699,16 @@ def run_batch(args):
                    "l2": "inputs larger than L2 (ray records of all models)"},
         "batch_layout": {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in lay.items() if k != "order"},
         "autotune": tuned,
-        "roofline": {"bound": "alu", "kernel": "k_fs_batch<float,31> (persistent, all models)",
+        "roofline": {"bound": "alu", "kernel": "k_fs_batch<float,30/14> (persistent, all models, two-row elimination)",
                      "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": f"{src} SM clock: issue roof {n_sms} SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz",
-                     "line_steps_per_launch": line_steps, "launch_ms": fs_ms,
-                     "launch_ms_source": "CUDA events around mgt_batch_formal_solve (line data + formal solution)",
+                     "line_steps_per_launch": line_steps, "bin_steps_per_launch": bin_steps,
+                     "ops_per_line_step": OPS_PER_LINE_STEP, "ops_per_bin_step": OPS_PER_BIN_STEP, "launch_ms": fs_ms,
+                     "launch_ms_source": "CUDA events around each persistent formal-solve launch (library kernel "
+                                         "timer); the whole mgt_batch_formal_solve call with line data: "
+                                         f"{fs_call_ms:.1f} ms",
                      "share_of_step": fs_ms / ms},
-        "one_launch_per_model": {"formal_solve_ms": seq_ms, "batch_speedup": seq_ms / fs_ms,
+        "one_launch_per_model": {"formal_solve_ms": seq_ms, "batch_speedup": seq_ms / fs_call_ms,
                                  "note": "mgt_formal_solve per model in turn (line data where stale + staged "
                                          "kernel), same schedules"},
         "gpu_launches": launches, "clocks": clk,

@@ -1378,16 +1378,22 @@ mgt_status fs_batch_launch(const void *d_args, const int64_t *d_item_end, int n_
     FSBatchArgs b{static_cast<const FSArgs *>(d_args), d_item_end, n_models, n_items, d_next};
     MGT_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), s));
     const int64_t g = std::min<int64_t>(grid, n_items);
-    if (bd == 32)
-        k_fs_batch<float, kChunkNarrow><<<(unsigned)g, bd, smem, s>>>(b);
-    else
-        k_fs_batch<float, kChunk><<<(unsigned)g, bd, smem, s>>>(b);
+    {
+        MGT_KTIMER("k_fs_batch", s);
+        if (bd == 32)
+            k_fs_batch<float, kChunkNarrow><<<(unsigned)g, bd, smem, s>>>(b);
+        else
+            k_fs_batch<float, kChunk><<<(unsigned)g, bd, smem, s>>>(b);
+    }
     MGT_LAUNCH_CHECK("k_fs_batch");
     // the items of models outside the two-row range (returns at once without)
-    if (bd == 32)
-        k_fs_batch_exact<float, kChunkNarrow><<<(unsigned)g, bd, smem, s>>>(b);
-    else
-        k_fs_batch_exact<float, kChunk><<<(unsigned)g, bd, smem, s>>>(b);
+    {
+        MGT_KTIMER("k_fs_batch_exact", s);
+        if (bd == 32)
+            k_fs_batch_exact<float, kChunkNarrow><<<(unsigned)g, bd, smem, s>>>(b);
+        else
+            k_fs_batch_exact<float, kChunk><<<(unsigned)g, bd, smem, s>>>(b);
+    }
     MGT_LAUNCH_CHECK("k_fs_batch_exact");
     return MGT_OK;
 }

@@ -273,6 +273,10 @@ __device__ __forceinline__ void line_data_point(const LDArgs &d, int64_t p, int 
     float *__restrict__ r32 = d.out32 + p * RS;
     double *__restrict__ r64 = d.out64 ? d.out64 + p * RS64 : nullptr;
     float chi_max = 0.0f, S_max = 0.0f;
+    // h L_unit / (4 pi sqrt(pi) w): one FP64 division per point (lane 0), not per line
+    double cw = 0.0;
+    if (lane == 0) cw = kH * d.Lunit / (4.0 * kPi * kSqrtPi * d.w64[p]);
+    cw = __shfl_sync(0xffffffffu, cw, 0);
     for (int k = lane; k < Mpad; k += 32) {
         double a0 = 0.0, a1 = 0.0;
         if (k < d.M) {
@@ -288,7 +292,7 @@ __device__ __forceinline__ void line_data_point(const LDArgs &d, int64_t p, int 
                 atomicAdd(d.n_floor, 1ULL);
             }
             if (net > 0.0) {
-                a0 = kH * net * d.Lunit / (4.0 * kPi * kSqrtPi * d.w64[p]);
+                a0 = net * cw;
                 a1 = b / (net * nbgmax);
             }
         }
@@ -548,11 +552,16 @@ __device__ __forceinline__ void write_step_records(const WalkArgs &a, int64_t o,
     out[sl] = make_int4((int)c, __float_as_int(dxs), __float_as_int(beta), __float_as_int(dbeta / wbar));
 }
 
-__device__ __forceinline__ float group16_min(float v)
+// Minimum over the calling lane's 16-lane group of a non-negative float: two
+// whole-warp integer min-reductions (non-negative floats order like their bit
+// patterns), each lane keeping its own group's.  One reduction instruction per
+// group instead of four dependent shuffle-and-min steps.
+__device__ __forceinline__ float group16_min_nonneg(float v, int grp)
 {
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+    const unsigned k = __float_as_uint(v);
+    const unsigned k0 = __reduce_min_sync(0xffffffffu, grp == 0 ? k : 0xffffffffu);
+    const unsigned k1 = __reduce_min_sync(0xffffffffu, grp == 1 ? k : 0xffffffffu);
+    return __uint_as_float(grp ? k1 : k0);
 }
 
 // ---------------------------------------------------------------------------
@@ -765,7 +774,7 @@ __global__ void __launch_bounds__(kWalkThreads, 8) k_walk(WalkArgs a, int64_t *_
             // (the ballot must run in every lane: no short-circuit around it)
             const bool und_grp = (__ballot_sync(full, und) & gmask) != 0u;
             undecided = undecided || und_grp;
-            const float m = group16_min(cand ? d2 : 3.0e38f);
+            const float m = group16_min_nonneg(cand ? d2 : 3.0e38f, grp);
             const unsigned wins = (__ballot_sync(full, cand && d2 == m) & gmask) >> (16 * grp);
             const int wl = wins ? __ffs(wins) - 1 : sl;
             const int src = 16 * grp + wl;
@@ -773,7 +782,9 @@ __global__ void __launch_bounds__(kWalkThreads, 8) k_walk(WalkArgs a, int64_t *_
             const float cZ = __shfl_sync(full, Z, src), ceZ = __shfl_sync(full, eZ, src);
             const uint32_t cword = __shfl_sync(full, word, src);
             const int32_t coff = __shfl_sync(full, eoff, src);
-            const float oL = group16_min((cand && sl != wl) ? Lo : 3.0e38f);
+            // (a negative lower bound counts as 0: the test below compares it
+            // with an upper bound >= 0, so either way the step is not accepted)
+            const float oL = group16_min_nonneg((cand && sl != wl) ? fmaxf(Lo, 0.0f) : 3.0e38f, grp);
             if (wins) {
                 if (!have || m < bd2) {
                     if (have) minLother = fminf(minLother, bL);
@@ -827,8 +838,10 @@ __global__ void __launch_bounds__(kWalkThreads, 8) k_walk(WalkArgs a, int64_t *_
             }
             v = walk_next_exact(a, c, xo, yo, zo, n0, n1, n2, Zc64, &Zn);
         }
-        v = __shfl_sync(full, v, 16 * grp);
-        Zn = __shfl_sync(full, Zn, 16 * grp);
+        if (__any_sync(full, exact)) {          // (rare) the FP64 result of lane 0 to its group
+            v = __shfl_sync(full, v, 16 * grp);
+            Zn = __shfl_sync(full, Zn, 16 * grp);
+        }
         int64_t nx = -1;
         bool nx_bnd = false;
         if (!done) {
