@@ -145,15 +145,27 @@ __device__ __forceinline__ void se_point(const SEArgs &a, int64_t p, double *sm,
         }
         __syncwarp();
     }
+    // back substitution n_k = sum_{i<k} n_i R_ik / S_k, column by column: lane
+    // j keeps the running sums of levels j and j + 32, and once n_{k-1} is
+    // known every lane adds its term to the levels above it (one FP64
+    // multiply-add per lane and level instead of a warp sum per level)
+    double acc0 = 0.0, acc1 = 0.0;
     if (lane == 0) xx[0] = 1.0;
-    __syncwarp();
-    for (int n = 1; n < L; ++n) {
-        double part = 0.0;
-        for (int i = lane; i < n; i += 32) part += xx[i] * R[i * L + n];
-        const double v = warp_sum_first(part, n);
-        if (lane == 0) xx[n] = v * Sn[n];
-        __syncwarp();
+    double xprev = 1.0;                   // n_0
+    for (int k = 1; k < L; ++k) {
+        const int i = k - 1;              // n_i is known: add n_i R_ij to every level j > i
+        if (lane > i && lane < L) acc0 += xprev * R[i * L + lane];
+        if (lane + 32 > i && lane + 32 < L) acc1 += xprev * R[i * L + lane + 32];
+        // n_k = acc[k] / S_k from the lane that holds level k
+        const double a = k < 32 ? acc0 : acc1;
+        double nk = 0.0;
+        if ((k & 31) == lane) {
+            nk = a * Sn[k];
+            xx[k] = nk;
+        }
+        xprev = __shfl_sync(0xffffffffu, nk, k & 31);
     }
+    __syncwarp();
     double part = 0.0;
     for (int i = lane; i < L; i += 32) part += xx[i];
     const double tot = warp_sum(part);
