@@ -379,7 +379,7 @@ def run_mine(args, model, cfg, emit=True, n_error_origins=None, min_warmup=3):
         ms = allreduce_max(world, ms)
         value = world * units / (ms * 1e-3)
         per = lambda *names: sum(kt[n]["total_ms"] for n in names if n in kt) / args.steps
-        fs_ms = per("k_fs_staged<f32>", "k_fs_exact", "k_fs_gather<f32>")
+        fs_ms = per("k_fs_staged<f32>", "k_fs_fused<f32>", "k_fs_exact", "k_fs_gather<f32>")
         walk_names = ("k_walk<fused>", "k_walk<list>", "k_walk_compact")
         trace_ms = per(*walk_names)
         se_ms = per("k_se")
@@ -419,9 +419,17 @@ def run_mine(args, model, cfg, emit=True, n_error_origins=None, min_warmup=3):
     bin_steps = tst["total_steps"] * model.n_quad
     ops = OPS_PER_LINE_STEP * line_steps + OPS_PER_BIN_STEP * bin_steps
     achieved = ops / (fs_ms * 1e-3) / 1e12
+    # the staged kernel the automatic schedule ran: 4 lines per thread up to 4
+    # lines, else 8; per-thread coefficients when the lines fit one group
+    lpt = 4 if model.lines.n_lines <= 4 else 8
+    fused = "k_fs_fused<f32>" in kt
+    kname = f"k_fs_staged<float,{lpt},30,2,true,{'true' if fused else 'false'}>"
     tr = traffic_record()
+    if tr and not tr["kernel"].startswith(kname):
+        tr = None                       # the capture is of another instance
     out["roofline"] = {
-        "bound": "alu", "kernel": "k_fs_staged<float,8,30,2,true> (formal solution + J-bar/Lambda* reduction, two-row elimination)",
+        "bound": "alu", "kernel": kname + " (formal solution + J-bar/Lambda* reduction, two-row elimination"
+                                          + (", per-thread coefficients)" if fused else ")"),
         "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak,
         "traffic": (tr["dram_bytes_per_traced_step"] * tst["total_steps"] if tr else None),
         "traffic_source": (tr["source"] if tr else None),
@@ -630,7 +638,7 @@ def run_batch(args):
             tuned[f"L{key[0]}-R{key[1]}"] = {"lines_per_thread": r["lines_per_thread"], "model_points":
                                              models[rep].n_points, "ms": {f"lpt{l}": t for _, l, t in r["tried"]}}
             for i in idx:
-                mgt.mgt_set_solve_opts(hs[i], lines_per_thread=r["lines_per_thread"], schedule=2)
+                mgt.mgt_set_solve_opts(hs[i], lines_per_thread=r["lines_per_thread"], schedule=0)
         b = mgt.mgt_batch_create(hs, stream=stream)
         lay = mgt.mgt_batch_get_layout(b)
 
@@ -667,8 +675,9 @@ def run_batch(args):
         bkt = mgt.mgt_kernel_times()
         mgt.mgt_kernel_timing(False)
         fs_kernel_ms = sum(bkt[k]["total_ms"] for k in ("k_fs_batch", "k_fs_batch_exact") if k in bkt) / reps
-        # the same formal solutions as one launch per model (schedule 2, the
-        # tuned lines per thread), for comparison with the persistent launch
+        # the same formal solutions as one launch per model (the automatic
+        # staged schedule the batch also takes, the tuned lines per thread),
+        # for comparison with the persistent launches
         a, c = ev(), ev()
         a.record(stream)
         for h in hs:

@@ -105,10 +105,15 @@ typedef struct {
     int32_t width_mode;       /* dnu_bar of a segment: 0 = from the averaged temperature
                                  and turbulence (default), 1 = mean of the endpoint widths */
     int32_t lines_per_thread; /* FP32 kernel schedule: 0 = auto, else 4 or 8 */
-    int32_t schedule;         /* formal-solve kernel: 0 = auto (currently 2), 1 = per-thread
-                                 gathers from global memory, 2 = bulk-copy staging of ray chunks
-                                 in shared memory (registers capped for two blocks per SM),
-                                 3 = staging with one block per SM */
+    int32_t schedule;         /* formal-solve kernel: 0 = auto (4 where it applies, else 2),
+                                 1 = per-thread gathers from global memory, 2 = bulk-copy staging
+                                 of ray chunks in shared memory, the segment coefficients of a
+                                 chunk computed once per bin in shared memory (registers capped
+                                 for two blocks per SM), 3 = as 2 with one block per SM, 4 = as 2
+                                 with each thread computing its own bin's coefficients in
+                                 registers (only when the lines fit one group: lines <=
+                                 lines_per_thread; MGT_ERR_ARG otherwise).  All staged schedules
+                                 give bit-identical results */
     int32_t subdivisions;     /* 0 = the switch rule above (default); n = 1..256: every segment's
                                  optical depth by the trapezoidal rule over n equal pieces with
                                  chi^{ij}, the width and the comoving offset interpolated linearly
@@ -402,9 +407,10 @@ mgt_status mgt_ng_extrapolate_noalloc(int32_t n_iterates, const double *iterates
 
 /*
  * Schedule autotuner.  Times the formal solution of model m in precision p
- * with every candidate (schedule, lines_per_thread) -- schedules 1, 2, 3 (only
- * 2, the schedule of batched launches, when staged_only != 0) times 4 or 8
- * lines per thread (FP32-mixed; 4 only in FP64) -- as the median of `reps`
+ * with every candidate (schedule, lines_per_thread) -- schedules 1, 2, 3, and 4
+ * where the lines fit one group (only 0, the automatic staged choice that
+ * batched launches make, when staged_only != 0) times 4 or 8 lines per thread
+ * (FP32-mixed; 4 only in FP64) -- as the median of `reps`
  * (1..100) launches after one warm-up, with CUDA events on `stream`, and sets
  * the fastest in the model's options.  Needs mgt_trace_rays and every ray
  * pair resident (pairs_per_batch = 0); overwrites the model's J-bar and
@@ -444,10 +450,11 @@ mgt_status mgt_autotune(mgt_model *m, mgt_precision p, int32_t staged_only, int3
  * mgt_batch_formal_solve: line data of every model from its current
  * populations, then J-bar and Lambda* of every model (the values of
  * mgt_formal_solve in FP32-mixed with schedule 2 and the model's lines per
- * thread) in one persistent launch per CTA width (bins x line groups of one
- * origin, rounded to warps; models of one width share a launch): CTAs take
- * (model, origin, line block) items from a counter, models with the most work
- * per item first.
+ * thread) in one persistent launch per class of models (one CTA width -- bins
+ * x line groups of one origin, rounded to warps -- and, within it, models
+ * whose lines fit one group, which run schedule 4's per-thread coefficients,
+ * apart from the rest): CTAs take (model, origin, line block) items from a
+ * counter, models with the most work per item first.
  * mgt_batch_stat_equilibrium: the statistical equilibrium of every point of
  * every model in one launch (the values of mgt_stat_equilibrium).
  * mgt_batch_iterate: n_iter ALI iterations of every model.  The first call
@@ -472,7 +479,7 @@ typedef struct {
     int64_t se_blocks;         /* CTAs of the statistical-equilibrium launch */
     int32_t graph_kernels;     /* kernels per replay of the captured iteration (0 before the
                                   first mgt_batch_iterate) */
-    int32_t fs_launches;       /* persistent formal-solution launches (one per CTA width) */
+    int32_t fs_launches;       /* persistent formal-solution launches (one per class of models) */
 } mgt_batch_layout;
 mgt_status mgt_batch_create(mgt_batch **out, mgt_model *const *models, int32_t n_models, void *stream);
 mgt_status mgt_batch_destroy(mgt_batch *b);

@@ -643,7 +643,7 @@ mgt_status mgt_set_solve_opts(mgt_model *m, const mgt_solve_opts *o)
     if (!m) return set_error(MGT_ERR_ARG, "model is NULL");
     mgt_solve_opts d{0.35, 0, 0, 0, 0, 0};
     if (o) {
-        if (o->schedule < 0 || o->schedule > 3) return set_error(MGT_ERR_ARG, "schedule must be 0..3");
+        if (o->schedule < 0 || o->schedule > 4) return set_error(MGT_ERR_ARG, "schedule must be 0..4");
         if (o->subdivisions < 0 || o->subdivisions > 256) return set_error(MGT_ERR_ARG, "subdivisions must be 0..256");
         if (o->pairs_per_batch < 0) return set_error(MGT_ERR_ARG, "pairs_per_batch must be >= 0");
         if (!(o->switch_threshold >= 0.0) || !std::isfinite(o->switch_threshold))

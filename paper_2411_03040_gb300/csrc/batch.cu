@@ -27,15 +27,15 @@ struct mgt_batch {
     std::vector<int32_t> order;            // table slot -> caller index (most work per item first)
     // host copies of the argument tables, in table order
     std::vector<unsigned char> fs_args, se_args, ld_args;
-    std::vector<int64_t> fs_end, se_end, ld_end;   // fs_end restarts at each width class
+    std::vector<int64_t> fs_end, se_end, ld_end;   // fs_end restarts at each class
     struct FsClass {
-        int threads = 0, grid = 0, first = 0, count = 0;
+        int threads = 0, fused = 0, lines = 0, grid = 0, first = 0, count = 0;
         size_t smem = 0;
         int64_t items = 0;
         bool operator==(const FsClass &o) const
         {
-            return threads == o.threads && grid == o.grid && first == o.first && count == o.count &&
-                   smem == o.smem && items == o.items;
+            return threads == o.threads && fused == o.fused && lines == o.lines && grid == o.grid &&
+                   first == o.first && count == o.count && smem == o.smem && items == o.items;
         }
     };
     std::vector<FsClass> fs_classes;               // in launch order, widest first
@@ -43,7 +43,7 @@ struct mgt_batch {
     // device copies
     unsigned char *d_fs_args = nullptr, *d_se_args = nullptr, *d_ld_args = nullptr;
     int64_t *d_fs_end = nullptr, *d_se_end = nullptr, *d_ld_end = nullptr;
-    unsigned long long *d_next = nullptr;          // one item counter per width class
+    unsigned long long *d_next = nullptr;          // one item counter per class
     int *h_err = nullptr;                          // pinned [n_models][4]: the models' device error words
     // the captured iteration
     cudaStream_t cap = nullptr;
@@ -98,18 +98,23 @@ mgt_status refresh(mgt_batch *b, cudaStream_t s)
     const size_t fsz = fs_args_bytes(), ssz = se_args_bytes(), lsz = ld_args_bytes();
     // each model's formal-solution arguments, CTA width and items (caller's order)
     std::vector<unsigned char> fa_c(fsz * n);
-    std::vector<int> width(n);
+    std::vector<int> width(n), fused(n), lines(n);
     std::vector<int64_t> items(n);
     std::vector<double> cost(n);
     for (int i = 0; i < n; ++i) {
-        MGT_TRY_STATUS(fs_batch_args(b->models[i], fa_c.data() + i * fsz, &width[i], &items[i]));
+        MGT_TRY_STATUS(
+            fs_batch_args(b->models[i], fa_c.data() + i * fsz, &width[i], &items[i], &fused[i], &lines[i]));
         cost[i] = item_cost(b->models[i]);
     }
-    // order: widest CTAs first, then most work per item, ties by caller index
+    // order: widest CTAs first, unfused before fused at one width, 8 lines per
+    // thread before 4, then most work per item, ties by caller index
     std::vector<int32_t> order(n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-        return width[x] != width[y] ? width[x] > width[y] : cost[x] > cost[y];
+        if (width[x] != width[y]) return width[x] > width[y];
+        if (fused[x] != fused[y]) return fused[x] < fused[y];
+        if (lines[x] != lines[y]) return lines[x] > lines[y];
+        return cost[x] > cost[y];
     });
 
     std::vector<unsigned char> fa(fsz * n), sa(ssz * n), la(lsz * n);
@@ -121,9 +126,12 @@ mgt_status refresh(mgt_batch *b, cudaStream_t s)
         const int i = order[k];
         const mgt_model *m = b->models[i];
         std::memcpy(fa.data() + k * fsz, fa_c.data() + i * fsz, fsz);
-        if (classes.empty() || classes.back().threads != width[i]) {
+        if (classes.empty() || classes.back().threads != width[i] || classes.back().fused != fused[i] ||
+            classes.back().lines != lines[i]) {
             classes.emplace_back();
             classes.back().threads = width[i];
+            classes.back().fused = fused[i];
+            classes.back().lines = lines[i];
             classes.back().first = k;
             fi = 0;
         }
@@ -142,17 +150,17 @@ mgt_status refresh(mgt_batch *b, cudaStream_t s)
     }
     if (li > 0x7fffffffLL || si > 0x7fffffffLL)
         return set_error(MGT_ERR_ARG, "batch: too many points for one launch");
-    // one-warp CTAs run another instance of the kernel (shorter chunks): the
-    // shared-memory limit is set per instance, to its largest class
-    size_t max_narrow = 0, max_wide = 0;
-    for (const mgt_batch::FsClass &c : classes) {
-        size_t &mx = c.threads == 32 ? max_narrow : max_wide;
-        mx = std::max(mx, c.smem);
-    }
-    if (std::max(max_narrow, max_wide) > 227 * 1024)
-        return set_error(MGT_ERR_ARG, "batch: formal-solution shared memory above 227 KB");
+    // each (chunk length, fused, lines per thread) runs its own instance of the
+    // kernel: the shared-memory limit is set per instance, to its largest class
+    auto instance = [](const mgt_batch::FsClass &c) {
+        return ((c.threads == 32 && !c.fused) ? 4 : 0) + (c.fused ? 2 : 0) + (c.lines == 8 ? 1 : 0);
+    };
+    size_t max_smem[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (const mgt_batch::FsClass &c : classes) max_smem[instance(c)] = std::max(max_smem[instance(c)], c.smem);
+    for (const mgt_batch::FsClass &c : classes)
+        if (c.smem > 227 * 1024) return set_error(MGT_ERR_ARG, "batch: formal-solution shared memory above 227 KB");
     for (mgt_batch::FsClass &c : classes)
-        MGT_TRY_STATUS(fs_batch_grid(c.threads, c.smem, c.threads == 32 ? max_narrow : max_wide, &c.grid));
+        MGT_TRY_STATUS(fs_batch_grid(c.threads, c.fused, c.lines, c.smem, max_smem[instance(c)], &c.grid));
 
     const bool same = order == b->order && fa == b->fs_args && sa == b->se_args && la == b->ld_args &&
                       classes == b->fs_classes && se_smem == b->se_smem;
@@ -193,7 +201,7 @@ mgt_status launch_fs(mgt_batch *b, cudaStream_t s)
     for (size_t c = 0; c < b->fs_classes.size(); ++c) {
         const mgt_batch::FsClass &k = b->fs_classes[c];
         MGT_TRY_STATUS(fs_batch_launch(b->d_fs_args + k.first * fsz, b->d_fs_end + k.first, k.count, k.items,
-                                       b->d_next + c, k.threads, k.smem, k.grid, s));
+                                       b->d_next + c, k.threads, k.fused, k.lines, k.smem, k.grid, s));
     }
     return MGT_OK;
 }
@@ -422,10 +430,18 @@ mgt_status mgt_autotune(mgt_model *m, mgt_precision p, int32_t staged_only, int3
     struct Cand {
         int schedule, lpt;
     };
+    // staged_only: the automatic staged choice (0), which batched launches run;
+    // otherwise schedules 1-3, and 4 where the lines fit one group
     std::vector<Cand> cands;
-    for (int sch = staged_only ? 2 : 1; sch <= (staged_only ? 2 : 3); ++sch)
-        for (int lpt : {4, 8})
-            if (p == MGT_FP32_MIXED || lpt == 4) cands.push_back({sch, lpt});
+    const int lpts[2] = {4, 8};
+    if (staged_only) {
+        for (int lpt : lpts)
+            if (p == MGT_FP32_MIXED || lpt == 4) cands.push_back({0, lpt});
+    } else {
+        for (int sch = 1; sch <= 4; ++sch)
+            for (int lpt : lpts)
+                if ((p == MGT_FP32_MIXED || lpt == 4) && (sch < 4 || m->M <= lpt)) cands.push_back({sch, lpt});
+    }
     const mgt_solve_opts saved = m->opts;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     MGT_CUDA(cudaEventCreate(&e0));

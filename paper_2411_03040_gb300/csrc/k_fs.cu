@@ -62,8 +62,13 @@ template <> struct Prec<float> {
         asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
         return r;
     }
-    static __device__ __forceinline__ float gauss(float u) { return __expf(-u * u); }
+    static __device__ __forceinline__ float gauss(float u) { return __expf(-__fmul_rn(u, u)); }
     static __device__ __forceinline__ float erfc_(float x) { return mgt::erfc_fit(x); }
+    // explicitly rounded operations (never contracted differently by context)
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
     static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
     static __device__ __forceinline__ float bg(float f, float hk) { return f * f * f / expm1f(hk * f); }
 };
@@ -71,11 +76,21 @@ template <> struct Prec<float> {
 template <> struct Prec<double> {
     using V2 = double2;
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-    static __device__ __forceinline__ double gauss(double u) { return exp(-u * u); }
+    static __device__ __forceinline__ double gauss(double u) { return exp(-__dmul_rn(u, u)); }
     static __device__ __forceinline__ double erfc_(double x) { return erfc(x); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
     static __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
     static __device__ __forceinline__ double bg(double f, double hk) { return f * f * f / expm1(hk * f); }
 };
+
+// A bin's comoving offset z = Aq + Bq beta at a point (beta its velocity
+// projection), and the point's Gaussian exp(-(z/w)^2) from its 1/w, with
+// explicit roundings, so that every schedule computes them identically.
+template <typename T> __device__ __forceinline__ T bin_z(T Aq, T Bq, T beta) { return Prec<T>::fma(Bq, beta, Aq); }
+template <typename T> __device__ __forceinline__ T point_gauss(T z, T rw) { return Prec<T>::gauss(Prec<T>::mul(z, rw)); }
 
 struct FSArgs {
     int64_t N;
@@ -96,6 +111,7 @@ struct FSArgs {
     int accumulate;            // add to J / Lstar (later pair batches) instead of writing them
     int lpt;                   // lines per thread of the staged schedule (batched launches)
     int nblk;                  // line blocks per origin (ceil(Gtot / Gb))
+    int fused;                 // staged schedule with each thread's coefficients in registers (Gtot == 1)
     double *J, *Lst;           // [N][M]
     int *err;
     const int *range_bad;      // nonzero: a point's range figure exceeds 1 (set by the line data)
@@ -195,22 +211,24 @@ template <typename T>
 __device__ __forceinline__ void segment_coefs(bool trap, T dx, T du, T z_f, T g_f, T w_f, T g_n, T w_n, int width_mode,
                                               T &cf, T &cn)
 {
+    using P = Prec<T>;
     if (trap) {
-        cf = T(0.25) * dx * g_f;
-        cn = T(0.25) * dx * g_n;
+        const T q = P::mul(T(0.25), dx);
+        cf = P::mul(q, g_f);
+        cn = P::mul(q, g_n);
     } else {
-        const T iwbar = width_mode == 0 ? Prec<T>::rsqrt_(T(0.5) * (w_f * w_f + w_n * w_n))
-                                        : Prec<T>::rcp(T(0.5) * (w_f + w_n));
-        T a = z_f * iwbar, b = a + du;
-        if (a + b < T(0)) {
+        const T iwbar = width_mode == 0 ? P::rsqrt_(P::mul(T(0.5), P::fma(w_f, w_f, P::mul(w_n, w_n))))
+                                        : P::rcp(P::mul(T(0.5), P::add(w_f, w_n)));
+        T a = P::mul(z_f, iwbar), b = P::add(a, du);
+        if (P::add(a, b) < T(0)) {
             const T t = a;
             a = -b;
             b = -t;
         }
-        const T E = Prec<T>::erfc_(a) - Prec<T>::erfc_(b);
-        const T kk = dx * T(0.125 * kSqrtPi) * E * iwbar * Prec<T>::rcp(du);
-        cf = kk * w_f;
-        cn = kk * w_n;
+        const T E = P::sub(P::erfc_(a), P::erfc_(b));
+        const T kk = P::mul(P::mul(P::mul(P::mul(dx, T(0.125 * kSqrtPi)), E), iwbar), P::rcp(du));
+        cf = P::mul(kk, w_f);
+        cn = P::mul(kk, w_n);
     }
 }
 
@@ -221,18 +239,20 @@ __device__ __forceinline__ void segment_coefs(bool trap, T dx, T du, T z_f, T g_
 template <typename T>
 __device__ __forceinline__ void subdiv_coefs(int n, T dx, T z_f, T w_f, T z_n, T w_n, T &cf, T &cn)
 {
+    using P = Prec<T>;
     T sf = T(0), sn = T(0);
     const T inv_n = T(1) / T(n);
     for (int k = 0; k <= n; ++k) {
-        const T x = T(k) * inv_n;
-        const T z = z_f + x * (z_n - z_f), w = w_f + x * (w_n - w_f);
+        const T x = P::mul(T(k), inv_n);
+        const T z = P::fma(x, P::sub(z_n, z_f), z_f), w = P::fma(x, P::sub(w_n, w_f), w_f);
         const T u = z / w;
-        const T g = Prec<T>::gauss(u) / w * ((k == 0 || k == n) ? T(0.5) : T(1));
-        sf += (T(1) - x) * g;
-        sn += x * g;
+        const T g = P::mul(P::gauss(u) / w, (k == 0 || k == n) ? T(0.5) : T(1));
+        sf = P::fma(P::sub(T(1), x), g, sf);
+        sn = P::fma(x, g, sn);
     }
-    cf = T(0.5) * dx * inv_n * w_f * sf;
-    cn = T(0.5) * dx * inv_n * w_n * sn;
+    const T c = P::mul(P::mul(P::mul(T(0.5), dx), inv_n), w_f);
+    cf = P::mul(c, sf);
+    cn = P::mul(P::mul(P::mul(P::mul(T(0.5), dx), inv_n), w_n), sn);
 }
 
 // One elimination row for the thread's LPT lines, in the halved variables:
@@ -242,14 +262,15 @@ template <typename T, int LPT>
 __device__ __forceinline__ void eliminate_row_scalar(T cf, T cn, const T (&chi_f)[LPT], const T (&S_f)[LPT],
                                                      const T (&chi_n)[LPT], T (&P)[LPT], T (&Y)[LPT], T (&aa)[LPT])
 {
+    using Op = Prec<T>;
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
-        const T b = cf * chi_f[l] + cn * chi_n[l];     // beta, half the segment depth
-        const T h = aa[l] + b;
-        const T G = T(2) * h + P[l];
-        const T q = Prec<T>::rcp(b * G + T(1));
-        P[l] = G * q;
-        Y[l] = (S_f[l] * h + Y[l]) * q;
+        const T b = Op::fma(cf, chi_f[l], Op::mul(cn, chi_n[l]));   // beta, half the segment depth
+        const T h = Op::add(aa[l], b);
+        const T G = Op::fma(T(2), h, P[l]);
+        const T q = Op::rcp(Op::fma(b, G, T(1)));
+        P[l] = Op::mul(G, q);
+        Y[l] = Op::mul(Op::fma(S_f[l], h, Y[l]), q);
         aa[l] = b;
     }
 }
@@ -507,8 +528,8 @@ __device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, 
     load_vec<LPT>(line + c_f * a.RS + line0, chi_f);
     load_vec<LPT>(line + c_f * a.RS + a.Mpad + line0, S_f);
     T w_f = line[c_f * a.RS + 2 * a.Mpad];
-    T z_f = Aq + Bq * sf.beta;
-    T g_f = Prec<T>::gauss(z_f * line[c_f * a.RS + 2 * a.Mpad + 1]);
+    T z_f = bin_z<T>(Aq, Bq, sf.beta);
+    T g_f = point_gauss<T>(z_f, line[c_f * a.RS + 2 * a.Mpad + 1]);
     for (int k = n; k >= 1; --k) {
         int64_t c_n = o;
         StepG<T> sn{T(0), T(0), T(0)};
@@ -521,9 +542,9 @@ __device__ __forceinline__ void sweep_gather(const FSArgs &a, int64_t o, int r, 
         load_vec<LPT>(row + line0, chi_n);
         load_vec<LPT>(row + a.Mpad + line0, S_n);
         const T w_n = row[2 * a.Mpad];
-        const T z_n = Aq + Bq * sn.beta;
-        const T g_n = Prec<T>::gauss(z_n * row[2 * a.Mpad + 1]);
-        const T du = -Bq * sf.dbw;
+        const T z_n = bin_z<T>(Aq, Bq, sn.beta);
+        const T g_n = point_gauss<T>(z_n, row[2 * a.Mpad + 1]);
+        const T du = -Prec<T>::mul(Bq, sf.dbw);
         bool trap = fabs(du) < thr;
         if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(kSwitchBand) * thr) trap = trapezoid_fp64(a, r, c_f, c_n, xq64, wo64);
         T cf, cn;
@@ -747,7 +768,7 @@ struct StagedLayout {
 // Staging buffers [2] and coefficient buffers [2] are contiguous; the final
 // FP64 reduction area aliases them once the last chunk is done.
 template <typename T, int LPT, int CH>
-__host__ __device__ inline StagedLayout staged_layout(int Q, int Mb, int RS, int bd, int P)
+__host__ __device__ inline StagedLayout staged_layout(int Q, int Mb, int RS, int bd, int P, bool fused)
 {
     constexpr int SB = sizeof(T) == 4 ? 16 : 32;
     constexpr int NPT = CH + 1;
@@ -755,7 +776,7 @@ __host__ __device__ inline StagedLayout staged_layout(int Q, int Mb, int RS, int
     StagedLayout L;
     const int rowB = RS * (int)sizeof(T);
     const int stage_bytes = 2 * NPT * (SB + rowB);
-    const int coef_bytes = 2 * CH * Q * 2 * (int)sizeof(T);
+    const int coef_bytes = fused ? 0 : 2 * CH * Q * 2 * (int)sizeof(T);
     const int red_bytes = 2 * Mb * Q * (int)sizeof(double);
     L.stage = 128;
     L.coef = L.stage + up(stage_bytes);
@@ -767,6 +788,42 @@ __host__ __device__ inline StagedLayout staged_layout(int Q, int Mb, int RS, int
     L.ext = L.half0 + up(3 * LPT * bd * (int)sizeof(T));
     L.total = L.ext + 2 * P * 16;
     return L;
+}
+
+// Halved {cf, cn} of step k (far point in staged slot jf = k - k_lo + 1, near
+// point in slot jf - 1) for the bin with offsets Aq, Bq: z_f = Aq + Bq beta_far;
+// gpair() gives the Gaussians {g_f, g_n} of the two points, which only the
+// trapezoid uses.  One function for every schedule, so that all of them
+// compute bit-identical coefficients.
+template <typename T, typename GP>
+__device__ __forceinline__ typename Prec<T>::V2 segment_item(const FSArgs &a, int64_t o, int r, int k, int q,
+                                                             const unsigned char *Sb, const T *Rb, int jf, T Aq, T Bq,
+                                                             const StepG<T> &sf, T z_f, GP gpair)
+{
+    using V2 = typename Prec<T>::V2;
+    constexpr int SB = sizeof(T) == 4 ? 16 : 32;
+    const T thr = (T)a.thr;
+    const int jn = jf - 1;
+    const T *rowf = Rb + jf * a.RS, *rown = Rb + jn * a.RS;
+    const T w_f = rowf[2 * a.Mpad], w_n = rown[2 * a.Mpad];
+    const T du = -Prec<T>::mul(Bq, sf.dbw);
+    bool trap = fabs(du) < thr;
+    if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(kSwitchBand) * thr) {
+        const int64_t c_f = reinterpret_cast<const int4 *>(Sb + jf * SB)->x;
+        const int64_t c_n = k > 1 ? (int64_t)reinterpret_cast<const int4 *>(Sb + jn * SB)->x : o;
+        trap = trapezoid_fp64(a, r, c_f, c_n, a.xq[q], a.w64[o]);
+    }
+    T cf, cn;
+    if (a.subdiv > 0) {
+        const T z_n = bin_z<T>(Aq, Bq, k > 1 ? step_from<T>(Sb + jn * SB).beta : T(0));
+        subdiv_coefs<T>(a.subdiv, sf.dx, z_f, w_f, z_n, w_n, cf, cn);
+    } else if (trap) {
+        const V2 g = gpair();
+        segment_coefs<T>(true, sf.dx, du, z_f, g.x, w_f, g.y, w_n, a.width_mode, cf, cn);
+    } else {
+        segment_coefs<T>(false, sf.dx, du, z_f, T(0), w_f, T(0), w_n, a.width_mode, cf, cn);
+    }
+    return V2{cf, cn};
 }
 
 // Line-independent coefficients of every (bin, step) of one chunk, shared by
@@ -783,29 +840,12 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
                                             const unsigned char *Sb, const T *Rb, const T *sA, const T *sB,
                                             typename Prec<T>::V2 *coef, int tid, int bd)
 {
+    using V2 = typename Prec<T>::V2;
     constexpr int SB = sizeof(T) == 4 ? 16 : 32;
-    const T thr = (T)a.thr;
     const int nst = k_hi - k_lo + 1;
-    // one segment's coefficients from its far and near point data
-    auto one = [&](int kk, int q, T Aq, T Bq, T g_n, const StepG<T> &sf, T z_f, T g_f) {
-        const int k = k_lo + kk, jf = kk + 1, jn = kk;
-        const T *rowf = Rb + jf * a.RS, *rown = Rb + jn * a.RS;
-        const T w_f = rowf[2 * a.Mpad], w_n = rown[2 * a.Mpad];
-        const T du = -Bq * sf.dbw;
-        bool trap = fabs(du) < thr;
-        if (sizeof(T) == 4 && fabs(fabs(du) - thr) < T(kSwitchBand) * thr) {
-            const int64_t c_f = reinterpret_cast<const int4 *>(Sb + jf * SB)->x;
-            const int64_t c_n = k > 1 ? (int64_t)reinterpret_cast<const int4 *>(Sb + jn * SB)->x : o;
-            trap = trapezoid_fp64(a, r, c_f, c_n, a.xq[q], a.w64[o]);
-        }
-        T cf, cn;
-        if (a.subdiv > 0) {
-            const T z_n = Aq + Bq * (k > 1 ? step_from<T>(Sb + jn * SB).beta : T(0));
-            subdiv_coefs<T>(a.subdiv, sf.dx, z_f, w_f, z_n, w_n, cf, cn);
-        } else {
-            segment_coefs<T>(trap, sf.dx, du, z_f, g_f, w_f, g_n, w_n, a.width_mode, cf, cn);
-        }
-        coef[kk * a.Q + q] = {cf, cn};
+    // one segment's coefficients into the chunk's buffer
+    auto one = [&](int kk, int q, T Aq, T Bq, const StepG<T> &sf, T z_f, auto gpair) {
+        coef[kk * a.Q + q] = segment_item<T>(a, o, r, k_lo + kk, q, Sb, Rb, kk + 1, Aq, Bq, sf, z_f, gpair);
     };
     if constexpr (CARRY) {
         const int nseg = bd / a.Q;                     // Q <= bd: bins x line groups fit the CTA
@@ -814,36 +854,45 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
         const int kk0 = seg * sps, kk1 = min(nst, kk0 + sps);
         if (seg >= nseg || kk0 >= kk1) return;
         const T Aq = sA[q], Bq = sB[q];
-        T g_n;
-        {
-            const T z_n = Aq + Bq * (k_lo + kk0 > 1 ? step_from<T>(Sb + kk0 * SB).beta : T(0));
-            g_n = Prec<T>::gauss(z_n * Rb[kk0 * a.RS + 2 * a.Mpad + 1]);
-        }
+        T g_n = point_gauss<T>(bin_z<T>(Aq, Bq, k_lo + kk0 > 1 ? step_from<T>(Sb + kk0 * SB).beta : T(0)),
+                               Rb[kk0 * a.RS + 2 * a.Mpad + 1]);
 #pragma unroll 1
         for (int kk = kk0; kk < kk1; ++kk) {
             const StepG<T> sf = step_from<T>(Sb + (kk + 1) * SB);
-            const T z_f = Aq + Bq * sf.beta;
-            const T g_f = Prec<T>::gauss(z_f * Rb[(kk + 1) * a.RS + 2 * a.Mpad + 1]);
-            one(kk, q, Aq, Bq, g_n, sf, z_f, g_f);
+            const T z_f = bin_z<T>(Aq, Bq, sf.beta);
+            const T g_f = point_gauss<T>(z_f, Rb[(kk + 1) * a.RS + 2 * a.Mpad + 1]);
+            one(kk, q, Aq, Bq, sf, z_f, [&] { return V2{g_f, g_n}; });
             g_n = g_f;
         }
     } else {
         // warp 0 issues the bulk copies after the barrier: in a wide CTA it
         // takes no items, and the last threads take the extra items of an
         // uneven split
+        // item it = kk Q + q; the stride advances (kk, q) by (dk, dq)
+        // without a division per item
         const int items = a.Q * nst;
         const int pw = bd >= 128 ? 32 : 0;
+        const int stride = bd - pw;
+        const int dk = stride / a.Q, dq = stride - dk * a.Q;
+        const int it0 = tid >= pw ? bd - 1 - tid : items;
+        int kk = it0 / a.Q, q = it0 - kk * a.Q;
 #pragma unroll 1
-        for (int it = tid >= pw ? bd - 1 - tid : items; it < items; it += bd - pw) {
-            const int kk = it / a.Q, q = it - kk * a.Q;
+        for (int it = it0; it < items; it += stride) {
             const int k = k_lo + kk;
             const StepG<T> sf = step_from<T>(Sb + (kk + 1) * SB);
             const T beta_n = k > 1 ? step_from<T>(Sb + kk * SB).beta : T(0);
             const T Aq = sA[q], Bq = sB[q];
-            const T z_f = Aq + Bq * sf.beta, z_n = Aq + Bq * beta_n;
-            const T g_f = Prec<T>::gauss(z_f * Rb[(kk + 1) * a.RS + 2 * a.Mpad + 1]);
-            const T g_n = Prec<T>::gauss(z_n * Rb[kk * a.RS + 2 * a.Mpad + 1]);
-            one(kk, q, Aq, Bq, g_n, sf, z_f, g_f);
+            const T z_f = bin_z<T>(Aq, Bq, sf.beta);
+            one(kk, q, Aq, Bq, sf, z_f, [&] {
+                return V2{point_gauss<T>(z_f, Rb[(kk + 1) * a.RS + 2 * a.Mpad + 1]),
+                          point_gauss<T>(bin_z<T>(Aq, Bq, beta_n), Rb[kk * a.RS + 2 * a.Mpad + 1])};
+            });
+            kk += dk;
+            q += dq;
+            if (q >= a.Q) {
+                q -= a.Q;
+                ++kk;
+            }
         }
     }
 }
@@ -854,7 +903,7 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
 // consumed so far, so their phases carry over from one item to the next.
 // Returns false if a wait gave up: the error word is set and no copy of this
 // CTA is left in flight.
-template <typename T, int LPT, int CH, bool FAST>
+template <typename T, int LPT, int CH, bool FAST, bool FUSED>
 __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int blk, unsigned char *smem, int &ci)
 {
     using V2 = typename Prec<T>::V2;
@@ -864,7 +913,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rowB = a.RS * (int)sizeof(T);
     const int Mb = a.Gb * LPT;
-    const StagedLayout lay = staged_layout<T, LPT, CH>(a.Q, Mb, a.RS, bd, a.P);
+    const StagedLayout lay = staged_layout<T, LPT, CH>(a.Q, Mb, a.RS, bd, a.P, FUSED);
 
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);                   // [2]
     int *abort_flag = reinterpret_cast<int *>(smem + 16);
@@ -910,6 +959,16 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
     const T wqn = active ? T(a.wq[q]) : T(0);
     bool ok = true;
     T P[LPT], Y[LPT], aa[LPT];
+    // FUSED (one line group: the thread is the only reader of its bin's
+    // coefficients): the bin's offsets, and the Gaussian of the far point of
+    // the next step, carried down the half-ray
+    T Aq = T(0), Bq = T(0), gcar = T(0);
+    if constexpr (FUSED) {
+        if (active) {
+            Aq = sA[q];
+            Bq = sB[q];
+        }
+    }
     for (int p = 0; p < a.P; ++p) {
         const int2 pr = a.pairs[p];
         for (int h = 0; h < 2; ++h) {
@@ -929,7 +988,9 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                 const unsigned char *Sb = steps_s + (ci & 1) * NPT * SB;
                 const T *Rb = reinterpret_cast<const T *>(rows_s + (ci & 1) * NPT * rowB);
                 V2 *cf_buf = coef + (ci & 1) * CH * a.Q;
-                if (ok) chunk_coefs<T, LPT == 4>(a, o, r, k_lo, k_hi, Sb, Rb, sA, sB, cf_buf, tid, bd);
+                if constexpr (!FUSED) {
+                    if (ok) chunk_coefs<T, LPT == 4>(a, o, r, k_lo, k_hi, Sb, Rb, sA, sB, cf_buf, tid, bd);
+                }
                 // one barrier per chunk: this chunk's coefficients are complete, and
                 // everyone is done with the previous chunk (its staging buffer is
                 // refilled next, its coefficient buffer on the following chunk);
@@ -946,7 +1007,64 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                         issue_chunk<T>(a, o, nx, steps_s + ((ci + 1) & 1) * NPT * SB,
                                        rows_s + ((ci + 1) & 1) * NPT * rowB, &bar[(ci + 1) & 1], rowB, lane);
                 }
-                if (active) {
+                if (FUSED && active) {
+                    // the same rows with each step's coefficients computed here
+                    // (segment_item, as the pre-pass does) instead of read
+                    const T *row = Rb + (k_hi - k_lo + 1) * a.RS + line0;
+                    auto coef_of = [&](int k) -> V2 {
+                        const int jf = k - k_lo + 1;
+                        const StepG<T> sf = step_from<T>(Sb + jf * SB);
+                        const T z_f = bin_z<T>(Aq, Bq, sf.beta);
+                        const T z_n = bin_z<T>(Aq, Bq, k > 1 ? step_from<T>(Sb + (jf - 1) * SB).beta : T(0));
+                        const T g_f = gcar;
+                        gcar = point_gauss<T>(z_n, Rb[(jf - 1) * a.RS + 2 * a.Mpad + 1]);
+                        const T g_n = gcar;
+                        return segment_item<T>(a, o, r, k, q, Sb, Rb, jf, Aq, Bq, sf, z_f,
+                                               [&] { return V2{g_f, g_n}; });
+                    };
+                    if (k_hi == n) {                   // the half-ray's far end
+                        const int jf = n - k_lo + 1;
+                        gcar = point_gauss<T>(bin_z<T>(Aq, Bq, step_from<T>(Sb + jf * SB).beta),
+                                              Rb[jf * a.RS + 2 * a.Mpad + 1]);
+                    }
+                    T chiA[LPT], chiB[LPT], S_f[LPT];
+                    load_vec<LPT>(row, chiA);
+                    int k = k_hi;
+                    if constexpr (FAST) {
+                        T D[LPT];
+#pragma unroll 1
+                        for (; k - 1 >= k_lo; k -= 2) {
+                            V2 cc = coef_of(k);
+                            load_vec<LPT>(row + a.Mpad, S_f);
+                            load_vec<LPT>(row - a.RS, chiB);
+                            homog_row1_packed<LPT>(cc.x, cc.y, chiA, S_f, chiB, P, Y, aa, D);
+                            cc = coef_of(k - 1);
+                            load_vec<LPT>(row - a.RS + a.Mpad, S_f);
+                            load_vec<LPT>(row - 2 * a.RS, chiA);
+                            homog_row2_packed<LPT>(cc.x, cc.y, chiB, S_f, chiA, P, Y, aa, D);
+                            row -= 2 * a.RS;
+                        }
+                    } else {
+#pragma unroll 1
+                        for (; k - 1 >= k_lo; k -= 2) {
+                            V2 cc = coef_of(k);
+                            load_vec<LPT>(row + a.Mpad, S_f);
+                            load_vec<LPT>(row - a.RS, chiB);
+                            eliminate_row<T, LPT>(cc.x, cc.y, chiA, S_f, chiB, P, Y, aa);
+                            cc = coef_of(k - 1);
+                            load_vec<LPT>(row - a.RS + a.Mpad, S_f);
+                            load_vec<LPT>(row - 2 * a.RS, chiA);
+                            eliminate_row<T, LPT>(cc.x, cc.y, chiB, S_f, chiA, P, Y, aa);
+                            row -= 2 * a.RS;
+                        }
+                    }
+                    if (k == k_lo) {
+                        const V2 cc = coef_of(k);
+                        load_vec<LPT>(row + a.Mpad, S_f);
+                        load_vec<LPT>(row - a.RS, chiB);
+                        eliminate_row<T, LPT>(cc.x, cc.y, chiA, S_f, chiB, P, Y, aa);
+                    }
+                } else if (!FUSED && active) {
                     // step k reads rows jf = k - k_lo + 1 and jn = jf - 1; the
                     // near row's chi is the next step's far chi, so two steps
                     // per trip swap the two chi arrays instead of reloading
@@ -1069,7 +1187,7 @@ __device__ __forceinline__ void staged_init(unsigned char *smem)
 // which only runs when no point of the model is outside its range (the line
 // data set *range_bad otherwise; every CTA then returns at once and
 // k_fs_exact does the work).
-template <typename T, int LPT, int CH, int MINB, bool FAST>
+template <typename T, int LPT, int CH, int MINB, bool FAST, bool FUSED>
 __global__ void __launch_bounds__(256, MINB) k_fs_staged(FSArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1078,13 +1196,13 @@ __global__ void __launch_bounds__(256, MINB) k_fs_staged(FSArgs a)
     }
     staged_init(smem);
     int ci = 0;
-    fs_staged_item<T, LPT, CH, FAST>(a, (int64_t)blockIdx.x, (int)blockIdx.y, smem, ci);
+    fs_staged_item<T, LPT, CH, FAST, FUSED>(a, (int64_t)blockIdx.x, (int)blockIdx.y, smem, ci);
 }
 
 // The one-row elimination of every item of a model whose range figures
 // exclude the two-row form (*range_bad set), in a persistent grid; launched
 // after the two-row kernel, it returns at once for every other model.
-template <typename T, int LPT, int CH> __global__ void __launch_bounds__(256, 2) k_fs_exact(FSArgs a)
+template <typename T, int LPT, int CH, bool FUSED> __global__ void __launch_bounds__(256, 2) k_fs_exact(FSArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!*a.range_bad) return;
@@ -1093,7 +1211,7 @@ template <typename T, int LPT, int CH> __global__ void __launch_bounds__(256, 2)
     const int64_t items = a.N * a.nblk;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int64_t oi = it / a.nblk;
-        if (!fs_staged_item<T, LPT, CH, false>(a, oi, (int)(it - oi * a.nblk), smem, ci)) return;
+        if (!fs_staged_item<T, LPT, CH, false, FUSED>(a, oi, (int)(it - oi * a.nblk), smem, ci)) return;
     }
 }
 
@@ -1117,7 +1235,7 @@ __device__ __forceinline__ bool two_row_ok(const FSArgs &a)
     return !*a.range_bad && a.subdiv == 0 && a.N < kFastSteps;
 }
 
-template <typename T, int CH> __global__ void __launch_bounds__(256, 2) k_fs_batch(FSBatchArgs b)
+template <typename T, int CH, bool FUSED, int LPT> __global__ void __launch_bounds__(256, 2) k_fs_batch(FSBatchArgs b)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ FSArgs sa;
@@ -1150,8 +1268,7 @@ template <typename T, int CH> __global__ void __launch_bounds__(256, 2) k_fs_bat
         const int64_t local = s_item - s_first;
         const int64_t oi = local / sa.nblk;
         const int blk = (int)(local - oi * sa.nblk);
-        const bool ok = sa.lpt == 8 ? fs_staged_item<T, 8, CH, true>(sa, oi, blk, smem, ci)
-                                    : fs_staged_item<T, 4, CH, true>(sa, oi, blk, smem, ci);
+        const bool ok = fs_staged_item<T, LPT, CH, true, FUSED>(sa, oi, blk, smem, ci);
         if (!ok) return;
     }
 }
@@ -1160,7 +1277,8 @@ template <typename T, int CH> __global__ void __launch_bounds__(256, 2) k_fs_bat
 // form, with the one-row elimination: every CTA walks the models and takes
 // every gridDim.x-th item of each such model (returns at once when there is
 // none).
-template <typename T, int CH> __global__ void __launch_bounds__(256, 2) k_fs_batch_exact(FSBatchArgs b)
+template <typename T, int CH, bool FUSED, int LPT>
+__global__ void __launch_bounds__(256, 2) k_fs_batch_exact(FSBatchArgs b)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ FSArgs sa;
@@ -1175,8 +1293,7 @@ template <typename T, int CH> __global__ void __launch_bounds__(256, 2) k_fs_bat
         for (int64_t it = blockIdx.x; it < n; it += gridDim.x) {
             const int64_t oi = it / sa.nblk;
             const int blk = (int)(it - oi * sa.nblk);
-            const bool ok = sa.lpt == 8 ? fs_staged_item<T, 8, CH, false>(sa, oi, blk, smem, ci)
-                                        : fs_staged_item<T, 4, CH, false>(sa, oi, blk, smem, ci);
+            const bool ok = fs_staged_item<T, LPT, CH, false, FUSED>(sa, oi, blk, smem, ci);
             if (!ok) return;
         }
     }
@@ -1226,20 +1343,22 @@ template <typename T, int LPT> FSArgs fill_fs_args(const mgt_model *m, bool accu
     return a;
 }
 
-template <typename T, int LPT, int MINB, bool FAST>
+template <typename T, int LPT, int MINB, bool FAST, bool FUSED>
 mgt_status launch_staged(const FSArgs &a, dim3 grid, int bd, size_t smem, double fs_bytes, cudaStream_t s)
 {
-    MGT_CUDA(cudaFuncSetAttribute(k_fs_staged<T, LPT, kChunk, MINB, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    auto kfast = k_fs_staged<T, LPT, kChunk, MINB, FAST, FUSED>;
+    MGT_CUDA(cudaFuncSetAttribute(kfast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
-        MGT_KTIMER_BYTES(sizeof(T) == 4 ? "k_fs_staged<f32>" : "k_fs_staged<f64>", s, fs_bytes);
-        k_fs_staged<T, LPT, kChunk, MINB, FAST><<<grid, bd, smem, s>>>(a);
+        MGT_KTIMER_BYTES(FUSED ? (sizeof(T) == 4 ? "k_fs_fused<f32>" : "k_fs_fused<f64>")
+                               : (sizeof(T) == 4 ? "k_fs_staged<f32>" : "k_fs_staged<f64>"),
+                         s, fs_bytes);
+        kfast<<<grid, bd, smem, s>>>(a);
     }
     MGT_LAUNCH_CHECK("k_fs_staged");
     if constexpr (FAST) {
         // the same items with the one-row elimination if the model is outside
         // the two-row range (a persistent grid; it returns at once otherwise)
-        auto kern = k_fs_exact<T, LPT, kChunk>;
+        auto kern = k_fs_exact<T, LPT, kChunk, FUSED>;
         MGT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int dev = 0, sms = 0, per_sm = 0;
         MGT_CUDA(cudaGetDevice(&dev));
@@ -1264,27 +1383,35 @@ template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_
     const double fs_bytes = (double)m->total_steps * (sizeof(T) == 4 ? 16.0 : 32.0) +
                             (double)m->N * (double)a.RS * sizeof(T) + 16.0 * (double)m->N * m->M;
     const int Mb = a.Gb * LPT;
-    // one origin per CTA: the staged kernel (schedule 2, also the automatic
-    // choice: register-capped for two blocks per SM; 3: one block per SM).
-    // It beats the gather kernel also when one origin fills a single warp
-    // (1.5x at 4 lines x 31 bins, 3x at 10 lines)
+    // one origin per CTA: the staged kernel (schedule 2: register-capped for
+    // two blocks per SM; 3: one block per SM; 4: each thread computes its own
+    // bin's coefficients, for models whose lines fit one line group).  The
+    // automatic choice is 4 where it applies, else 2.  The staged kernel beats
+    // the gather kernel also when one origin fills a single warp (1.5x at 4
+    // lines x 31 bins, 3x at 10 lines)
+    if (schedule == 4 && a.Gtot != 1)
+        return set_error(MGT_ERR_ARG, "formal solve: schedule 4 needs the lines in one group (lines <= lines per thread)");
     const bool staged = schedule != 1;
     if (staged) {
         a.OPB = 1;
+        a.fused = (schedule == 4 || (schedule == 0 && a.Gtot == 1)) ? 1 : 0;
         const int threads = a.Q * a.Gb;
         const int bd = ((threads + 31) / 32) * 32;
         if (bd > 256) return set_error(MGT_ERR_ARG, "formal solve: more than 256 bins per origin");
-        const size_t smem = (size_t)staged_layout<T, LPT, kChunk>(a.Q, Mb, a.RS, bd, a.P).total;
+        const size_t smem = (size_t)staged_layout<T, LPT, kChunk>(a.Q, Mb, a.RS, bd, a.P, a.fused != 0).total;
         dim3 grid((unsigned)m->N, (unsigned)ceil_div(a.Gtot, a.Gb));
         // the two-row elimination in FP32 (the subdivided reference keeps the
         // one-row form; the range argument needs half-rays below kFastSteps)
         if constexpr (sizeof(T) == 4) {
-            if (a.subdiv == 0 && m->N < kFastSteps)
-                return schedule == 3 ? launch_staged<T, LPT, 1, true>(a, grid, bd, smem, fs_bytes, s)
-                                     : launch_staged<T, LPT, 2, true>(a, grid, bd, smem, fs_bytes, s);
+            if (a.subdiv == 0 && m->N < kFastSteps) {
+                if (a.fused) return launch_staged<T, LPT, 2, true, true>(a, grid, bd, smem, fs_bytes, s);
+                return schedule == 3 ? launch_staged<T, LPT, 1, true, false>(a, grid, bd, smem, fs_bytes, s)
+                                     : launch_staged<T, LPT, 2, true, false>(a, grid, bd, smem, fs_bytes, s);
+            }
         }
-        return schedule == 3 ? launch_staged<T, LPT, 1, false>(a, grid, bd, smem, fs_bytes, s)
-                             : launch_staged<T, LPT, 2, false>(a, grid, bd, smem, fs_bytes, s);
+        if (a.fused) return launch_staged<T, LPT, 2, false, true>(a, grid, bd, smem, fs_bytes, s);
+        return schedule == 3 ? launch_staged<T, LPT, 1, false, false>(a, grid, bd, smem, fs_bytes, s)
+                             : launch_staged<T, LPT, 2, false, false>(a, grid, bd, smem, fs_bytes, s);
     }
     const int threads = a.OPB * a.Q * a.Gb;
     const int bd = ((threads + 31) / 32) * 32;
@@ -1313,7 +1440,8 @@ mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s, bo
 {
     const int lpt = fs_lines_per_thread(m, p);
     if (m->Mpad % lpt != 0) return set_error(MGT_ERR_STATE, "line padding does not match the schedule");
-    // 0: automatic, 1: gather kernel, 2: staged (two blocks per SM), 3: staged (one block per SM)
+    // 0: automatic, 1: gather kernel, 2: staged (two blocks per SM), 3: staged (one block per SM),
+    // 4: staged with per-thread coefficients (lines in one group)
     const int sch = m->opts.schedule;
     if (p == MGT_FP64) return launch_typed<double, 4>(m, s, sch, accumulate);
     return lpt == 4 ? launch_typed<float, 4>(m, s, sch, accumulate) : launch_typed<float, 8>(m, s, sch, accumulate);
@@ -1325,74 +1453,101 @@ mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s, bo
 // ---------------------------------------------------------------------------
 size_t fs_args_bytes() { return sizeof(FSArgs); }
 
-mgt_status fs_batch_args(const mgt_model *m, void *args, int *threads, int64_t *items)
+mgt_status fs_batch_args(const mgt_model *m, void *args, int *threads, int64_t *items, int *fused, int *lines)
 {
     const int lpt = fs_lines_per_thread(m, MGT_FP32_MIXED);
     if (m->Mpad % lpt != 0) return set_error(MGT_ERR_STATE, "line padding does not match the schedule");
     FSArgs a = lpt == 4 ? fill_fs_args<float, 4>(m, false) : fill_fs_args<float, 8>(m, false);
     a.OPB = 1;
+    a.fused = a.Gtot == 1 ? 1 : 0;     // as the automatic single-model choice
     const int bd = ((a.Q * a.Gb + 31) / 32) * 32;
     if (bd > 256) return set_error(MGT_ERR_ARG, "batched formal solve: more than 256 bins per origin");
     *threads = bd;
     *items = a.N * a.nblk;
+    *fused = a.fused;
+    *lines = a.lpt;
     std::memcpy(args, &a, sizeof a);
     return MGT_OK;
 }
 
-// One-warp CTAs (models with few lines) take chunks of 15 steps: half the
+// One-warp CTAs (models with few lines) take chunks of 14 steps: half the
 // staging and coefficient buffers, so twice as many CTAs fit on an SM, and a
-// barrier of one warp costs little.  The arithmetic does not depend on the
-// chunk length.
+// barrier of one warp costs little.  Fused items hold no coefficient buffers,
+// and their one-warp CTAs are limited by registers, not shared memory: they
+// keep the long chunks.  The arithmetic does not depend on the chunk length.
 constexpr int kChunkNarrow = 14;
+
+bool narrow_chunks(int bd, int fused) { return bd == 32 && !fused; }
 
 size_t fs_batch_smem(const void *args, int bd)
 {
     FSArgs a;
     std::memcpy(&a, args, sizeof a);
     const int Mb = a.Gb * a.lpt;
-    if (bd == 32)
-        return a.lpt == 4 ? (size_t)staged_layout<float, 4, kChunkNarrow>(a.Q, Mb, a.RS, bd, a.P).total
-                          : (size_t)staged_layout<float, 8, kChunkNarrow>(a.Q, Mb, a.RS, bd, a.P).total;
-    return a.lpt == 4 ? (size_t)staged_layout<float, 4, kChunk>(a.Q, Mb, a.RS, bd, a.P).total
-                      : (size_t)staged_layout<float, 8, kChunk>(a.Q, Mb, a.RS, bd, a.P).total;
+    const bool f = a.fused != 0;
+    if (narrow_chunks(bd, a.fused))
+        return a.lpt == 4 ? (size_t)staged_layout<float, 4, kChunkNarrow>(a.Q, Mb, a.RS, bd, a.P, f).total
+                          : (size_t)staged_layout<float, 8, kChunkNarrow>(a.Q, Mb, a.RS, bd, a.P, f).total;
+    return a.lpt == 4 ? (size_t)staged_layout<float, 4, kChunk>(a.Q, Mb, a.RS, bd, a.P, f).total
+                      : (size_t)staged_layout<float, 8, kChunk>(a.Q, Mb, a.RS, bd, a.P, f).total;
 }
 
-mgt_status fs_batch_grid(int bd, size_t smem, size_t max_smem, int *grid)
+namespace {
+
+// The persistent kernels of one class of a batch (one instance per chunk
+// length, fused flag and lines per thread, so that each holds one item body
+// and keeps the registers of the single-model kernel): one-warp CTAs of
+// unfused models take the narrow chunk length.
+struct BatchKernels {
+    void (*fast)(FSBatchArgs);
+    void (*exact)(FSBatchArgs);
+};
+
+template <int CH, bool FUSED, int LPT> BatchKernels batch_instance()
 {
-    auto kern = bd == 32 ? k_fs_batch<float, kChunkNarrow> : k_fs_batch<float, kChunk>;
-    auto kex = bd == 32 ? k_fs_batch_exact<float, kChunkNarrow> : k_fs_batch_exact<float, kChunk>;
-    MGT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
-    MGT_CUDA(cudaFuncSetAttribute(kex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
+    return BatchKernels{k_fs_batch<float, CH, FUSED, LPT>, k_fs_batch_exact<float, CH, FUSED, LPT>};
+}
+
+BatchKernels batch_kernels(int bd, int fused, int lpt)
+{
+    if (narrow_chunks(bd, fused))
+        return lpt == 8 ? batch_instance<kChunkNarrow, false, 8>() : batch_instance<kChunkNarrow, false, 4>();
+    if (fused) return lpt == 8 ? batch_instance<kChunk, true, 8>() : batch_instance<kChunk, true, 4>();
+    return lpt == 8 ? batch_instance<kChunk, false, 8>() : batch_instance<kChunk, false, 4>();
+}
+
+}  // namespace
+
+mgt_status fs_batch_grid(int bd, int fused, int lpt, size_t smem, size_t max_smem, int *grid)
+{
+    const BatchKernels k = batch_kernels(bd, fused, lpt);
+    MGT_CUDA(cudaFuncSetAttribute(k.fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
+    MGT_CUDA(cudaFuncSetAttribute(k.exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
     int dev = 0, sms = 0, per_sm = 0;
     MGT_CUDA(cudaGetDevice(&dev));
     MGT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    MGT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bd, smem));
+    MGT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fast, bd, smem));
     if (per_sm < 1) return set_error(MGT_ERR_ARG, "batched formal solve: a CTA does not fit on an SM");
     *grid = sms * per_sm;
     return MGT_OK;
 }
 
 mgt_status fs_batch_launch(const void *d_args, const int64_t *d_item_end, int n_models, int64_t n_items,
-                           unsigned long long *d_next, int bd, size_t smem, int grid, cudaStream_t s)
+                           unsigned long long *d_next, int bd, int fused, int lpt, size_t smem, int grid,
+                           cudaStream_t s)
 {
     FSBatchArgs b{static_cast<const FSArgs *>(d_args), d_item_end, n_models, n_items, d_next};
     MGT_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), s));
     const int64_t g = std::min<int64_t>(grid, n_items);
     {
         MGT_KTIMER("k_fs_batch", s);
-        if (bd == 32)
-            k_fs_batch<float, kChunkNarrow><<<(unsigned)g, bd, smem, s>>>(b);
-        else
-            k_fs_batch<float, kChunk><<<(unsigned)g, bd, smem, s>>>(b);
+        batch_kernels(bd, fused, lpt).fast<<<(unsigned)g, bd, smem, s>>>(b);
     }
     MGT_LAUNCH_CHECK("k_fs_batch");
     // the items of models outside the two-row range (returns at once without)
     {
         MGT_KTIMER("k_fs_batch_exact", s);
-        if (bd == 32)
-            k_fs_batch_exact<float, kChunkNarrow><<<(unsigned)g, bd, smem, s>>>(b);
-        else
-            k_fs_batch_exact<float, kChunk><<<(unsigned)g, bd, smem, s>>>(b);
+        batch_kernels(bd, fused, lpt).exact<<<(unsigned)g, bd, smem, s>>>(b);
     }
     MGT_LAUNCH_CHECK("k_fs_batch_exact");
     return MGT_OK;

@@ -720,10 +720,13 @@ __global__ void __launch_bounds__(kWalkThreads, 8) k_walk(WalkArgs a, int64_t *_
             gave_up = true;
             break;
         }
-        float bd2 = 3.0e38f, bU = 0.0f, bL = 0.0f, bZ = 0.0f, beZ = 0.0f, minLother = 3.0e38f;
+        // each lane keeps the best of its own entries over the row's chunks
+        // (smallest d2, the earlier chunk on ties) and the least lower bound
+        // of its other candidates; the group decides once per step
+        float bd2 = 3.0e38f, bU = 0.0f, bLo = 3.0e38f, bZ = 0.0f, beZ = 0.0f, lo2 = 3.0e38f;
         uint32_t bword = 0u;
         int32_t boff = 0;
-        bool have = false, undecided = false, row_open = !done;
+        bool und_lane = false, row_open = !done;
         int32_t chunks = 0;
         for (int32_t kb = c_off; __any_sync(full, row_open); kb += 16) {
             if (++chunks > a.max_row_chunks) {
@@ -731,8 +734,7 @@ __global__ void __launch_bounds__(kWalkThreads, 8) k_walk(WalkArgs a, int64_t *_
                 gave_up = true;
                 break;
             }
-            bool cand = false, und = false, last = false;
-            float d2 = 3.0e38f, U = 0.0f, Lo = 3.0e38f, Z = 0.0f, eZ = 0.0f;
+            bool last = false;
             uint32_t word = 0u;
             int32_t eoff = 0;
             float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = e0;
@@ -757,48 +759,32 @@ __global__ void __launch_bounds__(kWalkThreads, 8) k_walk(WalkArgs a, int64_t *_
                 const float dz = (e0.z - f.ohz) + (e1.y - f.olz);
                 const float adx = fabsf(dx), ady = fabsf(dy), adz = fabsf(dz);
                 const float ed = 2e-6f * (fmaxf(adx, fmaxf(ady, adz)) + a.pos_slack);
-                Z = fmaf(dz, f.f2, fmaf(dy, f.f1, dx * f.f0));
-                eZ = 2e-6f * (adx + ady + adz) + 2.0f * ed;
+                const float Z = fmaf(dz, f.f2, fmaf(dy, f.f1, dx * f.f0));
+                const float eZ = 2e-6f * (adx + ady + adz) + 2.0f * ed;
                 if (Z - eZ > Zc + eZc) {
-                    cand = true;
                     const float px = fmaf(-Z, f.f0, dx), py = fmaf(-Z, f.f1, dy), pz = fmaf(-Z, f.f2, dz);
-                    d2 = fmaf(pz, pz, fmaf(py, py, px * px));
+                    const float d2 = fmaf(pz, pz, fmaf(py, py, px * px));
                     const float ep = ed + eZ + 2e-7f * (fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz))) + fabsf(Z));
-                    const float e2 = 4.0f * sqrtf(d2) * ep + 4.0f * ep * ep + 1e-6f * d2;
-                    U = d2 + e2;
-                    Lo = d2 - e2;
+                    // |p32| from the approximate square root, raised by 2^-10
+                    // (far above its error) so that the bound stays an upper one
+                    float rp;
+                    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rp) : "f"(d2));
+                    const float e2 = 4.0f * (rp * 1.0009765625f) * ep + 4.0f * ep * ep + 1e-6f * d2;
+                    const float U = d2 + e2, Lo = d2 - e2;
+                    if (d2 < bd2) {
+                        lo2 = fminf(lo2, bLo);
+                        bd2 = d2;
+                        bU = U;
+                        bLo = Lo;
+                        bZ = Z;
+                        beZ = eZ;
+                        bword = word;
+                        boff = eoff;
+                    } else {
+                        lo2 = fminf(lo2, Lo);
+                    }
                 } else if (!(Z + eZ <= Zc - eZc)) {
-                    und = true;
-                }
-            }
-            // (the ballot must run in every lane: no short-circuit around it)
-            const bool und_grp = (__ballot_sync(full, und) & gmask) != 0u;
-            undecided = undecided || und_grp;
-            const float m = group16_min_nonneg(cand ? d2 : 3.0e38f, grp);
-            const unsigned wins = (__ballot_sync(full, cand && d2 == m) & gmask) >> (16 * grp);
-            const int wl = wins ? __ffs(wins) - 1 : sl;
-            const int src = 16 * grp + wl;
-            const float cU = __shfl_sync(full, U, src), cL = __shfl_sync(full, Lo, src);
-            const float cZ = __shfl_sync(full, Z, src), ceZ = __shfl_sync(full, eZ, src);
-            const uint32_t cword = __shfl_sync(full, word, src);
-            const int32_t coff = __shfl_sync(full, eoff, src);
-            // (a negative lower bound counts as 0: the test below compares it
-            // with an upper bound >= 0, so either way the step is not accepted)
-            const float oL = group16_min_nonneg((cand && sl != wl) ? fmaxf(Lo, 0.0f) : 3.0e38f, grp);
-            if (wins) {
-                if (!have || m < bd2) {
-                    if (have) minLother = fminf(minLother, bL);
-                    minLother = fminf(minLother, oL);
-                    have = true;
-                    bd2 = m;
-                    bU = cU;
-                    bL = cL;
-                    bZ = cZ;
-                    beZ = ceZ;
-                    bword = cword;
-                    boff = coff;
-                } else {
-                    minLother = fminf(minLother, fminf(cL, oL));
+                    und_lane = true;
                 }
             }
             row_open = row_open && lastbits == 0u;
@@ -806,8 +792,24 @@ __global__ void __launch_bounds__(kWalkThreads, 8) k_walk(WalkArgs a, int64_t *_
         if (gave_up) break;
         // The decision runs in both groups in lockstep (a finished group only
         // predicates itself off), so every warp intrinsic below names the
-        // whole warp.
-        const bool exact = !done && (undecided || (have && !(bU < minLother)));
+        // whole warp.  The FP32 winner is the group's smallest d2 (lowest lane
+        // on ties); it is accepted only if every other candidate's lower bound
+        // lies above its upper bound (a negative lower bound always fails,
+        // since upper bounds are >= 0), so a tie never decides.
+        const bool undecided = (__ballot_sync(full, und_lane) & gmask) != 0u;
+        const float m = group16_min_nonneg(bd2, grp);
+        const bool have = m < 3.0e38f;
+        const unsigned wins = (__ballot_sync(full, have && bd2 == m) & gmask) >> (16 * grp);
+        const int wl = wins ? __ffs(wins) - 1 : sl;
+        const int src = 16 * grp + wl;
+        bU = __shfl_sync(full, bU, src);
+        bZ = __shfl_sync(full, bZ, src);
+        beZ = __shfl_sync(full, beZ, src);
+        bword = __shfl_sync(full, bword, src);
+        boff = __shfl_sync(full, boff, src);
+        const float lo_other = sl == wl ? lo2 : fminf(bLo, lo2);
+        const bool close = (__ballot_sync(full, have && lo_other <= bU) & gmask) != 0u;
+        const bool exact = !done && (undecided || close);
         int64_t v = -1;
         double Zn = 0.0;
         if (exact && sl == 0) {
@@ -860,7 +862,6 @@ __global__ void __launch_bounds__(kWalkThreads, 8) k_walk(WalkArgs a, int64_t *_
                 if (nx >= a.N || boff < 0 || boff >= a.n_ent) {
                     walk_give_up(err, 12, wg, nx);
                     nx = -1;
-                    have = false;
                 }
                 nx_bnd = (bword & kEntBnd) != 0u;
                 c_off = boff;

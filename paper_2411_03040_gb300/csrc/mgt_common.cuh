@@ -227,11 +227,15 @@ int fs_lines_per_thread(const mgt_model *m, mgt_precision p);
 // batched launches over many models (argument tables built per model, read on
 // the device by table slot; see batch.cu)
 size_t fs_args_bytes();
-mgt_status fs_batch_args(const mgt_model *m, void *args, int *threads, int64_t *items);
+// (fused: the model's lines fit one group, its items run with per-thread
+// coefficients; lines: its lines per thread; models are launched in classes of
+// equal width, fused flag and lines per thread)
+mgt_status fs_batch_args(const mgt_model *m, void *args, int *threads, int64_t *items, int *fused, int *lines);
 size_t fs_batch_smem(const void *args, int threads);
-mgt_status fs_batch_grid(int threads, size_t smem, size_t max_smem, int *grid);
+mgt_status fs_batch_grid(int threads, int fused, int lines, size_t smem, size_t max_smem, int *grid);
 mgt_status fs_batch_launch(const void *d_args, const int64_t *d_item_end, int n_models, int64_t n_items,
-                           unsigned long long *d_next, int threads, size_t smem, int grid, cudaStream_t s);
+                           unsigned long long *d_next, int threads, int fused, int lines, size_t smem, int grid,
+                           cudaStream_t s);
 size_t se_args_bytes();
 mgt_status se_batch_args(const mgt_model *m, void *args, int64_t *blocks, size_t *smem);
 mgt_status se_batch_prepare(size_t smem);

@@ -24,8 +24,9 @@ __device__ __forceinline__ float erfc_fit(float x)
     p = fmaf(p, s, 1.815657182e-01f);
     p = fmaf(p, s, 3.218607602e-01f);
     p = fmaf(p, s, 4.216127275e-01f);
-    const float r = t * p * __expf(-ax * ax);
-    return x < 0.0f ? 2.0f - r : r;
+    // explicit roundings: no context may contract these into its own FMAs
+    const float r = __fmul_rn(__fmul_rn(t, p), __expf(-__fmul_rn(ax, ax)));
+    return x < 0.0f ? __fsub_rn(2.0f, r) : r;
 }
 
 }  // namespace mgt

@@ -60,7 +60,11 @@ def test_batch_formal_solve_and_se_match_single_model_calls(mgt, batch_models):
     assert lay["n_models"] == len(hs)
     assert lay["graph_kernels"] == 0
     assert lay["fs_threads"] == 160                       # 31 bins x 5 groups of 8 lines, in warps
-    assert lay["fs_launches"] == 2                        # CTA widths 160 and 32
+    # one launch per (CTA width, per-thread coefficients, lines per thread):
+    # width 160 at 8 and at 4 lines per thread; width 32 with the shared
+    # pre-pass at 8 and 4 (10 lines), with per-thread coefficients at 4 and 8
+    # (the 4-line models)
+    assert lay["fs_launches"] == 6
     # launch order: most work per item first
     assert sorted(lay["order"].tolist()) == list(range(len(hs)))
     mgt.mgt_batch_formal_solve(b)
@@ -158,20 +162,28 @@ def test_batch_rejects_bad_inputs(mgt, batch_models):
 
 def test_staged_schedule_on_small_blocks_matches_oracle(mgt):
     # 5 lines x 9 bins: one warp per origin in the staged kernel (as the
-    # batched launch runs small models)
+    # batched launch runs small models); schedule 4 (per-thread coefficients)
+    # with the 5 lines in one group of 8
     m = synth.sphere_model(700, n_levels=6, nside=1, n_quad=9, seed=77, name="ragged")
     rays = O.trace(m)
     pops = O.lte_populations(m.temp, m.n_spec, m.lines.energy_J, m.lines.g)
     chi, S, _ = O.line_chi_S(pops, m.lines)
     J, L = O.formal_solve(m, rays, chi, S)
-    for sched in (2, 3):
+    for sched in (2, 3, 4):
         for lpt in (4, 8):
+            if sched == 4 and lpt == 4:
+                continue                                  # 5 lines: two groups of 4
             h = mgt.mgt_model_create(m)
             mgt.mgt_set_solve_opts(h, lines_per_thread=lpt, schedule=sched)
             mgt.mgt_trace_rays(h)
             Jg, Lg = mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED)
             assert np.max(np.abs(Jg.T - J) / np.abs(J)) < TOL32
             assert np.max(np.abs(Lg.T - L) / np.abs(L)) < TOL32
+            if sched == 4:
+                # FP64 runs 4 lines per thread: the 5 lines need two groups
+                with pytest.raises(mgt.MgtError):
+                    mgt.mgt_formal_solve(h, mgt.MGT_FP64)
+                continue
             Jg, Lg = mgt.mgt_formal_solve(h, mgt.MGT_FP64)
             assert np.max(np.abs(Jg.T - J) / np.abs(J)) < 1e-10
 
@@ -194,4 +206,4 @@ def test_autotune_picks_a_timed_candidate(mgt, batch_models):
     Jb, Lb = mgt.mgt_formal_solve(h2, mgt.MGT_FP32_MIXED)
     np.testing.assert_array_equal(Ja, Jb)
     r64 = mgt.mgt_autotune(h, mgt.MGT_FP64, staged_only=True, reps=1)
-    assert [(s, l) for s, l, _ in r64["tried"]] == [(2, 4)]
+    assert [(s, l) for s, l, _ in r64["tried"]] == [(0, 4)]

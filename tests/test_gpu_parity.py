@@ -184,6 +184,41 @@ def test_items_outside_the_two_row_range_are_redone_exactly(mgt, lpt):
     assert rel_err(J64, J) < TOL64 and rel_err(L64, L) < TOL64
 
 
+@pytest.mark.parametrize("lpt", [4, 8])
+@pytest.mark.parametrize("thick", [False, True], ids=["two-row", "one-row"])
+def test_per_thread_coefficients_bit_identical_to_shared_prepass(mgt, lpt, thick):
+    # schedule 4 (each thread computes its own bin's segment coefficients)
+    # against schedule 2 (the CTA computes them once per bin in shared memory):
+    # one function computes every coefficient, so J-bar and Lambda* agree bit
+    # for bit in both precisions, with the two-row elimination and with the
+    # one-row fallback (inner points optically thick, as in the test above)
+    m = synth.config_model(1, n_points=800)
+    if thick:
+        r = np.linalg.norm(m.pos, axis=1)
+        m.n_spec = np.where(r < 0.5 * r.max(), m.n_spec * 1e12, m.n_spec)
+    out = {}
+    for sched in (2, 4):
+        h = mgt.mgt_model_create(m)
+        mgt.mgt_set_solve_opts(h, lines_per_thread=lpt, schedule=sched)
+        mgt.mgt_trace_rays(h)
+        out[sched] = [mgt.mgt_formal_solve(h, p) for p in (mgt.MGT_FP32_MIXED, mgt.MGT_FP64)]
+    for (J2, L2), (J4, L4) in zip(out[2], out[4]):
+        assert np.all(np.isfinite(J2)) and np.all(np.isfinite(L2))
+        np.testing.assert_array_equal(J4, J2)
+        np.testing.assert_array_equal(L4, L2)
+
+
+def test_per_thread_coefficients_need_one_line_group(mgt):
+    # 10 lines do not fit one group of 4 or 8 lines per thread
+    m = synth.sphere_model(300, n_levels=11, nside=1, n_quad=7, seed=5, name="ten-lines")
+    h = mgt.mgt_model_create(m)
+    mgt.mgt_set_solve_opts(h, lines_per_thread=8, schedule=4)
+    mgt.mgt_trace_rays(h)
+    with pytest.raises(mgt.MgtError) as e:
+        mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED)
+    assert e.value.status == mgt.MGT_ERR_ARG and "one group" in str(e.value)
+
+
 def test_single_point_model_is_background(mgt):
     # no neighbours: every half-ray is empty, u = I_bg, Lambda* = 0
     lines = synth.linear_rotor(3, np.random.default_rng(0))
