@@ -115,6 +115,7 @@ struct FSArgs {
     double *J, *Lst;           // [N][M]
     int *err;
     const int *range_bad;      // nonzero: a point's range figure exceeds 1 (set by the line data)
+    int64_t n_rec;             // step records held (the ray offsets index below this)
 };
 
 // Geometry of one traced step in the solver's precision.
@@ -188,6 +189,15 @@ constexpr float kSwitchBand = 2e-4f;
 __device__ __noinline__ bool trapezoid_fp64(const FSArgs &a, int r, int64_t c_far, int64_t c_near, double xq64,
                                             double wo64)
 {
+    if (c_far < 0 || c_far >= a.N || c_near < 0 || c_near >= a.N) {   // index check: record, use point 0
+        if (atomicCAS(a.err, 0, (int)kDevBounds) == 0) {
+            a.err[1] = 22;
+            a.err[2] = (int)c_far;
+            a.err[3] = (int)c_near;
+        }
+        c_far = c_far < 0 || c_far >= a.N ? 0 : c_far;
+        c_near = c_near < 0 || c_near >= a.N ? 0 : c_near;
+    }
     const double *n = a.dirs + 3 * (a.dir_map ? a.dir_map[r] : r);
     const double *vf = a.vel + 3 * c_far, *vn = a.vel + 3 * c_near;
     const double dbeta = (n[0] * (vf[0] - vn[0]) + n[1] * (vf[1] - vn[1]) + n[2] * (vf[2] - vn[2])) / kC;
@@ -477,6 +487,7 @@ __device__ __forceinline__ void reduce_out(const FSArgs &a, const double *red, i
         const int64_t oi = o_base + lo2;
         if (oi >= a.N || line >= a.M) continue;
         const int64_t o2 = ordered ? (int64_t)a.order[oi] : oi;
+        if (o2 < 0 || o2 >= a.N) continue;      // a bad visiting-order entry (recorded by the item)
         double sJ = 0.0, sL = 0.0;
         for (int qq = 0; qq < a.Q; ++qq) {
             sJ += red[((0 * a.OPB + lo2) * Mb + lb) * a.Q + qq];
@@ -684,8 +695,17 @@ __device__ __forceinline__ void fill_extents(const FSArgs &a, int64_t o, longlon
         const int2 pr = a.pairs[t >> 1];
         const int r = (t & 1) == 0 ? pr.y : pr.x;
         const int64_t i = (int64_t)r * a.N + o;
-        const int64_t s0 = a.ray_off[i];
-        ext[t] = make_longlong2(s0, a.ray_off[i + 1] - s0);
+        const int64_t s0 = a.ray_off[i], len = a.ray_off[i + 1] - s0;
+        if (s0 < 0 || len < 0 || len > a.N || s0 + len > a.n_rec) {   // index check: record, empty half-ray
+            if (atomicCAS(a.err, 0, (int)kDevBounds) == 0) {
+                a.err[1] = 23;
+                a.err[2] = (int)o;
+                a.err[3] = (int)t;
+            }
+            ext[t] = make_longlong2(0, 0);
+        } else {
+            ext[t] = make_longlong2(s0, len);
+        }
     }
 }
 
@@ -897,6 +917,20 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
     }
 }
 
+// The origin of visiting-order entry oi; an entry outside the model is
+// recorded in the error word (site 24) and replaced by point 0.
+__device__ __noinline__ int64_t checked_origin(const FSArgs &a, int64_t oi, int tid)
+{
+    const int64_t o = a.order[oi];
+    if (o >= 0 && o < a.N) return o;
+    if (tid == 0 && atomicCAS(a.err, 0, (int)kDevBounds) == 0) {
+        a.err[1] = 24;
+        a.err[2] = (int)oi;
+        a.err[3] = (int)o;
+    }
+    return 0;
+}
+
 // One (origin, line block) item of the staged schedule, run by the whole CTA:
 // origin order index oi, line block blk.  The mbarriers at the base of shared
 // memory are initialised once per CTA; `ci` counts the chunks the CTA has
@@ -927,7 +961,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
     longlong2 *ext = reinterpret_cast<longlong2 *>(smem + lay.ext);       // [2 P] half-ray extents
     double *red = reinterpret_cast<double *>(smem + lay.stage);           // reuses staging + coefficients at the end
 
-    const int64_t o = a.order[oi];
+    const int64_t o = checked_origin(a, oi, tid);
     const int gl = tid / a.Q, q = tid - gl * a.Q;
     const int gg = blk * a.Gb + gl;
     const int line0 = gg * LPT;
@@ -1338,6 +1372,7 @@ template <typename T, int LPT> FSArgs fill_fs_args(const mgt_model *m, bool accu
     a.Lst = m->d_Lst;
     a.err = m->d_err;
     a.range_bad = m->d_range_bad;
+    a.n_rec = m->total_steps;
     a.lpt = LPT;
     a.nblk = ceil_div(a.Gtot, a.Gb);
     return a;
