@@ -479,7 +479,10 @@ typedef struct {
     int64_t se_blocks;         /* CTAs of the statistical-equilibrium launch */
     int32_t graph_kernels;     /* kernels per replay of the captured iteration (0 before the
                                   first mgt_batch_iterate) */
-    int32_t fs_launches;       /* persistent formal-solution launches (one per class of models) */
+    int32_t fs_launches;       /* formal-solution launches: one persistent launch per class of
+                                  models, plus one per model launched on its own */
+    int32_t fs_solo;           /* models launched on their own (at least 8 waves of CTAs of their
+                                  persistent class: the single-model kernel, the same values) */
 } mgt_batch_layout;
 mgt_status mgt_batch_create(mgt_batch **out, mgt_model *const *models, int32_t n_models, void *stream);
 mgt_status mgt_batch_destroy(mgt_batch *b);

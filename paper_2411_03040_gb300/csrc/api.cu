@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <set>
 #include <string>
@@ -16,6 +17,20 @@ namespace mgt {
 
 static thread_local std::string g_last_error;
 static std::atomic<long long> g_launches{0};
+
+mgt_status raise_smem_limit(const void *func, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> lim;   // (kernel, device) -> limit set
+    int dev = 0;
+    MGT_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = lim[{func, dev}];
+    if (smem <= cur) return MGT_OK;
+    MGT_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cur = smem;
+    return MGT_OK;
+}
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }

@@ -39,6 +39,8 @@ struct mgt_batch {
         }
     };
     std::vector<FsClass> fs_classes;               // in launch order, widest first
+    std::vector<int32_t> fs_solo;                  // table slots launched on their own (large models)
+    int64_t fs_solo_items = 0;
     size_t se_smem = 0;
     // device copies
     unsigned char *d_fs_args = nullptr, *d_se_args = nullptr, *d_ld_args = nullptr;
@@ -106,11 +108,25 @@ mgt_status refresh(mgt_batch *b, cudaStream_t s)
             fs_batch_args(b->models[i], fa_c.data() + i * fsz, &width[i], &items[i], &fused[i], &lines[i]));
         cost[i] = item_cost(b->models[i]);
     }
-    // order: widest CTAs first, unfused before fused at one width, 8 lines per
-    // thread before 4, then most work per item, ties by caller index
+    // A model of at least kSoloWaves waves of its persistent instance runs its
+    // single-model launch instead: its tail is small anyway, and the
+    // single-model kernel reads its arguments as constant operands, where the
+    // persistent one holds them in registers (the same values either way).
+    constexpr int64_t kSoloWaves = 8;
+    std::vector<char> solo(n);
+    for (int i = 0; i < n; ++i) {
+        const size_t sm = fs_batch_smem(fa_c.data() + i * fsz, width[i]);
+        const int64_t wave = fs_batch_wave(fa_c.data() + i * fsz, width[i], sm);
+        solo[i] = wave > 0 && items[i] >= kSoloWaves * wave;
+    }
+    // order: the pooled models, widest CTAs first, unfused before fused at one
+    // width, 8 lines per thread before 4, then most work per item, ties by
+    // caller index; then the models launched on their own, most work first
     std::vector<int32_t> order(n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        if (solo[x] != solo[y]) return solo[x] < solo[y];
+        if (solo[x]) return items[x] * cost[x] > items[y] * cost[y];
         if (width[x] != width[y]) return width[x] > width[y];
         if (fused[x] != fused[y]) return fused[x] < fused[y];
         if (lines[x] != lines[y]) return lines[x] > lines[y];
@@ -120,26 +136,34 @@ mgt_status refresh(mgt_batch *b, cudaStream_t s)
     std::vector<unsigned char> fa(fsz * n), sa(ssz * n), la(lsz * n);
     std::vector<int64_t> fe(n), se(n), le(n);
     std::vector<mgt_batch::FsClass> classes;
+    std::vector<int32_t> solo_slots;
+    int64_t solo_items = 0;
     size_t se_smem = 0;
     int64_t si = 0, li = 0, fi = 0;
     for (int k = 0; k < n; ++k) {
         const int i = order[k];
         const mgt_model *m = b->models[i];
         std::memcpy(fa.data() + k * fsz, fa_c.data() + i * fsz, fsz);
-        if (classes.empty() || classes.back().threads != width[i] || classes.back().fused != fused[i] ||
-            classes.back().lines != lines[i]) {
-            classes.emplace_back();
-            classes.back().threads = width[i];
-            classes.back().fused = fused[i];
-            classes.back().lines = lines[i];
-            classes.back().first = k;
-            fi = 0;
+        if (solo[i]) {
+            solo_slots.push_back(k);
+            solo_items += items[i];
+            fe[k] = 0;
+        } else {
+            if (classes.empty() || classes.back().threads != width[i] || classes.back().fused != fused[i] ||
+                classes.back().lines != lines[i]) {
+                classes.emplace_back();
+                classes.back().threads = width[i];
+                classes.back().fused = fused[i];
+                classes.back().lines = lines[i];
+                classes.back().first = k;
+                fi = 0;
+            }
+            mgt_batch::FsClass &c = classes.back();
+            ++c.count;
+            c.items = (fi += items[i]);
+            c.smem = std::max(c.smem, fs_batch_smem(fa.data() + k * fsz, c.threads));
+            fe[k] = fi;
         }
-        mgt_batch::FsClass &c = classes.back();
-        ++c.count;
-        c.items = (fi += items[i]);
-        c.smem = std::max(c.smem, fs_batch_smem(fa.data() + k * fsz, c.threads));
-        fe[k] = fi;
         int64_t sblocks = 0, lblocks = 0;
         size_t ssm = 0;
         MGT_TRY_STATUS(se_batch_args(m, sa.data() + k * ssz, &sblocks, &ssm));
@@ -163,7 +187,7 @@ mgt_status refresh(mgt_batch *b, cudaStream_t s)
         MGT_TRY_STATUS(fs_batch_grid(c.threads, c.fused, c.lines, c.smem, max_smem[instance(c)], &c.grid));
 
     const bool same = order == b->order && fa == b->fs_args && sa == b->se_args && la == b->ld_args &&
-                      classes == b->fs_classes && se_smem == b->se_smem;
+                      classes == b->fs_classes && solo_slots == b->fs_solo && se_smem == b->se_smem;
     if (same && b->d_next) return MGT_OK;
     drop_graph(b);
     if (b->d_next && classes.size() != b->fs_classes.size()) {
@@ -178,7 +202,10 @@ mgt_status refresh(mgt_batch *b, cudaStream_t s)
     b->fs_end = fe;
     b->se_end = se;
     b->ld_end = le;
+    for (const int32_t k : solo_slots) MGT_TRY_STATUS(fs_batch_solo(b->models[order[k]], s, false));
     b->fs_classes = classes;
+    b->fs_solo = solo_slots;
+    b->fs_solo_items = solo_items;
     b->se_smem = se_smem;
     MGT_TRY_STATUS(se_batch_prepare(se_smem));
     MGT_TRY_STATUS(upload(&b->d_fs_args, fa, fa.size(), s));
@@ -187,7 +214,7 @@ mgt_status refresh(mgt_batch *b, cudaStream_t s)
     MGT_TRY_STATUS(upload(&b->d_fs_end, fe, n, s));
     MGT_TRY_STATUS(upload(&b->d_se_end, se, n, s));
     MGT_TRY_STATUS(upload(&b->d_ld_end, le, n, s));
-    if (!b->d_next) MGT_CUDA(cudaMalloc(&b->d_next, sizeof(unsigned long long) * classes.size()));
+    if (!b->d_next) MGT_CUDA(cudaMalloc(&b->d_next, sizeof(unsigned long long) * std::max<size_t>(classes.size(), 1)));
     // the host vectors must outlive the copies
     MGT_CUDA(cudaStreamSynchronize(s));
     return MGT_OK;
@@ -203,6 +230,7 @@ mgt_status launch_fs(mgt_batch *b, cudaStream_t s)
         MGT_TRY_STATUS(fs_batch_launch(b->d_fs_args + k.first * fsz, b->d_fs_end + k.first, k.count, k.items,
                                        b->d_next + c, k.threads, k.fused, k.lines, k.smem, k.grid, s));
     }
+    for (const int32_t k : b->fs_solo) MGT_TRY_STATUS(fs_batch_solo(b->models[b->order[k]], s, true));
     return MGT_OK;
 }
 
@@ -407,7 +435,9 @@ mgt_status mgt_batch_get_layout(const mgt_batch *b, mgt_batch_layout *layout, in
             layout->fs_threads = std::max(layout->fs_threads, c.threads);
             layout->fs_smem_bytes = std::max<int64_t>(layout->fs_smem_bytes, (int64_t)c.smem);
         }
-        layout->fs_launches = (int32_t)b->fs_classes.size();
+        layout->fs_items += b->fs_solo_items;
+        layout->fs_launches = (int32_t)(b->fs_classes.size() + b->fs_solo.size());
+        layout->fs_solo = (int32_t)b->fs_solo.size();
         layout->se_blocks = b->se_end.empty() ? 0 : b->se_end.back();
         layout->graph_kernels = b->graph_kernels;
     }

@@ -1378,11 +1378,16 @@ template <typename T, int LPT> FSArgs fill_fs_args(const mgt_model *m, bool accu
     return a;
 }
 
+// The staged launch: the two-row kernel and, for the two-row form, the
+// one-row fallback.  run = false only raises the kernels' shared-memory limits.
 template <typename T, int LPT, int MINB, bool FAST, bool FUSED>
-mgt_status launch_staged(const FSArgs &a, dim3 grid, int bd, size_t smem, double fs_bytes, cudaStream_t s)
+mgt_status launch_staged(const FSArgs &a, dim3 grid, int bd, size_t smem, double fs_bytes, cudaStream_t s, bool run)
 {
     auto kfast = k_fs_staged<T, LPT, kChunk, MINB, FAST, FUSED>;
-    MGT_CUDA(cudaFuncSetAttribute(kfast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MGT_TRY_STATUS(raise_smem_limit((const void *)kfast, smem));
+    auto kern = k_fs_exact<T, LPT, kChunk, FUSED>;
+    if constexpr (FAST) MGT_TRY_STATUS(raise_smem_limit((const void *)kern, smem));
+    if (!run) return MGT_OK;
     {
         MGT_KTIMER_BYTES(FUSED ? (sizeof(T) == 4 ? "k_fs_fused<f32>" : "k_fs_fused<f64>")
                                : (sizeof(T) == 4 ? "k_fs_staged<f32>" : "k_fs_staged<f64>"),
@@ -1393,8 +1398,6 @@ mgt_status launch_staged(const FSArgs &a, dim3 grid, int bd, size_t smem, double
     if constexpr (FAST) {
         // the same items with the one-row elimination if the model is outside
         // the two-row range (a persistent grid; it returns at once otherwise)
-        auto kern = k_fs_exact<T, LPT, kChunk, FUSED>;
-        MGT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int dev = 0, sms = 0, per_sm = 0;
         MGT_CUDA(cudaGetDevice(&dev));
         MGT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1410,7 +1413,8 @@ mgt_status launch_staged(const FSArgs &a, dim3 grid, int bd, size_t smem, double
     return MGT_OK;
 }
 
-template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_t s, int schedule, bool accumulate)
+template <typename T, int LPT>
+mgt_status launch_typed(mgt_model *m, cudaStream_t s, int schedule, bool accumulate, bool run = true)
 {
     FSArgs a = fill_fs_args<T, LPT>(m, accumulate);
     // least traffic of a launch: every step record of the held rays once, every
@@ -1439,20 +1443,20 @@ template <typename T, int LPT> mgt_status launch_typed(mgt_model *m, cudaStream_
         // one-row form; the range argument needs half-rays below kFastSteps)
         if constexpr (sizeof(T) == 4) {
             if (a.subdiv == 0 && m->N < kFastSteps) {
-                if (a.fused) return launch_staged<T, LPT, 2, true, true>(a, grid, bd, smem, fs_bytes, s);
-                return schedule == 3 ? launch_staged<T, LPT, 1, true, false>(a, grid, bd, smem, fs_bytes, s)
-                                     : launch_staged<T, LPT, 2, true, false>(a, grid, bd, smem, fs_bytes, s);
+                if (a.fused) return launch_staged<T, LPT, 2, true, true>(a, grid, bd, smem, fs_bytes, s, run);
+                return schedule == 3 ? launch_staged<T, LPT, 1, true, false>(a, grid, bd, smem, fs_bytes, s, run)
+                                     : launch_staged<T, LPT, 2, true, false>(a, grid, bd, smem, fs_bytes, s, run);
             }
         }
-        if (a.fused) return launch_staged<T, LPT, 2, false, true>(a, grid, bd, smem, fs_bytes, s);
-        return schedule == 3 ? launch_staged<T, LPT, 1, false, false>(a, grid, bd, smem, fs_bytes, s)
-                             : launch_staged<T, LPT, 2, false, false>(a, grid, bd, smem, fs_bytes, s);
+        if (a.fused) return launch_staged<T, LPT, 2, false, true>(a, grid, bd, smem, fs_bytes, s, run);
+        return schedule == 3 ? launch_staged<T, LPT, 1, false, false>(a, grid, bd, smem, fs_bytes, s, run)
+                             : launch_staged<T, LPT, 2, false, false>(a, grid, bd, smem, fs_bytes, s, run);
     }
     const int threads = a.OPB * a.Q * a.Gb;
     const int bd = ((threads + 31) / 32) * 32;
     if (bd > 256) return set_error(MGT_ERR_ARG, "formal solve: too many bins x line groups per block");
     const size_t smem = sizeof(T) * 4 * LPT * bd + sizeof(double) * 2 * a.OPB * Mb * a.Q;
-    MGT_CUDA(cudaFuncSetAttribute(k_fs_gather<T, LPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MGT_TRY_STATUS(raise_smem_limit((const void *)k_fs_gather<T, LPT>, smem));
     dim3 grid((unsigned)ceil_div(m->N, a.OPB), (unsigned)ceil_div(a.Gtot, a.Gb));
     {
         MGT_KTIMER_BYTES(sizeof(T) == 4 ? "k_fs_gather<f32>" : "k_fs_gather<f64>", s, fs_bytes);
@@ -1556,8 +1560,8 @@ BatchKernels batch_kernels(int bd, int fused, int lpt)
 mgt_status fs_batch_grid(int bd, int fused, int lpt, size_t smem, size_t max_smem, int *grid)
 {
     const BatchKernels k = batch_kernels(bd, fused, lpt);
-    MGT_CUDA(cudaFuncSetAttribute(k.fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
-    MGT_CUDA(cudaFuncSetAttribute(k.exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
+    MGT_TRY_STATUS(raise_smem_limit((const void *)k.fast, max_smem));
+    MGT_TRY_STATUS(raise_smem_limit((const void *)k.exact, max_smem));
     int dev = 0, sms = 0, per_sm = 0;
     MGT_CUDA(cudaGetDevice(&dev));
     MGT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1565,6 +1569,28 @@ mgt_status fs_batch_grid(int bd, int fused, int lpt, size_t smem, size_t max_sme
     if (per_sm < 1) return set_error(MGT_ERR_ARG, "batched formal solve: a CTA does not fit on an SM");
     *grid = sms * per_sm;
     return MGT_OK;
+}
+
+int64_t fs_batch_wave(const void *args, int bd, size_t smem)
+{
+    FSArgs a;
+    std::memcpy(&a, args, sizeof a);
+    const BatchKernels k = batch_kernels(bd, a.fused, a.lpt);
+    if (raise_smem_limit((const void *)k.fast, smem) != MGT_OK) return 0;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fast, bd, smem) != cudaSuccess)
+        return 0;
+    return (int64_t)sms * per_sm;
+}
+
+mgt_status fs_batch_solo(mgt_model *m, cudaStream_t s, bool run)
+{
+    const int lpt = fs_lines_per_thread(m, MGT_FP32_MIXED);
+    if (m->Mpad % lpt != 0) return set_error(MGT_ERR_STATE, "line padding does not match the schedule");
+    // the automatic staged schedule, as the persistent launches run it
+    return lpt == 4 ? launch_typed<float, 4>(m, s, 0, false, run) : launch_typed<float, 8>(m, s, 0, false, run);
 }
 
 mgt_status fs_batch_launch(const void *d_args, const int64_t *d_item_end, int n_models, int64_t n_items,

@@ -86,6 +86,16 @@ __device__ Chan channel(const ImgArgs &a, int f)
     return c;
 }
 
+// Reciprocal by the MUFU approximation (relative error about 2^-23): the
+// segment's 1/Delta (|Delta| >= switch x mean width in the erf branch) and
+// 1/t (t >= 0.05 where it is used) need no IEEE division.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 struct Pt {
     int64_t c;
     float chi, S, w, winv, beta, theta;
@@ -115,8 +125,9 @@ __device__ __noinline__ bool img_trapezoid_fp64(const ImgArgs &a, double rf, int
 // Optical depth of segment (A -> B) for channel ch; with `want` also its
 // partial derivatives d[0..2] = d/d(log T_A, log n_A, beta_A) and
 // d[3..5] = the same for B.
-__device__ float seg_dtau(const ImgArgs &a, const Chan &ch, const Pt &A, const Pt &B, float dx, float iwbar, bool want,
-                          float (&d)[6])
+template <bool want>
+__device__ __forceinline__ float seg_dtau(const ImgArgs &a, const Chan &ch, const Pt &A, const Pt &B, float dx,
+                                          float iwbar, float (&d)[6])
 {
     const float za = fmaf(-ch.rf, A.beta, ch.rf1), zb = fmaf(-ch.rf, B.beta, ch.rf1);
     const float du = (zb - za) * iwbar;
@@ -126,7 +137,7 @@ __device__ float seg_dtau(const ImgArgs &a, const Chan &ch, const Pt &A, const P
     if (trap) {
         const float ua = za * A.winv, ub = zb * B.winv;
         const float ga = __expf(-ua * ua), gb = __expf(-ub * ub);
-        if (want) {
+        if constexpr (want) {
             d[0] = 0.5f * dx * A.chi * ga * (A.theta * A.winv * A.winv) * (2.0f * ua * ua - 1.0f);
             d[1] = 0.5f * dx * A.chi * ga;
             d[2] = dx * A.chi * ga * ua * ch.rf * A.winv;
@@ -144,10 +155,10 @@ __device__ float seg_dtau(const ImgArgs &a, const Chan &ch, const Pt &A, const P
     }
     const float E = erfc_fit(lo) - erfc_fit(hi);
     const float Delta = zb - za;
-    const float iD = 1.0f / Delta;
+    const float iD = rcp_approx(Delta);
     const float Kc = dx * (0.25f * kSqrtPiF);
     const float K = Kc * (A.chi * A.w + B.chi * B.w);
-    if (want) {
+    if constexpr (want) {
         const float ea = (2.0f / kSqrtPiF) * __expf(-a_ * a_), eb = (2.0f / kSqrtPiF) * __expf(-b_ * b_);
         const float dza = K * (E * iD - ea * iwbar) * iD;
         const float dzb = K * (eb * iwbar - E * iD) * iD;
@@ -173,7 +184,7 @@ __device__ __forceinline__ void weights(float t, float &E, float &w0, float &w1,
         w0 = t * (0.5f - t * (1.0f / 3.0f - t * (1.0f / 8.0f - t * (1.0f / 30.0f - t * (1.0f / 144.0f)))));
         gp = -0.5f + t * (1.0f / 3.0f - t * (1.0f / 8.0f - t * (1.0f / 30.0f - t * (1.0f / 144.0f))));
     } else {
-        const float rt = 1.0f / t;
+        const float rt = rcp_approx(t);
         const float g = (1.0f - E) * rt;
         w0 = g - E;
         w1 = 1.0f - g;
@@ -262,7 +273,7 @@ __global__ void __launch_bounds__(256) k_image_fwd(ImgArgs a)
             for (int i = 0; i < n; ++i) {
                 const Pt B = staged_pt(a, geo, nullptr, pid, i, ch.l, false);
                 if (c0 + i > 0) {
-                    const float t = seg_dtau(a, ch, A, B, geo[i].w, siw[i], false, dd);
+                    const float t = seg_dtau<false>(a, ch, A, B, geo[i].w, siw[i], dd);
                     float E, w0, w1, gp;
                     weights(t, E, w0, w1, gp);
                     I = fmaf(E, I, fmaf(w0, A.S, w1 * B.S));
@@ -321,6 +332,8 @@ __global__ void __launch_bounds__(128) k_image_adj(ImgArgs a)
         float I = ch.I0;
         {
             Pt A{};
+            int64_t next_ck = 0;                           // segment d of the next checkpoint (every s-th)
+            int ick = 0;
             for (int64_t c0 = 0; c0 <= D; c0 += kImgStage) {
                 const int n = (int)min((int64_t)kImgStage, D + 1 - c0);
                 stage_points(a, base, c0, n, false, geo, siw, sth, pid);
@@ -328,8 +341,11 @@ __global__ void __launch_bounds__(128) k_image_adj(ImgArgs a)
                     const Pt B = staged_pt(a, geo, sth, pid, i, ch.l, false);
                     const int64_t d = c0 + i - 1;              // the segment ending at this point
                     if (d >= 0) {
-                        if (d % s == 0) ck[d / s] = I;
-                        const float t = seg_dtau(a, ch, A, B, geo[i].w, siw[i], false, dd);
+                        if (d == next_ck) {
+                            ck[ick++] = I;
+                            next_ck += s;
+                        }
+                        const float t = seg_dtau<false>(a, ch, A, B, geo[i].w, siw[i], dd);
                         float E, w0, w1, gp;
                         weights(t, E, w0, w1, gp);
                         I = fmaf(E, I, fmaf(w0, A.S, w1 * B.S));
@@ -349,7 +365,7 @@ __global__ void __launch_bounds__(128) k_image_adj(ImgArgs a)
                 const int i = (int)(d - d0) + 1;
                 loc[i - 1] = Ir;
                 const Pt B = staged_pt(a, geo, sth, pid, i, ch.l, false);
-                const float t = seg_dtau(a, ch, A, B, geo[i].w, siw[i], false, dd);
+                const float t = seg_dtau<false>(a, ch, A, B, geo[i].w, siw[i], dd);
                 float E, w0, w1, gp;
                 weights(t, E, w0, w1, gp);
                 Ir = fmaf(E, Ir, fmaf(w0, A.S, w1 * B.S));
@@ -359,7 +375,7 @@ __global__ void __launch_bounds__(128) k_image_adj(ImgArgs a)
                 const int i = (int)(d - d0);
                 const Pt Pa = staged_pt(a, geo, sth, pid, i, ch.l, true);
                 const Pt Pb = staged_pt(a, geo, sth, pid, i + 1, ch.l, true);
-                const float t = seg_dtau(a, ch, Pa, Pb, geo[i + 1].w, siw[i + 1], true, dd);
+                const float t = seg_dtau<true>(a, ch, Pa, Pb, geo[i + 1].w, siw[i + 1], dd);
                 float E, w0, w1, gp;
                 weights(t, E, w0, w1, gp);
                 const float dIdt = -E * loc[i] + (gp + E) * Pa.S - gp * Pb.S;

@@ -246,7 +246,7 @@ mgt_status launch_stat_eq(mgt_model *m, cudaStream_t s)
     if (wpb < 1) return set_error(MGT_ERR_ARG, "statistical equilibrium: too many levels/lines for shared memory");
     a.wpb = wpb;
     const size_t smem = per_warp * wpb;
-    MGT_CUDA(cudaFuncSetAttribute(k_se, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MGT_TRY_STATUS(raise_smem_limit((const void *)k_se, smem));
     {
         MGT_KTIMER("k_se", s);
         k_se<<<ceil_div(m->N, wpb), 32 * wpb, smem, s>>>(a);
@@ -275,7 +275,7 @@ mgt_status se_batch_args(const mgt_model *m, void *args, int64_t *blocks, size_t
 
 mgt_status se_batch_prepare(size_t smem)
 {
-    MGT_CUDA(cudaFuncSetAttribute(k_se_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MGT_TRY_STATUS(raise_smem_limit((const void *)k_se_batch, smem));
     return MGT_OK;
 }
 

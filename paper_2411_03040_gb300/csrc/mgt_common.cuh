@@ -224,6 +224,13 @@ void note_launches(long long n);
 mgt_status launch_formal_solve(mgt_model *m, mgt_precision p, cudaStream_t s, bool accumulate);
 int fs_lines_per_thread(const mgt_model *m, mgt_precision p);
 
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least smem bytes.  It never lowers the limit, so launches of one kernel with
+// different sizes (any model, any batch) all stay valid, and it calls the
+// runtime only when the limit grows, so a launch prepared once makes no
+// attribute call while its stream is being captured.
+mgt_status raise_smem_limit(const void *func, size_t smem);
+
 // batched launches over many models (argument tables built per model, read on
 // the device by table slot; see batch.cu)
 size_t fs_args_bytes();
@@ -236,6 +243,12 @@ mgt_status fs_batch_grid(int threads, int fused, int lines, size_t smem, size_t 
 mgt_status fs_batch_launch(const void *d_args, const int64_t *d_item_end, int n_models, int64_t n_items,
                            unsigned long long *d_next, int threads, int fused, int lines, size_t smem, int grid,
                            cudaStream_t s);
+// resident CTAs on the device of the model's persistent instance (0 if unknown)
+int64_t fs_batch_wave(const void *args, int threads, size_t smem);
+// one model's formal solution in a batch through its single-model launch
+// (the automatic staged schedule: the same values as the persistent launch);
+// run = false prepares it (kernel attributes) without launching
+mgt_status fs_batch_solo(mgt_model *m, cudaStream_t s, bool run);
 size_t se_args_bytes();
 mgt_status se_batch_args(const mgt_model *m, void *args, int64_t *blocks, size_t *smem);
 mgt_status se_batch_prepare(size_t smem);

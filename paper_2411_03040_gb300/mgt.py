@@ -70,7 +70,8 @@ class mgt_kernel_time(ctypes.Structure):
 
 class mgt_batch_layout(ctypes.Structure):
     _fields_ = [("n_models", _i32), ("fs_items", _i64), ("fs_grid", _i32), ("fs_threads", _i32),
-                ("fs_smem_bytes", _i64), ("se_blocks", _i64), ("graph_kernels", _i32), ("fs_launches", _i32)]
+                ("fs_smem_bytes", _i64), ("se_blocks", _i64), ("graph_kernels", _i32), ("fs_launches", _i32),
+                ("fs_solo", _i32)]
 
 
 # name -> argtypes (every function returns an int status, except mgt_last_error)

@@ -120,6 +120,42 @@ def test_batch_iterate_graph_matches_ali_per_model(mgt, batch_models, ng_mode):
     assert mgt.mgt_batch_get_layout(b)["graph_kernels"] == 3 + 2 * lay["fs_launches"]
 
 
+def test_large_model_runs_its_single_model_launch_inside_the_batch(mgt):
+    # a 40k-point 4-line model is more than 8 waves of its persistent class
+    # (one-warp CTAs, 16 per SM): the batch launches it through the
+    # single-model kernel, also inside the captured iteration; the small model
+    # stays in a persistent launch.  Both give the single-model values.
+    models = [synth.sphere_model(40_000, 5, 1, 31, seed=401, name="big"),
+              synth.sphere_model(600, 21, 1, 31, seed=402, name="small")]
+    ref = []
+    for m in models:
+        h = _handle(mgt, m, 4)
+        mgt.mgt_set_solve_opts(h, lines_per_thread=4, schedule=0)
+        J, L = mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED)
+        st = mgt.mgt_ali_solve(h, n_iter=3, precision=mgt.MGT_FP32_MIXED, ng_mode=0)
+        ref.append((J, L, mgt.mgt_get_populations(h)))
+    hs = []
+    for m in models:
+        h = _handle(mgt, m, 4)
+        mgt.mgt_set_solve_opts(h, lines_per_thread=4, schedule=0)
+        hs.append(h)
+    b = mgt.mgt_batch_create(hs)
+    lay = mgt.mgt_batch_get_layout(b)
+    assert lay["fs_solo"] == 1 and lay["fs_launches"] == 2
+    assert lay["order"].tolist() == [1, 0]              # the model launched on its own last
+    mgt.mgt_batch_formal_solve(b)
+    for h, (J, L, _) in zip(hs, ref):
+        Jb, Lb = mgt.mgt_get_jbar(h)
+        np.testing.assert_array_equal(Jb, J)
+        np.testing.assert_array_equal(Lb, L)
+    for h in hs:
+        mgt.mgt_set_populations(h)                        # back to LTE
+    mgt.mgt_batch_iterate(b, n_iter=3)
+    assert mgt.mgt_batch_get_layout(b)["graph_kernels"] == 3 + 2 * 2
+    for h, (_, _, P) in zip(hs, ref):
+        np.testing.assert_array_equal(mgt.mgt_get_populations(h), P)
+
+
 def test_batch_follows_model_changes(mgt, batch_models):
     hs = [_handle(mgt, m, s[4]) for m, s in zip(batch_models[:3], SPECS[:3])]
     b = mgt.mgt_batch_create(hs)
