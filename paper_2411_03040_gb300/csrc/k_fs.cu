@@ -64,6 +64,12 @@ template <> struct Prec<float> {
     }
     static __device__ __forceinline__ float gauss(float u) { return __expf(-__fmul_rn(u, u)); }
     static __device__ __forceinline__ float erfc_(float x) { return mgt::erfc_fit(x); }
+    // erfc(a) - erfc(b), the two fits on packed FP32
+    static __device__ __forceinline__ float erfc_diff(float a, float b)
+    {
+        const float2 r = mgt::erfc_fit2(a, b);
+        return __fsub_rn(r.x, r.y);
+    }
     // explicitly rounded operations (never contracted differently by context)
     static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
@@ -78,6 +84,7 @@ template <> struct Prec<double> {
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double gauss(double u) { return exp(-__dmul_rn(u, u)); }
     static __device__ __forceinline__ double erfc_(double x) { return erfc(x); }
+    static __device__ __forceinline__ double erfc_diff(double a, double b) { return __dsub_rn(erfc(a), erfc(b)); }
     static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
@@ -235,7 +242,7 @@ __device__ __forceinline__ void segment_coefs(bool trap, T dx, T du, T z_f, T g_
             a = -b;
             b = -t;
         }
-        const T E = P::sub(P::erfc_(a), P::erfc_(b));
+        const T E = P::erfc_diff(a, b);
         const T kk = P::mul(P::mul(P::mul(P::mul(dx, T(0.125 * kSqrtPi)), E), iwbar), P::rcp(du));
         cf = P::mul(kk, w_f);
         cn = P::mul(kk, w_n);

@@ -86,16 +86,6 @@ __device__ Chan channel(const ImgArgs &a, int f)
     return c;
 }
 
-// Reciprocal by the MUFU approximation (relative error about 2^-23): the
-// segment's 1/Delta (|Delta| >= switch x mean width in the erf branch) and
-// 1/t (t >= 0.05 where it is used) need no IEEE division.
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
 struct Pt {
     int64_t c;
     float chi, S, w, winv, beta, theta;
@@ -153,9 +143,12 @@ __device__ __forceinline__ float seg_dtau(const ImgArgs &a, const Chan &ch, cons
         lo = -b_;
         hi = -a_;
     }
-    const float E = erfc_fit(lo) - erfc_fit(hi);
+    const float2 ef = erfc_fit2(lo, hi);          // both fits on packed FP32
+    const float E = ef.x - ef.y;
     const float Delta = zb - za;
-    const float iD = rcp_approx(Delta);
+    // the MUFU reciprocal (relative error about 2^-23): |Delta| >= switch x
+    // mean width in the erf branch, so no IEEE division is needed
+    const float iD = rcp_mufu(Delta);
     const float Kc = dx * (0.25f * kSqrtPiF);
     const float K = Kc * (A.chi * A.w + B.chi * B.w);
     if constexpr (want) {
@@ -184,7 +177,7 @@ __device__ __forceinline__ void weights(float t, float &E, float &w0, float &w1,
         w0 = t * (0.5f - t * (1.0f / 3.0f - t * (1.0f / 8.0f - t * (1.0f / 30.0f - t * (1.0f / 144.0f)))));
         gp = -0.5f + t * (1.0f / 3.0f - t * (1.0f / 8.0f - t * (1.0f / 30.0f - t * (1.0f / 144.0f))));
     } else {
-        const float rt = rcp_approx(t);
+        const float rt = rcp_mufu(t);           // t >= 0.05 here
         const float g = (1.0f - E) * rt;
         w0 = g - E;
         w1 = 1.0f - g;

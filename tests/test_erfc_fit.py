@@ -20,10 +20,11 @@ import fit_erfcx  # noqa: E402
 
 def kernel_coefficients():
     src = open(os.path.join(CSRC, "mgt_erfc.cuh")).read()
-    body = src[src.index("__device__ __forceinline__ float erfc_fit(float x)"):]
-    body = body[:body.index("return x < 0.0f")]
+    body = src[src.index("float kErfcP[11] = {"):]
+    body = body[:body.index("};")]
     vals = [float(v) for v in re.findall(r"([-+]?\d\.\d+e[-+]\d+)f", body)]
-    # first literal is the leading (highest-degree) coefficient
+    assert len(vals) == 11
+    # the array lists the leading (highest-degree) coefficient first
     return np.array(vals[::-1])
 
 
