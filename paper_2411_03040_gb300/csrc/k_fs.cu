@@ -62,7 +62,12 @@ template <> struct Prec<float> {
         asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
         return r;
     }
-    static __device__ __forceinline__ float gauss(float u) { return __expf(-__fmul_rn(u, u)); }
+    // exp(-u^2) = 2^(-u^2 log2 e) with the MUFU exponential, explicitly rounded
+    // (gauss2 below is the same arithmetic on a pair)
+    static __device__ __forceinline__ float gauss(float u)
+    {
+        return mgt::ex2_mufu(__fmul_rn(__fmul_rn(u, u), -mgt::kLog2E));
+    }
     static __device__ __forceinline__ float erfc_(float x) { return mgt::erfc_fit(x); }
     // erfc(a) - erfc(b), the two fits on packed FP32
     static __device__ __forceinline__ float erfc_diff(float a, float b)
@@ -853,6 +858,69 @@ __device__ __forceinline__ typename Prec<T>::V2 segment_item(const FSArgs &a, in
     return V2{cf, cn};
 }
 
+// Two items of the FP32 pre-pass at once on packed FP32 (one lane per item),
+// lane for lane the arithmetic of segment_item / segment_coefs, so the
+// coefficients are bit-identical.  An item's inputs:
+struct PairIn {
+    float dx, z_f, z_n, du, w_f, w_n, rw_f, rw_n;
+    bool trap, band;
+};
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 f2s(float x) { return make_float2(x, x); }
+
+// Both items on the same branch (neither near the switch): their halved
+// {cf, cn} in c0, c1.
+__device__ __forceinline__ void segment_pair(const PairIn &i0, const PairIn &i1, int width_mode, float2 &c0,
+                                             float2 &c1)
+{
+    const float2 dx = f2(i0.dx, i1.dx), wf = f2(i0.w_f, i1.w_f), wn = f2(i0.w_n, i1.w_n);
+    float2 cf, cn;
+    if (i0.trap) {
+        // Gaussians of the far and near points (point_gauss on each lane)
+        const float2 uf = __fmul2_rn(f2(i0.z_f, i1.z_f), f2(i0.rw_f, i1.rw_f));
+        const float2 un = __fmul2_rn(f2(i0.z_n, i1.z_n), f2(i0.rw_n, i1.rw_n));
+        const float2 yf = __fmul2_rn(__fmul2_rn(uf, uf), f2s(-kLog2E));
+        const float2 yn = __fmul2_rn(__fmul2_rn(un, un), f2s(-kLog2E));
+        const float2 gf = f2(ex2_mufu(yf.x), ex2_mufu(yf.y)), gn = f2(ex2_mufu(yn.x), ex2_mufu(yn.y));
+        const float2 q = __fmul2_rn(f2s(0.25f), dx);
+        cf = __fmul2_rn(q, gf);
+        cn = __fmul2_rn(q, gn);
+    } else {
+        float2 iw;
+        if (width_mode == 0) {
+            const float2 h = __fmul2_rn(f2s(0.5f), __ffma2_rn(wf, wf, __fmul2_rn(wn, wn)));
+            iw = f2(rsqrtf(h.x), rsqrtf(h.y));
+        } else {
+            const float2 h = __fmul2_rn(f2s(0.5f), __fadd2_rn(wf, wn));
+            iw = f2(Prec<float>::rcp(h.x), Prec<float>::rcp(h.y));
+        }
+        const float2 du = f2(i0.du, i1.du);
+        float2 a = __fmul2_rn(f2(i0.z_f, i1.z_f), iw);
+        float2 b = __fadd2_rn(a, du);
+        const float2 sab = __fadd2_rn(a, b);
+        if (sab.x < 0.0f) {
+            const float t = a.x;
+            a.x = -b.x;
+            b.x = -t;
+        }
+        if (sab.y < 0.0f) {
+            const float t = a.y;
+            a.y = -b.y;
+            b.y = -t;
+        }
+        const float2 ea = erfc_fit2(a.x, a.y), eb = erfc_fit2(b.x, b.y);
+        const float2 E = __fadd2_rn(ea, f2(-eb.x, -eb.y));
+        const float2 rdu = f2(Prec<float>::rcp(du.x), Prec<float>::rcp(du.y));
+        const float2 kk =
+            __fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(dx, f2s(float(0.125 * kSqrtPi))), E), iw), rdu);
+        cf = __fmul2_rn(kk, wf);
+        cn = __fmul2_rn(kk, wn);
+    }
+    c0 = f2(cf.x, cn.x);
+    c1 = f2(cf.y, cn.y);
+}
+
 // Line-independent coefficients of every (bin, step) of one chunk, shared by
 // the CTA's line groups: coef[(k - k_lo) * Q + q] = halved {cf, cn} of step k.
 // Two ways to share the items among the CTA's threads:
@@ -903,6 +971,70 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
         const int dk = stride / a.Q, dq = stride - dk * a.Q;
         const int it0 = tid >= pw ? bd - 1 - tid : items;
         int kk = it0 / a.Q, q = it0 - kk * a.Q;
+        if constexpr (sizeof(T) == 4) {
+            if (a.subdiv == 0 && a.Gb <= 3) {
+                // two items per trip (it and it + stride), on packed FP32 when
+                // both take the same branch away from the switch.  Where at
+                // most three line groups share the pre-pass it weighs most:
+                // 10 and 20 lines 4 and 3 % faster; at 5 groups (40 lines) the
+                // single-item loop stays ahead
+                auto item_in = [&](int kk_, int q_, PairIn &in, StepG<T> &sf, T &Aq, T &Bq, T &beta_n) {
+                    const int k = k_lo + kk_, jf = kk_ + 1;
+                    sf = step_from<T>(Sb + jf * SB);
+                    beta_n = k > 1 ? step_from<T>(Sb + kk_ * SB).beta : T(0);
+                    Aq = sA[q_];
+                    Bq = sB[q_];
+                    in.dx = sf.dx;
+                    in.z_f = bin_z<T>(Aq, Bq, sf.beta);
+                    in.z_n = bin_z<T>(Aq, Bq, beta_n);
+                    in.w_f = Rb[jf * a.RS + 2 * a.Mpad];
+                    in.w_n = Rb[kk_ * a.RS + 2 * a.Mpad];
+                    in.rw_f = Rb[jf * a.RS + 2 * a.Mpad + 1];
+                    in.rw_n = Rb[kk_ * a.RS + 2 * a.Mpad + 1];
+                    in.du = -Prec<T>::mul(Bq, sf.dbw);
+                    in.trap = fabs(in.du) < (T)a.thr;
+                    in.band = fabs(fabs(in.du) - (T)a.thr) < T(kSwitchBand) * (T)a.thr;
+                };
+                auto single = [&](int kk_, int q_, const StepG<T> &sf, T Aq, T Bq, const PairIn &in) {
+                    one(kk_, q_, Aq, Bq, sf, in.z_f, [&] {
+                        return V2{point_gauss<T>(in.z_f, in.rw_f), point_gauss<T>(in.z_n, in.rw_n)};
+                    });
+                };
+#pragma unroll 1
+                for (int it = it0; it < items; it += 2 * stride) {
+                    int kk1 = kk + dk, q1 = q + dq;
+                    if (q1 >= a.Q) {
+                        q1 -= a.Q;
+                        ++kk1;
+                    }
+                    PairIn in0, in1;
+                    StepG<T> sf0, sf1;
+                    T A0, B0, bn0, A1, B1, bn1;
+                    item_in(kk, q, in0, sf0, A0, B0, bn0);
+                    if (it + stride < items) {
+                        item_in(kk1, q1, in1, sf1, A1, B1, bn1);
+                        if (!in0.band && !in1.band && in0.trap == in1.trap) {
+                            float2 c0, c1;
+                            segment_pair(in0, in1, a.width_mode, c0, c1);
+                            coef[kk * a.Q + q] = c0;
+                            coef[kk1 * a.Q + q1] = c1;
+                        } else {
+                            single(kk, q, sf0, A0, B0, in0);
+                            single(kk1, q1, sf1, A1, B1, in1);
+                        }
+                    } else {
+                        single(kk, q, sf0, A0, B0, in0);
+                    }
+                    kk = kk1 + dk;
+                    q = q1 + dq;
+                    if (q >= a.Q) {
+                        q -= a.Q;
+                        ++kk;
+                    }
+                }
+                return;
+            }
+        }
 #pragma unroll 1
         for (int it = it0; it < items; it += stride) {
             const int k = k_lo + kk;

@@ -313,7 +313,10 @@ __global__ void __launch_bounds__(128) k_image_adj(ImgArgs a)
     const int64_t q = blockIdx.x;
     const int64_t base = a.off[q];
     const int64_t D = a.off[q + 1] - base - 1;
-    const int64_t s = D > 0 ? (D + kCk - 1) / kCk : 1;      // segments per block (<= kBlk, checked on the host)
+    // segments per checkpoint block: as many as a block holds (kBlk), so that a
+    // short ray is one block (one staging of its points); at most kCk blocks
+    // because the host admits rays of up to kCk * kBlk segments
+    const int64_t s = D > 0 ? min(D, (int64_t)kBlk) : 1;
     const int64_t nblk = D > 0 ? (D + s - 1) / s : 0;
     float dd[6];
     float ck[kCk], loc[kBlk];
