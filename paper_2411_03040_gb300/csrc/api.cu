@@ -524,6 +524,8 @@ static mgt_status build_model(mgt_model *m, const mgt_model_desc *d, cudaStream_
             const int64_t deg = d->nbr_offsets[i + 1] - d->nbr_offsets[i];
             ne += deg > 0 ? deg : 1;
         }
+        // the packed entries carry their rows' offsets as 32-bit integers
+        if (ne + 16 > (int64_t)0x7fffffff) return set_error(MGT_ERR_ARG, "more than 2^31 - 1 neighbour entries");
         m->n_ent = ne + 16;
         MGT_TRY(dalloc(&m->d_ent, 2 * (size_t)m->n_ent));
         MGT_TRY(dalloc(&m->d_ent_off, (size_t)N));
