@@ -284,9 +284,12 @@ def pinned_copy(model):
 
 
 def issue_roof(sm_max_mhz):
-    """SMs of the current device and its issue roof in T lane-ops/s: SMs x 4
-    schedulers x 32 lanes x the SM clock (one FP32, packed-FP32 or MUFU
-    instruction per lane per issue slot)."""
+    """SMs of the current device and its FP32 roof in T lane-ops/s: SMs x 128
+    FP32 lanes (4 schedulers, each with two 16-lane FMA pipes) x the SM clock.
+    It equals the issue roof (4 schedulers x 32 lanes); a packed FP32
+    instruction's 64 lane-ops occupy both FMA pipes, so packing saves issue
+    slots, not pipe cycles.  MUFU lane-ops are counted against the same
+    budget."""
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     return sms, sms * 4 * 32 * sm_max_mhz * 1e6 / 1e12
@@ -433,8 +436,9 @@ def run_mine(args, model, cfg, emit=True, n_error_origins=None, min_warmup=3):
         "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak,
         "traffic": (tr["dram_bytes_per_traced_step"] * tst["total_steps"] if tr else None),
         "traffic_source": (tr["source"] if tr else None),
-        "peak_source": f"{src} SM clock: issue roof {n_sms} SMs (read from the device) x 4 schedulers x 32 lanes x "
-                       f"{sm_max:.0f} MHz (one FP32 or MUFU lane-op per issue slot)",
+        "peak_source": f"{src} SM clock: FP32 roof {n_sms} SMs (read from the device) x 128 FP32 lanes x "
+                       f"{sm_max:.0f} MHz (= the issue roof; packed FP32 saves issue slots, not FMA-pipe "
+                       f"cycles; MUFU lane-ops counted against the same budget)",
         "ops_per_line_step": OPS_PER_LINE_STEP, "ops_per_bin_step": OPS_PER_BIN_STEP,
         "ops_per_launch": ops, "line_steps_per_launch": line_steps, "bin_steps_per_launch": bin_steps,
         "launch_ms": fs_ms, "launch_ms_source": "CUDA events around each k_fs_staged launch (library kernel "
@@ -713,7 +717,7 @@ def run_batch(args):
         "roofline": {"bound": "alu", "kernel": "k_fs_batch<float,30/14> (persistent launches of the small models) "
                                                    "+ k_fs_staged (models of 8 waves or more), two-row elimination",
                      "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak, "traffic": None,
-                     "peak_source": f"{src} SM clock: issue roof {n_sms} SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz",
+                     "peak_source": f"{src} SM clock: FP32 roof {n_sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz",
                      "line_steps_per_launch": line_steps, "bin_steps_per_launch": bin_steps,
                      "ops_per_line_step": OPS_PER_LINE_STEP, "ops_per_bin_step": OPS_PER_BIN_STEP, "launch_ms": fs_ms,
                      "launch_ms_source": "CUDA events around each formal-solve launch of the batch (library kernel "
