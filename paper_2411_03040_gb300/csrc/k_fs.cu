@@ -972,12 +972,11 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
         const int it0 = tid >= pw ? bd - 1 - tid : items;
         int kk = it0 / a.Q, q = it0 - kk * a.Q;
         if constexpr (sizeof(T) == 4) {
-            if (a.subdiv == 0 && a.Gb <= 3) {
-                // two items per trip (it and it + stride), on packed FP32 when
-                // both take the same branch away from the switch.  Where at
-                // most three line groups share the pre-pass it weighs most:
-                // 10 and 20 lines 4 and 3 % faster; at 5 groups (40 lines) the
-                // single-item loop stays ahead
+            if (a.subdiv == 0) {
+                // two adjacent items per trip (bins q and q + 1 of one step,
+                // or the last bin of a step and the first of the next), on
+                // packed FP32 when both take the same branch away from the
+                // switch
                 auto item_in = [&](int kk_, int q_, PairIn &in, StepG<T> &sf, T &Aq, T &Bq, T &beta_n) {
                     const int k = k_lo + kk_, jf = kk_ + 1;
                     sf = step_from<T>(Sb + jf * SB);
@@ -1000,36 +999,41 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
                         return V2{point_gauss<T>(in.z_f, in.rw_f), point_gauss<T>(in.z_n, in.rw_n)};
                     });
                 };
+                const int npairs = (items + 1) >> 1;
+                const int pstride2 = 2 * stride;
+                const int dk2 = pstride2 / a.Q, dq2 = pstride2 - dk2 * a.Q;
+                const int p0 = tid >= pw ? bd - 1 - tid : npairs;
+                int kk0 = (2 * p0) / a.Q, q0 = 2 * p0 - kk0 * a.Q;
 #pragma unroll 1
-                for (int it = it0; it < items; it += 2 * stride) {
-                    int kk1 = kk + dk, q1 = q + dq;
+                for (int pi = p0; pi < npairs; pi += stride) {
+                    int kk1 = kk0, q1 = q0 + 1;
                     if (q1 >= a.Q) {
-                        q1 -= a.Q;
+                        q1 = 0;
                         ++kk1;
                     }
                     PairIn in0, in1;
                     StepG<T> sf0, sf1;
                     T A0, B0, bn0, A1, B1, bn1;
-                    item_in(kk, q, in0, sf0, A0, B0, bn0);
-                    if (it + stride < items) {
+                    item_in(kk0, q0, in0, sf0, A0, B0, bn0);
+                    if (2 * pi + 1 < items) {
                         item_in(kk1, q1, in1, sf1, A1, B1, bn1);
                         if (!in0.band && !in1.band && in0.trap == in1.trap) {
                             float2 c0, c1;
                             segment_pair(in0, in1, a.width_mode, c0, c1);
-                            coef[kk * a.Q + q] = c0;
+                            coef[kk0 * a.Q + q0] = c0;
                             coef[kk1 * a.Q + q1] = c1;
                         } else {
-                            single(kk, q, sf0, A0, B0, in0);
+                            single(kk0, q0, sf0, A0, B0, in0);
                             single(kk1, q1, sf1, A1, B1, in1);
                         }
                     } else {
-                        single(kk, q, sf0, A0, B0, in0);
+                        single(kk0, q0, sf0, A0, B0, in0);
                     }
-                    kk = kk1 + dk;
-                    q = q1 + dq;
-                    if (q >= a.Q) {
-                        q -= a.Q;
-                        ++kk;
+                    kk0 += dk2;
+                    q0 += dq2;
+                    if (q0 >= a.Q) {
+                        q0 -= a.Q;
+                        ++kk0;
                     }
                 }
                 return;
