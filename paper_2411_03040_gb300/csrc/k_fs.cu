@@ -474,6 +474,47 @@ __device__ __forceinline__ void combine_accumulate(T wqn, const T (&So)[LPT], co
     }
 }
 
+// Slot of accumulator / first-half value c (0..2) of the thread's line l in
+// the staged item's shared arrays: FP32 keeps line pairs adjacent ([3][LPT/2]
+// [bd][2]) for float2 accesses, FP64 the plain [3][LPT][bd] layout.
+template <typename T, int LPT> __device__ __forceinline__ int pair_slot(int c, int l, int bd, int tid)
+{
+    if constexpr (sizeof(T) == 4)
+        return ((c * (LPT / 2) + l / 2) * bd + tid) * 2 + (l & 1);
+    else
+        return (c * LPT + l) * bd + tid;
+}
+
+// combine_accumulate on line pairs in packed FP32 with explicit roundings,
+// the accumulators in the pair_slot layout (float2 per line pair).
+template <int LPT>
+__device__ __forceinline__ void combine_accumulate_packed(float wqn, const float (&So)[LPT], const float (&PL)[LPT],
+                                                          const float (&YL)[LPT], const float (&aL)[LPT],
+                                                          const float (&PR)[LPT], const float (&YR)[LPT],
+                                                          const float (&aR)[LPT], float *acc, int bd, int tid)
+{
+    float2 *a2 = reinterpret_cast<float2 *>(acc);
+    const float2 w2 = make_float2(wqn, wqn);
+#pragma unroll
+    for (int l = 0; l < LPT; l += 2) {
+        const float2 h = __fadd2_rn(make_float2(aL[l], aL[l + 1]), make_float2(aR[l], aR[l + 1]));
+        const float2 den = __ffma2_rn(make_float2(0.5f, 0.5f),
+                                      __fadd2_rn(make_float2(PL[l], PL[l + 1]), make_float2(PR[l], PR[l + 1])), h);
+        const float2 inv = make_float2(Prec<float>::rcp(den.x), Prec<float>::rcp(den.y));
+        const float2 num = __fadd2_rn(__ffma2_rn(make_float2(So[l], So[l + 1]), h, make_float2(YL[l], YL[l + 1])),
+                                      make_float2(YR[l], YR[l + 1]));
+        const float2 u = __fmul2_rn(num, inv), Ls = __fmul2_rn(h, inv);
+        float2 *sJ = a2 + (0 * (LPT / 2) + l / 2) * bd + tid, *cJ = a2 + (1 * (LPT / 2) + l / 2) * bd + tid;
+        float2 *sL = a2 + (2 * (LPT / 2) + l / 2) * bd + tid;
+        const float2 s0 = *sJ, c0 = *cJ;
+        const float2 y = __ffma2_rn(w2, u, make_float2(-c0.x, -c0.y));
+        const float2 tt = __fadd2_rn(s0, y);
+        *cJ = __fadd2_rn(__fadd2_rn(tt, make_float2(-s0.x, -s0.y)), make_float2(-y.x, -y.y));
+        *sJ = tt;
+        *sL = __ffma2_rn(w2, Ls, *sL);
+    }
+}
+
 // B_nu_q(T_bg) / U_line for the thread's bin and lines (depends on the origin
 // through nu_q = nu (1 + x_q w_o)).
 template <typename T, int LPT>
@@ -1123,7 +1164,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
             ibg[(gl * LPT + l) * a.Q + q] = Ibg[l];
-            for (int c = 0; c < 3; ++c) acc[(c * LPT + l) * bd + tid] = T(0);
+            for (int c = 0; c < 3; ++c) acc[pair_slot<T, LPT>(c, l, bd, tid)] = T(0);
         }
     }
     __syncthreads();
@@ -1294,9 +1335,9 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                 if (active) {
 #pragma unroll
                     for (int l = 0; l < LPT; ++l) {
-                        half0[(0 * LPT + l) * bd + tid] = P[l];
-                        half0[(1 * LPT + l) * bd + tid] = Y[l];
-                        half0[(2 * LPT + l) * bd + tid] = aa[l];
+                        half0[pair_slot<T, LPT>(0, l, bd, tid)] = P[l];
+                        half0[pair_slot<T, LPT>(1, l, bd, tid)] = Y[l];
+                        half0[pair_slot<T, LPT>(2, l, bd, tid)] = aa[l];
                     }
                 }
             } else if (active) {
@@ -1304,11 +1345,14 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                 load_vec<LPT>(reinterpret_cast<const T *>(a.line) + o * a.RS + a.Mpad + line0, So);
 #pragma unroll
                 for (int l = 0; l < LPT; ++l) {
-                    PL[l] = half0[(0 * LPT + l) * bd + tid];
-                    YL[l] = half0[(1 * LPT + l) * bd + tid];
-                    aL[l] = half0[(2 * LPT + l) * bd + tid];
+                    PL[l] = half0[pair_slot<T, LPT>(0, l, bd, tid)];
+                    YL[l] = half0[pair_slot<T, LPT>(1, l, bd, tid)];
+                    aL[l] = half0[pair_slot<T, LPT>(2, l, bd, tid)];
                 }
-                combine_accumulate<T, LPT>(wqn, So, PL, YL, aL, P, Y, aa, acc, bd, tid);
+                if constexpr (sizeof(T) == 4)
+                    combine_accumulate_packed<LPT>(wqn, So, PL, YL, aL, P, Y, aa, acc, bd, tid);
+                else
+                    combine_accumulate<T, LPT>(wqn, So, PL, YL, aL, P, Y, aa, acc, bd, tid);
             }
         }
     }
@@ -1333,9 +1377,8 @@ done:
         for (int l = 0; l < LPT; ++l) {
             if (line0 + l < a.M) {
                 red[(0 * Mb + lb + l) * a.Q + q] =
-                    (double)acc[(0 * LPT + l) * bd + tid] - (double)acc[(1 * LPT + l) * bd + tid];
-                red[(1 * Mb + lb + l) * a.Q + q] =
-                    (double)acc[(2 * LPT + l) * bd + tid];
+                    (double)acc[pair_slot<T, LPT>(0, l, bd, tid)] - (double)acc[pair_slot<T, LPT>(1, l, bd, tid)];
+                red[(1 * Mb + lb + l) * a.Q + q] = (double)acc[pair_slot<T, LPT>(2, l, bd, tid)];
             }
         }
     }
