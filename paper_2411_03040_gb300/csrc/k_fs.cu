@@ -415,28 +415,30 @@ __device__ __forceinline__ void renormalize_packed(float (&P)[LPT], float (&Y)[L
     }
 }
 
-// Range guard of the two-row form.  A row's half depth is at most
+// Range of the two-row form.  A row's half depth is at most
 // 0.5 dx (chi~max_far + chi~max_near), with chi~max the largest chi~' of a
 // point over the lines: the trapezoid has cf <= dx/4, the semi-analytic form
 // |erf difference| <= (2/sqrt(pi)) |du|, so cf <= dx w_far/(4 wbar) <= dx/2
 // for either averaged width.  A point's row stores
 //   G = max(chi~max dxmax / kFastB, S'max / kFastS)
-// with dxmax its longest graph edge (every walk step is a graph edge), so a
-// row between two points with G <= 1 has a half depth <= kFastB and sources
-// <= kFastS.  The elimination of a half-ray takes two rows at a time as long
-// as every row so far was such a row, the half-ray is shorter than
-// kFastSteps, its background is <= kFastY and the optical depths are the
-// switch rule's (not the subdivided reference's).  Then alpha, beta <= 2^8 (h <= 2^9), Pi <= 2^16 at
-// every row (Pi' <= 1/beta after a row, and it grows by less than 2^-13 per
-// row while beta < 2^-15, so rising past 2^16 takes more than 2^27 rows),
-// Y < 2^117 (Y grows by at most S' h <= 2^89 per row), and within a two-row
-// step d < 2^26 after the first row, then p < 2^37, y < 2^117, d < 2^46: all
-// finite and normal in FP32.  From the first row past the bounds on, the
-// half-ray is eliminated one row at a time.
+// with dxmax its longest graph edge (every walk step is a graph edge), and the
+// line data set the model's range flag when any point has G > 1, a
+// non-finite figure or a Doppler width of 1 % of c or more (below that the
+// background stays under kFastY whatever the line and T_bg).  With the flag
+// clear, every row between two points has a half depth <= kFastB and sources
+// <= kFastS, and on a half-ray shorter than kFastSteps with the switch rule's
+// optical depths (not the subdivided reference's): alpha, beta <= 2^8
+// (h <= 2^9), Pi <= 2^16 at every row (Pi' <= 1/beta after a row, and it
+// grows by less than 2^-13 per row while beta < 2^-15, so rising past 2^16
+// takes more than 2^27 rows), Y < 2^117 (Y grows by at most S' h <= 2^89 per
+// row), and within a two-row step d < 2^26 after the first row, then
+// p < 2^37, y < 2^117, d < 2^46: all finite and normal in FP32.  A model with
+// the flag set is eliminated one row at a time (k_fs_exact).
 constexpr float kFastB = kTwoRowDepth;           // 2^8
 constexpr float kFastY = 1.2676506002282294e30f;  // 2^100
 constexpr float kFastS = kTwoRowSource;           // 2^80
-static_assert(kFastB == 256.0f && kFastS == 1.2089258196146292e24f, "range of the two-row elimination");
+static_assert(kFastB == 256.0f && kFastS == 1.2089258196146292e24f && kFastY == 1.2676506002282294e30f,
+              "range of the two-row elimination");
 constexpr int kFastSteps = 1 << 27;
 
 template <typename T, int LPT>
