@@ -219,6 +219,31 @@ def test_per_thread_coefficients_need_one_line_group(mgt):
     assert e.value.status == mgt.MGT_ERR_ARG and "one group" in str(e.value)
 
 
+@pytest.mark.parametrize("q,levels,lpt", [(1, 5, 4), (2, 11, 8), (64, 41, 8), (64, 41, 4), (64, 5, 4)],
+                         ids=["1bin-4lines", "2bins-10lines", "64bins-40lines-lpt8", "64bins-40lines-lpt4",
+                              "64bins-4lines"])
+def test_extreme_bin_counts_and_line_blocks(mgt, q, levels, lpt):
+    # the smallest and largest bin counts the model accepts: with 1 bin every
+    # pre-pass pair spans two steps, with 2 bins every pair is one step; 64
+    # bins leave room for 4 line groups per CTA, so 40 lines take 2 (8 per
+    # thread) or 3 (4 per thread) line blocks per origin, the last one partly
+    # empty.  Every schedule that applies (gather, staged, and per-thread
+    # coefficients where the lines fit one group), both precisions, all points.
+    m = synth.sphere_model(500, n_levels=levels, nside=1, n_quad=q, seed=31, name=f"bins{q}")
+    rays = O.trace(m)
+    J, L = oracle_fields(m, rays)
+    schedules = [1, 2] + ([4] if m.lines.n_lines <= lpt else [])
+    for sched in schedules:
+        h = mgt.mgt_model_create(m)
+        mgt.mgt_set_solve_opts(h, lines_per_thread=lpt, schedule=sched)
+        mgt.mgt_trace_rays(h)
+        Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP32_MIXED)
+        assert rel_err(Jg, J) < TOL32 and rel_err(Lg, L) < TOL32, sched
+        Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP64)
+        assert rel_err(Jg, J) < TOL64 and rel_err(Lg, L) < TOL64, sched
+        h.close()
+
+
 def test_single_point_model_is_background(mgt):
     # no neighbours: every half-ray is empty, u = I_bg, Lambda* = 0
     lines = synth.linear_rotor(3, np.random.default_rng(0))
