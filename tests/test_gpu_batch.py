@@ -156,6 +156,39 @@ def test_large_model_runs_its_single_model_launch_inside_the_batch(mgt):
         np.testing.assert_array_equal(mgt.mgt_get_populations(h), P)
 
 
+def test_extreme_bin_counts_in_one_batch(mgt):
+    # 1, 2 and 64 bins in one batch: at 64 bins 40 lines take 2 (8 lines per
+    # thread) or 3 (4 per thread) line blocks per origin, each a batch item of
+    # a 256-thread class; J-bar, Lambda* and SE populations bit-identical to
+    # the models' own calls, and the 64-bin 40-line model within the FP32
+    # tolerance of the oracle
+    specs = [(300, 41, 1, 64, 8), (300, 41, 1, 64, 4), (300, 5, 1, 1, 4), (300, 11, 1, 2, 8), (300, 5, 1, 64, 4)]
+    models = [synth.sphere_model(n, L, ns, q, seed=500 + i, name=f"x{i}") for i, (n, L, ns, q, _) in enumerate(specs)]
+    hs = [_handle(mgt, m, s[4]) for m, s in zip(models, specs)]
+    singles = []
+    for h in hs:
+        J, L = mgt.mgt_formal_solve(h, mgt.MGT_FP32_MIXED)
+        mgt.mgt_stat_equilibrium(h, want=False)
+        singles.append((J, L, mgt.mgt_get_populations(h)))
+        mgt.mgt_set_populations(h)                        # back to LTE
+    b = mgt.mgt_batch_create(hs)
+    mgt.mgt_batch_formal_solve(b)
+    for h, (J, L, _) in zip(hs, singles):
+        Jb, Lb = mgt.mgt_get_jbar(h)
+        np.testing.assert_array_equal(Jb, J)
+        np.testing.assert_array_equal(Lb, L)
+    mgt.mgt_batch_stat_equilibrium(b)
+    for h, (_, _, P) in zip(hs, singles):
+        np.testing.assert_array_equal(mgt.mgt_get_populations(h), P)
+    m = models[0]
+    rays = O.trace(m)
+    pops = O.lte_populations(m.temp, m.n_spec, m.lines.energy_J, m.lines.g)
+    chi, S, _ = O.line_chi_S(pops, m.lines)
+    J, L = O.formal_solve(m, rays, chi, S)
+    assert np.max(np.abs(singles[0][0].T - J) / np.abs(J)) < TOL32
+    assert np.max(np.abs(singles[0][1].T - L) / np.abs(L)) < TOL32
+
+
 def test_batch_follows_model_changes(mgt, batch_models):
     hs = [_handle(mgt, m, s[4]) for m, s in zip(batch_models[:3], SPECS[:3])]
     b = mgt.mgt_batch_create(hs)
