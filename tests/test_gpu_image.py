@@ -79,6 +79,41 @@ def test_image_matches_oracle(mgt, case):
     assert np.max(np.abs(out.cpu().numpy() - ref2) / np.abs(ref2)) < 1e-4
 
 
+@pytest.mark.parametrize("npx,npy,nfreq,band", [(1, 1, 1, "centre"), (1, 9, 300, "line"), (5, 1, 2, "wings")],
+                         ids=["1x1-one-channel", "column-300-channels", "row-two-wing-channels"])
+def test_image_degenerate_sizes(mgt, npx, npy, nfreq, band):
+    # one pixel and one channel at the line centre (fmin = fmax); a one-pixel
+    # column of 300 channels (two trips of a 256-thread block over the
+    # channels); a one-pixel row of two channels far in the wings of the first
+    # two lines, where the image is the background
+    m = synth.config_model(1, n_points=800)
+    nu0, nu1 = m.lines.freq_Hz[0], m.lines.freq_Hz[1]
+    lo, hi = {"centre": (nu0, nu0), "line": _band(m), "wings": (0.9 * nu0, 1.1 * nu1)}[band]
+    h = mgt.mgt_model_create(m)
+    img = mgt.mgt_image(h, DIR, npx, npy, nfreq, lo, hi)
+    ref, _ = O.image(m, _pops(m), DIR, npx, npy, nfreq, lo, hi)
+    assert img.shape == ref.shape == (nfreq, npy, npx)
+    err = np.max(np.abs(img - ref) / np.abs(ref))
+    assert err < 1e-4, err
+    if band == "wings":
+        bg = np.array([O.planck(f, m.T_bg) for f in (lo, hi)])
+        assert np.max(np.abs(ref[:, 0, :] / bg[:, None] - 1)) < 1e-6
+    if band == "centre":
+        # the adjoint of the one-pixel, one-channel image: every point of its
+        # ray against the oracle's FP64 gradient, zero off the ray
+        w = np.ones((1, 1, 1), np.float32)
+        grads = mgt.mgt_image_adjoint(h, DIR, 1, 1, 1, lo, hi, w)
+        rays = O.image_rays(m, DIR, 1, 1)
+        refs = O.image_adjoint(m, _pops(m), DIR, 1, 1, 1, lo, hi, w.astype(np.float64), rays=rays)
+        on = np.unique(rays.pts)
+        off = np.setdiff1d(np.arange(m.n_points), on)
+        for key, g, r in zip("Tnv", grads, refs):
+            assert np.all(g[off] == 0) and np.all(r[off] == 0), key
+            scale = np.max(np.abs(r[on]))
+            assert scale > 0, key
+            assert np.all(np.abs(g[on] - r[on]) <= RTOL_ADJ * np.abs(r[on]) + ATOL_ADJ * scale), key
+
+
 def test_adjoint_matches_oracle_gradient(mgt):
     # element by element against the oracle's FP64 reverse sweep, on 64 random
     # points of the pixel rays, all three fields (the velocity gradient lies
