@@ -275,6 +275,29 @@ def test_stat_equilibrium_parity(mgt, sphere):
     np.testing.assert_allclose(pg.sum(1), m.n_spec, rtol=1e-13)
 
 
+@pytest.mark.parametrize("lpt", [4, 8])
+def test_two_level_model(mgt, lpt):
+    # the smallest molecule: two levels, one line (one group of lines padded
+    # to 4 or 8): J-bar and Lambda* in both precisions and the SE populations
+    # from the FP64 J-bar against the oracle
+    m = synth.sphere_model(600, n_levels=2, nside=1, n_quad=15, seed=41, name="two-level")
+    h = mgt.mgt_model_create(m)
+    mgt.mgt_set_solve_opts(h, lines_per_thread=lpt)
+    mgt.mgt_trace_rays(h)
+    rays = O.trace(m)
+    J, L = oracle_fields(m, rays)
+    assert J.shape == (m.n_points, 1)
+    Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP32_MIXED)
+    assert rel_err(Jg, J) < TOL32 and rel_err(Lg, L) < TOL32
+    Jg, Lg = gpu_fields(mgt, h, mgt.MGT_FP64)
+    assert rel_err(Jg, J) < TOL64 and rel_err(Lg, L) < TOL64
+    pg = mgt.mgt_stat_equilibrium(h)
+    p0 = O.lte_populations(m.temp, m.n_spec, m.lines.energy_J, m.lines.g)
+    po = O.stat_equilibrium(p0, J, L, m.temp, m.n_coll, m.n_spec, m.lines)
+    assert rel_err(pg, po) < 1e-8
+    np.testing.assert_allclose(pg.sum(1), m.n_spec, rtol=1e-13)
+
+
 def test_stat_equilibrium_tiny_populations_41_levels(mgt):
     # cold gas: upper levels ~1e-60 of the ground level keep full relative accuracy
     m = synth.shell_model(1500, 41, 1, 7, seed=12, name="cold")
