@@ -851,7 +851,7 @@ __host__ __device__ inline StagedLayout staged_layout(int Q, int Mb, int RS, int
     StagedLayout L;
     const int rowB = RS * (int)sizeof(T);
     const int stage_bytes = 2 * NPT * (SB + rowB);
-    const int coef_bytes = fused ? 0 : 2 * CH * Q * 2 * (int)sizeof(T);
+    const int coef_bytes = fused ? 0 : 2 * (CH + 1) * Q * 2 * (int)sizeof(T);
     const int red_bytes = 2 * Mb * Q * (int)sizeof(double);
     L.stage = 128;
     L.coef = L.stage + up(stage_bytes);
@@ -965,7 +965,10 @@ __device__ __forceinline__ void segment_pair(const PairIn &i0, const PairIn &i1,
 }
 
 // Line-independent coefficients of every (bin, step) of one chunk, shared by
-// the CTA's line groups: coef[(k - k_lo) * Q + q] = halved {cf, cn} of step k.
+// the CTA's line groups: coef[q * cs + (k - k_lo)] = halved {cf, cn} of step k
+// for bin q.  Each bin's steps are contiguous, so the elimination steps its
+// pointer by a constant; the row stride cs = CH + 1 is odd, so the threads of
+// consecutive bins read different banks.
 // Two ways to share the items among the CTA's threads:
 //  * strided (CARRY false): item kk * Q + q to thread (kk * Q + q) mod bd;
 //  * runs (CARRY true): thread t takes bin t mod Q and a run of consecutive
@@ -976,14 +979,14 @@ __device__ __forceinline__ void segment_pair(const PairIn &i0, const PairIn &i1,
 template <typename T, bool CARRY>
 __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, int k_lo, int k_hi,
                                             const unsigned char *Sb, const T *Rb, const T *sA, const T *sB,
-                                            typename Prec<T>::V2 *coef, int tid, int bd)
+                                            typename Prec<T>::V2 *coef, int cs, int tid, int bd)
 {
     using V2 = typename Prec<T>::V2;
     constexpr int SB = sizeof(T) == 4 ? 16 : 32;
     const int nst = k_hi - k_lo + 1;
     // one segment's coefficients into the chunk's buffer
     auto one = [&](int kk, int q, T Aq, T Bq, const StepG<T> &sf, T z_f, auto gpair) {
-        coef[kk * a.Q + q] = segment_item<T>(a, o, r, k_lo + kk, q, Sb, Rb, kk + 1, Aq, Bq, sf, z_f, gpair);
+        coef[q * cs + kk] = segment_item<T>(a, o, r, k_lo + kk, q, Sb, Rb, kk + 1, Aq, Bq, sf, z_f, gpair);
     };
     if constexpr (CARRY) {
         const int nseg = bd / a.Q;                     // Q <= bd: bins x line groups fit the CTA
@@ -1063,8 +1066,8 @@ __device__ __forceinline__ void chunk_coefs(const FSArgs &a, int64_t o, int r, i
                         if (!in0.band && !in1.band && in0.trap == in1.trap) {
                             float2 c0, c1;
                             segment_pair(in0, in1, a.width_mode, c0, c1);
-                            coef[kk0 * a.Q + q0] = c0;
-                            coef[kk1 * a.Q + q1] = c1;
+                            coef[q0 * cs + kk0] = c0;
+                            coef[q1 * cs + kk1] = c1;
                         } else {
                             single(kk0, q0, sf0, A0, B0, in0);
                             single(kk1, q1, sf1, A1, B1, in1);
@@ -1139,7 +1142,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
     int *abort_flag = reinterpret_cast<int *>(smem + 16);
     unsigned char *steps_s = smem + lay.stage;                            // steps [2][NPT][SB]
     unsigned char *rows_s = steps_s + 2 * NPT * SB;                       // rows [2][NPT][rowB]
-    V2 *coef = reinterpret_cast<V2 *>(smem + lay.coef);                   // [2][CH][Q]
+    V2 *coef = reinterpret_cast<V2 *>(smem + lay.coef);                   // [2][Q][CH + 1]
     T *ibg = reinterpret_cast<T *>(smem + lay.ibg);                       // [Mb][Q]
     T *sA = reinterpret_cast<T *>(smem + lay.sab), *sB = sA + a.Q;        // [Q] each
     T *acc = reinterpret_cast<T *>(smem + lay.acc);                       // [3][LPT][bd]
@@ -1207,9 +1210,9 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                 ok = mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1);
                 const unsigned char *Sb = steps_s + (ci & 1) * NPT * SB;
                 const T *Rb = reinterpret_cast<const T *>(rows_s + (ci & 1) * NPT * rowB);
-                V2 *cf_buf = coef + (ci & 1) * CH * a.Q;
+                V2 *cf_buf = coef + (ci & 1) * (CH + 1) * a.Q;
                 if constexpr (!FUSED) {
-                    if (ok) chunk_coefs<T, LPT == 4>(a, o, r, k_lo, k_hi, Sb, Rb, sA, sB, cf_buf, tid, bd);
+                    if (ok) chunk_coefs<T, LPT == 4>(a, o, r, k_lo, k_hi, Sb, Rb, sA, sB, cf_buf, CH + 1, tid, bd);
                 }
                 // one barrier per chunk: this chunk's coefficients are complete, and
                 // everyone is done with the previous chunk (its staging buffer is
@@ -1289,7 +1292,7 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                     // near row's chi is the next step's far chi, so two steps
                     // per trip swap the two chi arrays instead of reloading
                     const T *row = Rb + (k_hi - k_lo + 1) * a.RS + line0;
-                    const V2 *cfp = cf_buf + (k_hi - k_lo) * a.Q + q;
+                    const V2 *cfp = cf_buf + q * (CH + 1) + (k_hi - k_lo);
                     T chiA[LPT], chiB[LPT], S_f[LPT];
                     load_vec<LPT>(row, chiA);
                     int k = k_hi;
@@ -1302,12 +1305,12 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                             load_vec<LPT>(row + a.Mpad, S_f);
                             load_vec<LPT>(row - a.RS, chiB);
                             homog_row1_packed<LPT>(cc.x, cc.y, chiA, S_f, chiB, P, Y, aa, D);
-                            cc = *(cfp - a.Q);
+                            cc = *(cfp - 1);
                             load_vec<LPT>(row - a.RS + a.Mpad, S_f);
                             load_vec<LPT>(row - 2 * a.RS, chiA);
                             homog_row2_packed<LPT>(cc.x, cc.y, chiB, S_f, chiA, P, Y, aa, D);
                             row -= 2 * a.RS;
-                            cfp -= 2 * a.Q;
+                            cfp -= 2;
                         }
                     } else {
 #pragma unroll 1
@@ -1316,12 +1319,12 @@ __device__ __forceinline__ bool fs_staged_item(const FSArgs &a, int64_t oi, int 
                             load_vec<LPT>(row + a.Mpad, S_f);
                             load_vec<LPT>(row - a.RS, chiB);
                             eliminate_row<T, LPT>(cc.x, cc.y, chiA, S_f, chiB, P, Y, aa);
-                            cc = *(cfp - a.Q);
+                            cc = *(cfp - 1);
                             load_vec<LPT>(row - a.RS + a.Mpad, S_f);
                             load_vec<LPT>(row - 2 * a.RS, chiA);
                             eliminate_row<T, LPT>(cc.x, cc.y, chiB, S_f, chiA, P, Y, aa);
                             row -= 2 * a.RS;
-                            cfp -= 2 * a.Q;
+                            cfp -= 2;
                         }
                     }
                     if (k == k_lo) {
