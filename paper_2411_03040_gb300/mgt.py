@@ -159,6 +159,43 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _buffer(fn, name, a, n, dtype, device=None, writable=False):
+    """Check a caller's buffer before its pointer goes to the library, which
+    sees only the pointer: ``n`` elements of ``dtype``, C-contiguous, either a
+    numpy array (host) or a torch tensor on the current CUDA device.
+    ``device`` True or False asks for one of the two kinds.  Returns 1 for a
+    device buffer, 0 for a host one; ValueError otherwise."""
+    dt = np.dtype(dtype)
+    if hasattr(a, "data_ptr"):
+        kind = 1
+        if str(a.dtype) != "torch." + dt.name:
+            raise ValueError(f"{fn}: {name} must be a {dt.name} tensor, not {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError(f"{fn}: {name} must be contiguous")
+        if not a.is_cuda:
+            raise ValueError(f"{fn}: {name} must be a numpy array or a tensor on the current CUDA device")
+        import torch
+        if a.device.index != torch.cuda.current_device():
+            raise ValueError(f"{fn}: {name} must be on the current CUDA device")
+        size = int(a.numel())
+    elif isinstance(a, np.ndarray):
+        kind = 0
+        if a.dtype != dt:
+            raise ValueError(f"{fn}: {name} must be a {dt.name} array, not {a.dtype}")
+        if not a.flags.c_contiguous:
+            raise ValueError(f"{fn}: {name} must be C-contiguous")
+        if writable and not a.flags.writeable:
+            raise ValueError(f"{fn}: {name} is read-only")
+        size = int(a.size)
+    else:
+        raise ValueError(f"{fn}: {name} must be a numpy array or a torch CUDA tensor")
+    if size != n:
+        raise ValueError(f"{fn}: {name} has {size} elements, expected {n}")
+    if device is not None and kind != int(bool(device)):
+        raise ValueError(f"{fn}: {name} must be " + ("a torch CUDA tensor" if device else "a host numpy array"))
+    return kind
+
+
 class Model:
     """Owns one mgt_model handle and keeps its host inputs alive while in use."""
 
@@ -238,7 +275,11 @@ def mgt_get_rays(m: Model, stream=None):
 
 
 def mgt_set_populations(m: Model, pops=None, stream=None):
-    p = None if pops is None else np.ascontiguousarray(pops, np.float64)
+    p = None
+    if pops is not None:
+        s = mgt_model_sizes(m)
+        p = np.ascontiguousarray(pops, np.float64)
+        _buffer("mgt_set_populations", "pops", p, s["n_points"] * s["n_levels"], np.float64, device=False)
     _check(load().mgt_set_populations(m.handle, _ptr(p), _stream(stream)), "mgt_set_populations")
 
 
@@ -246,9 +287,17 @@ def mgt_get_populations(m: Model, out=None, stream=None):
     s = mgt_model_sizes(m)
     if out is None:
         out = np.zeros((s["n_points"], s["n_levels"]), np.float64)
-    on_dev = 1 if hasattr(out, "data_ptr") else 0
+    on_dev = _buffer("mgt_get_populations", "out", out, s["n_points"] * s["n_levels"], np.float64, writable=True)
     _check(load().mgt_get_populations(m.handle, _ptr(out), on_dev, _stream(stream)), "mgt_get_populations")
     return out
+
+
+def _jbar_buffers(fn, Jbar, Lstar, sizes):
+    """Both outputs [M][N] f64, of one memory kind; returns that kind."""
+    n = sizes["n_lines"] * sizes["n_points"]
+    on_dev = _buffer(fn, "Jbar", Jbar, n, np.float64, writable=True)
+    _buffer(fn, "Lstar", Lstar, n, np.float64, device=bool(on_dev), writable=True)
+    return on_dev
 
 
 def mgt_formal_solve(m: Model, precision=MGT_FP32_MIXED, Jbar=None, Lstar=None, want=True, stream=None):
@@ -262,7 +311,7 @@ def mgt_formal_solve(m: Model, precision=MGT_FP32_MIXED, Jbar=None, Lstar=None, 
         Jbar = np.zeros((s["n_lines"], s["n_points"]), np.float64)
     if Lstar is None:
         Lstar = np.zeros((s["n_lines"], s["n_points"]), np.float64)
-    on_dev = 1 if hasattr(Jbar, "data_ptr") else 0
+    on_dev = _jbar_buffers("mgt_formal_solve", Jbar, Lstar, s)
     _check(load().mgt_formal_solve(m.handle, precision, _ptr(Jbar), _ptr(Lstar), on_dev, _stream(stream)),
            "mgt_formal_solve")
     return Jbar, Lstar
@@ -275,7 +324,7 @@ def mgt_get_jbar(m: Model, Jbar=None, Lstar=None, stream=None):
         Jbar = np.zeros((s["n_lines"], s["n_points"]), np.float64)
     if Lstar is None:
         Lstar = np.zeros((s["n_lines"], s["n_points"]), np.float64)
-    on_dev = 1 if hasattr(Jbar, "data_ptr") else 0
+    on_dev = _jbar_buffers("mgt_get_jbar", Jbar, Lstar, s)
     _check(load().mgt_get_jbar(m.handle, _ptr(Jbar), _ptr(Lstar), on_dev, _stream(stream)), "mgt_get_jbar")
     return Jbar, Lstar
 
@@ -287,6 +336,10 @@ def mgt_stat_equilibrium(m: Model, want=True, stream=None, out=None):
         out = np.zeros((s["n_points"], s["n_levels"]), np.float64)
     if not want:
         out = None
+    else:
+        s = mgt_model_sizes(m)
+        _buffer("mgt_stat_equilibrium", "out", out, s["n_points"] * s["n_levels"], np.float64, device=False,
+                writable=True)
     _check(load().mgt_stat_equilibrium(m.handle, _ptr(out), _stream(stream)), "mgt_stat_equilibrium")
     return out
 
@@ -317,7 +370,7 @@ def mgt_image(m: Model, direction, npx, npy, nfreq, fmin, fmax, out=None, stream
     d = _dir(direction)
     if out is None:
         out = np.zeros((nfreq, npy, npx), np.float32)
-    on_dev = 1 if hasattr(out, "data_ptr") else 0
+    on_dev = _buffer("mgt_image", "out", out, int(nfreq) * int(npy) * int(npx), np.float32, writable=True)
     _check(load().mgt_image(m.handle, _ptr(d), npx, npy, nfreq, float(fmin), float(fmax), _ptr(out), on_dev,
                             _stream(stream)), "mgt_image")
     return out
@@ -328,13 +381,18 @@ def mgt_image_adjoint(m: Model, direction, npx, npy, nfreq, fmin, fmax, grad_out
     """(g_logT [N], g_logn [N], g_vel [N][3]) for dL/dI = grad_out.  With a
     torch CUDA ``grad_out`` the outputs must be torch CUDA tensors too."""
     d = _dir(direction)
+    fn = "mgt_image_adjoint"
     on_dev = 1 if hasattr(grad_out, "data_ptr") else 0
+    n = mgt_model_sizes(m)["n_points"]
     if not on_dev:
         grad_out = np.ascontiguousarray(grad_out, np.float32)
-        n = mgt_model_sizes(m)["n_points"]
         g_logT = np.zeros(n) if g_logT is None else g_logT
         g_logn = np.zeros(n) if g_logn is None else g_logn
         g_vel = np.zeros((n, 3)) if g_vel is None else g_vel
+    _buffer(fn, "grad_out", grad_out, int(nfreq) * int(npy) * int(npx), np.float32, device=bool(on_dev))
+    for name, g, k in (("g_logT", g_logT, 1), ("g_logn", g_logn, 1), ("g_vel", g_vel, 3)):
+        if g is not None:
+            _buffer(fn, name, g, k * n, np.float64, device=bool(on_dev), writable=True)
     _check(load().mgt_image_adjoint(m.handle, _ptr(d), npx, npy, nfreq, float(fmin), float(fmax), _ptr(grad_out),
                                     _ptr(g_logT), _ptr(g_logn), _ptr(g_vel), on_dev, _stream(stream)),
            "mgt_image_adjoint")
@@ -361,6 +419,10 @@ def mgt_set_point_fields(m: Model, temp=None, n_spec=None, vel=None, stream=None
     on_dev = 1 if any(hasattr(a, "data_ptr") for a in arrs if a is not None) else 0
     if not on_dev:
         arrs = [None if a is None else np.ascontiguousarray(a, np.float64) for a in arrs]
+    n = mgt_model_sizes(m)["n_points"]
+    for name, a, k in zip(("temp", "n_spec", "vel"), arrs, (1, 1, 3)):
+        if a is not None:
+            _buffer("mgt_set_point_fields", name, a, k * n, np.float64, device=bool(on_dev))
     _check(load().mgt_set_point_fields(m.handle, *[_ptr(a) for a in arrs], on_dev, _stream(stream)),
            "mgt_set_point_fields")
 

@@ -227,3 +227,31 @@ def test_noalloc_wrapper_rejects_bad_tensors_before_the_library():
     for it, pr, msg in cases:
         with pytest.raises(ValueError, match=msg):
             mgt.mgt_ng_extrapolate_noalloc(it, pr)
+
+
+def test_binding_checks_caller_buffers_before_the_library():
+    # the C entry points see only pointers: every wrapper that passes a
+    # caller's array or tensor checks its dtype, size, layout, writability and
+    # memory kind first (these CPU-side cases never reach the library)
+    from paper_2411_03040_gb300 import mgt
+    ok = np.zeros((4, 5), np.float64)
+    assert mgt._buffer("f", "x", ok, 20, np.float64, writable=True) == 0
+    ro = np.zeros((4, 5), np.float64)
+    ro.flags.writeable = False
+    cases = [
+        (np.zeros((4, 5), np.float32), 20, {}, "float64 array"),
+        (np.zeros((4, 4), np.float64), 20, {}, "16 elements, expected 20"),
+        (np.zeros((5, 4), np.float64).T, 20, {}, "C-contiguous"),
+        (ro, 20, {"writable": True}, "read-only"),
+        ([0.0] * 20, 20, {}, "numpy array or a torch CUDA tensor"),
+        (ok, 20, {"device": True}, "torch CUDA tensor"),
+    ]
+    for a, n, kw, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            mgt._buffer("f", "x", a, n, np.float64, **kw)
+    torch = pytest.importorskip("torch")
+    for t, msg in [(torch.zeros(20, dtype=torch.float32), "float64 tensor"),
+                   (torch.zeros((5, 4), dtype=torch.float64).t(), "contiguous"),
+                   (torch.zeros(20, dtype=torch.float64), "current CUDA device")]:
+        with pytest.raises(ValueError, match=msg):
+            mgt._buffer("f", "x", t, 20, np.float64)
